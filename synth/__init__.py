@@ -1,0 +1,120 @@
+"""Seeded synthetic inputs for the tests, the benchmark and the smoke run.
+
+This module only *generates inputs*: toroidal ±1 instances in CSR form, inverse
+temperature schedules and starting spin configurations.  It holds none of the
+annealing arithmetic (no energies, no acceptance rule, no random stream used by
+the method), so both the CUDA path and the CPU oracle may import it.
+
+Instance recipe (stands in for the Gset toroidal instances G72/G77/G81, which
+are 4-regular periodic square grids with i.i.d. weights w_ij in {-1,+1}; paper
+Section I and Appendix A):
+
+* the torus is X columns by Y rows, site i = y*X + x;
+* every site owns its right edge (x+1 mod X) and its down edge (y+1 mod Y), so
+  |E| = 2n, matching the |V|/|E| columns of Table I;
+* each edge weight is +1 or -1 with probability 1/2, drawn with numpy's PCG64
+  generator seeded by ``inst_seed`` (right edges first, then down edges, both
+  in site order);
+* the CSR handed to the library stores J = -w (the paper's Ising coupling,
+  Eq. 2), four entries per row sorted by column.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "torus_weights",
+    "torus_csr",
+    "torus_instance",
+    "linear_betas",
+    "random_spins",
+    "batched_config",
+]
+
+
+def torus_weights(X: int, Y: int, inst_seed: int):
+    """Return (w_right, w_down), each int8 [Y, X] with entries in {-1, +1}."""
+    rng = np.random.Generator(np.random.PCG64(int(inst_seed)))
+    bits = rng.integers(0, 2, size=(2, Y, X), dtype=np.int8)
+    w = (2 * bits - 1).astype(np.int8)
+    return w[0].copy(), w[1].copy()
+
+
+def torus_csr(X: int, Y: int, w_right: np.ndarray, w_down: np.ndarray):
+    """CSR (row_ptr int64[n+1], col int32[nnz], J int8[nnz]) of the torus.
+
+    J holds -w (Eq. 2 with J_ij = -w_ij).  Each row lists its four neighbours
+    sorted by column index.  Works for any X, Y >= 1 (tiny or odd dimensions
+    are produced on purpose by the validation tests).
+    """
+    n = X * Y
+    rows = []
+    for y in range(Y):
+        for x in range(X):
+            i = y * X + x
+            nb = {}
+            def add(j, w):
+                nb.setdefault(j, []).append(int(w))
+            add(y * X + (x + 1) % X, w_right[y, x])
+            add(y * X + (x - 1) % X, w_right[y, (x - 1) % X])
+            add(((y + 1) % Y) * X + x, w_down[y, x])
+            add(((y - 1) % Y) * X + x, w_down[(y - 1) % Y, x])
+            entries = []
+            for j in sorted(nb):
+                for w in nb[j]:
+                    entries.append((j, -w))
+            rows.append(entries)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    for i, e in enumerate(rows):
+        row_ptr[i + 1] = row_ptr[i] + len(e)
+    col = np.array([j for e in rows for (j, _) in e], dtype=np.int32)
+    J = np.array([v for e in rows for (_, v) in e], dtype=np.int8)
+    return row_ptr, col, J
+
+
+def torus_instance(X: int, Y: int, inst_seed: int):
+    """Convenience: dict with X, Y, n, w_right, w_down and the CSR arrays."""
+    wr, wd = torus_weights(X, Y, inst_seed)
+    row_ptr, col, J = torus_csr(X, Y, wr, wd)
+    return {
+        "X": X, "Y": Y, "n": X * Y, "inst_seed": inst_seed,
+        "w_right": wr, "w_down": wd,
+        "row_ptr": row_ptr, "col": col, "J": J,
+    }
+
+
+def linear_betas(beta0: float, beta1: float, S: int) -> np.ndarray:
+    """Inverse temperatures for S sweeps, linear from beta0 to beta1 inclusive.
+
+    beta_k = beta0 + (beta1 - beta0) * k / (S - 1); a single sweep uses beta0.
+    """
+    if S <= 0:
+        return np.zeros(0, dtype=np.float64)
+    if S == 1:
+        return np.array([beta0], dtype=np.float64)
+    k = np.arange(S, dtype=np.float64)
+    return beta0 + (beta1 - beta0) * k / float(S - 1)
+
+
+def random_spins(T: int, n: int, seed: int) -> np.ndarray:
+    """int8 [T, n] configuration with entries in {-1, +1} (PCG64, seeded)."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    return (2 * rng.integers(0, 2, size=(T, n), dtype=np.int8) - 1).astype(np.int8)
+
+
+def batched_config(count: int = 96, base_seed: int = 100):
+    """The uneven batch of tori: shapes {50,100,140,200}x100, 32..512 trials,
+    2,000..20,000 sweeps, instance seeds base_seed + k.
+
+    Returns a list of dicts (X, Y, inst_seed, trials, sweeps, seed).
+    """
+    out = []
+    widths = [50, 100, 140, 200]
+    for k in range(count):
+        out.append({
+            "X": widths[k % 4], "Y": 100, "inst_seed": base_seed + k,
+            "trials": 32 * (1 << (k % 5)),
+            "sweeps": 2000 + (k * 1889) % 18001,
+            "seed": 5000 + k,
+        })
+    return out

@@ -1,0 +1,66 @@
+"""Independent pure-Python restatements used to pin the C oracle on tiny cases.
+
+* ``philox`` follows the Philox4x32-10 round function of Salmon et al. (SC'11)
+  with Python integers; it is pinned by the published known-answer vectors.
+* ``anneal_full_energy`` is the Metropolis sweep written from its definition,
+  with the energy change of a flip taken as H(s') - H(s) by evaluating Eq. 2
+  on the whole edge list before and after (no local fields, no CSR), and the
+  acceptance probability exp(-beta dE) compared against u / 2^32 through the
+  threshold T = floor(exp(-beta dE) 2^32).
+"""
+import math
+
+import numpy as np
+
+MASK = 0xFFFFFFFF
+
+
+def philox(ctr, key, rounds=10):
+    c = [int(v) & MASK for v in ctr]
+    k0, k1 = int(key[0]) & MASK, int(key[1]) & MASK
+    for _ in range(rounds):
+        p0 = 0xD2511F53 * c[0]
+        p1 = 0xCD9E8D57 * c[2]
+        c = [((p1 >> 32) ^ c[1] ^ k0) & MASK, p1 & MASK, ((p0 >> 32) ^ c[3] ^ k1) & MASK, p0 & MASK]
+        k0 = (k0 + 0x9E3779B9) & MASK
+        k1 = (k1 + 0xBB67AE85) & MASK
+    return c
+
+
+def draw(a, b, t, seed):
+    out = philox((a, b, t >> 2, 0), (seed & MASK, (seed >> 32) & MASK))
+    return out[t & 3]
+
+
+def energy(edges, s):
+    i, j, w = edges
+    return int(sum(int(w[e]) * int(s[i[e]]) * int(s[j[e]]) for e in range(len(w))))
+
+
+def anneal_full_energy(X, Y, edges, betas, seed, trials, sweep_offset=0, init=None):
+    n = X * Y
+    out = np.zeros((trials, n), dtype=np.int8)
+    for t in range(trials):
+        if init is not None:
+            s = [1 if v > 0 else -1 for v in init[t]]
+        else:
+            s = [1 if (draw(i, 0xFFFFFFFF, t, seed) >> 31) else -1 for i in range(n)]
+        for jj, beta in enumerate(betas):
+            k = (sweep_offset + jj) & MASK
+            for colour in (0, 1):
+                for i in range(n):
+                    if ((i % X) + (i // X)) % 2 != colour:
+                        continue
+                    e0 = energy(edges, s)
+                    s[i] = -s[i]
+                    dE = energy(edges, s) - e0
+                    s[i] = -s[i]
+                    if dE <= 0:
+                        flip = True
+                    else:
+                        thr = min(math.floor(math.exp(-beta * dE) * 2.0 ** 32), 2 ** 32 - 1)
+                        flip = draw(i, k, t, seed) < thr
+                    if flip:
+                        s[i] = -s[i]
+        out[t] = s
+    return out
