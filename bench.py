@@ -1,0 +1,322 @@
+"""Benchmark: spin-updates/s and time-to-99.9%-cut of the plain GPU annealer.
+
+Workload (one "step"): the 200x100 toroidal +-1 instance (20,000 spins,
+instance seed 2), 1,024 trials x 10,000 Metropolis sweeps, beta linear
+0.1 -> 3.0, Philox seed 1002 + step; spins and exact cuts of every trial are
+produced on the device.  A step is T*S*n = 2.048e11 spin updates.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): every rank runs the full workload with its own seeds
+(independent trials, weak scaling), no collective on the data path.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "spin-updates/s; time-to-99.9%-cut on 200x100 +-1 torus, learned vs plain"
+WORKLOAD = {"X": 200, "Y": 100, "inst_seed": 2, "trials": 1024, "sweeps": 10000, "beta0": 0.1, "beta1": 3.0,
+            "seed": 1002}
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Integer multiply lanes per SM per clock (32-bit IMAD; a 32x32->64 multiply
+# counts as two) on this part: 4 sub-partitions x 16 lanes.
+IMAD_LANES_PER_SM = 64
+# Philox4x32-10 multiplies per spin update: 10 rounds x 2 products x 2 halves / 4 draws
+IMAD_OPS_PER_UPDATE = 10
+
+
+def updates_per_step(w):
+    return w["trials"] * w["sweeps"] * w["X"] * w["Y"]
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        self.path = None
+        self.device_index = device_index
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[4], f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for nm, v in zip(names, r[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def _oracle_slice(args):
+    import oracle  # test infrastructure: the CPU baseline leg only
+    inst, betas, seed, t_begin, t_count = args
+    t = time.perf_counter()
+    oracle.anneal(inst, betas, seed, t_begin=t_begin, t_count=t_count)
+    return time.perf_counter() - t
+
+
+def oracle_throughput(w, inst, sweeps=600, trials_per_proc=1, procs=None):
+    """The CPU oracle, as it stands, on a bounded sample of the workload:
+    `procs` processes (default: every host core), each running
+    `trials_per_proc` trials of the first `sweeps` sweeps of the schedule."""
+    import multiprocessing as mp
+    import oracle
+    oracle.lib()  # build before forking workers
+    procs = procs or os.cpu_count() or 1
+    betas = synth.linear_betas(w["beta0"], w["beta1"], w["sweeps"])[:sweeps]
+    jobs = [(inst, betas, w["seed"], p * trials_per_proc, trials_per_proc) for p in range(procs)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_slice, jobs)
+    wall = time.perf_counter() - t0
+    ups = procs * trials_per_proc * sweeps * w["X"] * w["Y"]
+    return {"value": ups / wall, "unit": "spin-updates/s", "cores": procs, "kind": "oracle",
+            "sample": f"{procs} processes x {trials_per_proc} trial(s) x first {sweeps} sweeps of the "
+                      f"{w['X']}x{w['Y']} workload ({ups:.3g} updates, {wall:.1f} s wall)"}
+
+
+# ------------------------------------------------------------------ helpers
+def ttt_stats(cuts, t_step_s, trials, sweeps, quality=0.999):
+    import oracle  # Eq. 3-5 helpers
+    best = int(cuts.max())
+    target = oracle.target_cut(best, quality)
+    Ps = oracle.success_probability(cuts, target)
+    r = oracle.repetitions(Ps)
+    t_trial = t_step_s / trials
+    return {"best_cut": best, "target": target, "P_s": Ps, "r": r, "STT_sweeps": sweeps * r,
+            "TTT_s_throughput_form": t_trial * r,
+            "TTT_s_latency_form": t_step_s * math.ceil(r / trials) if math.isfinite(r) else None,
+            "cut_mean": float(cuts.mean()), "cut_min": int(cuts.min())}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = dict(WORKLOAD)
+    inst = synth.torus_instance(w["X"], w["Y"], w["inst_seed"])
+    sweeps = 150
+    vals = []
+    for _ in range(args.warmup):
+        oracle_throughput(w, inst, sweeps=sweeps)
+    for _ in range(args.steps):
+        vals.append(oracle_throughput(w, inst, sweeps=sweeps))
+    v = float(np.mean([x["value"] for x in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = v
+    step_ups = vals[-1]["cores"] * sweeps * w["X"] * w["Y"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "spin-updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_ups / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": "200x100 torus, oracle sample (CPU)", **w},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ main arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--sweeps", type=int, default=None, help="override (profiling runs only)")
+    ap.add_argument("--trials", type=int, default=None, help="override (profiling runs only)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import paper_2505_18508_gb300 as ia
+    from paper_2505_18508_gb300 import build as lib_build
+
+    ws, rank, local = dist_env()
+    lib_build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    w = dict(WORKLOAD)
+    if args.sweeps:
+        w["sweeps"] = args.sweeps
+    if args.trials:
+        w["trials"] = args.trials
+    inst = synth.torus_instance(w["X"], w["Y"], w["inst_seed"])
+    betas = synth.linear_betas(w["beta0"], w["beta1"], w["sweeps"])
+    T, S, n = w["trials"], w["sweeps"], inst["n"]
+    ups = updates_per_step(w)
+    prob = ia.Problem.from_instance(inst)
+    dev = torch.device("cuda", local)
+    spins = torch.empty((T, n), dtype=torch.int8, device=dev)
+    cuts = torch.empty((T,), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def seed_of(step):
+        return w["seed"] + 1_000_003 * rank + step
+
+    for i in range(args.warmup):
+        ia.anneal(prob, T, betas, seed_of(-1 - i), out_spins=spins, out_cuts=cuts)
+    torch.cuda.synchronize()
+    shape = prob.last_launch()
+
+    clocks = ClockSampler(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    first_cuts = None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()                       # L2 flush between timed steps (not inside the events)
+        starts[i].record(stream)
+        ia.anneal(prob, T, betas, seed_of(i), out_spins=spins, out_cuts=cuts)
+        ends[i].record(stream)
+        if i == 0:
+            first_cuts = cuts.clone()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = float(np.mean(step_ms))
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * ups / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers: instance upload
+    # (ising_create from the host CSR), host betas, device->host copy of all
+    # spins and cuts into pinned memory, every step
+    h_spins = torch.empty((T, n), dtype=torch.int8, pin_memory=True)
+    h_cuts = torch.empty((T,), dtype=torch.int32, pin_memory=True)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for i in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        p2 = ia.Problem.from_instance(inst)
+        ia.anneal(p2, T, betas, seed_of(100 + i), out_spins=spins, out_cuts=cuts)
+        h_spins.copy_(spins, non_blocking=True)
+        h_cuts.copy_(cuts, non_blocking=True)
+        torch.cuda.synchronize()
+        p2.destroy()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_step_ms = float(np.mean(e2e_ms)) if e2e_ms else float("nan")
+    h2d = 2 * n + 8 * S                      # packed instance flags + threshold table
+    d2h = T * n + 4 * T
+
+    # ---- roofline: integer-multiply pipe (Philox), see the design doc
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tops = sms * IMAD_LANES_PER_SM * clk_mhz * 1e6 / 1e12
+    achieved_tops = ups * IMAD_OPS_PER_UPDATE / (ms / 1e3) / 1e12 / 1.0
+    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (32-bit IMAD)",
+                "frac": achieved_tops / peak_tops, "traffic": None,
+                "kernel": "anneal_strip_kernel", "peak_source": f"{sms} SMs x {IMAD_LANES_PER_SM} IMAD lanes x "
+                f"{clk_mhz:.0f} MHz (sm_max_mhz of measured peaks file)"}
+
+    stats = ttt_stats(first_cuts.cpu().numpy(), ms / 1e3, T, S) if args.steps > 0 else None
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = oracle_throughput(w, inst)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "plain annealer, 200x100 +-1 torus (20,000 spins), 1,024 trials x "
+                                   "10,000 sweeps, beta 0.1->3.0", **w, "updates_per_step": ups,
+                       "l2": "flushed between steps (256 MB write)", "launch": shape},
+            "e2e": {"value": ws * ups / (e2e_step_ms / 1e3), "unit": "spin-updates/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step_ms},
+            "gpu_launches": args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "ttt_99_9": stats,
+            "wall_s_timed": wall,
+            "step_ms": step_ms,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    prob.destroy()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * ising.h -- C ABI of the GB300 toroidal Ising / Max-Cut annealer.
+ *
+ * Problem (Zick 2025, Section II, Eq. 1 and Eq. 2): n = X*Y spins s_i in
+ * {-1,+1} on an X-by-Y periodic square grid (Section I, Appendix A), site
+ * i = y*X + x, each site coupled to its four nearest neighbours with weights
+ * w_ij in {-1,+1}.  The Ising form uses J_ij = -w_ij and h_i = 0, so
+ *     H(s)   = -sum_{i<j} J_ij s_i s_j = sum_{i<j} w_ij s_i s_j,
+ *     cut(s) = 1/2 sum_{i<j} w_ij (1 - s_i s_j) = (W - H(s)) / 2,
+ * with W = sum_{i<j} w_ij.
+ *
+ * Method: independent trials of sweeps (Section III: the sweep is the
+ * fundamental step; solutions are read out at the end of each trial).  The
+ * paper leaves its own update rule unpublished, so a sweep here is a
+ * Metropolis sweep over the checkerboard: colour (x+y) mod 2 = 0 first, then
+ * colour 1; a spin flips when its energy change dE = -2 s_i sum_j w_ij s_j is
+ * <= 0, or when the 32-bit draw u is below the threshold
+ * T_dE = min(floor(exp(-beta_k dE) 2^32), 2^32 - 1) of the sweep's inverse
+ * temperature beta_k.  The draw for trial t, sweep k, site i is word
+ * (t mod 4) of Philox4x32-10 (Salmon et al., SC'11) at counter
+ * (i, k, t/4, 0) with key (seed mod 2^32, seed / 2^32); the random starting
+ * spin is +1 when bit 31 of the word at counter (i, 0xFFFFFFFF, t/4, 0) is
+ * set.  Results are a pure function of (instance, trial index, sweep index,
+ * betas, seed): they do not depend on the launch configuration.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (ISING_OK) on success, a negative ISING_ERR_* code otherwise.
+ *     No C++ exception crosses this boundary.  ising_strerror names a code.
+ *   - "host" pointers are read during the call and may be freed on return;
+ *     "device" pointers are CUDA device (or managed) memory owned by the
+ *     caller, which must stay valid until the work queued on the stream is
+ *     done.
+ *   - Work is queued asynchronously on `cuda_stream` (a cudaStream_t; NULL is
+ *     the legacy default stream).  Errors found by argument checks return
+ *     before anything is queued.
+ *   - Spins are int8: any value > 0 reads as +1, anything else as -1; spins
+ *     written by the library are exactly +1 or -1.  Spin arrays are
+ *     row-major [trials][n].  Cuts are int32 (|cut| <= |E| = 2n).
+ *   - A problem handle is bound to the device that was current at creation;
+ *     do not use one handle from two streams at the same time.
+ */
+#ifndef ISING_H
+#define ISING_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ISING_OK                 0
+#define ISING_ERR_ARG           -1  /* bad pointer, size, beta <= 0 or NaN, J not +-1 */
+#define ISING_ERR_NOT_TORUS     -2  /* CSR is not the symmetric 4-neighbour X-by-Y torus */
+#define ISING_ERR_ODD_DIM       -3  /* X or Y odd: the checkerboard is not bipartite */
+#define ISING_ERR_H_UNSUPPORTED -4  /* a non-zero local field h_i was given */
+#define ISING_ERR_OOM           -5  /* host or device allocation failed */
+#define ISING_ERR_CUDA          -6  /* a CUDA runtime call or kernel launch failed */
+#define ISING_ERR_TIMEOUT       -7  /* a bounded device-side wait ran out */
+#define ISING_ERR_UNSUPPORTED   -8  /* valid input beyond what this build handles */
+
+typedef struct ising_problem ising_problem;
+
+/*
+ * ising_create -- validate a toroidal instance and pack it on the device.
+ * (Eq. 2 with J = -w, h = 0; the Gset toroidal grids of Section I.)
+ *
+ * n        number of spins, must equal X*Y.
+ * row_ptr  host, n+1 int64 CSR row offsets (row_ptr[0] = 0, nondecreasing).
+ * col_idx  host, row_ptr[n] int32 column indices.
+ * J        host, row_ptr[n] int8 couplings, each -1 or +1 (J = -w).
+ * h        host, n int8 local fields, or NULL; every entry must be 0.
+ * X, Y     torus width and height, both even and >= 4.
+ * out      receives the new handle (unchanged on error).
+ *
+ * Row i must list exactly the four torus neighbours of i (any order) and J
+ * must be symmetric.  Errors: ISING_ERR_ARG (NULL pointer, n != X*Y, |J| != 1,
+ * X or Y < 4), ISING_ERR_ODD_DIM, ISING_ERR_NOT_TORUS, ISING_ERR_H_UNSUPPORTED,
+ * ISING_ERR_OOM, ISING_ERR_CUDA.  All argument checks run before any CUDA call.
+ */
+int ising_create(int32_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                 const int8_t* J, const int8_t* h, int32_t X, int32_t Y,
+                 ising_problem** out);
+
+/* ising_destroy -- free a handle and its device memory (NULL is a no-op).
+ * Synchronises with nothing: the caller must not destroy a handle while work
+ * that uses it is still queued. */
+void ising_destroy(ising_problem* p);
+
+/*
+ * ising_anneal -- run `trials` independent trials of S Metropolis sweeps
+ * (Section III: trials, sweeps, read-out at the end of each trial).
+ *
+ * trials        number of trials T >= 0 (T = 0 queues nothing).
+ * betas         host, S doubles, inverse temperature of each sweep, each > 0
+ *               (+inf allowed: zero temperature).
+ * S             number of sweeps >= 0; sweep j of the call is global sweep
+ *               sweep_offset + j, which selects its random draws.
+ * seed          64-bit Philox key.
+ * sweep_offset  first global sweep index (resume: a run of S1 + S2 sweeps
+ *               equals S1 sweeps, then S2 more from the saved spins with
+ *               sweep_offset = S1 and betas[S1..]).
+ * init_spins    device [T][n] starting spins, or NULL for the Philox start.
+ * out_spins     device [T][n] final spins, or NULL.
+ * out_cuts      device [T] final Eq. 1 cuts, or NULL.
+ * cuda_stream   stream to queue on.
+ *
+ * Scratch: the per-sweep threshold table (8*S bytes) is allocated and freed
+ * in stream order with cudaMallocAsync / cudaFreeAsync.
+ * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (no launch shape fits),
+ * ISING_ERR_OOM, ISING_ERR_CUDA.
+ */
+int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t S,
+                 uint64_t seed, uint32_t sweep_offset, const int8_t* init_spins,
+                 int8_t* out_spins, int32_t* out_cuts, void* cuda_stream);
+
+/*
+ * ising_cut -- exact Eq. 1 cut of k configurations on the device.
+ *
+ * spins     device [k][n] int8.
+ * k         number of configurations >= 0.
+ * out_cuts  device [k] int32.
+ * Errors: ISING_ERR_ARG, ISING_ERR_CUDA.
+ */
+int ising_cut(const ising_problem* p, const int8_t* spins, int32_t k,
+              int32_t* out_cuts, void* cuda_stream);
+
+/*
+ * ising_anneal_batched -- anneal m instances of uneven sizes, trial counts and
+ * sweep counts in one persistent launch (Section III campaigns, run as one
+ * batch).  Instance q behaves exactly like
+ *   ising_anneal(probs[q], trials[q], betas[q], sweeps[q], seeds[q], 0, NULL,
+ *                out_spins[q], out_cuts[q], stream).
+ *
+ * probs      host array of m handles (all on the current device).
+ * trials     host, m trial counts >= 0.     sweeps  host, m sweep counts >= 0.
+ * betas      host array of m host pointers, betas[q] has sweeps[q] doubles.
+ * seeds      host, m seeds.
+ * out_spins  host array of m device pointers ([trials[q]][n_q] int8) or NULL
+ *            (the array itself or any entry).
+ * out_cuts   host array of m device pointers ([trials[q]] int32) or NULL.
+ * Scratch: descriptors, work list and thresholds in one stream-ordered
+ * allocation, freed in stream order.
+ */
+int ising_anneal_batched(ising_problem* const* probs, int32_t m, const int32_t* trials,
+                         const int32_t* sweeps, const double* const* betas,
+                         const uint64_t* seeds, int8_t* const* out_spins,
+                         int32_t* const* out_cuts, void* cuda_stream);
+
+/*
+ * Batch plans: the same work as ising_anneal_batched, prepared once (tables
+ * uploaded, work list sorted longest first) and replayed as a CUDA graph.
+ * ising_batch_create queues the uploads on `cuda_stream`; every
+ * ising_batch_launch replays the graph (reset the work counter, persistent
+ * kernel) on the given stream.  The output pointers are baked into the plan.
+ * group_trials (4..32, multiple of 4, or 0 = auto) and ctas_per_sm (1..4, or
+ * 0 = auto) set the work-unit width and the persistent grid.
+ */
+typedef struct ising_batch ising_batch;
+int ising_batch_create(ising_problem* const* probs, int32_t m, const int32_t* trials,
+                       const int32_t* sweeps, const double* const* betas,
+                       const uint64_t* seeds, int8_t* const* out_spins,
+                       int32_t* const* out_cuts, int32_t group_trials,
+                       int32_t ctas_per_sm, void* cuda_stream, ising_batch** out);
+int ising_batch_launch(ising_batch* b, void* cuda_stream);
+/* Frees the plan; waits for the plan's last launch to finish first. */
+void ising_batch_destroy(ising_batch* b);
+
+/*
+ * ising_set_launch -- fix the launch shape used by ising_anneal for this
+ * handle (the autotuner's knob).  0 in any field restores the automatic
+ * choice.
+ * group_trials   trials packed per 32-bit word, multiple of 4 in [4, 32].
+ * strips         CTAs that share one trial group as row strips (thread-block
+ *                cluster of that size, 1..16), at most Y.
+ * threads        threads per CTA, multiple of 32 in [64, 1024].
+ * Errors: ISING_ERR_ARG.  Results do not depend on the shape.
+ */
+int ising_set_launch(ising_problem* p, int32_t group_trials, int32_t strips, int32_t threads);
+
+/* ising_last_launch -- the shape the last ising_anneal call on this handle
+ * used (any pointer may be NULL). */
+int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* strips,
+                      int32_t* threads, int32_t* grid_ctas);
+
+/* ising_problem_info -- X, Y and W = sum of the weights over the 2n edges
+ * (so that H = W - 2 cut); any pointer may be NULL. */
+int ising_problem_info(const ising_problem* p, int32_t* X, int32_t* Y, int32_t* weight_sum);
+
+/* ising_strerror -- static description of a status code. */
+const char* ising_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISING_H */

@@ -1,0 +1,207 @@
+"""GB300 toroidal Ising / Max-Cut annealer: Python binding of include/ising.h.
+
+Every step of the annealing path runs in the CUDA kernels of libising.so;
+this module only marshals arguments.  PyTorch provides device memory and the
+current CUDA stream.
+
+    import paper_2505_18508_gb300 as ia
+    prob = ia.Problem.from_csr(n, row_ptr, col, J, X, Y)
+    spins, cuts = ia.anneal(prob, trials=1024, betas=betas, seed=1002)
+
+The method (Zick 2025, Sections II-III): independent trials of sweeps on the
+Ising form of a toroidal Max-Cut instance (J = -w, h = 0), read out at the
+end of each trial, with the exact cut of Eq. 1.  Each sweep is a Metropolis
+sweep over the two checkerboard colours with Philox4x32-10 draws.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import IsingError, check, lib
+
+__all__ = ["Problem", "anneal", "cut", "anneal_batched", "BatchPlan", "IsingError", "lib"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Problem:
+    """A validated toroidal instance packed on the current CUDA device."""
+
+    def __init__(self, handle, X, Y):
+        self._h = handle
+        self.X, self.Y, self.n = X, Y, X * Y
+
+    @classmethod
+    def from_csr(cls, n, row_ptr, col, J, X, Y, h=None):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        J = np.ascontiguousarray(J, dtype=np.int8)
+        hp = None
+        if h is not None:
+            h = np.ascontiguousarray(h, dtype=np.int8)
+            hp = h.ctypes.data_as(ctypes.c_void_p)
+        out = ctypes.c_void_p()
+        rc = lib().ising_create(int(n), row_ptr.ctypes.data_as(ctypes.c_void_p),
+                                col.ctypes.data_as(ctypes.c_void_p), J.ctypes.data_as(ctypes.c_void_p),
+                                hp, int(X), int(Y), ctypes.byref(out))
+        check(rc, "ising_create")
+        return cls(out, int(X), int(Y))
+
+    @classmethod
+    def from_instance(cls, inst):
+        """From a dict with n, row_ptr, col, J, X, Y (e.g. synth.torus_instance)."""
+        return cls.from_csr(inst["n"], inst["row_ptr"], inst["col"], inst["J"], inst["X"], inst["Y"])
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("problem already destroyed")
+        return self._h
+
+    def info(self):
+        X, Y, W = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib().ising_problem_info(self.handle, ctypes.byref(X), ctypes.byref(Y), ctypes.byref(W)),
+              "ising_problem_info")
+        return {"X": X.value, "Y": Y.value, "weight_sum": W.value}
+
+    def set_launch(self, group_trials=0, strips=0, threads=0):
+        check(lib().ising_set_launch(self.handle, int(group_trials), int(strips), int(threads)),
+              "ising_set_launch")
+
+    def last_launch(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        check(lib().ising_last_launch(self.handle, *[ctypes.byref(x) for x in v]), "ising_last_launch")
+        return {"group_trials": v[0].value, "strips": v[1].value, "threads": v[2].value,
+                "grid_ctas": v[3].value}
+
+    def destroy(self):
+        if self._h is not None:
+            lib().ising_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+
+def anneal(prob, trials, betas, seed, sweep_offset=0, init=None, out_spins=None, out_cuts=None,
+           want_spins=True, stream=None):
+    """Queue ``trials`` trials of len(betas) sweeps; returns (spins, cuts) CUDA tensors.
+
+    init: optional int8 CUDA tensor [trials, n] of starting spins.
+    out_spins / out_cuts: optional preallocated CUDA tensors to write into.
+    """
+    torch = _torch()
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if want_spins and out_spins is None:
+        out_spins = torch.empty((trials, prob.n), dtype=torch.int8, device=dev)
+    if out_cuts is None:
+        out_cuts = torch.empty((trials,), dtype=torch.int32, device=dev)
+    if init is not None:
+        assert init.is_cuda and init.dtype == torch.int8 and init.shape == (trials, prob.n)
+        init = init.contiguous()
+    rc = lib().ising_anneal(prob.handle, int(trials), betas.ctypes.data_as(ctypes.c_void_p),
+                            int(betas.shape[0]), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                            int(sweep_offset) & 0xFFFFFFFF, _dptr(init),
+                            _dptr(out_spins) if want_spins else None, _dptr(out_cuts), _stream_ptr(stream))
+    check(rc, "ising_anneal")
+    return out_spins, out_cuts
+
+
+def cut(prob, spins, out=None, stream=None):
+    """Exact Eq. 1 cut of each row of an int8 CUDA tensor [k, n]."""
+    torch = _torch()
+    spins = spins.contiguous()
+    k = spins.shape[0]
+    if out is None:
+        out = torch.empty((k,), dtype=torch.int32, device=spins.device)
+    check(lib().ising_cut(prob.handle, _dptr(spins), int(k), _dptr(out), _stream_ptr(stream)), "ising_cut")
+    return out
+
+
+def _batch_arrays(probs, trials, sweeps, betas, seeds, out_spins, out_cuts):
+    m = len(probs)
+    P = (ctypes.c_void_p * m)(*[p.handle.value for p in probs])
+    Tn = (ctypes.c_int32 * m)(*[int(t) for t in trials])
+    Sn = (ctypes.c_int32 * m)(*[int(s) for s in sweeps])
+    barrs = [np.ascontiguousarray(b, dtype=np.float64) for b in betas]
+    B = (ctypes.c_void_p * m)(*[b.ctypes.data for b in barrs])
+    Sd = (ctypes.c_uint64 * m)(*[int(s) & 0xFFFFFFFFFFFFFFFF for s in seeds])
+    Os = (ctypes.c_void_p * m)(*[(o.data_ptr() if o is not None else None) for o in out_spins])
+    Oc = (ctypes.c_void_p * m)(*[(o.data_ptr() if o is not None else None) for o in out_cuts])
+    return m, P, Tn, Sn, B, Sd, Os, Oc, barrs
+
+
+def _alloc_outputs(probs, trials, want_spins):
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spins = [torch.empty((t, p.n), dtype=torch.int8, device=dev) if want_spins else None
+             for p, t in zip(probs, trials)]
+    cuts = [torch.empty((t,), dtype=torch.int32, device=dev) for t in trials]
+    return spins, cuts
+
+
+def anneal_batched(probs, trials, sweeps, betas, seeds, want_spins=True, stream=None):
+    """One persistent launch over uneven instances; returns (spins list, cuts list)."""
+    spins, cuts = _alloc_outputs(probs, trials, want_spins)
+    m, P, Tn, Sn, B, Sd, Os, Oc, keep = _batch_arrays(probs, trials, sweeps, betas, seeds, spins, cuts)
+    rc = lib().ising_anneal_batched(P, m, Tn, Sn, B, Sd, Os, Oc, _stream_ptr(stream))
+    check(rc, "ising_anneal_batched")
+    return spins, cuts
+
+
+class BatchPlan:
+    """A prepared batch replayed as a CUDA graph (ising_batch_create / _launch)."""
+
+    def __init__(self, probs, trials, sweeps, betas, seeds, want_spins=True, group_trials=0,
+                 ctas_per_sm=0, stream=None):
+        self.probs = list(probs)
+        self.spins, self.cuts = _alloc_outputs(self.probs, trials, want_spins)
+        m, P, Tn, Sn, B, Sd, Os, Oc, keep = _batch_arrays(self.probs, trials, sweeps, betas, seeds,
+                                                          self.spins, self.cuts)
+        out = ctypes.c_void_p()
+        rc = lib().ising_batch_create(P, m, Tn, Sn, B, Sd, Os, Oc, int(group_trials), int(ctas_per_sm),
+                                      _stream_ptr(stream), ctypes.byref(out))
+        check(rc, "ising_batch_create")
+        self._h = out
+
+    def launch(self, stream=None):
+        check(lib().ising_batch_launch(self._h, _stream_ptr(stream)), "ising_batch_launch")
+        return self.spins, self.cuts
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None:
+            lib().ising_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -1,0 +1,87 @@
+"""ctypes binding of include/ising.h: the same names, argument marshalling only.
+
+Loading fails loudly when libising.so has not been built; there is no other
+implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libising.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ising.h")
+
+ISING_OK = 0
+ISING_ERR_ARG = -1
+ISING_ERR_NOT_TORUS = -2
+ISING_ERR_ODD_DIM = -3
+ISING_ERR_H_UNSUPPORTED = -4
+ISING_ERR_OOM = -5
+ISING_ERR_CUDA = -6
+ISING_ERR_TIMEOUT = -7
+ISING_ERR_UNSUPPORTED = -8
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+_SIGNATURES = {
+    "ising_create": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.POINTER(_vp)]),
+    "ising_destroy": (None, [_vp]),
+    "ising_anneal": (ctypes.c_int, [_vp, _i32, _vp, _i32, _u64, _u32, _vp, _vp, _vp, _vp]),
+    "ising_cut": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
+    "ising_anneal_batched": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "ising_batch_create": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp,
+                                          ctypes.POINTER(_vp)]),
+    "ising_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "ising_batch_destroy": (None, [_vp]),
+    "ising_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
+    "ising_last_launch": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p]),
+    "ising_problem_info": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
+    "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+class IsingError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = "unknown"
+        try:
+            msg = lib().ising_strerror(code).decode()
+        except Exception:  # pragma: no cover
+            pass
+        super().__init__(f"{where} failed: {msg} (code {code})")
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code, where):
+    if code != ISING_OK:
+        raise IsingError(code, where)
+
+
+def declared_symbols():
+    """Names of the functions include/ising.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ising_[a-z_]+)\s*\(", text)))

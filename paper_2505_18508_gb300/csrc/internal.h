@@ -1,0 +1,75 @@
+// internal.h -- host-side structures shared by the ABI and the kernel launchers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+struct ising_problem {
+  int32_t X = 0, Y = 0, n = 0, H = 0;   // H = X / 2 sites per colour per row
+  int32_t neg_edges = 0;                // edges with w = -1
+  int32_t weight_sum = 0;               // W = sum of w over the 2n edges
+  int device = 0;
+  // Plane-order site flags, index (c*Y + y)*H + h for the site of colour c in
+  // row y at x = 2h + ((y + c) & 1): bit0 left edge w=-1, bit1 right, bit2 up,
+  // bit3 down.
+  uint8_t* d_flags = nullptr;
+  // Natural-order edge flags, index y*X + x: bit0 right edge w=-1, bit1 down.
+  uint8_t* d_eflags = nullptr;
+  // launch overrides (0 = automatic) and the last shape used
+  int32_t cfg_group = 0, cfg_strips = 0, cfg_threads = 0;
+  int32_t last_group = 0, last_strips = 0, last_threads = 0, last_grid = 0;
+};
+
+namespace ising {
+
+// Everything the strip kernel reads; passed by value as the kernel parameter.
+struct AnnealArgs {
+  const uint8_t* flags;     // plane-order site flags [n]
+  const uint32_t* thr;      // [2*S]: (T4_k, T8_k) for call sweep k
+  const int8_t* init;       // [T][n] or null
+  int8_t* out_spins;        // [T][n] or null
+  int32_t* out_cuts;        // [T] or null
+  int32_t X, Y, H, n;
+  int32_t T;                // trials
+  int32_t G;                // trials per group (multiple of 4, <= 32)
+  int32_t S;                // sweeps in this call
+  uint32_t k0;              // global index of the first sweep
+  uint32_t key0, key1;      // Philox key
+  int32_t C;                // strips (CTAs) per group = cluster size
+  int32_t Rmax;             // ceil(Y / C)
+  int32_t neg_edges;
+};
+
+size_t anneal_smem_bytes(int32_t H, int32_t Rmax);
+// grid = (C, ceil(T/G)); cluster (C,1,1) when C > 1
+cudaError_t launch_anneal(const AnnealArgs& a, int threads, cudaStream_t stream);
+cudaError_t launch_cut(const ising_problem* p, const int8_t* spins, int32_t k, int32_t* out,
+                       cudaStream_t stream);
+
+// ---------------------------------------------------------------- batched
+struct BatchInst {                 // one instance of a batch (device-side descriptor)
+  const uint8_t* flags;
+  const uint32_t* thr;             // [2*S]
+  int8_t* out_spins;               // [T][n] or null
+  int32_t* out_cuts;               // [T] or null
+  int32_t X, Y, H, n;
+  int32_t T, S;
+  uint32_t key0, key1;
+  int32_t neg_edges;
+  int32_t pad_;
+};
+struct BatchUnit {                 // one work item: one trial group of one instance
+  int32_t inst;
+  int32_t group;
+};
+struct BatchArgs {
+  const BatchInst* inst;
+  const BatchUnit* units;
+  int32_t n_units;
+  int32_t G;                       // trials per group
+  uint32_t* counter;               // work-queue head
+  size_t smem_bytes;
+};
+size_t batched_smem_bytes(int32_t max_n);
+cudaError_t launch_batched(const BatchArgs& a, int grid, int threads, cudaStream_t stream);
+
+}  // namespace ising
