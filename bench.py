@@ -108,7 +108,7 @@ def _oracle_slice(args):
     return time.perf_counter() - t
 
 
-def oracle_throughput(w, inst, sweeps=600, trials_per_proc=1, procs=None):
+def oracle_throughput(w, inst, sweeps=3000, trials_per_proc=1, procs=None):
     """The CPU oracle, as it stands, on a bounded sample of the workload:
     `procs` processes (default: every host core), each running
     `trials_per_proc` trials of the first `sweeps` sweeps of the schedule."""
@@ -156,7 +156,7 @@ def reference_arm(args):
         return 0
     w = dict(WORKLOAD)
     inst = synth.torus_instance(w["X"], w["Y"], w["inst_seed"])
-    sweeps = 150
+    sweeps = 1000
     vals = []
     for _ in range(args.warmup):
         oracle_throughput(w, inst, sweeps=sweeps)
@@ -187,6 +187,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--sweeps", type=int, default=None, help="override (profiling runs only)")
     ap.add_argument("--trials", type=int, default=None, help="override (profiling runs only)")
+    ap.add_argument("--launch", default=None, help="G,C,threads launch shape (default: automatic)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -213,6 +214,8 @@ def main():
     T, S, n = w["trials"], w["sweeps"], inst["n"]
     ups = updates_per_step(w)
     prob = ia.Problem.from_instance(inst)
+    if args.launch:
+        prob.set_launch(*[int(v) for v in args.launch.split(",")])
     dev = torch.device("cuda", local)
     spins = torch.empty((T, n), dtype=torch.int8, device=dev)
     cuts = torch.empty((T,), dtype=torch.int32, device=dev)

@@ -7,6 +7,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "../../include/ising.h"
@@ -54,12 +56,14 @@ struct Shape {
   int G, C, threads, Rmax;
 };
 
-// threads per CTA: the multiple of 32 in [lo, hi] that leaves the fewest idle
-// item slots over the half-sweep (ties -> more threads)
-int pick_threads(int items, int lo, int hi) {
-  int best = hi;
+// threads per CTA: many warps hide the Philox dependency chains, so take
+// the multiple of 32 in [768, 1024] that leaves the fewest idle item slots
+// over a half-sweep (ties -> more threads); fewer when a strip has fewer items.
+int pick_threads(int items) {
+  if (items <= 768) return std::max(64, ((items + 31) / 32) * 32);
+  int best = 1024;
   double best_eff = -1.0;
-  for (int t = lo; t <= hi; t += 32) {
+  for (int t = 768; t <= 1024; t += 32) {
     const int iters = (items + t - 1) / t;
     const double eff = static_cast<double>(items) / (static_cast<double>(iters) * t);
     if (eff > best_eff + 1e-9 || (std::fabs(eff - best_eff) <= 1e-9 && t > best)) {
@@ -79,8 +83,10 @@ int choose_shape(const ising_problem* p, int32_t T, Shape* out) {
   const int groups = (T + G - 1) / G;
   int C = p->cfg_strips;
   if (C == 0) {
+    // widest cluster that still gives every CTA its own SM (one 1024-thread
+    // CTA per SM), with at least two rows per strip
     C = 1;
-    while (C < 8 && groups * C < sms && p->Y / (C * 2) >= 2) C *= 2;
+    while (C < 8 && groups * (C * 2) <= sms && p->Y / (C * 2) >= 2) C *= 2;
     while (C < 16 && ising::anneal_smem_bytes(p->H, (p->Y + C - 1) / C) > static_cast<size_t>(smem_max) &&
            (C * 2) <= p->Y)
       C *= 2;
@@ -90,12 +96,136 @@ int choose_shape(const ising_problem* p, int32_t T, Shape* out) {
   if (ising::anneal_smem_bytes(p->H, Rmax) > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
   if (groups > 65535) return ISING_ERR_UNSUPPORTED;
   int threads = p->cfg_threads;
-  if (threads == 0) threads = pick_threads(Rmax * p->H, 128, C == 1 ? 1024 : 512);
+  if (threads == 0) threads = pick_threads(Rmax * p->H);
   out->G = G;
   out->C = C;
   out->threads = threads;
   out->Rmax = Rmax;
   return ISING_OK;
+}
+
+// ---------------------------------------------------------------- batches
+struct HostBatch {
+  std::vector<ising::BatchInst> inst;
+  std::vector<ising::BatchUnit> units;
+  std::vector<uint32_t> thr;       // all threshold tables, concatenated
+  std::vector<size_t> thr_off;     // per instance, in uint32 words
+  size_t smem = 0;
+  int grid = 0, threads = 0;
+  // arena layout (bytes)
+  size_t off_inst = 0, off_units = 0, off_counter = 0, off_thr = 0, bytes = 0;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials, const int32_t* sweeps,
+                  const double* const* betas, const uint64_t* seeds, int8_t* const* out_spins,
+                  int32_t* const* out_cuts, int32_t group_trials, int32_t ctas_per_sm, HostBatch& hb) {
+  if (m < 0 || (m > 0 && (!probs || !trials || !sweeps || !betas || !seeds))) return ISING_ERR_ARG;
+  if (group_trials != 0 && (group_trials < 4 || group_trials > 32 || group_trials % 4)) return ISING_ERR_ARG;
+  if (ctas_per_sm < 0 || ctas_per_sm > 4) return ISING_ERR_ARG;
+  int device = 0;
+  for (int32_t q = 0; q < m; ++q) {
+    if (!probs[q] || trials[q] < 0 || sweeps[q] < 0 || (sweeps[q] > 0 && !betas[q])) return ISING_ERR_ARG;
+    if (q == 0) device = probs[q]->device;
+    else if (probs[q]->device != device) return ISING_ERR_ARG;
+  }
+  hb.inst.resize(m);
+  hb.thr_off.resize(m);
+  size_t max_smem = 0;
+  double total = 0.0;
+  for (int32_t q = 0; q < m; ++q) {
+    std::vector<uint32_t> t;
+    const int rc = make_thresholds(betas[q], sweeps[q], t);
+    if (rc != ISING_OK) return rc;
+    hb.thr_off[q] = hb.thr.size();
+    hb.thr.insert(hb.thr.end(), t.begin(), t.end());
+    const ising_problem* p = probs[q];
+    const size_t sb = ising::batched_smem_bytes(p->H, p->Y);
+    if (trials[q] > 0 && sb > max_smem) max_smem = sb;
+    total += static_cast<double>(p->n) * sweeps[q] * trials[q];
+  }
+  const int smem_max = max_smem_of(device);
+  if (max_smem > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
+  const int sms = num_sms_of(device);
+  int per_sm = ctas_per_sm;
+  if (per_sm == 0) {
+    per_sm = max_smem == 0 ? 1 : static_cast<int>((228 * 1024) / (max_smem + 1024));
+    if (per_sm > 2) per_sm = 2;
+    if (per_sm < 1) per_sm = 1;
+  }
+  if (max_smem > 0 && static_cast<size_t>(per_sm) * (max_smem + 1024) > 228 * 1024) return ISING_ERR_UNSUPPORTED;
+  hb.grid = sms * per_sm;
+  hb.threads = 1024 / per_sm;
+  hb.smem = max_smem;
+  // trials per unit: 32 unless one such unit would exceed the average load of
+  // a CTA, then the largest multiple of 4 that fits (at least 4)
+  const double per_cta = total / (hb.grid > 0 ? hb.grid : 1);
+  std::vector<std::pair<double, ising::BatchUnit>> order;
+  for (int32_t q = 0; q < m; ++q) {
+    const ising_problem* p = probs[q];
+    int G = group_trials;
+    if (G == 0) {
+      G = 32;
+      const double unit32 = static_cast<double>(p->n) * sweeps[q] * 32.0;
+      if (unit32 > per_cta && per_cta > 0) {
+        G = 4 * static_cast<int>(per_cta / (4.0 * p->n * (sweeps[q] > 0 ? sweeps[q] : 1)));
+        if (G < 4) G = 4;
+        if (G > 32) G = 32;
+      }
+    }
+    ising::BatchInst& in = hb.inst[q];
+    in.flags = p->d_flags;
+    in.thr = nullptr;  // patched once the arena address is known
+    in.out_spins = out_spins ? out_spins[q] : nullptr;
+    in.out_cuts = out_cuts ? out_cuts[q] : nullptr;
+    in.X = p->X; in.Y = p->Y; in.H = p->H; in.n = p->n;
+    in.T = trials[q]; in.S = sweeps[q];
+    in.key0 = static_cast<uint32_t>(seeds[q] & 0xFFFFFFFFull);
+    in.key1 = static_cast<uint32_t>(seeds[q] >> 32);
+    in.neg_edges = p->neg_edges;
+    in.G = G;
+    const int groups = (trials[q] + G - 1) / G;
+    for (int g = 0; g < groups; ++g) {
+      const int live = std::min(G, trials[q] - g * G);
+      const double cost = static_cast<double>(p->n) * (sweeps[q] + 1) * ((live + 3) / 4);
+      order.push_back({cost, ising::BatchUnit{q, g}});
+    }
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<double, ising::BatchUnit>& x, const std::pair<double, ising::BatchUnit>& y) {
+                     return x.first > y.first;
+                   });
+  hb.units.resize(order.size());
+  for (size_t u = 0; u < order.size(); ++u) hb.units[u] = order[u].second;
+  hb.off_inst = 0;
+  hb.off_units = align256(sizeof(ising::BatchInst) * hb.inst.size());
+  hb.off_counter = hb.off_units + align256(sizeof(ising::BatchUnit) * hb.units.size());
+  hb.off_thr = hb.off_counter + 256;
+  hb.bytes = hb.off_thr + align256(sizeof(uint32_t) * hb.thr.size());
+  return ISING_OK;
+}
+
+// host image of the arena once its device address is known
+std::vector<unsigned char> arena_image(HostBatch& hb, unsigned char* d_arena) {
+  std::vector<unsigned char> img(hb.bytes, 0);
+  for (size_t q = 0; q < hb.inst.size(); ++q)
+    hb.inst[q].thr = reinterpret_cast<const uint32_t*>(d_arena + hb.off_thr) + hb.thr_off[q];
+  if (!hb.inst.empty())
+    std::memcpy(img.data() + hb.off_inst, hb.inst.data(), sizeof(ising::BatchInst) * hb.inst.size());
+  if (!hb.units.empty())
+    std::memcpy(img.data() + hb.off_units, hb.units.data(), sizeof(ising::BatchUnit) * hb.units.size());
+  if (!hb.thr.empty()) std::memcpy(img.data() + hb.off_thr, hb.thr.data(), sizeof(uint32_t) * hb.thr.size());
+  return img;
+}
+
+ising::BatchArgs batch_args(const HostBatch& hb, unsigned char* d_arena) {
+  ising::BatchArgs a;
+  a.inst = reinterpret_cast<const ising::BatchInst*>(d_arena + hb.off_inst);
+  a.units = reinterpret_cast<const ising::BatchUnit*>(d_arena + hb.off_units);
+  a.n_units = static_cast<int32_t>(hb.units.size());
+  a.counter = reinterpret_cast<uint32_t*>(d_arena + hb.off_counter);
+  return a;
 }
 
 }  // namespace
@@ -271,6 +401,10 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
   a.k0 = sweep_offset;
   a.key0 = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
   a.key1 = static_cast<uint32_t>(seed >> 32);
+  for (uint32_t r = 0; r < 10; ++r) {   // Philox round keys (Weyl sequence)
+    a.rk[2 * r] = a.key0 + r * 0x9E3779B9u;
+    a.rk[2 * r + 1] = a.key1 + r * 0xBB67AE85u;
+  }
   a.C = sh.C;
   a.Rmax = sh.Rmax;
   a.neg_edges = p->neg_edges;
@@ -292,15 +426,110 @@ int ising_cut(const ising_problem* p, const int8_t* spins, int32_t k, int32_t* o
   return map_cuda(ising::launch_cut(p, spins, k, out_cuts, static_cast<cudaStream_t>(cuda_stream)));
 }
 
-int ising_anneal_batched(ising_problem* const*, int32_t, const int32_t*, const int32_t*, const double* const*,
-                         const uint64_t*, int8_t* const*, int32_t* const*, void*) {
-  return ISING_ERR_UNSUPPORTED;
+int ising_anneal_batched(ising_problem* const* probs, int32_t m, const int32_t* trials, const int32_t* sweeps,
+                         const double* const* betas, const uint64_t* seeds, int8_t* const* out_spins,
+                         int32_t* const* out_cuts, void* cuda_stream) {
+  HostBatch hb;
+  try {
+    const int rc = prepare_batch(probs, m, trials, sweeps, betas, seeds, out_spins, out_cuts, 0, 0, hb);
+    if (rc != ISING_OK) return rc;
+  } catch (const std::bad_alloc&) {
+    return ISING_ERR_OOM;
+  }
+  if (hb.units.empty()) return ISING_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  unsigned char* d_arena = nullptr;
+  cudaError_t e = ising::batched_prepare(hb.smem);
+  if (e != cudaSuccess) return map_cuda(e);
+  e = cudaMallocAsync(reinterpret_cast<void**>(&d_arena), hb.bytes, st);
+  if (e != cudaSuccess) return map_cuda(e);
+  std::vector<unsigned char> img;
+  try {
+    img = arena_image(hb, d_arena);
+  } catch (const std::bad_alloc&) {
+    cudaFreeAsync(d_arena, st);
+    return ISING_ERR_OOM;
+  }
+  e = cudaMemcpyAsync(d_arena, img.data(), hb.bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = ising::launch_batched(batch_args(hb, d_arena), hb.grid, hb.threads, hb.smem, st);
+  const cudaError_t e2 = cudaFreeAsync(d_arena, st);
+  if (e == cudaSuccess) e = e2;
+  return map_cuda(e);
 }
-int ising_batch_create(ising_problem* const*, int32_t, const int32_t*, const int32_t*, const double* const*,
-                       const uint64_t*, int8_t* const*, int32_t* const*, int32_t, int32_t, void*, ising_batch**) {
-  return ISING_ERR_UNSUPPORTED;
+
+struct ising_batch {
+  unsigned char* d_arena = nullptr;
+  cudaStream_t capture = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+void ising_batch_destroy(ising_batch* b) {
+  if (!b) return;
+  if (b->done) cudaEventSynchronize(b->done);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  if (b->d_arena) cudaFree(b->d_arena);
+  delete b;
 }
-int ising_batch_launch(ising_batch*, void*) { return ISING_ERR_UNSUPPORTED; }
-void ising_batch_destroy(ising_batch*) {}
+
+int ising_batch_create(ising_problem* const* probs, int32_t m, const int32_t* trials, const int32_t* sweeps,
+                       const double* const* betas, const uint64_t* seeds, int8_t* const* out_spins,
+                       int32_t* const* out_cuts, int32_t group_trials, int32_t ctas_per_sm, void* cuda_stream,
+                       ising_batch** out) {
+  if (!out) return ISING_ERR_ARG;
+  HostBatch hb;
+  try {
+    const int rc = prepare_batch(probs, m, trials, sweeps, betas, seeds, out_spins, out_cuts, group_trials,
+                                 ctas_per_sm, hb);
+    if (rc != ISING_OK) return rc;
+  } catch (const std::bad_alloc&) {
+    return ISING_ERR_OOM;
+  }
+  ising_batch* b = new (std::nothrow) ising_batch();
+  if (!b) return ISING_ERR_OOM;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_arena), hb.bytes);
+  std::vector<unsigned char> img;
+  if (e == cudaSuccess) {
+    try {
+      img = arena_image(hb, b->d_arena);
+    } catch (const std::bad_alloc&) {
+      ising_batch_destroy(b);
+      return ISING_ERR_OOM;
+    }
+    e = cudaMemcpyAsync(b->d_arena, img.data(), hb.bytes, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = ising::batched_prepare(hb.smem);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const ising::BatchArgs a = batch_args(hb, b->d_arena);
+    cudaError_t ec = cudaMemsetAsync(a.counter, 0, sizeof(uint32_t), b->capture);
+    if (ec == cudaSuccess) ec = ising::launch_batched(a, hb.grid, hb.threads, hb.smem, b->capture);
+    e = cudaStreamEndCapture(b->capture, &b->graph);
+    if (e == cudaSuccess) e = ec;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    ising_batch_destroy(b);
+    return map_cuda(e);
+  }
+  *out = b;
+  return ISING_OK;
+}
+
+int ising_batch_launch(ising_batch* b, void* cuda_stream) {
+  if (!b || !b->exec) return ISING_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGraphLaunch(b->exec, st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->done, st);
+  return map_cuda(e);
+}
 
 }  // extern "C"

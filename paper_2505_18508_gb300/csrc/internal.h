@@ -34,6 +34,7 @@ struct AnnealArgs {
   int32_t S;                // sweeps in this call
   uint32_t k0;              // global index of the first sweep
   uint32_t key0, key1;      // Philox key
+  uint32_t rk[20];          // round keys: rk[2r] = key0 + r*W0, rk[2r+1] = key1 + r*W1
   int32_t C;                // strips (CTAs) per group = cluster size
   int32_t Rmax;             // ceil(Y / C)
   int32_t neg_edges;
@@ -55,7 +56,7 @@ struct BatchInst {                 // one instance of a batch (device-side descr
   int32_t T, S;
   uint32_t key0, key1;
   int32_t neg_edges;
-  int32_t pad_;
+  int32_t G;                       // trials per work unit for this instance
 };
 struct BatchUnit {                 // one work item: one trial group of one instance
   int32_t inst;
@@ -65,11 +66,10 @@ struct BatchArgs {
   const BatchInst* inst;
   const BatchUnit* units;
   int32_t n_units;
-  int32_t G;                       // trials per group
-  uint32_t* counter;               // work-queue head
-  size_t smem_bytes;
+  uint32_t* counter;               // work-queue head, zero before the launch
 };
-size_t batched_smem_bytes(int32_t max_n);
-cudaError_t launch_batched(const BatchArgs& a, int grid, int threads, cudaStream_t stream);
+size_t batched_smem_bytes(int32_t H, int32_t Y);
+cudaError_t batched_prepare(size_t smem);
+cudaError_t launch_batched(const BatchArgs& a, int grid, int threads, size_t smem, cudaStream_t stream);
 
 }  // namespace ising
