@@ -186,6 +186,29 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
  * (so that H = W - 2 cut); any pointer may be NULL. */
 int ising_problem_info(const ising_problem* p, int32_t* X, int32_t* Y, int32_t* weight_sum);
 
+/*
+ * ising_anneal_noalloc -- ising_anneal for callers that cannot allocate
+ * device memory while they run (for example an application whose framework
+ * has already reserved the device memory it may use, or a loop that must not
+ * enter the CUDA allocator once started).  The paper has no counterpart; this
+ * is an interface variant of ising_anneal, with the same arguments, results
+ * and errors.
+ *
+ * The call allocates nothing: the per-sweep threshold table goes into one
+ * fixed array inside the library's device image, at most 32,768 sweeps
+ * (256 KiB, held by every GPU that loads the library until the process
+ * exits).  S above that limit returns ISING_ERR_UNSUPPORTED before anything
+ * is queued.  The first call on a device looks up that array's device address
+ * (with the problem's device current, which must also be the current device
+ * at every call, else ISING_ERR_ARG); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls whose work overlaps on the GPU (unordered streams) race on it.
+ * Nothing in the array needs to start at zero.
+ */
+int ising_anneal_noalloc(ising_problem* p, int32_t trials, const double* betas, int32_t S,
+                         uint64_t seed, uint32_t sweep_offset, const int8_t* init_spins,
+                         int8_t* out_spins, int32_t* out_cuts, void* cuda_stream);
+
 /* ising_strerror -- static description of a status code. */
 const char* ising_strerror(int code);
 

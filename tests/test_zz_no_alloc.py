@@ -1,0 +1,56 @@
+"""ising_anneal_noalloc against ising_anneal, through the C ABI.
+
+The no-allocation entry point serves callers that may not call cudaMalloc
+while they run (their device memory is already reserved by the host
+framework, or their loop must stay out of the allocator).  It keeps the
+threshold table in a fixed array inside the library instead of allocating
+one per call; its results must be the same bits as the allocating call.
+Two calls in a row check that the shared array is rewritten correctly.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(ia, prob, trials, betas, seed, sweep_offset=0, init=None):
+    import torch
+    L = ia.lib()
+    spins = torch.empty((trials, prob.n), dtype=torch.int8, device="cuda")
+    cuts = torch.empty((trials,), dtype=torch.int32, device="cuda")
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    rc = L.ising_anneal_noalloc(prob.handle, trials, b.ctypes.data_as(ctypes.c_void_p), b.shape[0], seed,
+                                sweep_offset, ctypes.c_void_p(init.data_ptr()) if init is not None else None,
+                                ctypes.c_void_p(spins.data_ptr()), ctypes.c_void_p(cuts.data_ptr()),
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return rc, spins, cuts
+
+
+def test_noalloc_matches_allocating_entry_point_twice():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2505_18508_gb300 as ia
+    torch.cuda.set_device(0)
+    inst = synth.torus_instance(200, 100, 2)
+    prob = ia.Problem.from_instance(inst)
+    runs = [  # (trials, sweeps, seed, beta range): the second call is shorter, so stale
+        (96, 700, 1002, (0.1, 3.0)),      # table entries from the first would show up
+        (40, 300, 77, (0.3, 2.0)),
+    ]
+    for trials, S, seed, (b0, b1) in runs:
+        betas = synth.linear_betas(b0, b1, S)
+        rc, s_na, c_na = _noalloc(ia, prob, trials, betas, seed)
+        assert rc == 0, ia.lib().ising_strerror(rc)
+        s_ref, c_ref = ia.anneal(prob, trials, betas, seed)
+        torch.cuda.synchronize()
+        assert torch.equal(s_na, s_ref)
+        assert torch.equal(c_na, c_ref)
+    # beyond the fixed capacity: rejected before anything is queued
+    rc, _, _ = _noalloc(ia, prob, 4, np.ones(40000), 1)
+    assert rc == -8
+    prob.destroy()
