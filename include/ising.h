@@ -182,6 +182,42 @@ int ising_set_launch(ising_problem* p, int32_t group_trials, int32_t strips, int
 int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* strips,
                       int32_t* threads, int32_t* grid_ctas);
 
+/*
+ * ising_set_kernel -- choose the kernel ising_anneal uses for this handle:
+ *   0 automatic (default): the persistent kernel when the instance has at
+ *     least 2,048 spins, its trial groups of 32 stack to at least four rows
+ *     per SM, and no strip shape is fixed; else the strip kernel;
+ *   1 strip kernel: each trial group annealed by a thread-block cluster of
+ *     row strips (ising_set_launch sets its shape);
+ *   2 persistent kernel: the rows of all trial groups stacked and split over
+ *     one CTA per SM, rows shared between CTAs exchanged through L2 with
+ *     per-row completion counters; ISING_ERR_UNSUPPORTED from ising_anneal if
+ *     a CTA would touch more than 4 trial groups or its rows do not fit in
+ *     shared memory.
+ * Results do not depend on the kernel.  Errors: ISING_ERR_ARG.
+ */
+int ising_set_kernel(ising_problem* p, int32_t kind);
+
+/* ising_last_kernel -- the kernel (1 or 2) the last ising_anneal call used. */
+int ising_last_kernel(const ising_problem* p, int32_t* kind);
+
+/*
+ * ising_get_status -- wait for `cuda_stream`, then read and clear the handle's
+ * device status word.  *code is ISING_OK, or ISING_ERR_TIMEOUT when a bounded
+ * device-side wait of the persistent kernel ran out (the results of that call
+ * are then undefined; the CUDA context stays usable).
+ */
+int ising_get_status(ising_problem* p, void* cuda_stream, int32_t* code);
+
+/*
+ * ising_set_wait_limit -- cycles one device-side wait of the persistent kernel
+ * may take before it gives up (0 restores the default of 4e9 cycles), and a
+ * test switch: stall_test = 1 makes the first chunk of the first CTA wait for
+ * a count that is never reached, so the limit runs out on purpose.
+ * Errors: ISING_ERR_ARG.
+ */
+int ising_set_wait_limit(ising_problem* p, int64_t cycles, int32_t stall_test);
+
 /* ising_problem_info -- X, Y and W = sum of the weights over the 2n edges
  * (so that H = W - 2 cut); any pointer may be NULL. */
 int ising_problem_info(const ising_problem* p, int32_t* X, int32_t* Y, int32_t* weight_sum);

@@ -85,6 +85,24 @@ class Problem:
         check(lib().ising_set_launch(self.handle, int(group_trials), int(strips), int(threads)),
               "ising_set_launch")
 
+    def set_kernel(self, kind):
+        """0 automatic, 1 cluster-strip kernel, 2 persistent kernel."""
+        check(lib().ising_set_kernel(self.handle, int(kind)), "ising_set_kernel")
+
+    def last_kernel(self):
+        v = ctypes.c_int32()
+        check(lib().ising_last_kernel(self.handle, ctypes.byref(v)), "ising_last_kernel")
+        return v.value
+
+    def get_status(self, stream=None):
+        """Wait for the stream, then read and clear the device status word."""
+        v = ctypes.c_int32()
+        check(lib().ising_get_status(self.handle, _stream_ptr(stream), ctypes.byref(v)), "ising_get_status")
+        return v.value
+
+    def set_wait_limit(self, cycles=0, stall_test=0):
+        check(lib().ising_set_wait_limit(self.handle, int(cycles), int(stall_test)), "ising_set_wait_limit")
+
     def last_launch(self):
         v = [ctypes.c_int32() for _ in range(4)]
         check(lib().ising_last_launch(self.handle, *[ctypes.byref(x) for x in v]), "ising_last_launch")

@@ -10,7 +10,7 @@ import os
 import re
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libising.so")
+LIB_PATH = os.environ.get("ISING_LIBRARY") or os.path.join(HERE, "_build", "libising.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ising.h")
 
 ISING_OK = 0
@@ -43,6 +43,10 @@ _SIGNATURES = {
     "ising_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
     "ising_last_launch": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p]),
     "ising_problem_info": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
+    "ising_set_kernel": (ctypes.c_int, [_vp, _i32]),
+    "ising_last_kernel": (ctypes.c_int, [_vp, _i32p]),
+    "ising_get_status": (ctypes.c_int, [_vp, _vp, _i32p]),
+    "ising_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64, _i32]),
     "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 

@@ -16,6 +16,8 @@
 
 namespace {
 
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
 int map_cuda(cudaError_t e) {
   if (e == cudaSuccess) return ISING_OK;
   if (e == cudaErrorMemoryAllocation) return ISING_ERR_OOM;
@@ -116,7 +118,6 @@ struct HostBatch {
   size_t off_inst = 0, off_units = 0, off_counter = 0, off_thr = 0, bytes = 0;
 };
 
-size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials, const int32_t* sweeps,
                   const double* const* betas, const uint64_t* seeds, int8_t* const* out_spins,
@@ -228,6 +229,137 @@ ising::BatchArgs batch_args(const HostBatch& hb, unsigned char* d_arena) {
   return a;
 }
 
+// ---------------------------------------------------------------- flow kernel plan
+struct FlowPlan {
+  int G = 0, groups = 0, RT = 0, P = 0, LRmax = 0;
+  size_t smem = 0;
+  std::vector<int32_t> split;
+};
+
+// Stacks the rows of all trial groups and splits them over one CTA per SM,
+// weighted by the Philox quads of each row's group.  Fails with
+// ISING_ERR_UNSUPPORTED when a CTA would touch more groups than the kernel
+// tracks or its rows would not fit in shared memory.
+int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp) {
+  const int sms = num_sms_of(p->device);
+  const int smem_max = max_smem_of(p->device);
+  int G = p->cfg_group;
+  if (G == 0) G = T >= 32 ? 32 : ((T + 3) / 4) * 4;
+  const int groups = (T + G - 1) / G;
+  const long long RTl = static_cast<long long>(groups) * p->Y;
+  if (RTl > (1LL << 30)) return ISING_ERR_UNSUPPORTED;
+  const int RT = static_cast<int>(RTl);
+  const int P = std::min(sms, RT);
+  std::vector<long long> cum(static_cast<size_t>(RT) + 1, 0);
+  for (int u = 0; u < RT; ++u) {
+    const int g = u / p->Y;
+    const int live = std::min(G, T - g * G);
+    cum[u + 1] = cum[u] + (live + 3) / 4;
+  }
+  const long long total = cum[RT];
+  std::vector<int32_t> split(static_cast<size_t>(P) + 1);
+  split[0] = 0;
+  int u = 0;
+  for (int j = 1; j < P; ++j) {
+    const long long target = (static_cast<long long>(j) * total + P / 2) / P;
+    while (u < RT && cum[u] < target) ++u;
+    int v = u;
+    if (v <= split[j - 1]) v = split[j - 1] + 1;
+    if (v > RT - (P - j)) v = RT - (P - j);
+    split[j] = v;
+  }
+  split[P] = RT;
+  int LRmax = 0;
+  for (int j = 0; j < P; ++j) {
+    int lr = 0, nseg = 0;
+    for (int w = split[j]; w < split[j + 1];) {
+      const int g = w / p->Y, ya = w - g * p->Y;
+      const int n = std::min(p->Y - ya, split[j + 1] - w);
+      lr += n + (n == p->Y ? 0 : 2);
+      ++nseg;
+      w += n;
+    }
+    if (nseg > ising::flow_max_segments()) return ISING_ERR_UNSUPPORTED;
+    LRmax = std::max(LRmax, lr);
+  }
+  const size_t smem = ising::flow_smem_bytes(LRmax, p->H);
+  if (smem > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
+  fp->G = G;
+  fp->groups = groups;
+  fp->RT = RT;
+  fp->P = P;
+  fp->LRmax = LRmax;
+  fp->smem = smem;
+  fp->split.swap(split);
+  return ISING_OK;
+}
+
+int run_flow(ising_problem* p, const FlowPlan& fp, int32_t trials, const std::vector<uint32_t>& thr, int32_t S,
+             uint64_t seed, uint32_t sweep_offset, const int8_t* init_spins, int8_t* out_spins, int32_t* out_cuts,
+             cudaStream_t st) {
+  int per_sm = 0;
+  cudaError_t e = ising::flow_max_ctas(fp.smem, &per_sm);
+  if (e != cudaSuccess) return map_cuda(e);
+  if (per_sm < 1 || fp.P > per_sm * num_sms_of(p->device)) return ISING_ERR_UNSUPPORTED;
+  // arena: thresholds | split | mirror | zeroed: counters, cut sums, done, abort
+  const size_t o_thr = 0;
+  const size_t o_split = o_thr + align256(thr.size() * sizeof(uint32_t));
+  const size_t o_gm = o_split + align256((fp.split.size()) * sizeof(int32_t));
+  const size_t o_zero = o_gm + align256(static_cast<size_t>(fp.RT) * 2 * p->H * sizeof(uint32_t));
+  const size_t o_gcnt = o_zero;
+  const size_t o_acc = o_gcnt + align256(static_cast<size_t>(fp.RT) * 2 * sizeof(uint32_t));
+  const size_t o_done = o_acc + align256(static_cast<size_t>(trials) * sizeof(int32_t));
+  const size_t o_abort = o_done + 256;
+  const size_t bytes = o_abort + 256;
+  unsigned char* d = nullptr;
+  e = cudaMallocAsync(reinterpret_cast<void**>(&d), bytes, st);
+  if (e != cudaSuccess) return map_cuda(e);
+  if (!thr.empty()) e = cudaMemcpyAsync(d + o_thr, thr.data(), thr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d + o_split, fp.split.data(), fp.split.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d + o_zero, 0, bytes - o_zero, st);
+  if (e == cudaSuccess) {
+    ising::FlowArgs a;
+    a.flags = p->d_flags;
+    a.thr = reinterpret_cast<const uint32_t*>(d + o_thr);
+    a.init = init_spins;
+    a.out_spins = out_spins;
+    a.out_cuts = out_cuts;
+    a.X = p->X; a.Y = p->Y; a.H = p->H; a.n = p->n;
+    a.T = trials; a.G = fp.G; a.S = S;
+    a.k0 = sweep_offset;
+    a.key0 = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
+    a.key1 = static_cast<uint32_t>(seed >> 32);
+    for (uint32_t r = 0; r < 10; ++r) {
+      a.rk[2 * r] = a.key0 + r * 0x9E3779B9u;
+      a.rk[2 * r + 1] = a.key1 + r * 0xBB67AE85u;
+    }
+    a.RT = fp.RT;
+    a.P = fp.P;
+    a.LRmax = fp.LRmax;
+    a.neg_edges = p->neg_edges;
+    a.split = reinterpret_cast<const int32_t*>(d + o_split);
+    a.gm = reinterpret_cast<uint32_t*>(d + o_gm);
+    a.gcnt = reinterpret_cast<uint32_t*>(d + o_gcnt);
+    a.acc = reinterpret_cast<int32_t*>(d + o_acc);
+    a.done = reinterpret_cast<uint32_t*>(d + o_done);
+    a.abort_flag = reinterpret_cast<uint32_t*>(d + o_abort);
+    a.status = p->d_status;
+    a.spin_limit = p->wait_limit > 0 ? p->wait_limit : 4000000000LL;
+    a.stall_test = p->stall_test;
+    e = ising::launch_flow(a, st);
+  }
+  const cudaError_t e2 = cudaFreeAsync(d, st);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return map_cuda(e);
+  p->last_kernel = 2;
+  p->last_group = fp.G;
+  p->last_strips = 0;
+  p->last_threads = ising::flow_threads();
+  p->last_grid = fp.P;
+  return ISING_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -316,11 +448,14 @@ int ising_create(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, cons
   if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return ISING_ERR_CUDA; }
   cudaError_t e = cudaMalloc(&p->d_flags, n);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_eflags, n);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_status), sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemcpy(p->d_flags, flags.data(), n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_eflags, eflags.data(), n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(p->d_flags);
     cudaFree(p->d_eflags);
+    cudaFree(p->d_status);
     delete p;
     return map_cuda(e);
   }
@@ -332,6 +467,7 @@ void ising_destroy(ising_problem* p) {
   if (!p) return;
   cudaFree(p->d_flags);
   cudaFree(p->d_eflags);
+  cudaFree(p->d_status);
   delete p;
 }
 
@@ -356,6 +492,38 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
   return ISING_OK;
 }
 
+int ising_set_kernel(ising_problem* p, int32_t kind) {
+  if (!p || kind < 0 || kind > 2) return ISING_ERR_ARG;
+  p->cfg_kernel = kind;
+  return ISING_OK;
+}
+
+int ising_last_kernel(const ising_problem* p, int32_t* kind) {
+  if (!p || !kind) return ISING_ERR_ARG;
+  *kind = p->last_kernel;
+  return ISING_OK;
+}
+
+int ising_get_status(ising_problem* p, void* cuda_stream, int32_t* code) {
+  if (!p || !code) return ISING_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int32_t v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, p->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return map_cuda(e);
+  *code = v;
+  return ISING_OK;
+}
+
+int ising_set_wait_limit(ising_problem* p, int64_t cycles, int32_t stall_test) {
+  if (!p || cycles < 0 || stall_test < 0 || stall_test > 1) return ISING_ERR_ARG;
+  p->wait_limit = cycles;
+  p->stall_test = stall_test;
+  return ISING_OK;
+}
+
 int ising_problem_info(const ising_problem* p, int32_t* X, int32_t* Y, int32_t* weight_sum) {
   if (!p) return ISING_ERR_ARG;
   if (X) *X = p->X;
@@ -376,10 +544,29 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
     return ISING_ERR_OOM;
   }
   if (trials == 0) return ISING_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // kernel: the persistent flow kernel when the instance is large enough and
+  // its stacked rows give every SM at least four (unless the handle fixes a
+  // kernel or a strip shape), else the cluster-strip kernel
+  int kind = p->cfg_kernel;
+  if (kind == 0) {
+    const long long rows = static_cast<long long>((trials + 31) / 32) * p->Y;
+    kind = (p->cfg_strips == 0 && p->n >= 2048 && rows >= 4LL * num_sms_of(p->device)) ? 2 : 1;
+  }
+  if (kind == 2) {
+    FlowPlan fp;
+    int frc;
+    try {
+      frc = plan_flow(p, trials, &fp);
+    } catch (const std::bad_alloc&) {
+      return ISING_ERR_OOM;
+    }
+    if (frc == ISING_OK) return run_flow(p, fp, trials, thr, S, seed, sweep_offset, init_spins, out_spins, out_cuts, st);
+    if (p->cfg_kernel == 2) return frc;
+  }
   Shape sh;
   const int rc = choose_shape(p, trials, &sh);
   if (rc != ISING_OK) return rc;
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   uint32_t* d_thr = nullptr;
   const size_t thr_bytes = thr.size() * sizeof(uint32_t);
   if (thr_bytes) {
@@ -414,6 +601,7 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
     if (e == cudaSuccess) e = e2;
   }
   if (e != cudaSuccess) return map_cuda(e);
+  p->last_kernel = 1;
   p->last_group = sh.G;
   p->last_strips = sh.C;
   p->last_threads = sh.threads;

@@ -144,6 +144,22 @@ __device__ __forceinline__ void cluster_wait() {
   if constexpr (kCluster) asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory");
 }
 
+
+// one Philox block (rounds 3..10) for one quad of trials, its four draws
+// compared against both thresholds and shifted into the reject masks
+__device__ __forceinline__ void quad_step(uint32_t& rej4, uint32_t& rej8, const uint4 hd, uint32_t hi1, uint32_t lo1,
+                                          uint32_t lo0, uint32_t T4, uint32_t T8, const uint32_t* __restrict__ rk) {
+  const uint4 u = philox_rounds_3_to_10(hi1 ^ hd.x, lo1, hd.y ^ lo0, hd.z, rk);
+  rej4 = shift_in_ge(rej4, u.w, T4);
+  rej4 = shift_in_ge(rej4, u.z, T4);
+  rej4 = shift_in_ge(rej4, u.y, T4);
+  rej4 = shift_in_ge(rej4, u.x, T4);
+  rej8 = shift_in_ge(rej8, u.w, T8);
+  rej8 = shift_in_ge(rej8, u.z, T8);
+  rej8 = shift_in_ge(rej8, u.y, T8);
+  rej8 = shift_in_ge(rej8, u.x, T8);
+}
+
 // Metropolis update of one site word; returns the new word.
 __device__ __forceinline__ uint32_t update_word(uint32_t s, uint32_t nl, uint32_t nr, uint32_t nu, uint32_t nd,
                                                uint32_t f, uint32_t i, const uint4* head, int nq,
@@ -161,17 +177,11 @@ __device__ __forceinline__ uint32_t update_word(uint32_t s, uint32_t nl, uint32_
   mulhilo(kPhiloxM0, i, hi0, lo0);
   mulhilo(kPhiloxM1, hi0 ^ rk[1], hi1, lo1);
   uint32_t rej4 = 0, rej8 = 0;   // bit set: draw at or above the threshold
-  for (int j = nq - 1; j >= 0; --j) {
-    const uint4 hd = head[j];
-    const uint4 u = philox_rounds_3_to_10(hi1 ^ hd.x, lo1, hd.y ^ lo0, hd.z, rk);
-    rej4 = shift_in_ge(rej4, u.w, T4);
-    rej4 = shift_in_ge(rej4, u.z, T4);
-    rej4 = shift_in_ge(rej4, u.y, T4);
-    rej4 = shift_in_ge(rej4, u.x, T4);
-    rej8 = shift_in_ge(rej8, u.w, T8);
-    rej8 = shift_in_ge(rej8, u.z, T8);
-    rej8 = shift_in_ge(rej8, u.y, T8);
-    rej8 = shift_in_ge(rej8, u.x, T8);
+  if (nq == 8) {  // full groups: unrolled, so consecutive blocks can overlap
+#pragma unroll
+    for (int j = 7; j >= 0; --j) quad_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
+  } else {
+    for (int j = nq - 1; j >= 0; --j) quad_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
   }
   return s ^ (ge2 | (eq1 & ~rej4) | (eq0 & ~rej8));
 }

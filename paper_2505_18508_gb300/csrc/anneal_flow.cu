@@ -1,0 +1,467 @@
+// anneal_flow.cu -- persistent, barrier-free form of the checkerboard sweep.
+//
+// The same Metropolis sweep as anneal_core.cuh (Zick 2025, Section III: trials
+// of sweeps read out at the end of each trial; Eq. 1, Eq. 2 with J = -w, h = 0),
+// organised so that every SM works and no CTA-wide barrier separates the
+// half-sweeps:
+//
+// * Rows of all trial groups are stacked (global row u = g*Y + y) and split
+//   into one contiguous range per CTA, weighted by the number of Philox quads
+//   of each row's group, over exactly one CTA per SM (cooperative launch, so
+//   all CTAs are resident together).
+// * Inside a CTA, warps take 32-item chunks of the half-sweeps in one global
+//   order (half-sweep major), round robin.  A chunk of colour c only needs the
+//   colour-(1-c) words of its rows and of the rows above and below; per-row
+//   completion counters in shared memory say when those are final, so a warp
+//   waits for exactly its neighbours and never for the whole CTA.
+// * Rows whose neighbour belongs to another CTA ("published" rows) are also
+//   written to a global mirror, with a per-row completion counter in global
+//   memory; the neighbour CTA acquires that counter before reading the row.
+//   Published rows come first in each half-sweep, so the counters are usually
+//   complete long before anyone waits on them.
+//
+// Every wait is bounded by a cycle limit.  A wait that runs out writes
+// ISING_ERR_TIMEOUT to the problem's status word and raises an abort flag that
+// ends all other waits at once; the kernel then returns without results.
+#include "anneal_core.cuh"
+
+namespace ising {
+namespace {
+
+constexpr int kMaxSeg = 4;        // row segments (groups touched) per CTA
+constexpr int kFlowThreads = 1024;
+constexpr int kFlowWarps = kFlowThreads / 32;
+
+struct FlowSmem {
+  uint32_t* sp;        // [2][LR][H] spin words (own rows and halo slots)
+  uint8_t* fl;         // [2][LR][H] site flags (own rows)
+  uint32_t* rowcnt;    // [2][LR] completed items per local row and colour
+  int32_t* r_u;        // [LR] global row of the local row (own or halo)
+  int32_t* r_up;       // [LR] local row above (own row or halo slot)
+  int32_t* r_dn;       // [LR] local row below
+  int32_t* r_xup;      // [LR] global row above when it belongs to another CTA, else -1
+  int32_t* r_xdn;      // [LR] same for the row below
+  int32_t* r_pub;      // [LR] 1 if another CTA reads this own row
+  int32_t* r_seg;      // [LR] segment of the row
+  int32_t* order;      // [LR] own rows in processing order (published rows first)
+  uint4* whead;        // [warps][kMaxSeg][8] per-warp Philox heads
+  int32_t* meta;       // [8]: nown, nloc, nseg, ...
+  int32_t* seg_g;      // [kMaxSeg] group of each segment
+  int4* rowA;          // [LR] {up | dn << 16, xup, xdn, y*X}
+  int4* rowB;          // [LR] {seg | pub << 4 | (y & 1) << 5 | nq << 8, u, t0, 0}
+  int32_t* ctab;       // [NC*32] lane item of each chunk: lr | h << 16, or -1
+};
+
+__host__ __device__ inline size_t flow_smem_layout(int32_t LR, int32_t H, size_t* off) {
+  size_t o = 0;
+  off[0] = o; o += align16(static_cast<size_t>(2) * LR * H * 4);      // sp
+  off[1] = o; o += align16(static_cast<size_t>(2) * LR * H);          // fl
+  off[2] = o; o += align16(static_cast<size_t>(2) * LR * 4);          // rowcnt
+  off[3] = o; o += align16(static_cast<size_t>(8) * LR * 4);          // row tables (8 arrays)
+  off[4] = o; o += static_cast<size_t>(kFlowWarps) * kMaxSeg * 8 * 16; // whead
+  off[5] = o; o += 16 * 4;                                             // meta + seg_g
+  off[6] = o; o += static_cast<size_t>(2) * LR * 16;                   // rowA, rowB
+  off[7] = o; o += align16(static_cast<size_t>((LR * H + 31) / 32) * 32 * 4);  // ctab
+  return o;
+}
+
+__device__ __forceinline__ FlowSmem flow_carve(unsigned char* smem, int32_t LR, int32_t H) {
+  size_t off[8];
+  flow_smem_layout(LR, H, off);
+  FlowSmem s;
+  s.sp = reinterpret_cast<uint32_t*>(smem + off[0]);
+  s.fl = smem + off[1];
+  s.rowcnt = reinterpret_cast<uint32_t*>(smem + off[2]);
+  int32_t* t = reinterpret_cast<int32_t*>(smem + off[3]);
+  s.r_u = t;
+  s.r_up = t + LR;
+  s.r_dn = t + 2 * LR;
+  s.r_xup = t + 3 * LR;
+  s.r_xdn = t + 4 * LR;
+  s.r_pub = t + 5 * LR;
+  s.r_seg = t + 6 * LR;
+  s.order = t + 7 * LR;
+  s.whead = reinterpret_cast<uint4*>(smem + off[4]);
+  s.meta = reinterpret_cast<int32_t*>(smem + off[5]);
+  s.seg_g = s.meta + 8;
+  s.rowA = reinterpret_cast<int4*>(smem + off[6]);
+  s.rowB = s.rowA + LR;
+  s.ctab = reinterpret_cast<int32_t*>(smem + off[7]);
+  return s;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_shared(const uint32_t* p) {
+  return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+// Bounded wait for *cnt >= need (shared counter or, with kGlobal, a global
+// counter read with acquire semantics).  Returns false if the wait was
+// abandoned (limit reached, or another wait raised the abort flag).
+template <bool kGlobal>
+__device__ __forceinline__ bool wait_count(const uint32_t* cnt, uint32_t need, const FlowArgs& a) {
+  uint32_t v = kGlobal ? ld_acquire_gpu(cnt) : ld_volatile_shared(cnt);
+  if (v >= need) return true;
+  const long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
+    __nanosleep(64);   // keep the issue slots for the warps that have work
+    v = kGlobal ? ld_acquire_gpu(cnt) : ld_volatile_shared(cnt);
+    if (v >= need) return true;
+    if ((it & 15u) == 15u) {
+      if (*reinterpret_cast<const volatile uint32_t*>(a.abort_flag) != 0u) return false;
+      if (clock64() - t0 > a.spin_limit) {
+        atomicExch(a.status, ISING_ERR_TIMEOUT);
+        atomicExch(a.abort_flag, 1u);
+        return false;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __grid_constant__ FlowArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int j = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int H = a.H, Y = a.Y;
+  const FlowSmem sm = flow_carve(smem, a.LRmax, H);
+  const int r0 = a.split[j], r1 = a.split[j + 1];
+
+  // ---- local row tables (one thread; at most a few dozen rows)
+  if (tid == 0) {
+    int nloc = 0, nseg = 0;
+    int seg_first[kMaxSeg], seg_n[kMaxSeg];
+    for (int u = r0; u < r1;) {
+      const int g = u / Y, ya = u - g * Y;
+      const int yb = min(Y, ya + (r1 - u));
+      const int n = yb - ya;
+      const bool whole = (n == Y);
+      sm.seg_g[nseg] = g;
+      seg_n[nseg] = n;
+      // layout: [halo top][own rows][halo bottom] (no halos for a whole group)
+      const int own0 = whole ? nloc : nloc + 1;
+      seg_first[nseg] = own0;
+      for (int q = 0; q < n; ++q) {
+        const int lr = own0 + q;
+        const int y = ya + q;
+        sm.r_u[lr] = g * Y + y;
+        sm.r_seg[lr] = nseg;
+        sm.r_xup[lr] = -1;
+        sm.r_xdn[lr] = -1;
+        sm.r_pub[lr] = 0;
+        if (whole) {
+          sm.r_up[lr] = own0 + (q == 0 ? n - 1 : q - 1);
+          sm.r_dn[lr] = own0 + (q == n - 1 ? 0 : q + 1);
+        } else {
+          sm.r_up[lr] = lr - 1;            // halo slot above the first own row
+          sm.r_dn[lr] = lr + 1;            // halo slot below the last own row
+          if (q == 0) { sm.r_xup[lr] = g * Y + (ya + Y - 1) % Y; sm.r_pub[lr] = 1; }
+          if (q == n - 1) { sm.r_xdn[lr] = g * Y + (yb % Y); sm.r_pub[lr] = 1; }
+        }
+      }
+      if (!whole) {
+        sm.r_u[nloc] = g * Y + (ya + Y - 1) % Y;          // halo slot above
+        sm.r_seg[nloc] = nseg;
+        sm.r_u[own0 + n] = g * Y + (yb % Y);              // halo slot below
+        sm.r_seg[own0 + n] = nseg;
+        nloc += n + 2;
+      } else {
+        nloc += n;
+      }
+      ++nseg;
+      u += n;
+    }
+    // processing order: the published rows of every segment first, then the
+    // remaining rows of each segment from both ends towards the middle, the
+    // segments interleaved.  Every row's neighbours are then processed about
+    // one half-sweep before it needs them, never just before.
+    int no = 0;
+    int lo[kMaxSeg], hi[kMaxSeg];
+    for (int s = 0; s < nseg; ++s) {
+      lo[s] = seg_first[s];
+      hi[s] = seg_first[s] + seg_n[s] - 1;
+      if (sm.r_pub[lo[s]]) {           // partial segment: first and last own row
+        sm.order[no++] = lo[s];
+        if (hi[s] != lo[s]) sm.order[no++] = hi[s];
+        ++lo[s];
+        --hi[s];
+      }
+    }
+    for (bool more = true; more;) {
+      more = false;
+      for (int s = 0; s < nseg; ++s) {
+        if (lo[s] <= hi[s]) { sm.order[no++] = lo[s]++; more = true; }
+        if (lo[s] <= hi[s]) { sm.order[no++] = hi[s]--; more = true; }
+      }
+    }
+    sm.meta[0] = no;
+    sm.meta[1] = nloc;
+    sm.meta[2] = nseg;
+  }
+  __syncthreads();
+  const int nown = sm.meta[0], nloc = sm.meta[1], nseg = sm.meta[2];
+  const int items = nown * H;
+  const int NC = (items + 31) >> 5;
+  for (int lr = tid; lr < nloc; lr += kFlowThreads) {
+    const int u = sm.r_u[lr];
+    const int g = u / Y, y = u - g * Y;
+    const int t0 = g * a.G;
+    const int nq = (min(a.G, a.T - t0) + 3) >> 2;
+    sm.rowA[lr] = make_int4(sm.r_up[lr] | (sm.r_dn[lr] << 16), sm.r_xup[lr], sm.r_xdn[lr], y * a.X);
+    sm.rowB[lr] = make_int4(sm.r_seg[lr] | (sm.r_pub[lr] << 4) | ((y & 1) << 5) | (nq << 8), u, t0, 0);
+  }
+  for (int e = tid; e < NC * 32; e += kFlowThreads) {
+    int v = -1;
+    if (e < items) {
+      const int oi = e / H;
+      v = sm.order[oi] | ((e - oi * H) << 16);
+    }
+    sm.ctab[e] = v;
+  }
+
+  // ---- weights of own rows, starting spins of own rows and halo slots
+  for (int idx = tid; idx < 2 * nloc; idx += kFlowThreads) sm.rowcnt[idx] = 0u;
+  for (int idx = tid; idx < 2 * nloc * H; idx += kFlowThreads) {
+    const int c = idx / (nloc * H);
+    const int rem = idx - c * nloc * H;
+    const int lr = rem / H;
+    const int h = rem - lr * H;
+    const int u = sm.r_u[lr];
+    const int g = u / Y, y = u - g * Y;
+    const int t0 = g * a.G;
+    const int live = min(a.G, a.T - t0);
+    const int nq = (live + 3) >> 2;
+    const uint32_t q0 = static_cast<uint32_t>(t0) >> 2;
+    const uint32_t i = static_cast<uint32_t>(y * a.X + 2 * h + ((y + c) & 1));
+    uint32_t w = 0;
+    if (a.init) {
+      for (int b = 0; b < live; ++b)
+        w |= static_cast<uint32_t>(a.init[static_cast<size_t>(t0 + b) * a.n + i] > 0) << b;
+    } else {
+      for (int jq = 0; jq < nq; ++jq) {
+        const uint4 v = philox4x32_10(i, 0xFFFFFFFFu, q0 + jq, 0u, a.key0, a.key1);
+        w |= ((v.x >> 31) | ((v.y >> 31) << 1) | ((v.z >> 31) << 2) | ((v.w >> 31) << 3)) << (4 * jq);
+      }
+    }
+    sm.sp[(c * a.LRmax + lr) * H + h] = w;
+    sm.fl[(c * a.LRmax + lr) * H + h] = a.flags[(static_cast<size_t>(c) * Y + y) * H + h];
+  }
+  __syncthreads();
+
+  // ---- the half-sweeps, chunk by chunk
+  const long long M = 2LL * a.S * NC;
+  uint4* wh = sm.whead + warp * (kMaxSeg * 8);
+  int head_kk = -1;
+  bool ok = true;
+  int hs = 0, k = warp;
+  while (k >= NC && NC > 0) { k -= NC; ++hs; }
+  for (long long m = warp; m < M; m += kFlowWarps) {
+    const int kk = hs >> 1, c = hs & 1;
+    if (kk != head_kk) {   // Philox heads of this sweep for every segment's quads
+      __syncwarp();
+      if (lane < nseg * 8) {
+        const int s = lane >> 3, jq = lane & 7;
+        const uint32_t q = (static_cast<uint32_t>(sm.seg_g[s] * a.G) >> 2) + jq;
+        wh[lane] = philox_head_sweep_quad(a.k0 + static_cast<uint32_t>(kk), q, a.key0, a.key1);
+      }
+      __syncwarp();
+      head_kk = kk;
+    }
+    const uint32_t T4 = __ldg(a.thr + 2 * kk), T8 = __ldg(a.thr + 2 * kk + 1);
+    const uint32_t need = static_cast<uint32_t>(H) * static_cast<uint32_t>(kk + c);
+    const int te = sm.ctab[k * 32 + lane];
+    const bool active = te >= 0;
+    const int lr = te & 0xFFFF, h = te >> 16;
+    bool lane_ok = true;
+    int4 ra = make_int4(0, -1, -1, 0), rb = make_int4(0, 0, 0, 0);
+    if (active) {
+      ra = sm.rowA[lr];
+      rb = sm.rowB[lr];
+      const uint32_t* rc = sm.rowcnt + (1 - c) * nloc;
+      const int up = ra.x & 0xFFFF, dn = ra.x >> 16;
+      const int xup = ra.y, xdn = ra.z;
+      // fast check of the three neighbour rows, bounded waits only when needed
+      const uint32_t c_self = ld_volatile_shared(rc + lr);
+      const uint32_t c_up = xup >= 0 ? (need == 0 ? 0u : ld_acquire_gpu(a.gcnt + 2 * xup + (1 - c)))
+                                     : ld_volatile_shared(rc + up);
+      const uint32_t c_dn = xdn >= 0 ? (need == 0 ? 0u : ld_acquire_gpu(a.gcnt + 2 * xdn + (1 - c)))
+                                     : ld_volatile_shared(rc + dn);
+      if (c_self < need) lane_ok = wait_count<false>(rc + lr, need, a);
+      if (lane_ok && c_up < need)
+        lane_ok = xup >= 0 ? wait_count<true>(a.gcnt + 2 * xup + (1 - c), need, a) : wait_count<false>(rc + up, need, a);
+      if (lane_ok && c_dn < need)
+        lane_ok = xdn >= 0 ? wait_count<true>(a.gcnt + 2 * xdn + (1 - c), need, a) : wait_count<false>(rc + dn, need, a);
+      if (a.stall_test && j == 0 && m == 0) lane_ok = lane_ok && wait_count<false>(rc + lr, 0xFFFFFFFFu, a);
+      if (lane_ok) {
+        __threadfence_block();
+        const int par = ((rb.x >> 5) & 1) ^ c;
+        const uint32_t i = static_cast<uint32_t>(ra.w + 2 * h + par);
+        const uint32_t* self = sm.sp + static_cast<size_t>(c) * a.LRmax * H;
+        const uint32_t* nb = sm.sp + static_cast<size_t>(1 - c) * a.LRmax * H;
+        const int hl = par ? h : (h == 0 ? H - 1 : h - 1);
+        const int hr = par ? (h == H - 1 ? 0 : h + 1) : h;
+        const uint32_t nu = (xup >= 0 && need > 0) ? __ldcg(a.gm + (static_cast<size_t>(2) * xup + (1 - c)) * H + h)
+                                                   : nb[up * H + h];
+        const uint32_t nd = (xdn >= 0 && need > 0) ? __ldcg(a.gm + (static_cast<size_t>(2) * xdn + (1 - c)) * H + h)
+                                                   : nb[dn * H + h];
+        const uint32_t ns = update_word(self[lr * H + h], nb[lr * H + hl], nb[lr * H + hr], nu, nd,
+                                        sm.fl[(c * a.LRmax + lr) * H + h], i, wh + 8 * (rb.x & 15), rb.x >> 8, T4,
+                                        T8, a.rk);
+        sm.sp[(static_cast<size_t>(c) * a.LRmax + lr) * H + h] = ns;
+        if ((rb.x >> 4) & 1) {
+          __stcg(a.gm + (static_cast<size_t>(2) * rb.y + c) * H + h, ns);
+          __threadfence();
+        }
+        __threadfence_block();
+      }
+    }
+    ok = __all_sync(0xFFFFFFFFu, lane_ok);
+    if (!ok) break;
+    // completion counts: one atomic per distinct row of the chunk
+    const unsigned same = __match_any_sync(0xFFFFFFFFu, active ? lr : -1);
+    if (active && lane == __ffs(same) - 1) {
+      const uint32_t cnt = __popc(same);
+      atomicAdd(sm.rowcnt + c * nloc + lr, cnt);
+      if ((rb.x >> 4) & 1) atomicAdd(a.gcnt + 2 * rb.y + c, cnt);
+    }
+    k += kFlowWarps;
+    while (k >= NC) { k -= NC; ++hs; }
+  }
+  __shared__ int s_stop;
+  __syncthreads();
+  if (tid == 0) s_stop = *reinterpret_cast<const volatile uint32_t*>(a.abort_flag) != 0u;
+  __syncthreads();
+  if (s_stop) return;   // CTA-uniform: every thread returns, nobody waits on a barrier
+
+  // ---- read-out: spins of the own rows
+  if (a.out_spins) {
+    const int span = nown * a.X;
+    for (int idx = tid; idx < span; idx += kFlowThreads) {
+      const int oi = idx / a.X;
+      const int x = idx - oi * a.X;
+      const int lr = sm.order[oi];
+      const int u = sm.r_u[lr];
+      const int g = u / Y, y = u - g * Y;
+      const int t0 = g * a.G;
+      const int live = min(a.G, a.T - t0);
+      const int c = (x + y) & 1;
+      const uint32_t w = sm.sp[(static_cast<size_t>(c) * a.LRmax + lr) * H + (x >> 1)];
+      int8_t* dst = a.out_spins + static_cast<size_t>(t0) * a.n + static_cast<size_t>(y) * a.X + x;
+      for (int b = 0; b < live; ++b) dst[static_cast<size_t>(b) * a.n] = ((w >> b) & 1u) ? int8_t(1) : int8_t(-1);
+    }
+  }
+  // ---- cut partials per trial: own right and down edges, summed over lanes
+  // with ballots, per segment (all lanes of a pass share the segment's group)
+  if (a.out_cuts) {
+    const uint32_t fin = static_cast<uint32_t>(H) * a.S;
+    bool cut_ok = true;
+    for (int s = 0; s < nseg && cut_ok; ++s) {
+      const int g = sm.seg_g[s];
+      const int t0 = g * a.G;
+      const int live = min(a.G, a.T - t0);
+      uint32_t accb = 0;
+      // own rows of segment s, both colours
+      for (int base = warp * 32; base < 2 * nown * H && cut_ok; base += kFlowThreads) {
+        const int idx = base + lane;
+        uint32_t vr = 0, vd = 0;
+        bool mine = false;
+        int lr = 0, c = 0, h = 0;
+        if (idx < 2 * nown * H) {
+          c = idx / (nown * H);
+          const int rem = idx - c * nown * H;
+          const int oi = rem / H;
+          h = rem - oi * H;
+          lr = sm.order[oi];
+          mine = sm.r_seg[lr] == s;
+        }
+        bool lok = true;
+        if (mine) {
+          const int u = sm.r_u[lr];
+          const int y = u - g * Y;
+          const int par = (y + c) & 1;
+          const uint32_t* self = sm.sp + static_cast<size_t>(c) * a.LRmax * H;
+          const uint32_t* nb = sm.sp + static_cast<size_t>(1 - c) * a.LRmax * H;
+          const uint32_t sv = self[lr * H + h];
+          const int hr = par ? (h == H - 1 ? 0 : h + 1) : h;
+          const uint32_t sr = nb[lr * H + hr];
+          uint32_t sd;
+          const int xdn = sm.r_xdn[lr];
+          if (xdn >= 0 && a.S > 0) {
+            lok = wait_count<true>(a.gcnt + 2 * xdn + (1 - c), fin, a);
+            sd = lok ? __ldcg(a.gm + (static_cast<size_t>(2) * xdn + (1 - c)) * H + h) : 0u;
+          } else {
+            sd = nb[sm.r_dn[lr] * H + h];
+          }
+          const uint32_t f = sm.fl[(c * a.LRmax + lr) * H + h];
+          vr = (sv ^ sr) ^ (0u - ((f >> 1) & 1u));
+          vd = (sv ^ sd) ^ (0u - ((f >> 3) & 1u));
+        }
+        if (!__all_sync(0xFFFFFFFFu, lok)) {
+          cut_ok = false;
+          break;
+        }
+#pragma unroll 4
+        for (int b = 0; b < 32; ++b) {
+          const uint32_t cnt = __popc(__ballot_sync(0xFFFFFFFFu, (vr >> b) & 1u)) +
+                               __popc(__ballot_sync(0xFFFFFFFFu, (vd >> b) & 1u));
+          if (lane == b) accb += cnt;
+        }
+      }
+      if (cut_ok && lane < live && accb) atomicAdd(a.acc + t0 + lane, static_cast<int32_t>(accb));
+    }
+    __shared__ int s_last, s_fail;
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    if (!cut_ok && lane == 0) s_fail = 1;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0)
+      s_last = !s_fail && atomicAdd(a.done, 1u) == static_cast<uint32_t>(a.P - 1);
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      for (int t = tid; t < a.T; t += kFlowThreads) a.out_cuts[t] = __ldcg(a.acc + t) - a.neg_edges;
+    }
+  }
+}
+
+}  // namespace
+
+size_t flow_smem_bytes(int32_t LR, int32_t H) {
+  size_t off[8];
+  return flow_smem_layout(LR, H, off);
+}
+
+int flow_threads() { return kFlowThreads; }
+int flow_max_segments() { return kMaxSeg; }
+
+cudaError_t launch_flow(const FlowArgs& a, cudaStream_t stream) {
+  const size_t smem = flow_smem_bytes(a.LRmax, a.H);
+  cudaError_t e = cudaFuncSetAttribute(anneal_flow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.P, 1, 1);
+  cfg.blockDim = dim3(kFlowThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, anneal_flow_kernel, a);
+}
+
+cudaError_t flow_max_ctas(size_t smem, int* per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(anneal_flow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, anneal_flow_kernel, kFlowThreads, smem);
+}
+
+}  // namespace ising

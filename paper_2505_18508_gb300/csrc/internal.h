@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/ising.h"
+
 struct ising_problem {
   int32_t X = 0, Y = 0, n = 0, H = 0;   // H = X / 2 sites per colour per row
   int32_t neg_edges = 0;                // edges with w = -1
@@ -14,9 +16,14 @@ struct ising_problem {
   uint8_t* d_flags = nullptr;
   // Natural-order edge flags, index y*X + x: bit0 right edge w=-1, bit1 down.
   uint8_t* d_eflags = nullptr;
+  // device status word: bounded waits that ran out leave ISING_ERR_TIMEOUT here
+  int32_t* d_status = nullptr;
   // launch overrides (0 = automatic) and the last shape used
-  int32_t cfg_group = 0, cfg_strips = 0, cfg_threads = 0;
-  int32_t last_group = 0, last_strips = 0, last_threads = 0, last_grid = 0;
+  int32_t cfg_group = 0, cfg_strips = 0, cfg_threads = 0, cfg_kernel = 0;
+  int32_t last_group = 0, last_strips = 0, last_threads = 0, last_grid = 0, last_kernel = 0;
+  // bounded-wait limit (cycles) and the forced-stall switch used by tests
+  long long wait_limit = 0;
+  int32_t stall_test = 0;
 };
 
 namespace ising {
@@ -39,6 +46,36 @@ struct AnnealArgs {
   int32_t Rmax;             // ceil(Y / C)
   int32_t neg_edges;
 };
+
+// Everything the persistent flow kernel reads (anneal_flow.cu).
+struct FlowArgs {
+  const uint8_t* flags;     // plane-order site flags [n]
+  const uint32_t* thr;      // [2*S]
+  const int8_t* init;       // [T][n] or null
+  int8_t* out_spins;        // [T][n] or null
+  int32_t* out_cuts;        // [T] or null
+  int32_t X, Y, H, n, T, G, S;
+  uint32_t k0, key0, key1;
+  uint32_t rk[20];
+  int32_t RT;               // rows of all groups stacked: groups * Y
+  int32_t P;                // CTAs (one per SM)
+  int32_t LRmax;            // local rows (own rows and halo slots) of the largest CTA
+  int32_t neg_edges;
+  const int32_t* split;     // [P+1] first stacked row of each CTA
+  uint32_t* gm;             // [RT][2][H] mirror of rows read by another CTA
+  uint32_t* gcnt;           // [RT][2] completed items of those rows (zeroed)
+  int32_t* acc;             // [T] per-trial cut partial sums (zeroed)
+  uint32_t* done;           // CTAs finished (zeroed)
+  uint32_t* abort_flag;     // set by a wait that ran out (zeroed)
+  int32_t* status;          // the problem's status word
+  long long spin_limit;     // cycles one wait may take
+  int32_t stall_test;       // 1: the first chunk of CTA 0 waits for a count nothing reaches
+};
+size_t flow_smem_bytes(int32_t LR, int32_t H);
+int flow_threads();
+int flow_max_segments();
+cudaError_t launch_flow(const FlowArgs& a, cudaStream_t stream);
+cudaError_t flow_max_ctas(size_t smem, int* per_sm);
 
 size_t anneal_smem_bytes(int32_t H, int32_t Rmax);
 // grid = (C, ceil(T/G)); cluster (C,1,1) when C > 1

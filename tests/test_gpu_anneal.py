@@ -22,11 +22,12 @@ def ia():
     return ia
 
 
-def _gpu(ia, inst, trials, betas, seed, shape=None, **kw):
+def _gpu(ia, inst, trials, betas, seed, shape=None, kernel=0, **kw):
     import torch
     prob = ia.Problem.from_instance(inst)
     if shape is not None:
         prob.set_launch(*shape)
+    prob.set_kernel(kernel)
     spins, cuts = ia.anneal(prob, trials, betas, seed, **kw)
     torch.cuda.synchronize()
     last = prob.last_launch()
@@ -192,4 +193,90 @@ def test_config2_full_size_sampled(ia):
         rs, rc = oracle.anneal(inst, betas, 1002, t_begin=t, t_count=1)
         np.testing.assert_array_equal(s[t], rs[0])
         assert cuts[t].item() == rc[0]
+    prob.destroy()
+
+
+# ---------------------------------------------------------------- persistent kernel
+FLOW_CASES = [
+    # X, Y, inst_seed, trials, sweeps, group_trials (0 = auto)
+    (4, 4, 71, 64, 20, 0),
+    (8, 6, 72, 37, 25, 0),
+    (50, 50, 73, 64, 40, 0),
+    (50, 50, 74, 1000, 12, 0),     # many groups: CTAs span several groups
+    (100, 100, 75, 512, 10, 16),
+    (200, 100, 76, 1024, 6, 0),
+    (200, 100, 77, 100, 8, 28),    # ragged last group
+    (140, 100, 78, 7, 20, 0),      # a single partial group over many CTAs
+    (24, 16, 79, 3000, 5, 8),
+]
+
+
+@pytest.mark.parametrize("X,Y,iseed,trials,S,G", FLOW_CASES)
+def test_flow_kernel_parity(ia, X, Y, iseed, trials, S, G):
+    inst = synth.torus_instance(X, Y, iseed)
+    betas = synth.linear_betas(0.1, 3.0, S)
+    seed = 0x5EED0000 + iseed
+    import torch
+    prob = ia.Problem.from_instance(inst)
+    prob.set_kernel(2)
+    if G:
+        prob.set_launch(G, 0, 0)
+    spins, cuts = ia.anneal(prob, trials, betas, seed)
+    torch.cuda.synchronize()
+    assert prob.last_kernel() == 2
+    assert prob.get_status() == 0
+    gs, gc = spins.cpu().numpy(), cuts.cpu().numpy()
+    prob.destroy()
+    if trials <= 128 or X * Y <= 2500:
+        rs, rc = oracle.anneal(inst, betas, seed, t_count=trials)
+        np.testing.assert_array_equal(gs, rs)
+        np.testing.assert_array_equal(gc, rc)
+    else:   # first, middle and last trial
+        for t in (0, trials // 2, trials - 1):
+            rs, rc = oracle.anneal(inst, betas, seed, t_begin=t, t_count=1)
+            np.testing.assert_array_equal(gs[t], rs[0])
+            assert gc[t] == rc[0]
+
+
+def test_flow_equals_strip_kernel_and_resume(ia):
+    import torch
+    inst = synth.torus_instance(200, 100, 80)
+    betas = synth.linear_betas(0.1, 3.0, 60)
+    prob = ia.Problem.from_instance(inst)
+    prob.set_kernel(1)
+    a_s, a_c = ia.anneal(prob, 1024, betas, 9)
+    prob.set_kernel(2)
+    b_s, b_c = ia.anneal(prob, 1024, betas, 9)
+    half, _ = ia.anneal(prob, 1024, betas[:25], 9)
+    c_s, c_c = ia.anneal(prob, 1024, betas[25:], 9, sweep_offset=25, init=half)
+    torch.cuda.synchronize()
+    assert torch.equal(a_s, b_s) and torch.equal(a_c, b_c)
+    assert torch.equal(a_s, c_s) and torch.equal(a_c, c_c)
+    # cuts only, no spins
+    _, d_c = ia.anneal(prob, 1024, betas, 9, want_spins=False)
+    torch.cuda.synchronize()
+    assert torch.equal(a_c, d_c)
+    prob.destroy()
+
+
+def test_flow_wait_timeout_is_reported_and_context_survives(ia):
+    """A wait that nothing satisfies (test switch) must give up after its
+    limit, report ISING_ERR_TIMEOUT through the status word, and leave the
+    context usable for the next, normal call."""
+    import torch
+    inst = synth.torus_instance(100, 100, 81)
+    betas = synth.linear_betas(0.1, 3.0, 20)
+    prob = ia.Problem.from_instance(inst)
+    prob.set_kernel(2)
+    prob.set_wait_limit(2_000_000, stall_test=1)       # about 1 ms of cycles
+    ia.anneal(prob, 256, betas, 3)
+    assert prob.get_status() == -7                      # ISING_ERR_TIMEOUT
+    assert prob.get_status() == 0                       # read-and-clear
+    prob.set_wait_limit(0, 0)
+    s, c = ia.anneal(prob, 64, betas, 3)
+    torch.cuda.synchronize()
+    assert prob.get_status() == 0
+    rs, rc = oracle.anneal(inst, betas, 3, t_count=64)
+    np.testing.assert_array_equal(s.cpu().numpy(), rs)
+    np.testing.assert_array_equal(c.cpu().numpy(), rc)
     prob.destroy()
