@@ -1,0 +1,150 @@
+"""Pins for the FP64 CNN oracle and the exact proposal step.
+
+* forward: a direct numpy loop over taps, channels and torus positions;
+* gradient: central finite differences in FP64;
+* loss: exact values (zero logits give ln 2);
+* targets: gauge invariance;
+* proposals: acceptance re-derived from whole-lattice energy differences.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import cnn
+
+torch = pytest.importorskip("torch")
+
+
+def _direct_conv(x, W, b):
+    """out[o, y, x] = b[o] + sum W[o, c, ky, kx] in[c, (y+ky-1)%Y, (x+kx-1)%X]."""
+    C, Y, X = x.shape
+    O = W.shape[0]
+    out = np.zeros((O, Y, X))
+    for o in range(O):
+        for y in range(Y):
+            for xx in range(X):
+                acc = b[o]
+                for c in range(C):
+                    for ky in range(3):
+                        for kx in range(3):
+                            acc += W[o, c, ky, kx] * x[c, (y + ky - 1) % Y, (xx + kx - 1) % X]
+                out[o, y, xx] = acc
+    return out
+
+
+def test_forward_matches_direct_loop():
+    X, Y = 5, 4
+    inst = synth.torus_instance(6, 4, 3)     # weights only; use a 6x4 torus
+    wr, wd = inst["w_right"], inst["w_down"]
+    X = 6
+    params = cnn.init_params(11) + 0.05 * np.random.default_rng(2).normal(size=cnn.N_PARAMS)
+    s = synth.random_spins(2, X * Y, 5)
+    got = cnn.forward(params, s, wr, wd, return_all=True)
+    p = cnn.unflatten(params)
+    for b in range(2):
+        x = cnn.features(s[b:b + 1], wr, wd)[0]
+        h1 = np.maximum(_direct_conv(x, p["W1"], p["b1"]), 0)
+        h2 = np.maximum(_direct_conv(h1, p["W2"], p["b2"]), 0)
+        h3 = np.maximum(_direct_conv(h2, p["W3"], p["b3"]), 0)
+        z = _direct_conv(h3, p["W4"], p["b4"])[0]
+        np.testing.assert_allclose(got["h1"][b], h1, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(got["z"][b], z, rtol=1e-11, atol=1e-11)
+
+
+def test_zero_network_loss_is_ln2():
+    params = np.zeros(cnn.N_PARAMS)
+    inst = synth.torus_instance(8, 6, 1)
+    s = synth.random_spins(3, 48, 1)
+    y = np.random.default_rng(0).integers(0, 2, size=(3, 48)).astype(np.uint8)
+    loss, g = cnn.loss_and_grad(params, s, y, inst["w_right"], inst["w_down"])
+    assert abs(loss - math.log(2.0)) < 1e-15
+    # with all weights zero, only the last bias gets a gradient: mean(sigmoid(0) - y)
+    b4 = cnn.N_PARAMS - 1
+    assert abs(g[b4] - (0.5 - y.mean())) < 1e-15
+    assert np.abs(np.delete(g, b4)).max() == 0.0
+
+
+def test_gradient_matches_finite_differences():
+    inst = synth.torus_instance(6, 4, 7)
+    s = synth.random_spins(2, 24, 3)
+    y = np.random.default_rng(4).integers(0, 2, size=(2, 24)).astype(np.uint8)
+    params = cnn.init_params(5) + 0.1 * np.random.default_rng(6).normal(size=cnn.N_PARAMS)
+    loss, g = cnn.loss_and_grad(params, s, y, inst["w_right"], inst["w_down"])
+    rng = np.random.default_rng(8)
+    idx = list(rng.choice(cnn.N_PARAMS, size=40, replace=False)) + [cnn.N_PARAMS - 1, 864, 864 + 32 + 9216]
+    h = 1e-6
+    for i in idx:
+        pp = params.copy(); pp[i] += h
+        pm = params.copy(); pm[i] -= h
+        lp, _ = cnn.loss_and_grad(pp, s, y, inst["w_right"], inst["w_down"])
+        lm, _ = cnn.loss_and_grad(pm, s, y, inst["w_right"], inst["w_down"])
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(g[i]), (i, fd, g[i])
+
+
+def test_flip_targets_are_gauge_invariant():
+    s = synth.random_spins(4, 50, 1)
+    r = synth.random_spins(4, 50, 2)
+    a = cnn.flip_targets(s, r)
+    b = cnn.flip_targets(s, -r)
+    np.testing.assert_array_equal(a, b)
+    assert (cnn.flip_targets(s, s) == 0).all() and (cnn.flip_targets(s, -s) == 0).all()
+    assert (a.sum(axis=1) <= 25).all()
+
+
+def _energy(inst, s):
+    return oracle.energy_csr(inst, s)
+
+
+@pytest.mark.parametrize("X,Y,tile", [(16, 8, 2), (16, 8, 4), (16, 8, 8), (18, 8, 5), (12, 4, 6)])
+def test_tile_proposals_are_exact(X, Y, tile):
+    inst = synth.torus_instance(X, Y, 21)
+    wr, wd = inst["w_right"], inst["w_down"]
+    s = synth.random_spins(6, X * Y, 9)
+    z = np.random.default_rng(3).normal(size=(6, Y, X))
+    new, acc = cnn.propose_tiles(s, z, wr, wd, tile)
+    # re-derive every decision from whole-lattice energies, tile by tile
+    ntx, nty = -(-X // tile), -(-Y // tile)
+    for b in range(6):
+        cur = s[b].copy()
+        n_acc = 0
+        for phase in (0, 1):
+            for ty in range(nty):
+                for tx in range(ntx):
+                    if (tx + ty) % 2 != phase:
+                        continue
+                    m = np.zeros((Y, X), dtype=bool)
+                    m[ty * tile:(ty + 1) * tile, tx * tile:(tx + 1) * tile] = \
+                        z[b, ty * tile:(ty + 1) * tile, tx * tile:(tx + 1) * tile] > 0
+                    if not m.any():
+                        continue
+                    cand = cur.copy()
+                    cand[m.reshape(-1)] *= -1
+                    if _energy(inst, cand) <= _energy(inst, cur):
+                        cur = cand
+                        n_acc += 1
+        np.testing.assert_array_equal(new[b], cur)
+        assert acc[b] == n_acc
+        assert _energy(inst, new[b]) <= _energy(inst, s[b])
+
+
+def test_odd_tile_counts_are_rejected():
+    inst = synth.torus_instance(12, 8, 1)
+    with pytest.raises(ValueError):
+        cnn.propose_tiles(synth.random_spins(1, 96, 1), np.zeros((1, 8, 12)), inst["w_right"], inst["w_down"], 4)
+
+
+def test_global_proposal_is_exact():
+    X, Y = 10, 6
+    inst = synth.torus_instance(X, Y, 31)
+    s = synth.random_spins(8, X * Y, 4)
+    z = np.random.default_rng(5).normal(size=(8, Y, X))
+    new, acc = cnn.propose_global(s, z, inst["w_right"], inst["w_down"])
+    for b in range(8):
+        cand = s[b] * np.where(z[b].reshape(-1) > 0, -1, 1).astype(np.int8)
+        take = _energy(inst, cand) <= _energy(inst, s[b])
+        np.testing.assert_array_equal(new[b], cand if take else s[b])
+        assert acc[b] == int(take)
