@@ -245,6 +245,77 @@ int ising_anneal_noalloc(ising_problem* p, int32_t trials, const double* betas, 
                          uint64_t seed, uint32_t sweep_offset, const int8_t* init_spins,
                          int8_t* out_spins, int32_t* out_cuts, void* cuda_stream);
 
+/* ======================================================================
+ * Learned proposals (this project's extension; the paper's own update rule
+ * is unpublished, Section III).  A circular-padded CNN on the torus with
+ * four 3x3 convolutions of 32 channels (ReLU between them) maps, per site,
+ * the inputs (s_i, w right, w down) to a logit for "flip this spin".
+ * Proposals built from the logits are accepted only by their exact integer
+ * energy change (Eq. 2), so they can never make a trial worse.
+ *
+ * Parameters: ISING_CNN_PARAMS floats in the order W1[32,3,3,3], b1[32],
+ * W2[32,32,3,3], b2[32], W3[32,32,3,3], b3[32], W4[1,32,3,3], b4[1], each
+ * weight laid out (out channel, in channel, ky, kx); convolution:
+ * out[y,x] = b + sum W[o,c,ky,kx] in[c,(y+ky-1) mod Y,(x+kx-1) mod X].
+ * Weights are used rounded to BF16, activations are stored in BF16, sums
+ * accumulate in FP32.
+ * ====================================================================== */
+#define ISING_CNN_PARAMS 19681
+typedef struct ising_cnn ising_cnn;
+
+/* ising_cnn_create -- copy ISING_CNN_PARAMS host floats to a new network on
+ * the current device (Adam state zeroed).  Errors: ISING_ERR_ARG, _OOM, _CUDA. */
+int ising_cnn_create(const float* params, ising_cnn** out);
+void ising_cnn_destroy(ising_cnn* net);
+/* host copy of the FP32 master parameters */
+int ising_cnn_get_params(const ising_cnn* net, float* params);
+/* replace the parameters (host) and reset the Adam state */
+int ising_cnn_set_params(ising_cnn* net, const float* params);
+
+/* Device workspace (bytes) for B configurations of n spins; train != 0 for
+ * ising_cnn_grad.  The caller allocates it; the calls allocate nothing. */
+size_t ising_cnn_workspace_bytes(int32_t B, int32_t n, int32_t train);
+
+/*
+ * ising_cnn_forward -- logits for B configurations of problem p.
+ * spins    device [B][n] int8 (>0 is +1).
+ * logits   device [B][n] float (site order y*X + x).
+ * ws       device workspace of at least ising_cnn_workspace_bytes(B, n, 0).
+ * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (X > 2,000), ISING_ERR_CUDA.
+ */
+int ising_cnn_forward(const ising_cnn* net, const ising_problem* p, const int8_t* spins, int32_t B,
+                      float* logits, void* ws, size_t ws_bytes, void* cuda_stream);
+
+/*
+ * ising_cnn_grad -- mean binary cross-entropy of the logits against the flip
+ * targets and its gradient with respect to the parameters.
+ * targets  device [B][n] uint8 (1 = the site should flip).
+ * grad     device ISING_CNN_PARAMS floats (overwritten).
+ * loss     device float (overwritten).
+ * ws       device workspace of at least ising_cnn_workspace_bytes(B, n, 1).
+ */
+int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* spins, const uint8_t* targets,
+                   int32_t B, float* grad, float* loss, void* ws, size_t ws_bytes, void* cuda_stream);
+
+/* ising_cnn_adam_step -- one Adam update of the FP32 master parameters with
+ * the device gradient `grad`, then refresh the BF16 copies. */
+int ising_cnn_adam_step(ising_cnn* net, const float* grad, float lr, float beta1, float beta2, float eps,
+                        void* cuda_stream);
+
+/*
+ * ising_propose -- apply proposals built from the logits, each accepted iff
+ * its exact energy change dE = -2 sum_{i in B, j ~ i, j not in B} w_ij s_i s_j
+ * is <= 0.
+ * tile > 0: B = sites with logit > 0 in each tile of side `tile`; tiles with
+ *   even (tx + ty) first, then odd.  The number of tiles along each side must
+ *   be 1 or even (ISING_ERR_ARG otherwise).
+ * tile = 0: B = all sites with logit > 0 (whole-lattice proposal).
+ * spins    device [B][n] int8, updated in place.
+ * accepted device [B] int32 or NULL: proposals taken per configuration.
+ */
+int ising_propose(const ising_problem* p, int8_t* spins, int32_t B, const float* logits, int32_t tile,
+                  int32_t* accepted, void* cuda_stream);
+
 /* ising_strerror -- static description of a status code. */
 const char* ising_strerror(int code);
 

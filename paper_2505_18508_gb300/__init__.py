@@ -223,3 +223,92 @@ class BatchPlan:
             self.destroy()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- learned proposals
+CNN_PARAMS = 19681
+
+
+class CNN:
+    """The proposal network on the device (ising_cnn_*); params: float array of CNN_PARAMS."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.shape == (CNN_PARAMS,)
+        out = ctypes.c_void_p()
+        check(lib().ising_cnn_create(p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out)), "ising_cnn_create")
+        self._h = out
+        self._ws = {}
+
+    @property
+    def handle(self):
+        return self._h
+
+    def params(self):
+        out = np.zeros(CNN_PARAMS, dtype=np.float32)
+        check(lib().ising_cnn_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p)), "ising_cnn_get_params")
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        check(lib().ising_cnn_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p)), "ising_cnn_set_params")
+
+    def _workspace(self, B, n, train):
+        torch = _torch()
+        need = int(lib().ising_cnn_workspace_bytes(int(B), int(n), int(train)))
+        key = bool(train)
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 1), dtype=torch.uint8, device="cuda")
+            self._ws[key] = ws
+        return ws, need
+
+    def forward(self, prob, spins, out=None, stream=None):
+        torch = _torch()
+        spins = spins.contiguous()
+        B = spins.shape[0]
+        if out is None:
+            out = torch.empty((B, prob.n), dtype=torch.float32, device=spins.device)
+        ws, need = self._workspace(B, prob.n, 0)
+        check(lib().ising_cnn_forward(self._h, prob.handle, _dptr(spins), int(B), _dptr(out), _dptr(ws),
+                                      ctypes.c_size_t(ws.numel()), _stream_ptr(stream)), "ising_cnn_forward")
+        return out
+
+    def grad(self, prob, spins, targets, stream=None):
+        torch = _torch()
+        spins = spins.contiguous()
+        targets = targets.contiguous()
+        B = spins.shape[0]
+        g = torch.empty(CNN_PARAMS, dtype=torch.float32, device=spins.device)
+        loss = torch.empty(1, dtype=torch.float32, device=spins.device)
+        ws, need = self._workspace(B, prob.n, 1)
+        check(lib().ising_cnn_grad(self._h, prob.handle, _dptr(spins), _dptr(targets), int(B), _dptr(g), _dptr(loss),
+                                   _dptr(ws), ctypes.c_size_t(ws.numel()), _stream_ptr(stream)), "ising_cnn_grad")
+        return loss, g
+
+    def adam_step(self, grad, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        check(lib().ising_cnn_adam_step(self._h, _dptr(grad), ctypes.c_float(lr), ctypes.c_float(beta1),
+                                        ctypes.c_float(beta2), ctypes.c_float(eps), _stream_ptr(stream)),
+              "ising_cnn_adam_step")
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None:
+            lib().ising_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def propose(prob, spins, logits, tile, accepted=None, stream=None):
+    """Exact-acceptance proposals in place on spins (see ising_propose); returns accepted [B]."""
+    torch = _torch()
+    B = spins.shape[0]
+    if accepted is None:
+        accepted = torch.zeros(B, dtype=torch.int32, device=spins.device)
+    check(lib().ising_propose(prob.handle, _dptr(spins), int(B), _dptr(logits.contiguous()), int(tile),
+                              _dptr(accepted), _stream_ptr(stream)), "ising_propose")
+    return accepted

@@ -47,6 +47,16 @@ _SIGNATURES = {
     "ising_last_kernel": (ctypes.c_int, [_vp, _i32p]),
     "ising_get_status": (ctypes.c_int, [_vp, _vp, _i32p]),
     "ising_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64, _i32]),
+    "ising_cnn_create": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+    "ising_cnn_destroy": (None, [_vp]),
+    "ising_cnn_get_params": (ctypes.c_int, [_vp, _vp]),
+    "ising_cnn_set_params": (ctypes.c_int, [_vp, _vp]),
+    "ising_cnn_workspace_bytes": (ctypes.c_size_t, [_i32, _i32, _i32]),
+    "ising_cnn_forward": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, ctypes.c_size_t, _vp]),
+    "ising_cnn_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "ising_cnn_adam_step": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                           ctypes.c_float, _vp]),
+    "ising_propose": (ctypes.c_int, [_vp, _vp, _i32, _vp, _i32, _vp, _vp]),
     "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
