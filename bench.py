@@ -143,6 +143,67 @@ def ttt_stats(cuts, t_step_s, trials, sweeps, quality=0.999):
             "cut_mean": float(cuts.mean()), "cut_min": int(cuts.min())}
 
 
+def learned_leg(sweeps=10000, every=100, tile=10, n_train=256, train_sweeps=1000, steps=800):
+    """Config 5 of the workload set: 200x100 tori, 8 seeds x 512 trials, the
+    plain annealer against the learned form (network retrained on 20,000-spin
+    snapshots of the plain annealer on held-out seeds) at a matched 99.9%
+    target: per seed, best = highest cut either form found, target =
+    ceil(0.999 best), TTT = (batch wall time / trials) * r(P_s) (Eq. 3, 5)."""
+    import torch
+    import oracle
+    import paper_2505_18508_gb300 as ia
+    from oracle import cnn as ocnn
+    from paper_2505_18508_gb300 import learned
+    t0 = time.perf_counter()
+    tb = synth.linear_betas(0.1, 3.0, train_sweeps)
+    train = [synth.torus_instance(200, 100, 40000 + k) for k in range(n_train)]
+    data = learned.make_dataset(train, tb, every, snap_trials=4, target="future")
+    net = ia.CNN(ocnn.init_params(3, scale=0.7))
+    losses = learned.train(net, data, steps, batch=16, lr=2e-3, log_every=steps // 4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    for d in data:
+        d[0].destroy()
+    betas = synth.linear_betas(0.1, 3.0, sweeps)
+    T = 512
+    rows = []
+    for q in range(8):
+        inst = synth.torus_instance(200, 100, 30000 + q)
+        prob = ia.Problem.from_instance(inst)
+        seed = 70000 + q
+        torch.cuda.synchronize(); a = time.perf_counter()
+        _, cp = ia.anneal(prob, T, betas, seed)
+        torch.cuda.synchronize(); b = time.perf_counter()
+        st = {}
+        _, cl = learned.anneal_learned(prob, net, T, betas, seed, every=every, tile=tile, stats=st)
+        torch.cuda.synchronize(); c = time.perf_counter()
+        cp, cl = cp.cpu().numpy(), cl.cpu().numpy()
+        best = int(max(cp.max(), cl.max()))
+        tgt = oracle.target_cut(best)
+        row = {"seed": 30000 + q, "best": best, "target": tgt}
+        for name, cuts, wall in (("plain", cp, b - a), ("learned", cl, c - b)):
+            Ps = oracle.success_probability(cuts, tgt)
+            r = oracle.repetitions(Ps)
+            row[name] = {"P_s": Ps, "mean_cut": float(cuts.mean()), "wall_s": wall,
+                         "TTT_s": (wall / T) * r if math.isfinite(r) else None}
+        row["learned"]["accepted_per_trial"] = st.get("accepted_per_trial")
+        rows.append(row)
+        prob.destroy()
+    net.destroy()
+
+    def med(key):
+        v = [r[key]["TTT_s"] for r in rows if r[key]["TTT_s"] is not None]
+        return float(np.median(v)) if v else None
+    return {"workload": "200x100 tori, seeds 30000-30007, 512 trials each, 10,000 sweeps, beta 0.1->3.0; "
+                        "proposals every 100 sweeps, tiles 10x10",
+            "train": {"instances": n_train, "snapshot_sweeps": train_sweeps, "steps": steps, "loss": losses,
+                      "seconds": t_train},
+            "median_TTT_s": {"plain": med("plain"), "learned": med("learned")},
+            "reached": {"plain": sum(r["plain"]["TTT_s"] is not None for r in rows),
+                        "learned": sum(r["learned"]["TTT_s"] is not None for r in rows)},
+            "per_seed": rows}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -188,6 +249,7 @@ def main():
     ap.add_argument("--sweeps", type=int, default=None, help="override (profiling runs only)")
     ap.add_argument("--trials", type=int, default=None, help="override (profiling runs only)")
     ap.add_argument("--launch", default=None, help="G,C,threads launch shape (default: automatic)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -295,6 +357,9 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_throughput(w, inst)
+    learned_cmp = None
+    if rank == 0 and not args.no_learned and not args.sweeps and not args.trials:
+        learned_cmp = learned_leg()
 
     if rank == 0:
         line = {
@@ -311,6 +376,7 @@ def main():
             "cpu_baseline": cpu,
             "clocks": clk,
             "ttt_99_9": stats,
+            "learned_vs_plain": learned_cmp,
             "wall_s_timed": wall,
             "step_ms": step_ms,
         }

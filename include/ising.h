@@ -316,6 +316,16 @@ int ising_cnn_adam_step(ising_cnn* net, const float* grad, float lr, float beta1
 int ising_propose(const ising_problem* p, int8_t* spins, int32_t B, const float* logits, int32_t tile,
                   int32_t* accepted, void* cuda_stream);
 
+/*
+ * ising_flip_targets -- training targets for the network: for each of B
+ * configurations, y_i = [s_i != r'_i] where r' is ref or -ref, whichever is
+ * closer to s in Hamming distance (on a tie, the one that keeps site 0); the
+ * global flip s -> -s is a symmetry of H, so only the relative orientation
+ * is meaningful.  spins, ref: device [B][n] int8; targets: device [B][n] uint8.
+ */
+int ising_flip_targets(const int8_t* spins, const int8_t* ref, int32_t B, int32_t n, uint8_t* targets,
+                       void* cuda_stream);
+
 /* ising_strerror -- static description of a status code. */
 const char* ising_strerror(int code);
 

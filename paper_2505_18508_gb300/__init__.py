@@ -312,3 +312,16 @@ def propose(prob, spins, logits, tile, accepted=None, stream=None):
     check(lib().ising_propose(prob.handle, _dptr(spins), int(B), _dptr(logits.contiguous()), int(tile),
                               _dptr(accepted), _stream_ptr(stream)), "ising_propose")
     return accepted
+
+
+def flip_targets(spins, ref, out=None, stream=None):
+    """Gauge-aligned flip targets (ising_flip_targets): uint8 [B, n]."""
+    torch = _torch()
+    spins = spins.contiguous()
+    ref = ref.contiguous()
+    B, n = spins.shape
+    if out is None:
+        out = torch.empty((B, n), dtype=torch.uint8, device=spins.device)
+    check(lib().ising_flip_targets(_dptr(spins), _dptr(ref), int(B), int(n), _dptr(out), _stream_ptr(stream)),
+          "ising_flip_targets")
+    return out

@@ -57,6 +57,7 @@ _SIGNATURES = {
     "ising_cnn_adam_step": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                            ctypes.c_float, _vp]),
     "ising_propose": (ctypes.c_int, [_vp, _vp, _i32, _vp, _i32, _vp, _vp]),
+    "ising_flip_targets": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
     "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 

@@ -113,8 +113,41 @@ __global__ void __launch_bounds__(1024) propose_global_kernel(int8_t* __restrict
     if (z[i] > 0.f) s[i] = s[i] > 0 ? int8_t(-1) : int8_t(1);
 }
 
+// y = [s != r'] with r' = r or -r, whichever is closer to s (a tie keeps site 0)
+__global__ void __launch_bounds__(1024) flip_targets_kernel(const int8_t* __restrict__ spins,
+                                                            const int8_t* __restrict__ ref, int n,
+                                                            uint8_t* __restrict__ targets) {
+  __shared__ int red[32];
+  __shared__ int s_flip;
+  const int b = blockIdx.x;
+  const int8_t* s = spins + static_cast<size_t>(b) * n;
+  const int8_t* r = ref + static_cast<size_t>(b) * n;
+  int d = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) d += (s[i] > 0) != (r[i] > 0);
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xFFFFFFFFu, d, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t += red[w];
+    s_flip = (2 * t > n) || (2 * t == n && ((s[0] > 0) != (r[0] > 0)));
+  }
+  __syncthreads();
+  const int f = s_flip;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    targets[static_cast<size_t>(b) * n + i] = static_cast<uint8_t>(((s[i] > 0) != (r[i] > 0)) ^ f);
+}
+
 }  // namespace
 }  // namespace ising
+
+extern "C" int ising_flip_targets(const int8_t* spins, const int8_t* ref, int32_t B, int32_t n, uint8_t* targets,
+                                  void* cuda_stream) {
+  if (B < 0 || n <= 0 || (B > 0 && (!spins || !ref || !targets))) return ISING_ERR_ARG;
+  if (B == 0) return ISING_OK;
+  ising::flip_targets_kernel<<<B, 1024, 0, static_cast<cudaStream_t>(cuda_stream)>>>(spins, ref, n, targets);
+  return cudaGetLastError() == cudaSuccess ? ISING_OK : ISING_ERR_CUDA;
+}
 
 extern "C" int ising_propose(const ising_problem* p, int8_t* spins, int32_t B, const float* logits, int32_t tile,
                              int32_t* accepted, void* cuda_stream) {
