@@ -204,6 +204,36 @@ def learned_leg(sweeps=10000, every=100, tile=10, n_train=256, train_sweeps=1000
             "per_seed": rows}
 
 
+def batched_leg(reps=2):
+    """Config 3: the 96-instance uneven batch ({50,100,140,200}x100, 32-512
+    trials, 2,000-20,000 sweeps) as one graph-replayed persistent launch."""
+    import torch
+    import paper_2505_18508_gb300 as ia
+    cfg = synth.batched_config()
+    insts = [synth.torus_instance(c["X"], c["Y"], c["inst_seed"]) for c in cfg]
+    probs = [ia.Problem.from_instance(i) for i in insts]
+    trials = [c["trials"] for c in cfg]
+    sweeps = [c["sweeps"] for c in cfg]
+    betas = [synth.linear_betas(0.1, 3.0, S) for S in sweeps]
+    seeds = [c["seed"] for c in cfg]
+    plan = ia.BatchPlan(probs, trials, sweeps, betas, seeds)
+    plan.launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ups = sum(t * s * i["n"] for t, s, i in zip(trials, sweeps, insts))
+    plan.destroy()
+    for p in probs:
+        p.destroy()
+    return {"workload": "96 tori {50,100,140,200}x100, 32-512 trials, 2,000-20,000 sweeps, one CUDA-graph replay",
+            "updates": ups, "ms_per_replay": ms, "value": ups / (ms / 1e3), "unit": "spin-updates/s"}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -357,6 +387,9 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_throughput(w, inst)
+    batched = None
+    if rank == 0 and not args.sweeps and not args.trials:
+        batched = batched_leg()
     learned_cmp = None
     if rank == 0 and not args.no_learned and not args.sweeps and not args.trials:
         learned_cmp = learned_leg()
@@ -376,6 +409,7 @@ def main():
             "cpu_baseline": cpu,
             "clocks": clk,
             "ttt_99_9": stats,
+            "batched": batched,
             "learned_vs_plain": learned_cmp,
             "wall_s_timed": wall,
             "step_ms": step_ms,

@@ -44,32 +44,22 @@ def torus_csr(X: int, Y: int, w_right: np.ndarray, w_down: np.ndarray):
     """CSR (row_ptr int64[n+1], col int32[nnz], J int8[nnz]) of the torus.
 
     J holds -w (Eq. 2 with J_ij = -w_ij).  Each row lists its four neighbours
-    sorted by column index.  Works for any X, Y >= 1 (tiny or odd dimensions
+    sorted by column index (right, left, down, up for equal columns, which only
+    happen when a side is 2).  Works for any X, Y >= 1 (tiny or odd dimensions
     are produced on purpose by the validation tests).
     """
     n = X * Y
-    rows = []
-    for y in range(Y):
-        for x in range(X):
-            i = y * X + x
-            nb = {}
-            def add(j, w):
-                nb.setdefault(j, []).append(int(w))
-            add(y * X + (x + 1) % X, w_right[y, x])
-            add(y * X + (x - 1) % X, w_right[y, (x - 1) % X])
-            add(((y + 1) % Y) * X + x, w_down[y, x])
-            add(((y - 1) % Y) * X + x, w_down[(y - 1) % Y, x])
-            entries = []
-            for j in sorted(nb):
-                for w in nb[j]:
-                    entries.append((j, -w))
-            rows.append(entries)
-    row_ptr = np.zeros(n + 1, dtype=np.int64)
-    for i, e in enumerate(rows):
-        row_ptr[i + 1] = row_ptr[i] + len(e)
-    col = np.array([j for e in rows for (j, _) in e], dtype=np.int32)
-    J = np.array([v for e in rows for (_, v) in e], dtype=np.int8)
-    return row_ptr, col, J
+    y, x = np.divmod(np.arange(n, dtype=np.int64), X)
+    wr = np.asarray(w_right, dtype=np.int64)
+    wd = np.asarray(w_down, dtype=np.int64)
+    cols = np.stack([y * X + (x + 1) % X, y * X + (x - 1) % X,
+                     ((y + 1) % Y) * X + x, ((y - 1) % Y) * X + x], axis=1)
+    ws = np.stack([wr[y, x], wr[y, (x - 1) % X], wd[y, x], wd[(y - 1) % Y, x]], axis=1)
+    order = np.argsort(cols, axis=1, kind="stable")
+    cols = np.take_along_axis(cols, order, axis=1)
+    ws = np.take_along_axis(ws, order, axis=1)
+    row_ptr = np.arange(n + 1, dtype=np.int64) * 4
+    return row_ptr, cols.reshape(-1).astype(np.int32), (-ws).reshape(-1).astype(np.int8)
 
 
 def torus_instance(X: int, Y: int, inst_seed: int):
