@@ -7,12 +7,12 @@
 // Convolution: out[y,x] = b + sum W[o,c,ky,kx] in[c,(y+ky-1) mod Y,(x+kx-1) mod X].
 //
 // Numerics: weights are rounded to BF16, activations are stored as BF16
-// [batch][site][32], and every sum accumulates in FP32.  The two 32->32
-// layers (and their input gradients) are implicit GEMMs on the tensor cores:
-// per output row, M = pixels, N = 32 output channels, K = 9 taps x 32 input
-// channels, with the input rows (and the periodic wrap) gathered through
-// shared memory and ldmatrix row addresses.  The 3->32 and 32->1 layers and
-// the weight gradients run on the CUDA cores.
+// [batch][site][32], and every sum accumulates in FP32.  All four forward
+// convolutions and the two 32->32 input gradients are implicit GEMMs on the
+// tcgen05 tensor cores (conv_tc.cu: per output row, M = pixels, N = output
+// channels, K = 9 taps x input channels, accumulators in tensor memory).  The
+// layer-4 input gradient, the loss and the weight gradients run on the CUDA
+// cores.
 //
 // Parameters: one flat FP32 vector in the order W1[32,3,3,3], b1[32],
 // W2[32,32,3,3], b2[32], W3[32,32,3,3], b3[32], W4[1,32,3,3], b4[1].
@@ -29,227 +29,47 @@ namespace {
 
 constexpr int OFF_W1 = 0, OFF_B1 = 864, OFF_W2 = 896, OFF_B2 = 10112, OFF_W3 = 10144, OFF_B3 = 19360,
               OFF_W4 = 19392, OFF_B4 = 19680, NPARAM = 19681;
-constexpr int PIX_STRIDE = 40;   // bf16 per pixel row in shared memory (32 + 8 padding: no bank conflicts)
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16(v)); }
 
 // ------------------------------------------------------------------ weights
-// fp32 master -> BF16-rounded copies used by the kernels:
-//   w1r[864], w4r[288]          fp32 values already rounded to BF16
-//   wf2/wf3 [9][32 out][40]     forward weights, BF16, [tap][out][in] (+pad)
-//   wb2/wb3 [9][32 in][40]      input-gradient weights: W'[in][out][tap'] = W[out][in][8-tap]
-__global__ void prepare_weights_kernel(const float* __restrict__ master, float* __restrict__ w1r,
-                                       float* __restrict__ w4r, __nv_bfloat16* __restrict__ wf2,
-                                       __nv_bfloat16* __restrict__ wf3, __nv_bfloat16* __restrict__ wb2,
-                                       __nv_bfloat16* __restrict__ wb3) {
+// fp32 master -> the copies the kernels read: w4r[288], W4 rounded to BF16
+// (held in fp32) for the layer-4 backward, and the BF16 tensor-core operands.
+__global__ void prepare_w4r_kernel(const float* __restrict__ master, float* __restrict__ w4r) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < 864) w1r[t] = bf16r(master[OFF_W1 + t]);
   if (t < 288) w4r[t] = bf16r(master[OFF_W4 + t]);
-  if (t < 9 * 32 * PIX_STRIDE) {
-    const int tap = t / (32 * PIX_STRIDE);
-    const int rem = t - tap * 32 * PIX_STRIDE;
-    const int o = rem / PIX_STRIDE, i = rem - o * PIX_STRIDE;
-    float f2 = 0.f, f3 = 0.f, b2 = 0.f, b3 = 0.f;
-    if (i < 32) {
-      f2 = master[OFF_W2 + (o * 32 + i) * 9 + tap];
-      f3 = master[OFF_W3 + (o * 32 + i) * 9 + tap];
-      // input gradient: output channel o is the forward input channel, input
-      // channel i the forward output channel, taps mirrored
-      b2 = master[OFF_W2 + (i * 32 + o) * 9 + (8 - tap)];
-      b3 = master[OFF_W3 + (i * 32 + o) * 9 + (8 - tap)];
-    }
-    wf2[t] = __float2bfloat16(f2);
-    wf3[t] = __float2bfloat16(f3);
-    wb2[t] = __float2bfloat16(b2);
-    wb3[t] = __float2bfloat16(b3);
-  }
 }
 
-// ------------------------------------------------------------------ layer 1
-// x = (s, w_right, w_down) at the 9 neighbours -> relu(conv + b1) as BF16.
-__global__ void __launch_bounds__(256) layer1_kernel(const int8_t* __restrict__ spins,
-                                                     const uint8_t* __restrict__ eflags, int B, int X, int Y,
-                                                     const float* __restrict__ w1r, const float* __restrict__ master,
-                                                     __nv_bfloat16* __restrict__ h1) {
-  __shared__ float w[864];
-  __shared__ float bias[32];
-  for (int i = threadIdx.x; i < 864; i += blockDim.x) w[i] = w1r[i];
-  if (threadIdx.x < 32) bias[threadIdx.x] = master[OFF_B1 + threadIdx.x];
-  __syncthreads();
-  const int n = X * Y;
-  const long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p >= static_cast<long long>(B) * n) return;
-  const int b = static_cast<int>(p / n);
-  const int site = static_cast<int>(p - static_cast<long long>(b) * n);
-  const int y = site / X, x = site - y * X;
-  float in[3][9];
-  for (int ky = 0; ky < 3; ++ky) {
-    int yy = y + ky - 1;
-    yy = yy < 0 ? yy + Y : (yy >= Y ? yy - Y : yy);
-    for (int kx = 0; kx < 3; ++kx) {
-      int xx = x + kx - 1;
-      xx = xx < 0 ? xx + X : (xx >= X ? xx - X : xx);
-      const int j = yy * X + xx;
-      const uint8_t f = eflags[j];
-      in[0][ky * 3 + kx] = spins[static_cast<size_t>(b) * n + j] > 0 ? 1.f : -1.f;
-      in[1][ky * 3 + kx] = (f & 1u) ? -1.f : 1.f;
-      in[2][ky * 3 + kx] = (f & 2u) ? -1.f : 1.f;
-    }
-  }
-  __align__(16) __nv_bfloat16 out[32];
-#pragma unroll 4
-  for (int o = 0; o < 32; ++o) {
-    float acc = bias[o];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int t = 0; t < 9; ++t) acc = fmaf(w[(o * 3 + c) * 9 + t], in[c][t], acc);
-    out[o] = __float2bfloat16(fmaxf(acc, 0.f));
-  }
-  uint4* dst = reinterpret_cast<uint4*>(h1 + static_cast<size_t>(p) * 32);
-  const uint4* src = reinterpret_cast<const uint4*>(out);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) dst[q] = src[q];
+// Canonical tensor-core layouts: element (tap, k, n) at
+// (((tap*KC + k/8)*NG + n/8)*8 + n%8)*8 + k%8, KC = K/8 input chunks, NG = N/8.
+__device__ __forceinline__ int tc_index(int tap, int k, int n, int KC, int NG) {
+  return (((tap * KC + (k >> 3)) * NG + (n >> 3)) * 8 + (n & 7)) * 8 + (k & 7);
 }
 
-// ------------------------------------------------------------------ 32 -> 32 on tensor cores
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// One CTA per (image b, output row y).  mode 0: out = relu(conv + bias);
-// mode 1: out = conv * [mask > 0] (input gradient through the previous ReLU).
-template <int kMode>
-__global__ void __launch_bounds__(256) conv32_kernel(const __nv_bfloat16* __restrict__ in,
-                                                     const __nv_bfloat16* __restrict__ wt,
-                                                     const float* __restrict__ bias,
-                                                     const __nv_bfloat16* __restrict__ mask, int X, int Y,
-                                                     __nv_bfloat16* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(smem);            // [9][32][40]
-  __nv_bfloat16* sin = sw + 9 * 32 * PIX_STRIDE;                          // [3][X][40]
-  const int b = blockIdx.y, y = blockIdx.x;
-  const int n = X * Y;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // weights: 9*32 rows of 80 bytes
-  for (int i = tid; i < 9 * 32 * PIX_STRIDE / 8; i += blockDim.x)
-    reinterpret_cast<uint4*>(sw)[i] = reinterpret_cast<const uint4*>(wt)[i];
-  // input rows y-1, y, y+1 (periodic), 64 bytes per pixel into 80-byte rows
-  for (int i = tid; i < 3 * X * 4; i += blockDim.x) {
-    const int r = i / (X * 4);
-    const int rem = i - r * X * 4;
-    const int px = rem >> 2, q = rem & 3;
-    int yy = y + r - 1;
-    yy = yy < 0 ? yy + Y : (yy >= Y ? yy - Y : yy);
-    const uint4 v = reinterpret_cast<const uint4*>(in + (static_cast<size_t>(b) * n + yy * X + px) * 32)[q];
-    reinterpret_cast<uint4*>(sin + (r * X + px) * PIX_STRIDE)[q] = v;
+// tc1: layer 1 (K = 16 with 3 used, N = 32); tc2f/tc3f: forward 32 -> 32;
+// tc2b/tc3b: input gradients W'[in][out][tap'] = W[out][in][8 - tap'];
+// tc4: layer 4 (K = 32, N = 16 with 1 used)
+__global__ void prepare_tc_weights_kernel(const float* __restrict__ master, __nv_bfloat16* __restrict__ tc1,
+                                          __nv_bfloat16* __restrict__ tc2f, __nv_bfloat16* __restrict__ tc3f,
+                                          __nv_bfloat16* __restrict__ tc2b, __nv_bfloat16* __restrict__ tc3b,
+                                          __nv_bfloat16* __restrict__ tc4) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 9 * 16 * 32) {                       // (tap, k < 16, n < 32)
+    const int tap = t / 512, rem = t - tap * 512, k = rem / 32, n = rem - k * 32;
+    tc1[tc_index(tap, k, n, 2, 4)] = __float2bfloat16(k < 3 ? master[OFF_W1 + (n * 3 + k) * 9 + tap] : 0.f);
   }
-  __syncthreads();
-  const uint32_t sin_base = static_cast<uint32_t>(__cvta_generic_to_shared(sin));
-  const uint32_t sw_base = static_cast<uint32_t>(__cvta_generic_to_shared(sw));
-  const int mt_count = (X + 15) >> 4;
-  const int g = lane >> 2, tg = lane & 3;
-  for (int mt = warp; mt < mt_count; mt += 8) {
-    float acc[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
-    // this lane's ldmatrix row: pixel x0 + (lane & 15), channel half (lane >> 4)
-    const int prow = (mt << 4) + (lane & 15);
-    const int pxl = prow < X ? prow : X - 1;   // rows past the end read a valid pixel, results dropped
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-      const int ky = tap / 3, kx = tap - ky * 3;
-      int sx = pxl + kx - 1;
-      sx = sx < 0 ? sx + X : (sx >= X ? sx - X : sx);
-      const uint32_t arow = sin_base + ((ky * X + sx) * PIX_STRIDE + (lane >> 4) * 8) * 2;
-#pragma unroll
-      for (int ks = 0; ks < 2; ++ks) {
-        uint32_t a0, a1, a2, a3;
-        ldsm_x4(arow + ks * 32, a0, a1, a2, a3);
-#pragma unroll
-        for (int np = 0; np < 2; ++np) {   // two n8 tiles per ldmatrix.x4
-          const int nrow = np * 16 + ((lane >> 4) << 3) + (lane & 7);
-          const int kcol = ks * 16 + ((lane >> 3) & 1) * 8;
-          uint32_t b0, b1, b2, b3;
-          ldsm_x4(sw_base + ((tap * 32 + nrow) * PIX_STRIDE + kcol) * 2, b0, b1, b2, b3);
-          mma_bf16(acc[np * 2 + 0], a0, a1, a2, a3, b0, b1);
-          mma_bf16(acc[np * 2 + 1], a0, a1, a2, a3, b2, b3);
-        }
-      }
-    }
-    // epilogue: rows g and g+8 of the tile, channels nt*8 + 2tg, +1
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int px = (mt << 4) + g + half * 8;
-      if (px >= X) continue;
-      const size_t pix = static_cast<size_t>(b) * n + y * X + px;
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int ch = nt * 8 + 2 * tg;
-        float v0 = acc[nt][half * 2 + 0], v1 = acc[nt][half * 2 + 1];
-        if (kMode == 0) {
-          v0 = fmaxf(v0 + bias[ch], 0.f);
-          v1 = fmaxf(v1 + bias[ch + 1], 0.f);
-        } else {
-          const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(mask + pix * 32 + ch);
-          v0 = __bfloat162float(m.x) > 0.f ? v0 : 0.f;
-          v1 = __bfloat162float(m.y) > 0.f ? v1 : 0.f;
-        }
-        *reinterpret_cast<__nv_bfloat162*>(out + pix * 32 + ch) = __floats2bfloat162_rn(v0, v1);
-      }
-    }
+  if (t < 9 * 32 * 32) {                       // (tap, k < 32, n < 32)
+    const int tap = t / 1024, rem = t - tap * 1024, k = rem / 32, n = rem - k * 32;
+    const int i = tc_index(tap, k, n, 4, 4);
+    tc2f[i] = __float2bfloat16(master[OFF_W2 + (n * 32 + k) * 9 + tap]);
+    tc3f[i] = __float2bfloat16(master[OFF_W3 + (n * 32 + k) * 9 + tap]);
+    tc2b[i] = __float2bfloat16(master[OFF_W2 + (k * 32 + n) * 9 + (8 - tap)]);
+    tc3b[i] = __float2bfloat16(master[OFF_W3 + (k * 32 + n) * 9 + (8 - tap)]);
   }
-}
-
-// ------------------------------------------------------------------ layer 4
-__global__ void __launch_bounds__(256) layer4_kernel(const __nv_bfloat16* __restrict__ h3, int B, int X, int Y,
-                                                     const float* __restrict__ w4r, const float* __restrict__ master,
-                                                     float* __restrict__ z) {
-  __shared__ float w[288];
-  for (int i = threadIdx.x; i < 288; i += blockDim.x) w[i] = w4r[i];
-  __syncthreads();
-  const int n = X * Y;
-  const long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p >= static_cast<long long>(B) * n) return;
-  const int b = static_cast<int>(p / n);
-  const int site = static_cast<int>(p - static_cast<long long>(b) * n);
-  const int y = site / X, x = site - y * X;
-  float acc = master[OFF_B4];
-  for (int ky = 0; ky < 3; ++ky) {
-    int yy = y + ky - 1;
-    yy = yy < 0 ? yy + Y : (yy >= Y ? yy - Y : yy);
-    for (int kx = 0; kx < 3; ++kx) {
-      int xx = x + kx - 1;
-      xx = xx < 0 ? xx + X : (xx >= X ? xx - X : xx);
-      const uint4* src = reinterpret_cast<const uint4*>(h3 + (static_cast<size_t>(b) * n + yy * X + xx) * 32);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint4 v = src[q];
-        const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 f = __bfloat1622float2(hv[e]);
-          const int c = q * 8 + e * 2;
-          acc = fmaf(w[c * 9 + ky * 3 + kx], f.x, acc);
-          acc = fmaf(w[(c + 1) * 9 + ky * 3 + kx], f.y, acc);
-        }
-      }
-    }
+  if (t < 9 * 32 * 16) {                       // (tap, k < 32, n < 16)
+    const int tap = t / 512, rem = t - tap * 512, k = rem / 16, n = rem - k * 16;
+    tc4[tc_index(tap, k, n, 4, 2)] = __float2bfloat16(n == 0 ? master[OFF_W4 + k * 9 + tap] : 0.f);
   }
-  z[p] = acc;
 }
 
 // ------------------------------------------------------------------ loss
@@ -421,12 +241,13 @@ struct ising_cnn {
   float* master = nullptr;   // [NPARAM]
   float* adam_m = nullptr;
   float* adam_v = nullptr;
-  float* w1r = nullptr;      // [864]
   float* w4r = nullptr;      // [288]
-  __nv_bfloat16* wf2 = nullptr;
-  __nv_bfloat16* wf3 = nullptr;
-  __nv_bfloat16* wb2 = nullptr;
-  __nv_bfloat16* wb3 = nullptr;
+  __nv_bfloat16* tc1 = nullptr;    // canonical tensor-core layouts
+  __nv_bfloat16* tc2f = nullptr;
+  __nv_bfloat16* tc3f = nullptr;
+  __nv_bfloat16* tc2b = nullptr;
+  __nv_bfloat16* tc3b = nullptr;
+  __nv_bfloat16* tc4 = nullptr;
   int64_t step = 0;
 };
 
@@ -440,13 +261,30 @@ int cnn_map(cudaError_t e) {
   return ISING_ERR_CUDA;
 }
 
-constexpr size_t kWT = 9 * 32 * PIX_STRIDE;   // bf16 elements per prepared 32x32 weight set
 
 cudaError_t refresh(ising_cnn* net, cudaStream_t st) {
-  prepare_weights_kernel<<<(static_cast<int>(kWT) + 255) / 256, 256, 0, st>>>(net->master, net->w1r, net->w4r,
-                                                                                net->wf2, net->wf3, net->wb2,
-                                                                                net->wb3);
+  prepare_w4r_kernel<<<2, 256, 0, st>>>(net->master, net->w4r);
+  prepare_tc_weights_kernel<<<(9 * 32 * 32 + 255) / 256, 256, 0, st>>>(net->master, net->tc1, net->tc2f, net->tc3f,
+                                                                       net->tc2b, net->tc3b, net->tc4);
   return cudaGetLastError();
+}
+
+int sm_count() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      v <= 0)
+    v = 148;
+  return v;
+}
+
+TcConvArgs tc_args(const ising_problem* p, int32_t B) {
+  TcConvArgs a{};
+  a.X = p->X;
+  a.Y = p->Y;
+  a.B = B;
+  a.eflags = p->d_eflags;
+  a.status = p->d_status;
+  return a;
 }
 
 size_t act_bytes(int32_t B, int32_t n) { return static_cast<size_t>(B) * n * 32 * sizeof(__nv_bfloat16); }
@@ -483,22 +321,39 @@ size_t ws_layout(int32_t B, int32_t n, int train, WS* w, unsigned char* base) {
   return o;
 }
 
-size_t conv_smem(int X) { return (9 * 32 + 3 * static_cast<size_t>(X)) * PIX_STRIDE * sizeof(__nv_bfloat16); }
-
 cudaError_t forward_pass(const ising_cnn* net, const ising_problem* p, const int8_t* spins, int32_t B, float* z,
                          const WS& w, cudaStream_t st) {
-  const long long N = static_cast<long long>(B) * p->n;
-  const int blocks = static_cast<int>((N + 255) / 256);
-  layer1_kernel<<<blocks, 256, 0, st>>>(spins, p->d_eflags, B, p->X, p->Y, net->w1r, net->master, w.h1);
-  const size_t sm = conv_smem(p->X);
-  cudaError_t e = cudaFuncSetAttribute(conv32_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sm));
+  const int sms = sm_count();
+  TcConvArgs a = tc_args(p, B);
+  a.spins = spins;
+  a.wt = net->tc1;
+  a.bias = net->master + OFF_B1;
+  a.out_bf16 = w.h1;
+  cudaError_t e = launch_conv_tc(0, a, sms, st);
   if (e != cudaSuccess) return e;
-  const dim3 grid(p->Y, B);
-  conv32_kernel<0><<<grid, 256, sm, st>>>(w.h1, net->wf2, net->master + OFF_B2, nullptr, p->X, p->Y, w.h2);
-  conv32_kernel<0><<<grid, 256, sm, st>>>(w.h2, net->wf3, net->master + OFF_B3, nullptr, p->X, p->Y, w.h3);
-  layer4_kernel<<<blocks, 256, 0, st>>>(w.h3, B, p->X, p->Y, net->w4r, net->master, z);
-  return cudaGetLastError();
+  a = tc_args(p, B);
+  a.in = w.h1;
+  a.wt = net->tc2f;
+  a.bias = net->master + OFF_B2;
+  a.out_bf16 = w.h2;
+  e = launch_conv_tc(1, a, sms, st);
+  if (e != cudaSuccess) return e;
+  a.in = w.h2;
+  a.wt = net->tc3f;
+  a.bias = net->master + OFF_B3;
+  a.out_bf16 = w.h3;
+  e = launch_conv_tc(1, a, sms, st);
+  if (e != cudaSuccess) return e;
+  a = tc_args(p, B);
+  a.in = w.h3;
+  a.wt = net->tc4;
+  a.bias = net->master + OFF_B4;
+  a.out_f32 = z;
+  return launch_conv_tc(3, a, sms, st);
+}
+
+bool tc_supported(const ising_problem* p) {
+  return p->X <= 1024 && conv_tc_smem(1, p->X) <= 227 * 1024;
 }
 
 }  // namespace
@@ -512,12 +367,13 @@ int ising_cnn_create(const float* params, ising_cnn** out) {
   cudaError_t e = cudaMalloc(&net->master, NPARAM * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&net->adam_m, NPARAM * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&net->adam_v, NPARAM * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&net->w1r, 864 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&net->w4r, 288 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&net->wf2, kWT * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) e = cudaMalloc(&net->wf3, kWT * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) e = cudaMalloc(&net->wb2, kWT * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) e = cudaMalloc(&net->wb3, kWT * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&net->tc1, 9 * 16 * 32 * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&net->tc2f, 9 * 32 * 32 * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&net->tc3f, 9 * 32 * 32 * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&net->tc2b, 9 * 32 * 32 * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&net->tc3b, 9 * 32 * 32 * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc(&net->tc4, 9 * 32 * 16 * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMemcpy(net->master, params, NPARAM * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(net->adam_m, 0, NPARAM * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(net->adam_v, 0, NPARAM * sizeof(float));
@@ -536,12 +392,13 @@ void ising_cnn_destroy(ising_cnn* net) {
   cudaFree(net->master);
   cudaFree(net->adam_m);
   cudaFree(net->adam_v);
-  cudaFree(net->w1r);
   cudaFree(net->w4r);
-  cudaFree(net->wf2);
-  cudaFree(net->wf3);
-  cudaFree(net->wb2);
-  cudaFree(net->wb3);
+  cudaFree(net->tc1);
+  cudaFree(net->tc2f);
+  cudaFree(net->tc3f);
+  cudaFree(net->tc2b);
+  cudaFree(net->tc3b);
+  cudaFree(net->tc4);
   delete net;
 }
 
@@ -571,7 +428,7 @@ int ising_cnn_forward(const ising_cnn* net, const ising_problem* p, const int8_t
   if (!net || !p || B < 0 || (B > 0 && (!spins || !logits || !ws))) return ISING_ERR_ARG;
   if (B == 0) return ISING_OK;
   if (ws_bytes < ws_layout(B, p->n, 0, nullptr, nullptr)) return ISING_ERR_ARG;
-  if (conv_smem(p->X) > 227 * 1024) return ISING_ERR_UNSUPPORTED;
+  if (!tc_supported(p)) return ISING_ERR_UNSUPPORTED;
   WS w;
   ws_layout(B, p->n, 0, &w, static_cast<unsigned char*>(ws));
   return cnn_map(forward_pass(net, p, spins, B, logits, w, static_cast<cudaStream_t>(cuda_stream)));
@@ -581,7 +438,7 @@ int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* s
                    int32_t B, float* grad, float* loss, void* ws, size_t ws_bytes, void* cuda_stream) {
   if (!net || !p || B <= 0 || !spins || !targets || !grad || !loss || !ws) return ISING_ERR_ARG;
   if (ws_bytes < ws_layout(B, p->n, 1, nullptr, nullptr)) return ISING_ERR_ARG;
-  if (conv_smem(p->X) > 227 * 1024) return ISING_ERR_UNSUPPORTED;
+  if (!tc_supported(p)) return ISING_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   WS w;
   ws_layout(B, p->n, 1, &w, static_cast<unsigned char*>(ws));
@@ -594,12 +451,22 @@ int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* s
   const int X = p->X, Y = p->Y;
   loss_kernel<<<blocks, 256, 0, st>>>(w.z, targets, N, w.dz, loss);
   layer4_back_kernel<<<blocks, 256, 0, st>>>(w.dz, w.h3, B, X, Y, net->w4r, w.g3);
-  const size_t sm = conv_smem(X);
-  e = cudaFuncSetAttribute(conv32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
-  if (e != cudaSuccess) return cnn_map(e);
-  const dim3 grid(Y, B);
-  conv32_kernel<1><<<grid, 256, sm, st>>>(w.g3, net->wb3, nullptr, w.h2, X, Y, w.g2);
-  conv32_kernel<1><<<grid, 256, sm, st>>>(w.g2, net->wb2, nullptr, w.h1, X, Y, w.g1);
+  {
+    TcConvArgs a = tc_args(p, B);
+    a.in = w.g3;
+    a.wt = net->tc3b;
+    a.mask = w.h2;
+    a.out_bf16 = w.g2;
+    e = launch_conv_tc(2, a, sm_count(), st);
+    if (e == cudaSuccess) {
+      a.in = w.g2;
+      a.wt = net->tc2b;
+      a.mask = w.h1;
+      a.out_bf16 = w.g1;
+      e = launch_conv_tc(2, a, sm_count(), st);
+    }
+    if (e != cudaSuccess) return cnn_map(e);
+  }
   // weight gradients
   const int rows = 4;
   const dim3 wgrid((Y + rows - 1) / rows, B);

@@ -1,0 +1,310 @@
+// conv_tc.cu -- the network's 3x3 circular convolutions on the 5th-generation
+// tensor cores (tcgen05.mma, accumulators in tensor memory).
+//
+// Per output row (image b, row y) the convolution is a GEMM with M = pixels,
+// N = output channels and K = 9 taps x input channels.  Instead of expanding
+// the nine shifted copies of the input (im2col), each staged input row is
+// laid out in shared memory as [8-channel chunk][pixel][16 bytes]: eight
+// consecutive pixels of one chunk are then one "core matrix" of the
+// no-swizzle K-major operand layout, whatever pixel they start at.  A tap's
+// x-shift is just a 16-byte move of the descriptor's start address and its
+// y-shift picks one of the three staged rows, so each input row is staged
+// once per output row band and read by all nine taps in place.
+//
+// The row layout: [chunk][X + 2 padded to the tile grid][8 x BF16], pixel
+// index + 1 (index 0 holds the periodic left neighbour x = X-1, index X+1
+// the right neighbour x = 0, the rest of the padding is zero).
+// Descriptor (SM100 shared-memory matrix descriptor, no swizzle): start >> 4,
+// leading byte offset (next 8-channel chunk) >> 4, stride byte offset (next
+// 8 pixels = 128 bytes) >> 4, version 1.  Instruction: kind::f16, BF16 A and
+// B, FP32 D, both K-major, M = 128, N = 16 or 32.
+//
+// Persistent CTAs of 128 threads walk consecutive output rows, keeping a ring
+// of three staged input rows, so each new output row stages one input row.
+// Per row: stage -> fence.proxy.async -> one thread issues the MMAs of every
+// 128-pixel tile of the row (9 taps x K/16 each) and commits to an mbarrier
+// -> all threads wait (bounded) -> tcgen05.ld of their pixel's accumulator ->
+// fused epilogue -> store.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "../../include/ising.h"
+#include "internal.h"
+
+namespace ising {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr long long kWaitCycles = 4000000000LL;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (static_cast<uint64_t>(1) << 46);
+}
+
+// kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9 = 1, 10-12 = 1), K-major A and B, N >> 3 at bits 17-22, M >> 4 at 24-28
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tc(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+template <int kN>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v);
+
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ int wrapi(int v, int m) { return v < 0 ? v + m : (v >= m ? v - m : v); }
+
+// kIn: 0 = features (s, w_right, w_down) of spins/eflags, 16 channels (3 used);
+//      1 = BF16 activations [P][32].
+// kOut: 0 = BF16 [P][32] relu(acc + bias); 1 = BF16 [P][32] acc * [mask > 0];
+//       2 = FP32 [P] acc(channel 0) + bias[0].
+template <int kIn, int kOut>
+__global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(TcConvArgs a) {
+  constexpr int KC = kIn == 0 ? 2 : 4;          // 8-channel chunks of the input
+  constexpr int N = kOut == 2 ? 16 : 32;         // output channels (padded)
+  constexpr int NG = N / 8;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int X = a.X, Y = a.Y, n = X * Y;
+  const int ntile = (X + 127) >> 7;
+  const int RP = ntile * 128 + 2;                // pixels per staged chunk row
+  const size_t wbytes = static_cast<size_t>(9) * KC * NG * 128;
+  unsigned char* sw = smem;                                        // weights [9][KC][NG][8][16B]
+  unsigned char* srow = smem + wbytes;                              // 3 slots x [KC][RP][16B]
+  const size_t slot_bytes = static_cast<size_t>(KC) * RP * 16;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(srow + 3 * slot_bytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // weights, once per CTA
+  for (int i = tid; i < static_cast<int>(wbytes / 16); i += kTcThreads)
+    reinterpret_cast<uint4*>(sw)[i] = reinterpret_cast<const uint4*>(a.wt)[i];
+  // zero the padding of all slots once (never rewritten)
+  for (int i = tid; i < static_cast<int>(3 * slot_bytes / 16); i += kTcThreads)
+    reinterpret_cast<uint4*>(srow)[i] = make_uint4(0, 0, 0, 0);
+  uint32_t tcols = 32;
+  while (tcols < static_cast<uint32_t>(ntile * N)) tcols <<= 1;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)));
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  const long long R = static_cast<long long>(a.B) * Y;
+  const long long r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
+  uint32_t phase = 0;
+  int staged_b = -1, staged_next = 0;   // rows staged for image staged_b up to unwrapped row staged_next - 1
+  bool ok = true;
+  for (long long row = r0; row < r1 && ok; ++row) {
+    const int b = static_cast<int>(row / Y), y = static_cast<int>(row - static_cast<long long>(b) * Y);
+    int first = y - 1;
+    if (staged_b == b && staged_next == y + 1) first = y + 1;   // only the new lower row
+    // ---- stage input rows first .. y+1 (unwrapped y-1 .. y+1) into ring slots
+    for (int yu = first; yu <= y + 1; ++yu) {
+      const int yy = wrapi(yu, Y);
+      unsigned char* slot = srow + static_cast<size_t>((yu + 3) % 3) * slot_bytes;
+      for (int i = tid; i < (X + 2) * KC; i += kTcThreads) {
+        const int pidx = i / KC, kc = i - pidx * KC;
+        const int x = wrapi(pidx - 1, X);
+        uint4 v;
+        if (kIn == 0) {
+          const int j = yy * X + x;
+          __align__(16) __nv_bfloat16 f[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) f[e] = __float2bfloat16(0.f);
+          if (kc == 0) {
+            const uint8_t fl = a.eflags[j];
+            f[0] = __float2bfloat16(a.spins[static_cast<size_t>(b) * n + j] > 0 ? 1.f : -1.f);
+            f[1] = __float2bfloat16((fl & 1u) ? -1.f : 1.f);
+            f[2] = __float2bfloat16((fl & 2u) ? -1.f : 1.f);
+          }
+          v = *reinterpret_cast<const uint4*>(f);
+        } else {
+          v = reinterpret_cast<const uint4*>(a.in + (static_cast<size_t>(b) * n + yy * X + x) * 32)[kc];
+        }
+        *reinterpret_cast<uint4*>(slot + (static_cast<size_t>(kc) * RP + pidx) * 16) = v;
+      }
+    }
+    staged_b = b;
+    staged_next = y + 2;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- MMAs: per tile, 9 taps x KC/2 K-slices of 16
+    if (tid == 0) {
+      const uint32_t idesc = idesc_bf16(128, N);
+      const uint32_t lbo_a = static_cast<uint32_t>(RP) * 16, lbo_b = NG * 128;
+      for (int t = 0; t < ntile; ++t) {
+        for (int tap = 0; tap < 9; ++tap) {
+          const int ky = tap / 3, kx = tap - ky * 3;
+          const unsigned char* slot = srow + static_cast<size_t>((y + ky - 1 + 3) % 3) * slot_bytes;
+#pragma unroll
+          for (int ks = 0; ks < KC / 2; ++ks) {
+            const uint32_t a_addr = saddr(slot) + static_cast<uint32_t>(2 * ks) * lbo_a + (t * 128 + kx) * 16;
+            const uint32_t b_addr = saddr(sw) + static_cast<uint32_t>((tap * KC + 2 * ks) * NG * 128);
+            mma_tc(tmem + static_cast<uint32_t>(t * N), smem_desc(a_addr, lbo_a, 128), smem_desc(b_addr, lbo_b, 128),
+                   idesc, (tap | ks) != 0);
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(mbar))
+                   : "memory");
+    }
+    // ---- bounded wait for the MMAs
+    uint32_t done = 0;
+    const long long t_start = clock64();
+    while (!done) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(saddr(mbar)), "r"(phase)
+          : "memory");
+      if (!done && clock64() - t_start > kWaitCycles) break;   // about two seconds
+    }
+    phase ^= 1u;
+    done = __syncthreads_and(done);   // one decision for the whole CTA
+    if (!done) {
+      if (tid == 0) atomicExch(a.status, ISING_ERR_TIMEOUT);
+      ok = false;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- epilogue: this thread's pixel of every tile
+    if (ok) {
+      for (int t = 0; t < ntile; ++t) {
+        float v[N];
+        tmem_ld<N>(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(t * N), v);
+        const int x = t * 128 + warp * 32 + lane;
+        if (x >= X) continue;
+        const size_t p = static_cast<size_t>(b) * n + y * X + x;
+        if (kOut == 2) {
+          a.out_f32[p] = v[0] + a.bias[0];
+        } else {
+          __align__(16) __nv_bfloat16 o[32];
+          if (kOut == 0) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) o[c] = __float2bfloat16(fmaxf(v[c] + a.bias[c], 0.f));
+          } else {
+            const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * 32);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const uint4 mv = mk[q];
+              const __nv_bfloat16* m8 = reinterpret_cast<const __nv_bfloat16*>(&mv);
+#pragma unroll
+              for (int e = 0; e < 8; ++e)
+                o[q * 8 + e] = __float2bfloat16(__bfloat162float(m8[e]) > 0.f ? v[q * 8 + e] : 0.f);
+            }
+          }
+          uint4* dst = reinterpret_cast<uint4*>(a.out_bf16 + p * 32);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+}
+
+template <int kIn, int kOut>
+size_t smem_bytes_for(int X) {
+  constexpr int KC = kIn == 0 ? 2 : 4;
+  constexpr int NG = (kOut == 2 ? 16 : 32) / 8;
+  const int RP = ((X + 127) / 128) * 128 + 2;
+  return static_cast<size_t>(9) * KC * NG * 128 + 3 * static_cast<size_t>(KC) * RP * 16 + 16;
+}
+
+template <int kIn, int kOut>
+cudaError_t launch_one(const TcConvArgs& a, int sms, cudaStream_t st) {
+  const size_t sm = smem_bytes_for<kIn, kOut>(a.X);
+  cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<kIn, kOut>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm));
+  if (e != cudaSuccess) return e;
+  // residency from shared memory (per-SM capacity, 1 KB reserved per CTA) and
+  // tensor memory (512 columns per SM), at most 16 CTAs of 4 warps
+  int dev = 0, smem_sm = 0, reserved = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e != cudaSuccess) return e;
+  int per_sm = static_cast<int>(static_cast<size_t>(smem_sm) / (sm + static_cast<size_t>(reserved)));
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int cols = ((a.X + 127) / 128) * (kOut == 2 ? 16 : 32);
+  int tc = 32;
+  while (tc < cols) tc <<= 1;
+  per_sm = std::min(std::min(per_sm, 512 / tc), 16);
+  const long long rows = static_cast<long long>(a.B) * a.Y;
+  const long long grid = std::min<long long>(rows, static_cast<long long>(sms) * per_sm);
+  conv_tc_kernel<kIn, kOut><<<static_cast<int>(grid), kTcThreads, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t conv_tc_smem(int kind, int X) {
+  switch (kind) {
+    case 0: return smem_bytes_for<0, 0>(X);
+    case 1: return smem_bytes_for<1, 0>(X);
+    case 2: return smem_bytes_for<1, 1>(X);
+    default: return smem_bytes_for<1, 2>(X);
+  }
+}
+
+// kind 0: layer 1 (features -> relu); 1: 32 -> 32 relu; 2: 32 -> 32 masked (input
+// gradient); 3: 32 -> 1 logits.
+cudaError_t launch_conv_tc(int kind, const TcConvArgs& a, int sms, cudaStream_t st) {
+  switch (kind) {
+    case 0: return launch_one<0, 0>(a, sms, st);
+    case 1: return launch_one<1, 0>(a, sms, st);
+    case 2: return launch_one<1, 1>(a, sms, st);
+    default: return launch_one<1, 2>(a, sms, st);
+  }
+}
+
+}  // namespace ising

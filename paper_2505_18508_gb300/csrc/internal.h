@@ -1,6 +1,7 @@
 // internal.h -- host-side structures shared by the ABI and the kernel launchers.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/ising.h"
@@ -76,6 +77,22 @@ int flow_threads();
 int flow_max_segments();
 cudaError_t launch_flow(const FlowArgs& a, cudaStream_t stream);
 cudaError_t flow_max_ctas(size_t smem, int* per_sm);
+
+// One 3x3 circular convolution layer on the tensor cores (conv_tc.cu).
+struct TcConvArgs {
+  const __nv_bfloat16* in;      // [B*n][32] input activations (kinds 1-3)
+  const int8_t* spins;          // [B][n] (kind 0: features s, w_right, w_down)
+  const uint8_t* eflags;        // [n]    (kind 0)
+  const __nv_bfloat16* wt;      // weights in the canonical [tap][chunk][n-group][8][8] layout
+  const float* bias;            // [32] (kinds 0, 1) or [1] (kind 3)
+  const __nv_bfloat16* mask;    // [B*n][32] (kind 2)
+  __nv_bfloat16* out_bf16;      // [B*n][32] (kinds 0-2)
+  float* out_f32;               // [B*n] (kind 3)
+  int32_t* status;              // bounded-wait failures
+  int X, Y, B;
+};
+size_t conv_tc_smem(int kind, int X);
+cudaError_t launch_conv_tc(int kind, const TcConvArgs& a, int sms, cudaStream_t st);
 
 size_t anneal_smem_bytes(int32_t H, int32_t Rmax);
 // grid = (C, ceil(T/G)); cluster (C,1,1) when C > 1
