@@ -11,13 +11,14 @@
 // convolutions and the two 32->32 input gradients are implicit GEMMs on the
 // tcgen05 tensor cores (conv_tc.cu: per output row, M = pixels, N = output
 // channels, K = 9 taps x input channels, accumulators in tensor memory).  The
-// layer-4 input gradient, the loss and the weight gradients run on the CUDA
-// cores.
+// weight gradients are tensor-core GEMMs over the pixels as well; the layer-4
+// input gradient and the loss run on the CUDA cores.
 //
 // Parameters: one flat FP32 vector in the order W1[32,3,3,3], b1[32],
 // W2[32,32,3,3], b2[32], W3[32,32,3,3], b3[32], W4[1,32,3,3], b4[1].
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 
@@ -136,89 +137,6 @@ __global__ void __launch_bounds__(256) layer4_back_kernel(const float* __restric
   for (int q = 0; q < 4; ++q) dst[q] = src[q];
 }
 
-// ------------------------------------------------------------------ weight gradients (CUDA cores)
-// dW[o][c][tap] += sum_p g[p][o] * a[p + tap - 1][c], db[o] += sum_p g[p][o], over
-// kRows output rows of one image per CTA.  Inputs:
-//   kind 0: a = features of (spins, eflags) (3 channels), g BF16 [32]   (layer 1)
-//   kind 1: a = BF16 [32], g BF16 [32]                                   (layers 2, 3)
-//   kind 2: a = BF16 [32], g = dz FP32 [1]                               (layer 4)
-// Thread t owns outputs t, t + 256, ... of the layer's O*C*9 weights.
-template <int kKind>
-__global__ void __launch_bounds__(256) wgrad_kernel(const void* __restrict__ gsrc, const __nv_bfloat16* __restrict__ act,
-                                                    const int8_t* __restrict__ spins,
-                                                    const uint8_t* __restrict__ eflags, int B, int X, int Y,
-                                                    int rows_per_cta, float* __restrict__ dW, float* __restrict__ db) {
-  constexpr int C = kKind == 0 ? 3 : 32;
-  constexpr int O = kKind == 2 ? 1 : 32;
-  constexpr int NW = O * C * 9;
-  constexpr int PER = (NW + 255) / 256;
-  extern __shared__ __align__(16) float sm[];
-  float* sa = sm;                       // [3][X][C] activations of rows y-1, y, y+1
-  float* sg = sa + 3 * X * C;           // [X][O] gradients of row y
-  const int n = X * Y;
-  const int b = blockIdx.y;
-  float acc[PER];
-#pragma unroll
-  for (int e = 0; e < PER; ++e) acc[e] = 0.f;
-  float bacc = 0.f;
-  const int y_begin = blockIdx.x * rows_per_cta;
-  const int y_end = min(Y, y_begin + rows_per_cta);
-  for (int y = y_begin; y < y_end; ++y) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < 3 * X * C; i += blockDim.x) {
-      const int r = i / (X * C);
-      const int rem = i - r * X * C;
-      const int px = rem / C, c = rem - px * C;
-      int yy = y + r - 1;
-      yy = yy < 0 ? yy + Y : (yy >= Y ? yy - Y : yy);
-      const int j = yy * X + px;
-      float v;
-      if (kKind == 0) {
-        if (c == 0) v = spins[static_cast<size_t>(b) * n + j] > 0 ? 1.f : -1.f;
-        else v = (eflags[j] & (c == 1 ? 1u : 2u)) ? -1.f : 1.f;
-      } else {
-        v = __bfloat162float(act[(static_cast<size_t>(b) * n + j) * 32 + c]);
-      }
-      sa[i] = v;
-    }
-    for (int i = threadIdx.x; i < X * O; i += blockDim.x) {
-      const int px = i / O, o = i - px * O;
-      const size_t q = static_cast<size_t>(b) * n + y * X + px;
-      sg[i] = kKind == 2 ? static_cast<const float*>(gsrc)[q]
-                         : __bfloat162float(static_cast<const __nv_bfloat16*>(gsrc)[q * 32 + o]);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < PER; ++e) {
-      const int wi = threadIdx.x + e * 256;
-      if (wi < NW) {
-        const int o = wi / (C * 9);
-        const int rem = wi - o * C * 9;
-        const int c = rem / 9, tap = rem - c * 9;
-        const int ky = tap / 3, kx = tap - ky * 3;
-        float s = 0.f;
-        for (int px = 0; px < X; ++px) {
-          int sx = px + kx - 1;
-          sx = sx < 0 ? sx + X : (sx >= X ? sx - X : sx);
-          s = fmaf(sg[px * O + o], sa[(ky * X + sx) * C + c], s);
-        }
-        acc[e] += s;
-      }
-    }
-    if (threadIdx.x < O) {
-      float s = 0.f;
-      for (int px = 0; px < X; ++px) s += sg[px * O + threadIdx.x];
-      bacc += s;
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < PER; ++e) {
-    const int wi = threadIdx.x + e * 256;
-    if (wi < NW) atomicAdd(dW + wi, acc[e]);
-  }
-  if (threadIdx.x < O) atomicAdd(db + threadIdx.x, bacc);
-}
-
 // ------------------------------------------------------------------ Adam
 __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ g, int count, float lr, float b1, float b2, float eps,
@@ -294,8 +212,16 @@ size_t al256(size_t v) { return (v + 255) & ~size_t(255); }
 // g3, g2, g1 (BF16 [B][n][32])
 struct WS {
   __nv_bfloat16 *h1, *h2, *h3, *g1, *g2, *g3;
-  float *z, *dz;
+  float *z, *dz, *part, *bpart;
+  int max_ctas;
 };
+
+// CTAs of one weight-gradient launch: at most one per output row (B*Y <= B*n/4
+// since X >= 4) and at most kWgradMaxCtas
+int wgrad_ctas(int32_t B, int32_t n) {
+  const long long rows = std::max<long long>(1, static_cast<long long>(B) * n / 4);
+  return static_cast<int>(std::min<long long>(rows, kWgradMaxCtas));
+}
 
 size_t ws_layout(int32_t B, int32_t n, int train, WS* w, unsigned char* base) {
   size_t o = 0;
@@ -316,6 +242,9 @@ size_t ws_layout(int32_t B, int32_t n, int train, WS* w, unsigned char* base) {
     t.g3 = reinterpret_cast<__nv_bfloat16*>(take(A));
     t.g2 = reinterpret_cast<__nv_bfloat16*>(take(A));
     t.g1 = reinterpret_cast<__nv_bfloat16*>(take(A));
+    t.max_ctas = wgrad_ctas(B, n);
+    t.part = reinterpret_cast<float*>(take(al256(static_cast<size_t>(t.max_ctas) * 96 * 96 * sizeof(float))));
+    t.bpart = reinterpret_cast<float*>(take(al256(static_cast<size_t>(t.max_ctas) * 32 * sizeof(float))));
   }
   if (w) *w = t;
   return o;
@@ -438,7 +367,7 @@ int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* s
                    int32_t B, float* grad, float* loss, void* ws, size_t ws_bytes, void* cuda_stream) {
   if (!net || !p || B <= 0 || !spins || !targets || !grad || !loss || !ws) return ISING_ERR_ARG;
   if (ws_bytes < ws_layout(B, p->n, 1, nullptr, nullptr)) return ISING_ERR_ARG;
-  if (!tc_supported(p)) return ISING_ERR_UNSUPPORTED;
+  if (!tc_supported(p) || wgrad_tc_smem(1, p->X) > 227 * 1024) return ISING_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   WS w;
   ws_layout(B, p->n, 1, &w, static_cast<unsigned char*>(ws));
@@ -467,24 +396,39 @@ int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* s
     }
     if (e != cudaSuccess) return cnn_map(e);
   }
-  // weight gradients
-  const int rows = 4;
-  const dim3 wgrid((Y + rows - 1) / rows, B);
-  const size_t sm32 = (3 * static_cast<size_t>(X) * 32 + static_cast<size_t>(X) * 32) * sizeof(float);
-  const size_t sm4 = (3 * static_cast<size_t>(X) * 32 + static_cast<size_t>(X) * 1) * sizeof(float);
-  const size_t sm1 = (3 * static_cast<size_t>(X) * 3 + static_cast<size_t>(X) * 32) * sizeof(float);
-  if (sm32 > 227 * 1024) return ISING_ERR_UNSUPPORTED;
-  e = cudaFuncSetAttribute(wgrad_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm32));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(wgrad_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm4));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(wgrad_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm1));
-  if (e != cudaSuccess) return cnn_map(e);
-  wgrad_kernel<2><<<wgrid, 256, sm4, st>>>(w.dz, w.h3, nullptr, nullptr, B, X, Y, rows, grad + OFF_W4, grad + OFF_B4);
-  wgrad_kernel<1><<<wgrid, 256, sm32, st>>>(w.g3, w.h2, nullptr, nullptr, B, X, Y, rows, grad + OFF_W3, grad + OFF_B3);
-  wgrad_kernel<1><<<wgrid, 256, sm32, st>>>(w.g2, w.h1, nullptr, nullptr, B, X, Y, rows, grad + OFF_W2, grad + OFF_B2);
-  wgrad_kernel<0><<<wgrid, 256, sm1, st>>>(w.g1, nullptr, spins, p->d_eflags, B, X, Y, rows, grad + OFF_W1,
-                                           grad + OFF_B1);
+  // weight gradients (tensor cores), layer 4 first
+  {
+    TcWgradArgs a{};
+    a.X = X;
+    a.Y = Y;
+    a.B = B;
+    a.part = w.part;
+    a.bpart = w.bpart;
+    a.status = p->d_status;
+    a.max_ctas = w.max_ctas;
+    const int sms = sm_count();
+    a.act = w.h3;
+    a.g = w.dz;
+    e = launch_wgrad_tc(2, a, sms, grad + OFF_W4, grad + OFF_B4, st);
+    if (e == cudaSuccess) {
+      a.act = w.h2;
+      a.g = w.g3;
+      e = launch_wgrad_tc(1, a, sms, grad + OFF_W3, grad + OFF_B3, st);
+    }
+    if (e == cudaSuccess) {
+      a.act = w.h1;
+      a.g = w.g2;
+      e = launch_wgrad_tc(1, a, sms, grad + OFF_W2, grad + OFF_B2, st);
+    }
+    if (e == cudaSuccess) {
+      a.act = nullptr;
+      a.spins = spins;
+      a.eflags = p->d_eflags;
+      a.g = w.g1;
+      e = launch_wgrad_tc(0, a, sms, grad + OFF_W1, grad + OFF_B1, st);
+    }
+    if (e != cudaSuccess) return cnn_map(e);
+  }
   return cnn_map(cudaGetLastError());
 }
 

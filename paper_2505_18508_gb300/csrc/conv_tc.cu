@@ -285,6 +285,261 @@ cudaError_t launch_one(const TcConvArgs& a, int sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ weight gradients
+// dW[o][c][ky][kx] = sum over images, rows y and pixels p of
+//   g[y][p][o] * a[y+ky-1][p+kx-1][c]   (indices mod Y, X).
+// Per output row y this is one GEMM with K = pixels:
+//   D[(ky, c)][(kx, o)] += sum_p a[y+ky-1][p][c] * g[y][p-kx+1][o]
+// A (M = 128: three activation rows x 32 channels, plus 32 ignored rows) is
+// the three rows staged unshifted; B (N = 96: three copies of the gradient row
+// shifted by kx - 1 pixels, x 32 channels) is staged three times.  Both are
+// MN-major (8 channels contiguous per pixel, 8 pixels per core matrix), so the
+// staged layout [8-channel block][pixel][16 B] serves as is: the leading byte
+// offset steps 8 pixels (128 B), the stride byte offset one channel block.
+// One FP32 accumulator (128 x N) per CTA sums all of the CTA's rows; the CTA
+// writes it out once and a second kernel reduces the CTAs in a fixed order.
+// Kinds: 0 = layer 1 (a = features s, w_right, w_down; g BF16 [32]);
+//        1 = layers 2, 3 (a, g BF16 [32]);
+//        2 = layer 4 (a BF16 [32]; g = dz FP32, split into BF16 hi + lo).
+template <int kKind>
+__global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(TcWgradArgs a) {
+  constexpr int NB = kKind == 2 ? 4 : 12;          // B blocks of 8 columns (kind 2: 3 used)
+  constexpr int N = NB * 8;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int X = a.X, Y = a.Y, n = X * Y;
+  const int ksteps = (X + 15) >> 4;
+  const int RP = ksteps * 16;                        // pixels per staged block row
+  const size_t blk = static_cast<size_t>(RP) * 16;   // bytes per block row
+  unsigned char* sA = smem;                          // 12 blocks: [ky][chunk][pixel][16 B]
+  unsigned char* sB = smem + 12 * blk;               // NB blocks: [kx][chunk][pixel][16 B]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + NB * blk);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  float* sbias = reinterpret_cast<float*>(tslot + 4);   // [32]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  for (int i = tid; i < static_cast<int>((12 + NB) * blk / 16); i += kTcThreads)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+  if (tid < 32) sbias[tid] = 0.f;
+  constexpr uint32_t tcols = N <= 32 ? 32 : 128;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)));
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  const long long R = static_cast<long long>(a.B) * Y;
+  const long long r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
+  float bsum[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) bsum[e] = 0.f;
+  uint32_t phase = 0;
+  bool ok = true, first = true;
+  for (long long row = r0; row < r1 && ok; ++row) {
+    const int b = static_cast<int>(row / Y), y = static_cast<int>(row - static_cast<long long>(b) * Y);
+    const size_t ib = static_cast<size_t>(b) * n;
+    // ---- A: activation rows y-1, y, y+1
+    if (kKind == 0) {
+      for (int i = tid; i < 3 * X; i += kTcThreads) {
+        const int ky = i / X, x = i - ky * X;
+        const int j = wrapi(y + ky - 1, Y) * X + x;
+        const uint8_t fl = a.eflags[j];
+        __align__(16) __nv_bfloat16 f[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] = __float2bfloat16(0.f);
+        f[0] = __float2bfloat16(a.spins[ib + j] > 0 ? 1.f : -1.f);
+        f[1] = __float2bfloat16((fl & 1u) ? -1.f : 1.f);
+        f[2] = __float2bfloat16((fl & 2u) ? -1.f : 1.f);
+        *reinterpret_cast<uint4*>(sA + (static_cast<size_t>(ky) * 4) * blk + static_cast<size_t>(x) * 16) =
+            *reinterpret_cast<const uint4*>(f);
+      }
+    } else {
+      const int total = 3 * X * 4;
+      for (int i0 = tid; i0 < total; i0 += 4 * kTcThreads) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * kTcThreads;
+          if (i < total) {
+            const int ky = i / (X * 4), rem = i - ky * X * 4, x = rem >> 2, ch = rem & 3;
+            v[u] = reinterpret_cast<const uint4*>(a.act + (ib + static_cast<size_t>(wrapi(y + ky - 1, Y)) * X + x) * 32)[ch];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * kTcThreads;
+          if (i < total) {
+            const int ky = i / (X * 4), rem = i - ky * X * 4, x = rem >> 2, ch = rem & 3;
+            *reinterpret_cast<uint4*>(sA + static_cast<size_t>(ky * 4 + ch) * blk + static_cast<size_t>(x) * 16) = v[u];
+          }
+        }
+      }
+    }
+    // ---- B: gradient row y at positions p = x + kx - 1 (mod X) of copy kx
+    if (kKind == 2) {
+      const float* dz = static_cast<const float*>(a.g) + ib + static_cast<size_t>(y) * X;
+      for (int x = tid; x < X; x += kTcThreads) {
+        const float v = dz[x];
+        bsum[0] += v;
+        const __nv_bfloat16 hi = __float2bfloat16(v);
+        const __nv_bfloat16 lo = __float2bfloat16(v - __bfloat162float(hi));
+        __align__(16) __nv_bfloat16 f[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] = __float2bfloat16(0.f);
+        f[0] = hi;
+        f[1] = lo;
+        const uint4 q = *reinterpret_cast<const uint4*>(f);
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx)
+          *reinterpret_cast<uint4*>(sB + static_cast<size_t>(kx) * blk + static_cast<size_t>(wrapi(x + kx - 1, X)) * 16) = q;
+      }
+    } else {
+      const __nv_bfloat16* g = static_cast<const __nv_bfloat16*>(a.g) + (ib + static_cast<size_t>(y) * X) * 32;
+      for (int i = tid; i < X * 4; i += kTcThreads) {
+        const int x = i >> 2, ch = i & 3;   // ch == tid & 3 for every i of this thread
+        const uint4 q = reinterpret_cast<const uint4*>(g + static_cast<size_t>(x) * 32)[ch];
+        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&q);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) bsum[e] += __bfloat162float(h[e]);
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx)
+          *reinterpret_cast<uint4*>(sB + static_cast<size_t>(kx * 4 + ch) * blk +
+                                    static_cast<size_t>(wrapi(x + kx - 1, X)) * 16) = q;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      const uint32_t idesc = idesc_bf16(128, N) | (1u << 15) | (1u << 16);   // A and B MN-major
+      const uint32_t sbo = static_cast<uint32_t>(blk);
+      for (int ks = 0; ks < ksteps; ++ks) {
+        mma_tc(tmem, smem_desc(saddr(sA) + ks * 256, 128, sbo), smem_desc(saddr(sB) + ks * 256, 128, sbo), idesc,
+               (first && ks == 0) ? 0u : 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(mbar))
+                   : "memory");
+    }
+    first = false;
+    // the next row's staging overwrites what these MMAs read: wait for them
+    uint32_t done = 0;
+    const long long t_start = clock64();
+    while (!done) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(saddr(mbar)), "r"(phase)
+          : "memory");
+      if (!done && clock64() - t_start > kWaitCycles) break;
+    }
+    phase ^= 1u;
+    done = __syncthreads_and(done);
+    if (!done) {
+      if (tid == 0) atomicExch(a.status, ISING_ERR_TIMEOUT);
+      ok = false;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  // ---- bias partial sums
+  if (kKind == 2) {
+    atomicAdd(&sbias[0], bsum[0]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) atomicAdd(&sbias[(tid & 3) * 8 + e], bsum[e]);
+  }
+  __syncthreads();
+  if (tid < 32) a.bpart[static_cast<size_t>(blockIdx.x) * 32 + tid] = sbias[tid];
+  // ---- accumulator rows (ky, c) = warp, lane; rows 96..127 are not used
+  float* out = a.part + static_cast<size_t>(blockIdx.x) * 96 * N;
+  if (ok && !first) {
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 32) {
+      float v[32];
+      if (N - c0 >= 32) {
+        tmem_ld<32>(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+      } else {
+        tmem_ld<16>(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+      }
+      if (warp < 3) {
+        const int w = N - c0 >= 32 ? 32 : 16;
+        for (int q = 0; q < w; ++q) out[static_cast<size_t>(warp * 32 + lane) * N + c0 + q] = v[q];
+      }
+    }
+  } else if (warp < 3) {
+    for (int q = 0; q < N; ++q) out[static_cast<size_t>(warp * 32 + lane) * N + q] = 0.f;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+}
+
+// Sum the CTAs' partials (fixed order) into dW[o][c][ky*3+kx] and db[o].
+template <int kKind>
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ bpart, int ncta,
+                                    float* __restrict__ dW, float* __restrict__ db) {
+  constexpr int C = kKind == 0 ? 3 : 32;
+  constexpr int O = kKind == 2 ? 1 : 32;
+  constexpr int N = kKind == 2 ? 32 : 96;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < O * C * 9) {
+    const int o = t % O, rest = t / O, c = rest % C, tap = rest / C, ky = tap / 3, kx = tap - ky * 3;
+    const size_t row = static_cast<size_t>(ky * 32 + c) * N;
+    float s = 0.f;
+    if (kKind == 2) {
+      for (int k = 0; k < ncta; ++k) {
+        const float* pk = part + static_cast<size_t>(k) * 96 * N + row + kx * 8;
+        s += pk[0] + pk[1];
+      }
+    } else {
+      for (int k = 0; k < ncta; ++k) s += part[static_cast<size_t>(k) * 96 * N + row + kx * 32 + o];
+    }
+    dW[(o * C + c) * 9 + tap] = s;
+  } else if (t < O * C * 9 + O) {
+    const int o = t - O * C * 9;
+    float s = 0.f;
+    for (int k = 0; k < ncta; ++k) s += bpart[static_cast<size_t>(k) * 32 + o];
+    db[o] = s;
+  }
+}
+
+template <int kKind>
+size_t wgrad_smem_for(int X) {
+  constexpr int NB = kKind == 2 ? 4 : 12;
+  const size_t RP = static_cast<size_t>((X + 15) / 16) * 16;
+  return (12 + NB) * RP * 16 + 32 + 32 * sizeof(float);
+}
+
+template <int kKind>
+cudaError_t launch_wgrad_one(const TcWgradArgs& a, int sms, float* dW, float* db, cudaStream_t st) {
+  const size_t sm = wgrad_smem_for<kKind>(a.X);
+  cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel<kKind>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm));
+  if (e != cudaSuccess) return e;
+  int dev = 0, smem_sm = 0, reserved = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e != cudaSuccess) return e;
+  int per_sm = static_cast<int>(static_cast<size_t>(smem_sm) / (sm + static_cast<size_t>(reserved)));
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  per_sm = std::min(per_sm, kKind == 2 ? 16 : 4);   // tensor memory: 512 columns per SM
+  const long long rows = static_cast<long long>(a.B) * a.Y;
+  long long grid = std::min<long long>(rows, static_cast<long long>(sms) * per_sm);
+  grid = std::min<long long>(grid, a.max_ctas);
+  wgrad_tc_kernel<kKind><<<static_cast<int>(grid), kTcThreads, sm, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  constexpr int outs = (kKind == 0 ? 3 : 32) * (kKind == 2 ? 1 : 32) * 9 + (kKind == 2 ? 1 : 32);
+  wgrad_reduce_kernel<kKind><<<(outs + 255) / 256, 256, 0, st>>>(a.part, a.bpart, static_cast<int>(grid), dW, db);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t conv_tc_smem(int kind, int X) {
@@ -293,6 +548,18 @@ size_t conv_tc_smem(int kind, int X) {
     case 1: return smem_bytes_for<1, 0>(X);
     case 2: return smem_bytes_for<1, 1>(X);
     default: return smem_bytes_for<1, 2>(X);
+  }
+}
+
+size_t wgrad_tc_smem(int kind, int X) {
+  return kind == 2 ? wgrad_smem_for<2>(X) : wgrad_smem_for<1>(X);
+}
+
+cudaError_t launch_wgrad_tc(int kind, const TcWgradArgs& a, int sms, float* dW, float* db, cudaStream_t st) {
+  switch (kind) {
+    case 0: return launch_wgrad_one<0>(a, sms, dW, db, st);
+    case 1: return launch_wgrad_one<1>(a, sms, dW, db, st);
+    default: return launch_wgrad_one<2>(a, sms, dW, db, st);
   }
 }
 

@@ -92,6 +92,24 @@ struct TcConvArgs {
   int X, Y, B;
 };
 size_t conv_tc_smem(int kind, int X);
+
+// Weight and bias gradients of one convolution layer on the tensor cores
+// (conv_tc.cu).  kind 0: layer 1 (features of spins/eflags, g BF16 [32]);
+// 1: 32 -> 32 (act and g BF16 [32]); 2: layer 4 (act BF16 [32], g FP32 [1]).
+struct TcWgradArgs {
+  const __nv_bfloat16* act;     // [B*n][32] layer input (kinds 1, 2)
+  const int8_t* spins;          // kind 0
+  const uint8_t* eflags;        // kind 0
+  const void* g;                // gradient at the layer output: BF16 [B*n][32] or FP32 [B*n]
+  float* part;                  // [max_ctas][96][96] per-CTA accumulators
+  float* bpart;                 // [max_ctas][32]
+  int32_t* status;
+  int X, Y, B;
+  int max_ctas;
+};
+constexpr int kWgradMaxCtas = 640;
+size_t wgrad_tc_smem(int kind, int X);
+cudaError_t launch_wgrad_tc(int kind, const TcWgradArgs& a, int sms, float* dW, float* db, cudaStream_t st);
 cudaError_t launch_conv_tc(int kind, const TcConvArgs& a, int sms, cudaStream_t st);
 
 size_t anneal_smem_bytes(int32_t H, int32_t Rmax);
