@@ -35,7 +35,9 @@
 namespace ising {
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 128;        // weight-gradient kernel
+constexpr int kConvThreads = 256;      // convolution kernel: two warpgroups
+constexpr int kRing = 5;               // staged input rows per convolution CTA
 constexpr long long kWaitCycles = 4000000000LL;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -91,14 +93,57 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <>
+__device__ __forceinline__ void tmem_ld<1>(uint32_t taddr, float* v) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  v[0] = __uint_as_float(r);
+}
+
 __device__ __forceinline__ int wrapi(int v, int m) { return v < 0 ? v + m : (v >= m ? v - m : v); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Bounded wait on an mbarrier phase by the calling thread.
+__device__ __forceinline__ bool wait_mbar(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  const long long t_start = clock64();
+  while (!done) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase)
+        : "memory");
+    if (!done && clock64() - t_start > kWaitCycles) break;   // about two seconds
+  }
+  return done != 0;
+}
 
 // kIn: 0 = features (s, w_right, w_down) of spins/eflags, 16 channels (3 used);
 //      1 = BF16 activations [P][32].
 // kOut: 0 = BF16 [P][32] relu(acc + bias); 1 = BF16 [P][32] acc * [mask > 0];
 //       2 = FP32 [P] acc(channel 0) + bias[0].
+//
+// Pipeline over the output rows y of one image (a CTA's rows split at image
+// boundaries into segments): input rows live in a ring of five slots (slot =
+// unwrapped row mod 5) and accumulators in two TMEM buffers (row mod 2).  In
+// iteration y: barrier (row y+1 staged, buffer y mod 2 drained) -> MMAs of row
+// y -> wait for the MMAs of row y-1 (frees slot y-2 and buffer y-1) -> start
+// copying row y+3 into slot y+3 = y-2 (cp.async) -> epilogue of row y-1 ->
+// wait for the copies of row y+2 (issued one iteration earlier).  Row y's
+// MMAs overlap row y-1's epilogue, and each row's loads have a whole
+// iteration to land.  256 threads: warp w drains TMEM lanes 32 (w mod 4) ..
+// and columns 16 (w / 4) .. of the accumulator.
 template <int kIn, int kOut>
-__global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(TcConvArgs a) {
+__global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(TcConvArgs a) {
   constexpr int KC = kIn == 0 ? 2 : 4;          // 8-channel chunks of the input
   constexpr int N = kOut == 2 ? 16 : 32;         // output channels (padded)
   constexpr int NG = N / 8;
@@ -108,146 +153,178 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(TcConvArgs a) {
   const int RP = ntile * 128 + 2;                // pixels per staged chunk row
   const size_t wbytes = static_cast<size_t>(9) * KC * NG * 128;
   unsigned char* sw = smem;                                        // weights [9][KC][NG][8][16B]
-  unsigned char* srow = smem + wbytes;                              // 3 slots x [KC][RP][16B]
+  unsigned char* srow = smem + wbytes;                              // kRing slots x [KC][RP][16B]
   const size_t slot_bytes = static_cast<size_t>(KC) * RP * 16;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(srow + 3 * slot_bytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(srow + kRing * slot_bytes);   // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // weights, once per CTA
-  for (int i = tid; i < static_cast<int>(wbytes / 16); i += kTcThreads)
+  for (int i = tid; i < static_cast<int>(wbytes / 16); i += kConvThreads)
     reinterpret_cast<uint4*>(sw)[i] = reinterpret_cast<const uint4*>(a.wt)[i];
-  // zero the padding of all slots once (never rewritten)
-  for (int i = tid; i < static_cast<int>(3 * slot_bytes / 16); i += kTcThreads)
-    reinterpret_cast<uint4*>(srow)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < static_cast<int>(kRing * slot_bytes / 16); i += kConvThreads)
+    reinterpret_cast<uint4*>(srow)[i] = make_uint4(0, 0, 0, 0);   // padding: never rewritten
+  const uint32_t bufcols = static_cast<uint32_t>(ntile * N);
   uint32_t tcols = 32;
-  while (tcols < static_cast<uint32_t>(ntile * N)) tcols <<= 1;
+  while (tcols < 2 * bufcols) tcols <<= 1;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
                  "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)));
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar + 1)));
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
+  const uint32_t lane_off = static_cast<uint32_t>((warp & 3) * 32) << 16;
+  const int half = warp >> 2;                    // which 16 of the 32 output channels
+
+  // stage unwrapped input row yu of image b into its ring slot
+  auto stage = [&](int b, int yu) {
+    const int yy = wrapi(yu, Y);
+    unsigned char* slot = srow + static_cast<size_t>((yu + kRing) % kRing) * slot_bytes;
+    for (int i = tid; i < (X + 2) * KC; i += kConvThreads) {
+      const int pidx = i / KC, kc = i - pidx * KC;
+      const int x = wrapi(pidx - 1, X);
+      unsigned char* dst = slot + (static_cast<size_t>(kc) * RP + pidx) * 16;
+      if (kIn == 0) {
+        const int j = yy * X + x;
+        __align__(16) __nv_bfloat16 f[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] = __float2bfloat16(0.f);
+        if (kc == 0) {
+          const uint8_t fl = a.eflags[j];
+          f[0] = __float2bfloat16(a.spins[static_cast<size_t>(b) * n + j] > 0 ? 1.f : -1.f);
+          f[1] = __float2bfloat16((fl & 1u) ? -1.f : 1.f);
+          f[2] = __float2bfloat16((fl & 2u) ? -1.f : 1.f);
+        }
+        *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(f);
+      } else {
+        cp_async16(saddr(dst), a.in + (static_cast<size_t>(b) * n + yy * X + x) * 32 + kc * 8);
+      }
+    }
+  };
+
+  // Descriptor bases: the start-address field is the low 14 bits (address >> 4)
+  // and shared addresses stay below 256 KB, so offsets add without carries.
+  const uint32_t lbo_a = static_cast<uint32_t>(RP) * 16;
+  const uint64_t adesc0 = smem_desc(saddr(srow), lbo_a, 128);
+  const uint64_t bdesc0 = smem_desc(saddr(sw), NG * 128, 128);
+  const uint32_t slot16 = static_cast<uint32_t>(slot_bytes >> 4);
+  auto issue_mmas = [&](int y, uint32_t buf) {
+    constexpr uint32_t idesc = idesc_bf16(128, N);
+    uint64_t arow[3];
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) arow[ky] = adesc0 + static_cast<uint64_t>(((y + ky - 1 + kRing) % kRing) * slot16);
+    for (int t = 0; t < ntile; ++t) {
+      const uint32_t d = tmem + buf * bufcols + static_cast<uint32_t>(t * N);
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+#pragma unroll
+        for (int ks = 0; ks < KC / 2; ++ks) {
+          const uint64_t ad = arow[tap / 3] + static_cast<uint64_t>((2 * ks * lbo_a + (t * 128 + tap % 3) * 16) >> 4);
+          const uint64_t bd = bdesc0 + static_cast<uint64_t>(((tap * KC + 2 * ks) * NG * 128) >> 4);
+          mma_tc(d, ad, bd, idesc, (tap | ks) != 0);
+        }
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     saddr(mbar + buf))
+                 : "memory");
+  };
+
+  auto epilogue = [&](int b, int y, uint32_t buf) {
+    if (kOut == 2 && half) return;               // one logit channel: the first warpgroup alone
+    for (int t = 0; t < ntile; ++t) {
+      const int x = t * 128 + (warp & 3) * 32 + lane;
+      const size_t p = static_cast<size_t>(b) * n + static_cast<size_t>(y) * X + x;
+      const uint32_t col = tmem + lane_off + buf * bufcols + static_cast<uint32_t>(t * N);
+      if (kOut == 2) {
+        float v[1];
+        tmem_ld<1>(col, v);
+        if (x < X) a.out_f32[p] = v[0] + a.bias[0];
+        continue;
+      }
+      float v[16];
+      tmem_ld<16>(col + static_cast<uint32_t>(half * 16), v);
+      if (x >= X) continue;
+      __align__(16) __nv_bfloat16 o[16];
+      if (kOut == 0) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16(fmaxf(v[c] + a.bias[half * 16 + c], 0.f));
+      } else {
+        const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * 32 + half * 16);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const uint4 mv = mk[q];
+          const __nv_bfloat16* m8 = reinterpret_cast<const __nv_bfloat16*>(&mv);
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            o[q * 8 + e] = __float2bfloat16(__bfloat162float(m8[e]) > 0.f ? v[q * 8 + e] : 0.f);
+        }
+      }
+      uint4* dst = reinterpret_cast<uint4*>(a.out_bf16 + p * 32 + half * 16);
+      dst[0] = reinterpret_cast<const uint4*>(o)[0];
+      dst[1] = reinterpret_cast<const uint4*>(o)[1];
+    }
+  };
 
   const long long R = static_cast<long long>(a.B) * Y;
   const long long r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
-  uint32_t phase = 0;
-  int staged_b = -1, staged_next = 0;   // rows staged for image staged_b up to unwrapped row staged_next - 1
+  uint32_t phases = 0;   // bit j: parity to wait for on mbar[j]
   bool ok = true;
-  for (long long row = r0; row < r1 && ok; ++row) {
-    const int b = static_cast<int>(row / Y), y = static_cast<int>(row - static_cast<long long>(b) * Y);
-    int first = y - 1;
-    if (staged_b == b && staged_next == y + 1) first = y + 1;   // only the new lower row
-    // ---- stage input rows first .. y+1 (unwrapped y-1 .. y+1) into ring slots
-    for (int yu = first; yu <= y + 1; ++yu) {
-      const int yy = wrapi(yu, Y);
-      unsigned char* slot = srow + static_cast<size_t>((yu + 3) % 3) * slot_bytes;
-      for (int i = tid; i < (X + 2) * KC; i += kTcThreads) {
-        const int pidx = i / KC, kc = i - pidx * KC;
-        const int x = wrapi(pidx - 1, X);
-        uint4 v;
-        if (kIn == 0) {
-          const int j = yy * X + x;
-          __align__(16) __nv_bfloat16 f[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) f[e] = __float2bfloat16(0.f);
-          if (kc == 0) {
-            const uint8_t fl = a.eflags[j];
-            f[0] = __float2bfloat16(a.spins[static_cast<size_t>(b) * n + j] > 0 ? 1.f : -1.f);
-            f[1] = __float2bfloat16((fl & 1u) ? -1.f : 1.f);
-            f[2] = __float2bfloat16((fl & 2u) ? -1.f : 1.f);
-          }
-          v = *reinterpret_cast<const uint4*>(f);
-        } else {
-          v = reinterpret_cast<const uint4*>(a.in + (static_cast<size_t>(b) * n + yy * X + x) * 32)[kc];
-        }
-        *reinterpret_cast<uint4*>(slot + (static_cast<size_t>(kc) * RP + pidx) * 16) = v;
+  for (long long row = r0; row < r1 && ok;) {
+    const int b = static_cast<int>(row / Y);
+    const long long img_end = static_cast<long long>(b + 1) * Y;
+    const long long seg_end = r1 < img_end ? r1 : img_end;
+    const int ya = static_cast<int>(row - static_cast<long long>(b) * Y);
+    const int yb = static_cast<int>(seg_end - 1 - static_cast<long long>(b) * Y);
+    stage(b, ya - 1);
+    stage(b, ya);
+    stage(b, ya + 1);
+    if (kIn != 0) cp_async_commit_wait_all();
+    if (ya + 2 <= yb + 1) stage(b, ya + 2);
+    if (kIn != 0) cp_async_commit();
+    for (int y = ya; y <= yb; ++y) {
+      // row y+1 staged by every thread, buffer y mod 2 drained by every thread;
+      // a wait that ran out anywhere ends the CTA's work here
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      ok = __syncthreads_and(ok) != 0;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok) break;
+      if (tid == 0) issue_mmas(y, static_cast<uint32_t>(y & 1));
+      bool prev = false;
+      if (y > ya) {
+        const uint32_t pb = static_cast<uint32_t>((y - 1) & 1);
+        prev = wait_mbar(saddr(mbar + pb), (phases >> pb) & 1u);
+        phases ^= 1u << pb;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!prev) ok = false;
       }
+      if (ok && y + 3 <= yb + 1) stage(b, y + 3);
+      if (kIn != 0) cp_async_commit();       // (possibly empty) group of row y+3
+      if (prev) epilogue(b, y - 1, static_cast<uint32_t>((y - 1) & 1));
+      if (kIn != 0) cp_async_wait_all_but_one();   // row y+2 has landed
     }
-    staged_b = b;
-    staged_next = y + 2;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- MMAs: per tile, 9 taps x KC/2 K-slices of 16
-    if (tid == 0) {
-      const uint32_t idesc = idesc_bf16(128, N);
-      const uint32_t lbo_a = static_cast<uint32_t>(RP) * 16, lbo_b = NG * 128;
-      for (int t = 0; t < ntile; ++t) {
-        for (int tap = 0; tap < 9; ++tap) {
-          const int ky = tap / 3, kx = tap - ky * 3;
-          const unsigned char* slot = srow + static_cast<size_t>((y + ky - 1 + 3) % 3) * slot_bytes;
-#pragma unroll
-          for (int ks = 0; ks < KC / 2; ++ks) {
-            const uint32_t a_addr = saddr(slot) + static_cast<uint32_t>(2 * ks) * lbo_a + (t * 128 + kx) * 16;
-            const uint32_t b_addr = saddr(sw) + static_cast<uint32_t>((tap * KC + 2 * ks) * NG * 128);
-            mma_tc(tmem + static_cast<uint32_t>(t * N), smem_desc(a_addr, lbo_a, 128), smem_desc(b_addr, lbo_b, 128),
-                   idesc, (tap | ks) != 0);
-          }
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(mbar))
-                   : "memory");
-    }
-    // ---- bounded wait for the MMAs
-    uint32_t done = 0;
-    const long long t_start = clock64();
-    while (!done) {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(done)
-          : "r"(saddr(mbar)), "r"(phase)
-          : "memory");
-      if (!done && clock64() - t_start > kWaitCycles) break;   // about two seconds
-    }
-    phase ^= 1u;
-    done = __syncthreads_and(done);   // one decision for the whole CTA
-    if (!done) {
-      if (tid == 0) atomicExch(a.status, ISING_ERR_TIMEOUT);
-      ok = false;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- epilogue: this thread's pixel of every tile
     if (ok) {
-      for (int t = 0; t < ntile; ++t) {
-        float v[N];
-        tmem_ld<N>(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(t * N), v);
-        const int x = t * 128 + warp * 32 + lane;
-        if (x >= X) continue;
-        const size_t p = static_cast<size_t>(b) * n + y * X + x;
-        if (kOut == 2) {
-          a.out_f32[p] = v[0] + a.bias[0];
-        } else {
-          __align__(16) __nv_bfloat16 o[32];
-          if (kOut == 0) {
-#pragma unroll
-            for (int c = 0; c < 32; ++c) o[c] = __float2bfloat16(fmaxf(v[c] + a.bias[c], 0.f));
-          } else {
-            const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * 32);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const uint4 mv = mk[q];
-              const __nv_bfloat16* m8 = reinterpret_cast<const __nv_bfloat16*>(&mv);
-#pragma unroll
-              for (int e = 0; e < 8; ++e)
-                o[q * 8 + e] = __float2bfloat16(__bfloat162float(m8[e]) > 0.f ? v[q * 8 + e] : 0.f);
-            }
-          }
-          uint4* dst = reinterpret_cast<uint4*>(a.out_bf16 + p * 32);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
-        }
-      }
+      const uint32_t lb = static_cast<uint32_t>(yb & 1);
+      const bool last = wait_mbar(saddr(mbar + lb), (phases >> lb) & 1u);
+      phases ^= 1u << lb;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (last) epilogue(b, yb, lb);
+      else ok = false;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    row = seg_end;
   }
+  if (!ok && tid == 0) atomicExch(a.status, ISING_ERR_TIMEOUT);
+  if (kIn != 0) cp_async_commit_wait_all();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
@@ -257,7 +334,7 @@ size_t smem_bytes_for(int X) {
   constexpr int KC = kIn == 0 ? 2 : 4;
   constexpr int NG = (kOut == 2 ? 16 : 32) / 8;
   const int RP = ((X + 127) / 128) * 128 + 2;
-  return static_cast<size_t>(9) * KC * NG * 128 + 3 * static_cast<size_t>(KC) * RP * 16 + 16;
+  return static_cast<size_t>(9) * KC * NG * 128 + kRing * static_cast<size_t>(KC) * RP * 16 + 32;
 }
 
 template <int kIn, int kOut>
@@ -267,7 +344,7 @@ cudaError_t launch_one(const TcConvArgs& a, int sms, cudaStream_t st) {
                                        static_cast<int>(sm));
   if (e != cudaSuccess) return e;
   // residency from shared memory (per-SM capacity, 1 KB reserved per CTA) and
-  // tensor memory (512 columns per SM), at most 16 CTAs of 4 warps
+  // tensor memory (512 columns per SM: two accumulator buffers per CTA)
   int dev = 0, smem_sm = 0, reserved = 0;
   e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -275,13 +352,14 @@ cudaError_t launch_one(const TcConvArgs& a, int sms, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   int per_sm = static_cast<int>(static_cast<size_t>(smem_sm) / (sm + static_cast<size_t>(reserved)));
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int cols = ((a.X + 127) / 128) * (kOut == 2 ? 16 : 32);
+  const int cols = 2 * ((a.X + 127) / 128) * (kOut == 2 ? 16 : 32);
   int tc = 32;
   while (tc < cols) tc <<= 1;
-  per_sm = std::min(std::min(per_sm, 512 / tc), 16);
+  if (tc > 512) return cudaErrorInvalidConfiguration;
+  per_sm = std::min(std::min(per_sm, 512 / tc), 8);
   const long long rows = static_cast<long long>(a.B) * a.Y;
   const long long grid = std::min<long long>(rows, static_cast<long long>(sms) * per_sm);
-  conv_tc_kernel<kIn, kOut><<<static_cast<int>(grid), kTcThreads, sm, st>>>(a);
+  conv_tc_kernel<kIn, kOut><<<static_cast<int>(grid), kConvThreads, sm, st>>>(a);
   return cudaGetLastError();
 }
 
