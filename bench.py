@@ -34,6 +34,7 @@ METRIC = "spin-updates/s; time-to-99.9%-cut on 200x100 +-1 torus, learned vs pla
 WORKLOAD = {"X": 200, "Y": 100, "inst_seed": 2, "trials": 1024, "sweeps": 10000, "beta0": 0.1, "beta1": 3.0,
             "seed": 1002}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PEAK_HBM_GBS = float(json.load(open(PEAKS_FILE)).get("hbm_gbs", 6800.0)) if os.path.exists(PEAKS_FILE) else 6800.0
 # Integer multiply lanes per SM per clock (32-bit IMAD; a 32x32->64 multiply
 # counts as two) on this part: 4 sub-partitions x 16 lanes.
 IMAD_LANES_PER_SM = 64
@@ -99,6 +100,10 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+CNN_FLOP_PER_SITE = 2 * 9 * (3 * 32 + 32 * 32 * 2 + 32 * 1)
+CNN_BYTES_PER_SITE = 1 + 3 * 2 * 64 + 4   # spins in, three BF16 maps written and read, FP32 logits out
+
+
 # ------------------------------------------------------------------ CPU oracle
 def _oracle_slice(args):
     import oracle  # test infrastructure: the CPU baseline leg only
@@ -131,11 +136,11 @@ def oracle_throughput(w, inst, sweeps=3000, trials_per_proc=1, procs=None):
 
 # ------------------------------------------------------------------ helpers
 def ttt_stats(cuts, t_step_s, trials, sweeps, quality=0.999):
-    import oracle  # Eq. 3-5 helpers
+    from paper_2505_18508_gb300 import stats  # Eq. 3-5
     best = int(cuts.max())
-    target = oracle.target_cut(best, quality)
-    Ps = oracle.success_probability(cuts, target)
-    r = oracle.repetitions(Ps)
+    target = stats.target_cut(best, quality)
+    Ps = stats.success_probability(cuts, target)
+    r = stats.repetitions(Ps)
     t_trial = t_step_s / trials
     return {"best_cut": best, "target": target, "P_s": Ps, "r": r, "STT_sweeps": sweeps * r,
             "TTT_s_throughput_form": t_trial * r,
@@ -143,64 +148,102 @@ def ttt_stats(cuts, t_step_s, trials, sweeps, quality=0.999):
             "cut_mean": float(cuts.mean()), "cut_min": int(cuts.min())}
 
 
-def learned_leg(sweeps=10000, every=100, tile=10, n_train=256, train_sweeps=1000, steps=800):
+def learned_leg(budgets=(1000, 3000, 10000, 30000), every=100, tile=10, n_train=256, train_sweeps=1000,
+                steps=800):
     """Config 5 of the workload set: 200x100 tori, 8 seeds x 512 trials, the
-    plain annealer against the learned form (network retrained on 20,000-spin
-    snapshots of the plain annealer on held-out seeds) at a matched 99.9%
-    target: per seed, best = highest cut either form found, target =
-    ceil(0.999 best), TTT = (batch wall time / trials) * r(P_s) (Eq. 3, 5)."""
+    plain annealer against the learned form (network trained on 20,000-spin
+    snapshots of the plain annealer on held-out seeds), on the sweep-budget
+    ladder.  Per seed: best = the highest cut either form found at any budget,
+    target = ceil(0.999 best); per (form, budget): P_s, r and
+    TTT = (batch wall time / trials) * r (Eq. 3, 5)."""
     import torch
-    import oracle
     import paper_2505_18508_gb300 as ia
-    from oracle import cnn as ocnn
-    from paper_2505_18508_gb300 import learned
+    from paper_2505_18508_gb300 import learned, stats
     t0 = time.perf_counter()
     tb = synth.linear_betas(0.1, 3.0, train_sweeps)
     train = [synth.torus_instance(200, 100, 40000 + k) for k in range(n_train)]
     data = learned.make_dataset(train, tb, every, snap_trials=4, target="future")
-    net = ia.CNN(ocnn.init_params(3, scale=0.7))
+    net = ia.CNN(synth.cnn_init_params(3, scale=0.7))
     losses = learned.train(net, data, steps, batch=16, lr=2e-3, log_every=steps // 4)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     for d in data:
         d[0].destroy()
-    betas = synth.linear_betas(0.1, 3.0, sweeps)
     T = 512
+    # the network's forward pass on this workload (one proposal round's logits)
+    prob = ia.Problem.from_instance(synth.torus_instance(200, 100, 30000))
+    s0 = torch.from_numpy(synth.random_spins(T, prob.n, 1)).cuda()
+    z = torch.empty((T, prob.n), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        net.forward(prob, s0, out=z)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        net.forward(prob, s0, out=z)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 10
+    sites = T * prob.n
+    fwd_gbs = CNN_BYTES_PER_SITE * sites / (fwd_ms * 1e-3) / 1e9
+    cnn = {"forward_ms": fwd_ms, "sites": sites,
+           "useful_tflops": CNN_FLOP_PER_SITE * sites / (fwd_ms * 1e-3) / 1e12,
+           "algorithmic_gbs": fwd_gbs, "hbm_frac": fwd_gbs / PEAK_HBM_GBS,
+           "note": "forward = 4 tcgen05 convolution launches; 389 algorithmic HBM bytes per site; "
+                   "hbm_frac of measured copy bandwidth"}
+    prob.destroy()
     rows = []
     for q in range(8):
         inst = synth.torus_instance(200, 100, 30000 + q)
         prob = ia.Problem.from_instance(inst)
         seed = 70000 + q
-        torch.cuda.synchronize(); a = time.perf_counter()
-        _, cp = ia.anneal(prob, T, betas, seed)
-        torch.cuda.synchronize(); b = time.perf_counter()
-        st = {}
-        _, cl = learned.anneal_learned(prob, net, T, betas, seed, every=every, tile=tile, stats=st)
-        torch.cuda.synchronize(); c = time.perf_counter()
-        cp, cl = cp.cpu().numpy(), cl.cpu().numpy()
-        best = int(max(cp.max(), cl.max()))
-        tgt = oracle.target_cut(best)
+        runs = {}
+        for S in budgets:
+            betas = synth.linear_betas(0.1, 3.0, S)
+            torch.cuda.synchronize(); a = time.perf_counter()
+            _, cp = ia.anneal(prob, T, betas, seed)
+            torch.cuda.synchronize(); b = time.perf_counter()
+            st = {}
+            _, cl = learned.anneal_learned(prob, net, T, betas, seed, every=every, tile=tile, stats=st)
+            torch.cuda.synchronize(); c = time.perf_counter()
+            runs[S] = {"plain": (cp.cpu().numpy(), b - a, None),
+                       "learned": (cl.cpu().numpy(), c - b, st.get("accepted_per_trial"))}
+        best = int(max(max(v[f][0].max() for f in ("plain", "learned")) for v in runs.values()))
+        tgt = stats.target_cut(best)
         row = {"seed": 30000 + q, "best": best, "target": tgt}
-        for name, cuts, wall in (("plain", cp, b - a), ("learned", cl, c - b)):
-            Ps = oracle.success_probability(cuts, tgt)
-            r = oracle.repetitions(Ps)
-            row[name] = {"P_s": Ps, "mean_cut": float(cuts.mean()), "wall_s": wall,
-                         "TTT_s": (wall / T) * r if math.isfinite(r) else None}
-        row["learned"]["accepted_per_trial"] = st.get("accepted_per_trial")
+        for S in budgets:
+            for name in ("plain", "learned"):
+                cuts, wall, acc = runs[S][name]
+                Ps = stats.success_probability(cuts, tgt)
+                r = stats.repetitions(Ps)
+                e = {"P_s": Ps, "mean_cut": float(cuts.mean()), "wall_s": wall,
+                     "TTT_s": (wall / T) * r if math.isfinite(r) else None}
+                if acc is not None:
+                    e["accepted_per_trial"] = acc
+                row[f"{name}@{S}"] = e
         rows.append(row)
         prob.destroy()
     net.destroy()
 
     def med(key):
         v = [r[key]["TTT_s"] for r in rows if r[key]["TTT_s"] is not None]
-        return float(np.median(v)) if v else None
-    return {"workload": "200x100 tori, seeds 30000-30007, 512 trials each, 10,000 sweeps, beta 0.1->3.0; "
-                        "proposals every 100 sweeps, tiles 10x10",
+        return float(np.median(v)) if len(v) == len(rows) else None
+    ladder = {f"{name}@{S}": {"median_TTT_s": med(f"{name}@{S}"),
+                              "reached": sum(r[f"{name}@{S}"]["TTT_s"] is not None for r in rows),
+                              "mean_P_s": float(np.mean([r[f"{name}@{S}"]["P_s"] for r in rows]))}
+              for S in budgets for name in ("plain", "learned")}
+
+    def best_budget(name):
+        c = [(v["median_TTT_s"], k) for k, v in ladder.items() if k.startswith(name) and v["median_TTT_s"]]
+        return min(c) if c else (None, None)
+    bp, bl = best_budget("plain"), best_budget("learned")
+    return {"workload": "200x100 tori, seeds 30000-30007, 512 trials each, beta 0.1->3.0 over S sweeps, "
+                        f"S in {list(budgets)}; proposals every {every} sweeps, tiles {tile}x{tile}",
             "train": {"instances": n_train, "snapshot_sweeps": train_sweeps, "steps": steps, "loss": losses,
                       "seconds": t_train},
-            "median_TTT_s": {"plain": med("plain"), "learned": med("learned")},
-            "reached": {"plain": sum(r["plain"]["TTT_s"] is not None for r in rows),
-                        "learned": sum(r["learned"]["TTT_s"] is not None for r in rows)},
+            "cnn_forward": cnn,
+            "ladder": ladder,
+            "best_median_TTT_s": {"plain": bp[0], "plain_budget": bp[1], "learned": bl[0],
+                                  "learned_budget": bl[1]},
             "per_seed": rows}
 
 
@@ -371,7 +414,7 @@ def main():
     h2d = 2 * n + 8 * S                      # packed instance flags + threshold table
     d2h = T * n + 4 * T
 
-    # ---- roofline: integer-multiply pipe (Philox), see the design doc
+    # ---- roofline: integer-multiply pipe (Philox multiplies per update vs IMAD lanes)
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -380,7 +423,8 @@ def main():
     achieved_tops = ups * IMAD_OPS_PER_UPDATE / (ms / 1e3) / 1e12 / 1.0
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (32-bit IMAD)",
                 "frac": achieved_tops / peak_tops, "traffic": None,
-                "kernel": "anneal_strip_kernel", "peak_source": f"{sms} SMs x {IMAD_LANES_PER_SM} IMAD lanes x "
+                "kernel": {1: "anneal_strip_kernel", 2: "anneal_flow_kernel"}.get(prob.last_kernel(), "?"),
+                "peak_source": f"{sms} SMs x {IMAD_LANES_PER_SM} IMAD lanes x "
                 f"{clk_mhz:.0f} MHz (sm_max_mhz of measured peaks file)"}
 
     stats = ttt_stats(first_cuts.cpu().numpy(), ms / 1e3, T, S) if args.steps > 0 else None

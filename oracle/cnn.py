@@ -54,16 +54,9 @@ def unflatten(params):
 
 
 def init_params(seed, scale=1.0):
-    """He-style initialisation (std sqrt(2/fan_in) * scale), zero biases."""
-    rng = np.random.Generator(np.random.PCG64(int(seed)))
-    parts = []
-    for name, shp in SHAPES:
-        if name.startswith("b"):
-            parts.append(np.zeros(shp))
-        else:
-            fan_in = shp[1] * shp[2] * shp[3]
-            parts.append(rng.normal(0.0, scale * np.sqrt(2.0 / fan_in), size=shp))
-    return np.concatenate([p.reshape(-1) for p in parts]).astype(np.float64)
+    """Seeded starting weights: the shared input generator (synth)."""
+    import synth
+    return synth.cnn_init_params(seed, scale)
 
 
 def features(spins, w_right, w_down):

@@ -98,7 +98,9 @@ __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ z, 
 }
 
 // ------------------------------------------------------------------ layer 4 backward
-// g3[p][c] = [h3[p][c] > 0] * sum_tap W4[c][tap] dz[p - tap + 1]
+// g3[p][c] = [h3[p][c] > 0] * sum_tap W4[c][tap] dz[p - tap + 1].  One thread
+// per (pixel, 8-channel chunk): a warp reads and writes 8 whole pixels
+// (512 contiguous bytes) of h3 and g3.
 __global__ void __launch_bounds__(256) layer4_back_kernel(const float* __restrict__ dz,
                                                           const __nv_bfloat16* __restrict__ h3, int B, int X, int Y,
                                                           const float* __restrict__ w4r,
@@ -107,34 +109,37 @@ __global__ void __launch_bounds__(256) layer4_back_kernel(const float* __restric
   for (int i = threadIdx.x; i < 288; i += blockDim.x) w[i] = w4r[i];
   __syncthreads();
   const int n = X * Y;
-  const long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (p >= static_cast<long long>(B) * n) return;
+  const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= static_cast<long long>(B) * n * 4) return;
+  const long long p = q >> 2;
+  const int ch = static_cast<int>(q & 3);
   const int b = static_cast<int>(p / n);
   const int site = static_cast<int>(p - static_cast<long long>(b) * n);
   const int y = site / X, x = site - y * X;
   float d[9];
+#pragma unroll
   for (int ky = 0; ky < 3; ++ky) {
     int yy = y - ky + 1;
     yy = yy < 0 ? yy + Y : (yy >= Y ? yy - Y : yy);
+#pragma unroll
     for (int kx = 0; kx < 3; ++kx) {
       int xx = x - kx + 1;
       xx = xx < 0 ? xx + X : (xx >= X ? xx - X : xx);
       d[ky * 3 + kx] = dz[static_cast<size_t>(b) * n + yy * X + xx];
     }
   }
-  const __nv_bfloat16* hp = h3 + static_cast<size_t>(p) * 32;
-  __align__(16) __nv_bfloat16 out[32];
-#pragma unroll 4
-  for (int c = 0; c < 32; ++c) {
+  const uint4 hv = reinterpret_cast<const uint4*>(h3 + static_cast<size_t>(p) * 32)[ch];
+  const __nv_bfloat16* hp = reinterpret_cast<const __nv_bfloat16*>(&hv);
+  __align__(16) __nv_bfloat16 out[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int c = ch * 8 + e;
     float acc = 0.f;
 #pragma unroll
     for (int t = 0; t < 9; ++t) acc = fmaf(w[c * 9 + t], d[t], acc);
-    out[c] = __float2bfloat16(__bfloat162float(hp[c]) > 0.f ? acc : 0.f);
+    out[e] = __float2bfloat16(__bfloat162float(hp[e]) > 0.f ? acc : 0.f);
   }
-  uint4* dst = reinterpret_cast<uint4*>(g3 + static_cast<size_t>(p) * 32);
-  const uint4* src = reinterpret_cast<const uint4*>(out);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) dst[q] = src[q];
+  reinterpret_cast<uint4*>(g3 + static_cast<size_t>(p) * 32)[ch] = *reinterpret_cast<const uint4*>(out);
 }
 
 // ------------------------------------------------------------------ Adam
@@ -379,7 +384,7 @@ int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* s
   const int blocks = static_cast<int>((N + 255) / 256);
   const int X = p->X, Y = p->Y;
   loss_kernel<<<blocks, 256, 0, st>>>(w.z, targets, N, w.dz, loss);
-  layer4_back_kernel<<<blocks, 256, 0, st>>>(w.dz, w.h3, B, X, Y, net->w4r, w.g3);
+  layer4_back_kernel<<<static_cast<int>((4 * N + 255) / 256), 256, 0, st>>>(w.dz, w.h3, B, X, Y, net->w4r, w.g3);
   {
     TcConvArgs a = tc_args(p, B);
     a.in = w.g3;

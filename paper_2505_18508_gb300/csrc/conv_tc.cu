@@ -557,9 +557,32 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(TcWgradArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
-// Sum the CTAs' partials (fixed order) into dW[o][c][ky*3+kx] and db[o].
+// First reduction stage: group g of kGroups sums the partials of CTAs
+// g, g + kGroups, ... (increasing order) and leaves the sum in CTA g's slot.
+constexpr int kGroups = 16;
 template <int kKind>
-__global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ bpart, int ncta,
+__global__ void wgrad_group_kernel(float* __restrict__ part, float* __restrict__ bpart, int ncta) {
+  constexpr int N = kKind == 2 ? 32 : 96;
+  constexpr int E = 96 * N;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;
+  if (g >= ncta) return;
+  if (e < E) {
+    float s = 0.f;
+    for (int k = g; k < ncta; k += kGroups) s += part[static_cast<size_t>(k) * E + e];
+    part[static_cast<size_t>(g) * E + e] = s;
+  } else if (e < E + 32) {
+    const int o = e - E;
+    float s = 0.f;
+    for (int k = g; k < ncta; k += kGroups) s += bpart[static_cast<size_t>(k) * 32 + o];
+    bpart[static_cast<size_t>(g) * 32 + o] = s;
+  }
+}
+
+// Second stage: sum the group results (fixed order) into dW[o][c][ky*3+kx]
+// and db[o].
+template <int kKind>
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ bpart, int ngroups,
                                     float* __restrict__ dW, float* __restrict__ db) {
   constexpr int C = kKind == 0 ? 3 : 32;
   constexpr int O = kKind == 2 ? 1 : 32;
@@ -570,18 +593,18 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float*
     const size_t row = static_cast<size_t>(ky * 32 + c) * N;
     float s = 0.f;
     if (kKind == 2) {
-      for (int k = 0; k < ncta; ++k) {
+      for (int k = 0; k < ngroups; ++k) {
         const float* pk = part + static_cast<size_t>(k) * 96 * N + row + kx * 8;
         s += pk[0] + pk[1];
       }
     } else {
-      for (int k = 0; k < ncta; ++k) s += part[static_cast<size_t>(k) * 96 * N + row + kx * 32 + o];
+      for (int k = 0; k < ngroups; ++k) s += part[static_cast<size_t>(k) * 96 * N + row + kx * 32 + o];
     }
     dW[(o * C + c) * 9 + tap] = s;
   } else if (t < O * C * 9 + O) {
     const int o = t - O * C * 9;
     float s = 0.f;
-    for (int k = 0; k < ncta; ++k) s += bpart[static_cast<size_t>(k) * 32 + o];
+    for (int k = 0; k < ngroups; ++k) s += bpart[static_cast<size_t>(k) * 32 + o];
     db[o] = s;
   }
 }
@@ -613,8 +636,14 @@ cudaError_t launch_wgrad_one(const TcWgradArgs& a, int sms, float* dW, float* db
   wgrad_tc_kernel<kKind><<<static_cast<int>(grid), kTcThreads, sm, st>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const int ncta = static_cast<int>(grid);
+  const int ngroups = std::min(ncta, kGroups);
+  constexpr int elems = 96 * (kKind == 2 ? 32 : 96) + 32;
+  wgrad_group_kernel<kKind><<<dim3((elems + 255) / 256, ngroups), 256, 0, st>>>(a.part, a.bpart, ncta);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   constexpr int outs = (kKind == 0 ? 3 : 32) * (kKind == 2 ? 1 : 32) * 9 + (kKind == 2 ? 1 : 32);
-  wgrad_reduce_kernel<kKind><<<(outs + 255) / 256, 256, 0, st>>>(a.part, a.bpart, static_cast<int>(grid), dW, db);
+  wgrad_reduce_kernel<kKind><<<(outs + 255) / 256, 256, 0, st>>>(a.part, a.bpart, ngroups, dW, db);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ __all__ = [
     "linear_betas",
     "random_spins",
     "batched_config",
+    "cnn_init_params",
 ]
 
 
@@ -108,3 +109,28 @@ def batched_config(count: int = 96, base_seed: int = 100):
             "seed": 5000 + k,
         })
     return out
+
+
+# Parameter shapes of the learned stage's network, in the order of its flat
+# FP32 parameter vector: W1[32,3,3,3] b1 W2[32,32,3,3] b2 W3[32,32,3,3] b3
+# W4[1,32,3,3] b4.
+CNN_SHAPES = [
+    ("W1", (32, 3, 3, 3)), ("b1", (32,)),
+    ("W2", (32, 32, 3, 3)), ("b2", (32,)),
+    ("W3", (32, 32, 3, 3)), ("b3", (32,)),
+    ("W4", (1, 32, 3, 3)), ("b4", (1,)),
+]
+
+
+def cnn_init_params(seed: int, scale: float = 1.0) -> np.ndarray:
+    """Seeded starting weights (float64 [19681]): normal with standard deviation
+    scale * sqrt(2 / fan_in) for the convolution weights, zero biases (PCG64)."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    parts = []
+    for name, shp in CNN_SHAPES:
+        if name.startswith("b"):
+            parts.append(np.zeros(shp))
+        else:
+            fan_in = shp[1] * shp[2] * shp[3]
+            parts.append(rng.normal(0.0, scale * np.sqrt(2.0 / fan_in), size=shp))
+    return np.concatenate([p.reshape(-1) for p in parts]).astype(np.float64)
