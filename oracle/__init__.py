@@ -52,6 +52,12 @@ def lib():
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,   # init, spins, cuts, check
         ]
         L.oracle_anneal.restype = ctypes.c_int
+        L.oracle_anneal_bits.argtypes = L.oracle_anneal.argtypes + [ctypes.c_int32]   # + draw_bits
+        L.oracle_anneal_bits.restype = ctypes.c_int
+        L.oracle_thresholds16.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_thresholds16.restype = ctypes.c_int
+        L.oracle_draw.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32]
+        L.oracle_draw.restype = ctypes.c_uint32
         _lib = L
     return _lib
 
@@ -72,27 +78,36 @@ def philox4x32_10(ctr, key):
     return [int(v) for v in o]
 
 
-def thresholds(betas):
-    """(T4, T8) uint32 arrays: T_d = min(floor(exp(-beta d) 2^32), 2^32-1)."""
+def thresholds(betas, draw_bits=32):
+    """(T4, T8) uint32 arrays: T_d = min(floor(exp(-beta d) 2^B), 2^B - 1),
+    B = draw_bits (32, or 16 for the 16-bit draw mode)."""
     b = np.ascontiguousarray(betas, dtype=np.float64)
     S = b.shape[0]
     T4 = np.zeros(S, dtype=np.uint32)
     T8 = np.zeros(S, dtype=np.uint32)
-    rc = lib().oracle_thresholds(_ptr(b), S, _ptr(T4), _ptr(T8))
+    fn = lib().oracle_thresholds16 if draw_bits == 16 else lib().oracle_thresholds
+    rc = fn(_ptr(b), S, _ptr(T4), _ptr(T8))
     if rc != 0:
         raise ValueError("inverse temperatures must be positive")
     return T4, T8
+
+
+def decision_draw(i, k, t, seed, draw_bits=32):
+    """The uniform draw of trial t at site i in sweep k (32- or 16-bit mode)."""
+    return int(lib().oracle_draw(int(i) & 0xFFFFFFFF, int(k) & 0xFFFFFFFF, int(t),
+                                 int(seed) & 0xFFFFFFFFFFFFFFFF, int(draw_bits)))
 
 
 # --------------------------------------------------------------------------
 # The annealer (C) and Eq. 1 / Eq. 2 on the CSR (C)
 # --------------------------------------------------------------------------
 def anneal(inst, betas, seed, trials=None, t_begin=0, t_count=None, sweep_offset=0,
-           init=None, check_fields=False):
+           init=None, check_fields=False, draw_bits=32):
     """Run the sequential Metropolis annealer on the CSR instance ``inst``.
 
     Trials t_begin .. t_begin+t_count-1 (global indices select the random
-    stream).  Returns (spins int8 [t_count, n], cuts int32 [t_count]).
+    stream).  draw_bits: 32 (the default stream) or 16 (the 16-bit draw
+    mode).  Returns (spins int8 [t_count, n], cuts int32 [t_count]).
     """
     if t_count is None:
         t_count = trials if trials is not None else 0
@@ -107,10 +122,11 @@ def anneal(inst, betas, seed, trials=None, t_begin=0, t_count=None, sweep_offset
     if init is not None:
         ini = np.ascontiguousarray(init, dtype=np.int8)
         assert ini.shape == (t_count, n)
-    rc = lib().oracle_anneal(n, _ptr(row_ptr), _ptr(col), _ptr(J), int(inst["X"]),
-                             int(t_begin), int(t_count), _ptr(b), int(b.shape[0]),
-                             int(seed) & 0xFFFFFFFFFFFFFFFF, int(sweep_offset) & 0xFFFFFFFF,
-                             _ptr(ini), _ptr(spins), _ptr(cuts), 1 if check_fields else 0)
+    rc = lib().oracle_anneal_bits(n, _ptr(row_ptr), _ptr(col), _ptr(J), int(inst["X"]),
+                                  int(t_begin), int(t_count), _ptr(b), int(b.shape[0]),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(sweep_offset) & 0xFFFFFFFF,
+                                  _ptr(ini), _ptr(spins), _ptr(cuts), 1 if check_fields else 0,
+                                  int(draw_bits))
     if rc == -3:
         raise AssertionError("incremental local fields diverged from recomputed fields")
     if rc != 0:

@@ -32,6 +32,13 @@
  *     bits); trial t uses output word t mod 4.  The starting spin of trial t
  *     at site i is +1 when bit 31 of word t mod 4 of the block for counter
  *     (i, 0xFFFFFFFF, t/4, 0) is set.
+ *   - 16-bit draw mode (a variant of this project, not of the paper: one
+ *     Philox block serves eight trials instead of four).  Trial t at site i
+ *     in sweep k draws the 16-bit half (t mod 2: low half for even t, high
+ *     half for odd t) of word (t mod 8)/2 of the block at counter
+ *     (i, k, t/8, 0), and the thresholds are
+ *     T_dE = min(floor(exp(-beta dE) 2^16), 2^16 - 1).  The starting spins
+ *     are the same as in the 32-bit mode.
  *
  * Every function returns 0 on success and a negative value on bad input.
  */
@@ -81,6 +88,24 @@ static uint32_t draw(uint32_t a, uint32_t b, int32_t t, uint64_t seed)
     return out[t & 3];
 }
 
+/* one 16-bit draw: half (t mod 2) of word (t mod 8)/2 of the block at      */
+/* counter (a, b, t/8, 0); the low half for even t                          */
+static uint32_t draw16(uint32_t a, uint32_t b, int32_t t, uint64_t seed)
+{
+    uint32_t ctr[4] = {a, b, (uint32_t)t >> 3, 0u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    uint32_t word = out[(t & 7) >> 1];
+    return (t & 1) ? (word >> 16) : (word & 0xFFFFu);
+}
+
+/* exported for the pins: the decision draw of either mode */
+uint32_t oracle_draw(uint32_t i, uint32_t k, int32_t t, uint64_t seed, int32_t bits)
+{
+    return bits == 16 ? draw16(i, k, t, seed) : draw(i, k, t, seed);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Acceptance thresholds for the Metropolis test, one pair per sweep:        */
 /*   T_d = min(floor(exp(-beta d) * 2^32), 2^32 - 1),  d in {4, 8}.          */
@@ -94,6 +119,27 @@ static int threshold_one(double beta, double d, uint32_t* out)
     double fl = floor(scaled);
     if (fl >= 4294967295.0) *out = 0xFFFFFFFFu;
     else *out = (uint32_t)fl;
+    return 0;
+}
+
+/* the 16-bit mode: T_d = min(floor(exp(-beta d) * 2^16), 2^16 - 1) */
+static int threshold16_one(double beta, double d, uint32_t* out)
+{
+    if (!(beta > 0.0)) return -1;
+    double p = exp(-(beta * d));
+    double fl = floor(p * 65536.0);
+    if (fl >= 65535.0) *out = 0xFFFFu;
+    else *out = (uint32_t)fl;
+    return 0;
+}
+
+int oracle_thresholds16(const double* betas, int32_t S, uint32_t* T4, uint32_t* T8)
+{
+    if (S < 0) return -1;
+    for (int32_t k = 0; k < S; ++k) {
+        if (threshold16_one(betas[k], 4.0, &T4[k]) != 0) return -1;
+        if (threshold16_one(betas[k], 8.0, &T8[k]) != 0) return -1;
+    }
     return 0;
 }
 
@@ -159,13 +205,15 @@ int64_t oracle_energy(int32_t n, const int64_t* row_ptr, const int32_t* col,
 /* a mismatch).                                                              */
 /* Returns 0, -1 for bad arguments, -2 for a dE outside {-8,-4,0,4,8}.      */
 /* ------------------------------------------------------------------------ */
-int oracle_anneal(int32_t n, const int64_t* row_ptr, const int32_t* col, const int8_t* J,
-                  int32_t X, int32_t t_begin, int32_t t_count,
-                  const double* betas, int32_t S, uint64_t seed, uint32_t sweep_offset,
-                  const int8_t* init, int8_t* out_spins, int32_t* out_cuts,
-                  int32_t check_fields)
+/* draw_bits: 32 (the default stream) or 16 (the 16-bit draw mode).         */
+int oracle_anneal_bits(int32_t n, const int64_t* row_ptr, const int32_t* col, const int8_t* J,
+                       int32_t X, int32_t t_begin, int32_t t_count,
+                       const double* betas, int32_t S, uint64_t seed, uint32_t sweep_offset,
+                       const int8_t* init, int8_t* out_spins, int32_t* out_cuts,
+                       int32_t check_fields, int32_t draw_bits)
 {
     if (n <= 0 || X <= 0 || n % X != 0 || t_begin < 0 || t_count < 0 || S < 0) return -1;
+    if (draw_bits != 32 && draw_bits != 16) return -1;
     uint32_t* T4 = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(S > 0 ? S : 1));
     uint32_t* T8 = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(S > 0 ? S : 1));
     int* s = (int*)malloc(sizeof(int) * (size_t)n);
@@ -173,7 +221,11 @@ int oracle_anneal(int32_t n, const int64_t* row_ptr, const int32_t* col, const i
     int* colour = (int*)malloc(sizeof(int) * (size_t)n);
     int rc = 0;
     if (!T4 || !T8 || !s || !f || !colour) { rc = -1; goto done; }
-    if (oracle_thresholds(betas, S, T4, T8) != 0) { rc = -1; goto done; }
+    if (draw_bits == 16) {
+        if (oracle_thresholds16(betas, S, T4, T8) != 0) { rc = -1; goto done; }
+    } else {
+        if (oracle_thresholds(betas, S, T4, T8) != 0) { rc = -1; goto done; }
+    }
     for (int32_t i = 0; i < n; ++i) colour[i] = ((i % X) + (i / X)) & 1;
 
     for (int32_t tt = 0; tt < t_count; ++tt) {
@@ -203,7 +255,9 @@ int oracle_anneal(int32_t n, const int64_t* row_ptr, const int32_t* col, const i
                         if (dE == 4) thr = T4[j];
                         else if (dE == 8) thr = T8[j];
                         else { rc = -2; goto done; }
-                        flip = draw((uint32_t)i, k, t, seed) < thr;
+                        uint32_t u = draw_bits == 16 ? draw16((uint32_t)i, k, t, seed)
+                                                     : draw((uint32_t)i, k, t, seed);
+                        flip = u < thr;
                     }
                     if (flip) {
                         s[i] = -s[i];
@@ -234,4 +288,14 @@ int oracle_anneal(int32_t n, const int64_t* row_ptr, const int32_t* col, const i
 done:
     free(T4); free(T8); free(s); free(f); free(colour);
     return rc;
+}
+
+int oracle_anneal(int32_t n, const int64_t* row_ptr, const int32_t* col, const int8_t* J,
+                  int32_t X, int32_t t_begin, int32_t t_count,
+                  const double* betas, int32_t S, uint64_t seed, uint32_t sweep_offset,
+                  const int8_t* init, int8_t* out_spins, int32_t* out_cuts,
+                  int32_t check_fields)
+{
+    return oracle_anneal_bits(n, row_ptr, col, J, X, t_begin, t_count, betas, S, seed, sweep_offset,
+                              init, out_spins, out_cuts, check_fields, 32);
 }

@@ -5,8 +5,9 @@
 * ``anneal_full_energy`` is the Metropolis sweep written from its definition,
   with the energy change of a flip taken as H(s') - H(s) by evaluating Eq. 2
   on the whole edge list before and after (no local fields, no CSR), and the
-  acceptance probability exp(-beta dE) compared against u / 2^32 through the
-  threshold T = floor(exp(-beta dE) 2^32).
+  acceptance probability exp(-beta dE) compared against u / 2^B through the
+  threshold T = floor(exp(-beta dE) 2^B), B = 32 (or 16 in the 16-bit draw
+  mode).
 """
 import math
 
@@ -32,12 +33,20 @@ def draw(a, b, t, seed):
     return out[t & 3]
 
 
+def draw16(a, b, t, seed):
+    """16-bit draw mode: trial t takes the low (t even) or high (t odd) half of
+    word (t mod 8) // 2 of the block at counter (a, b, t // 8, 0)."""
+    out = philox((a, b, t // 8, 0), (seed & MASK, (seed >> 32) & MASK))
+    word = out[(t % 8) // 2]
+    return (word >> 16) if t % 2 else (word & 0xFFFF)
+
+
 def energy(edges, s):
     i, j, w = edges
     return int(sum(int(w[e]) * int(s[i[e]]) * int(s[j[e]]) for e in range(len(w))))
 
 
-def anneal_full_energy(X, Y, edges, betas, seed, trials, sweep_offset=0, init=None):
+def anneal_full_energy(X, Y, edges, betas, seed, trials, sweep_offset=0, init=None, draw_bits=32):
     n = X * Y
     out = np.zeros((trials, n), dtype=np.int8)
     for t in range(trials):
@@ -58,8 +67,10 @@ def anneal_full_energy(X, Y, edges, betas, seed, trials, sweep_offset=0, init=No
                     if dE <= 0:
                         flip = True
                     else:
-                        thr = min(math.floor(math.exp(-beta * dE) * 2.0 ** 32), 2 ** 32 - 1)
-                        flip = draw(i, k, t, seed) < thr
+                        B = draw_bits
+                        thr = min(math.floor(math.exp(-beta * dE) * 2.0 ** B), 2 ** B - 1)
+                        u = draw16(i, k, t, seed) if B == 16 else draw(i, k, t, seed)
+                        flip = u < thr
                     if flip:
                         s[i] = -s[i]
         out[t] = s

@@ -9,6 +9,10 @@
   zero-temperature monotonicity, gauge invariance, resume, and incremental
   versus recomputed local fields.
 * Eq. 3-5: the printed rows of Table I.
+* The 16-bit draw mode (a variant of this project): its thresholds against a
+  high-precision evaluation of floor(exp(-beta d) 2^16), its draws against
+  the Python Philox, the whole annealer against the full-energy restatement,
+  and the Boltzmann distribution at fixed beta.
 """
 import math
 import os
@@ -88,6 +92,49 @@ def test_threshold_limits_and_order():
         oracle.thresholds(np.array([np.nan]))
 
 
+def _exact_threshold16(beta, d):
+    getcontext().prec = 60
+    v = (-(Decimal(beta) * d)).exp() * (Decimal(2) ** 16)
+    return min(int(v), 2**16 - 1), v
+
+
+def test_thresholds16_against_high_precision():
+    betas = np.concatenate([synth.linear_betas(0.1, 3.0, 997), [1e-12, 1e-3, 1.5, 7.5, 40.0]])
+    T4, T8 = oracle.thresholds(betas, draw_bits=16)
+    for k, b in enumerate(betas):
+        for d, T in ((4, T4[k]), (8, T8[k])):
+            exact, v = _exact_threshold16(float(b), d)
+            if abs(v - int(v)) > Decimal("1e-9") and abs(v - int(v) - 1) > Decimal("1e-9"):
+                assert int(T) == exact, (b, d, int(T), exact)
+            else:
+                assert abs(int(T) - exact) <= 1
+
+
+def test_thresholds16_limits():
+    T4, T8 = oracle.thresholds(np.array([1e-300, 0.5, 2.0, np.inf]), draw_bits=16)
+    assert T4[0] == 2**16 - 1 and T8[0] == 2**16 - 1
+    assert T4[-1] == 0 and T8[-1] == 0
+    # beta 2: exp(-8) 2^16 = 21.98..., exp(-16) 2^16 = 0.0074...
+    assert T4[2] == 21 and T8[2] == 0
+    # beta 0.5: exp(-2) 2^16 = 8869.2..., exp(-4) 2^16 = 1200.3...
+    assert T4[1] == 8869 and T8[1] == 1200
+    assert all(T8 <= T4)
+
+
+def test_draw16_matches_python_philox_halves():
+    rng = np.random.default_rng(17)
+    for _ in range(300):
+        i, k = (int(v) for v in rng.integers(0, 2**32, 2, dtype=np.uint64))
+        t = int(rng.integers(0, 4096))
+        seed = int(rng.integers(0, 2**63, dtype=np.uint64))
+        assert oracle.decision_draw(i, k, t, seed, 16) == _pyref.draw16(i, k, t, seed)
+        assert oracle.decision_draw(i, k, t, seed, 32) == _pyref.draw(i, k, t, seed)
+    # the eight trials of one block cover its four words, low half first
+    blk = _pyref.philox((5, 9, 3, 0), (0x11, 0x22))
+    halves = [w >> (16 * h) & 0xFFFF for w in blk for h in (0, 1)]
+    assert [oracle.decision_draw(5, 9, 24 + j, 0x22_0000_0011, 16) for j in range(8)] == halves
+
+
 # ---------------------------------------------------------------- Eq. 1 / Eq. 2
 @pytest.mark.parametrize("X,Y,seed", [(4, 4, 1), (6, 4, 2), (10, 8, 3), (50, 50, 1)])
 def test_cut_energy_identities(X, Y, seed):
@@ -131,23 +178,27 @@ def test_brute_force_4x4_and_low_temperature_anneal():
 
 
 # ---------------------------------------------------------------- pure-Python equality
-@pytest.mark.parametrize("X,Y,seed,S,trials", [(4, 4, 3, 6, 5), (6, 4, 4, 4, 4), (4, 6, 5, 5, 3)])
-def test_oracle_equals_full_energy_restatement(X, Y, seed, S, trials):
+@pytest.mark.parametrize("bits", [32, 16])
+@pytest.mark.parametrize("X,Y,seed,S,trials", [(4, 4, 3, 6, 5), (6, 4, 4, 4, 4), (4, 6, 5, 5, 3), (4, 4, 6, 3, 17)])
+def test_oracle_equals_full_energy_restatement(X, Y, seed, S, trials, bits):
     inst = synth.torus_instance(X, Y, seed)
     edges = oracle.torus_edges(X, Y, inst["w_right"], inst["w_down"])
     betas = synth.linear_betas(0.2, 1.5, S)
     ref = _pyref.anneal_full_energy(X, Y, edges, betas, seed=0x1234_5678_9ABC, trials=trials,
-                                    sweep_offset=7)
-    got, cuts = oracle.anneal(inst, betas, seed=0x1234_5678_9ABC, t_count=trials, sweep_offset=7)
+                                    sweep_offset=7, draw_bits=bits)
+    got, cuts = oracle.anneal(inst, betas, seed=0x1234_5678_9ABC, t_count=trials, sweep_offset=7,
+                              draw_bits=bits)
     np.testing.assert_array_equal(got, ref)
     for s, c in zip(got, cuts):
         assert c == int(oracle.cut_eq1(edges, s))
 
 
 # ---------------------------------------------------------------- Boltzmann
-def test_fixed_beta_samples_follow_boltzmann():
+@pytest.mark.parametrize("bits", [32, 16])
+def test_fixed_beta_samples_follow_boltzmann(bits):
     """Each Metropolis update leaves exp(-beta H) invariant, so after many sweeps
-    independent trials sample the exact distribution (chi-square on energies)."""
+    independent trials sample the exact distribution (chi-square on energies).
+    The 16-bit mode quantises each acceptance probability down by < 2^-16."""
     inst = synth.torus_instance(4, 4, 21)
     edges = oracle.torus_edges(4, 4, inst["w_right"], inst["w_down"])
     _, _, E, _ = oracle.brute_force(edges, 16)
@@ -156,7 +207,7 @@ def test_fixed_beta_samples_follow_boltzmann():
     levels, inv = np.unique(E, return_inverse=True)
     p_level = np.bincount(inv, weights=p_state)
     trials = 6000
-    spins, _ = oracle.anneal(inst, np.full(60, beta), seed=99, t_count=trials)
+    spins, _ = oracle.anneal(inst, np.full(60, beta), seed=99, t_count=trials, draw_bits=bits)
     got = np.array([oracle.energy_csr(inst, s) for s in spins])
     obs = np.array([(got == L).sum() for L in levels], dtype=np.float64)
     exp = p_level * trials
