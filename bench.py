@@ -431,6 +431,27 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_throughput(w, inst)
+    # ---- the 16-bit draw mode on the same workload (one Philox block per
+    # eight trials): a variant line, not the headline stream
+    draw16 = None
+    if args.steps > 0:
+        prob.set_draw_bits(16)
+        for i in range(2):
+            ia.anneal(prob, T, betas, seed_of(-10 - i), out_spins=spins, out_cuts=cuts)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        for i, (e0, e1) in enumerate(ev):
+            flush.zero_()
+            e0.record(stream)
+            ia.anneal(prob, T, betas, seed_of(200 + i), out_spins=spins, out_cuts=cuts)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms16 = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        prob.set_draw_bits(32)
+        a16 = ups * (IMAD_OPS_PER_UPDATE / 2) / (ms16 / 1e3) / 1e12
+        draw16 = {"value": ws * ups / (ms16 / 1e3), "unit": "spin-updates/s", "ms_per_step": ms16,
+                  "workload": "same as the headline, 16-bit draws (decision stream of the 16-bit mode)",
+                  "roofline": {"bound": "alu", "achieved": a16, "peak": peak_tops, "frac": a16 / peak_tops,
+                               "unit": "Tops/s (32-bit IMAD)", "ops_per_update": IMAD_OPS_PER_UPDATE / 2}}
     batched = None
     if rank == 0 and not args.sweeps and not args.trials:
         batched = batched_leg()
@@ -453,6 +474,7 @@ def main():
             "cpu_baseline": cpu,
             "clocks": clk,
             "ttt_99_9": stats,
+            "draw16_variant": draw16,
             "batched": batched,
             "learned_vs_plain": learned_cmp,
             "wall_s_timed": wall,

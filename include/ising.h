@@ -198,6 +198,25 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
  */
 int ising_set_kernel(ising_problem* p, int32_t kind);
 
+/*
+ * ising_set_draw_bits -- the decision stream of this handle's anneals
+ * (ising_anneal, ising_anneal_noalloc and the batch entry points):
+ *   32 (default): trial t at site i in sweep k draws word t mod 4 of the
+ *     Philox4x32-10 block at counter (i, k, t/4, 0) and compares it with
+ *     T_d = min(floor(exp(-beta d) 2^32), 2^32 - 1);
+ *   16: one block serves eight trials -- trial t draws the low (t even) or
+ *     high (t odd) 16-bit half of word (t mod 8)/2 of the block at counter
+ *     (i, k, t/8, 0) and compares it with T_d = min(floor(exp(-beta d) 2^16),
+ *     2^16 - 1).  About half the Philox work per update; the acceptance
+ *     probabilities are quantised to 2^-16.
+ * The starting spins are the same in both modes.  The paper has no
+ * counterpart (its update rule is unpublished, Section III); the 16-bit mode
+ * is a variant of this library.  In the 16-bit mode a fixed trials-per-group
+ * (ising_set_launch, the batch group_trials) must be a multiple of 8, else
+ * the anneal returns ISING_ERR_ARG.  Errors: ISING_ERR_ARG (bits not 16 or 32).
+ */
+int ising_set_draw_bits(ising_problem* p, int32_t bits);
+
 /* ising_last_kernel -- the kernel (1 or 2) the last ising_anneal call used. */
 int ising_last_kernel(const ising_problem* p, int32_t* kind);
 

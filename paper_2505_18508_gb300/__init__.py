@@ -85,6 +85,10 @@ class Problem:
         check(lib().ising_set_launch(self.handle, int(group_trials), int(strips), int(threads)),
               "ising_set_launch")
 
+    def set_draw_bits(self, bits):
+        """32 (default decision stream) or 16 (one Philox block per eight trials)."""
+        check(lib().ising_set_draw_bits(self.handle, int(bits)), "ising_set_draw_bits")
+
     def set_kernel(self, kind):
         """0 automatic, 1 cluster-strip kernel, 2 persistent kernel."""
         check(lib().ising_set_kernel(self.handle, int(kind)), "ising_set_kernel")

@@ -44,6 +44,7 @@ _SIGNATURES = {
     "ising_last_launch": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p]),
     "ising_problem_info": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "ising_set_kernel": (ctypes.c_int, [_vp, _i32]),
+    "ising_set_draw_bits": (ctypes.c_int, [_vp, _i32]),
     "ising_last_kernel": (ctypes.c_int, [_vp, _i32p]),
     "ising_get_status": (ctypes.c_int, [_vp, _vp, _i32p]),
     "ising_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64, _i32]),

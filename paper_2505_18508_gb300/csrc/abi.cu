@@ -26,19 +26,31 @@ int map_cuda(cudaError_t e) {
 
 // T_d = min(floor(exp(-beta d) 2^32), 2^32 - 1) for d = 4 and 8: the
 // Metropolis acceptance probability min(1, exp(-beta dE)) of an uphill move,
-// as an integer threshold for a uniform 32-bit draw (accept iff u < T).
-int make_thresholds(const double* betas, int32_t S, std::vector<uint32_t>& out) {
+// as an integer threshold for a uniform 32-bit draw (accept iff u < T).  In
+// the 16-bit draw mode T_d = min(floor(exp(-beta d) 2^16), 2^16 - 1), stored
+// shifted left by 16 bits (the kernels compare draws placed in the top half).
+int make_thresholds(const double* betas, int32_t S, std::vector<uint32_t>& out, int bits = 32) {
   out.assign(static_cast<size_t>(2) * (S > 0 ? S : 0), 0u);
+  const double scale = bits == 16 ? 65536.0 : 4294967296.0;
+  const double top = scale - 1.0;
   for (int32_t k = 0; k < S; ++k) {
     const double beta = betas[k];
     if (!(beta > 0.0)) return ISING_ERR_ARG;
     for (int d = 0; d < 2; ++d) {
       const double dE = d == 0 ? 4.0 : 8.0;
-      const double v = std::floor(std::exp(-(beta * dE)) * 4294967296.0);
-      out[2 * static_cast<size_t>(k) + d] = v >= 4294967295.0 ? 0xFFFFFFFFu : static_cast<uint32_t>(v);
+      const double v = std::floor(std::exp(-(beta * dE)) * scale);
+      const uint32_t T = v >= top ? static_cast<uint32_t>(top) : static_cast<uint32_t>(v);
+      out[2 * static_cast<size_t>(k) + d] = bits == 16 ? T << 16 : T;
     }
   }
   return ISING_OK;
+}
+
+// trials per group when the handle does not fix it: 32, or all trials rounded
+// up to a multiple of the Philox block (4 trials, 8 in the 16-bit mode)
+int default_group(const ising_problem* p, int32_t T) {
+  const int unit = p->draw_bits == 16 ? 8 : 4;
+  return T >= 32 ? 32 : ((T + unit - 1) / unit) * unit;
 }
 
 int num_sms_of(int device) {
@@ -80,7 +92,7 @@ int choose_shape(const ising_problem* p, int32_t T, Shape* out) {
   const int sms = num_sms_of(p->device);
   const int smem_max = max_smem_of(p->device);
   int G = p->cfg_group;
-  if (G == 0) G = T >= 32 ? 32 : ((T + 3) / 4) * 4;
+  if (G == 0) G = default_group(p, T);
   if (G < 4) G = 4;
   const int groups = (T + G - 1) / G;
   int C = p->cfg_strips;
@@ -137,7 +149,8 @@ int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials,
   double total = 0.0;
   for (int32_t q = 0; q < m; ++q) {
     std::vector<uint32_t> t;
-    const int rc = make_thresholds(betas[q], sweeps[q], t);
+    if (probs[q]->draw_bits == 16 && group_trials % 8) return ISING_ERR_ARG;
+    const int rc = make_thresholds(betas[q], sweeps[q], t, probs[q]->draw_bits);
     if (rc != ISING_OK) return rc;
     hb.thr_off[q] = hb.thr.size();
     hb.thr.insert(hb.thr.end(), t.begin(), t.end());
@@ -165,13 +178,14 @@ int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials,
   std::vector<std::pair<double, ising::BatchUnit>> order;
   for (int32_t q = 0; q < m; ++q) {
     const ising_problem* p = probs[q];
+    const int blk = p->draw_bits == 16 ? 8 : 4;   // trials per Philox block
     int G = group_trials;
     if (G == 0) {
       G = 32;
       const double unit32 = static_cast<double>(p->n) * sweeps[q] * 32.0;
       if (unit32 > per_cta && per_cta > 0) {
-        G = 4 * static_cast<int>(per_cta / (4.0 * p->n * (sweeps[q] > 0 ? sweeps[q] : 1)));
-        if (G < 4) G = 4;
+        G = blk * static_cast<int>(per_cta / (blk * static_cast<double>(p->n) * (sweeps[q] > 0 ? sweeps[q] : 1)));
+        if (G < blk) G = blk;
         if (G > 32) G = 32;
       }
     }
@@ -186,10 +200,11 @@ int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials,
     in.key1 = static_cast<uint32_t>(seeds[q] >> 32);
     in.neg_edges = p->neg_edges;
     in.G = G;
+    in.u16 = p->draw_bits == 16 ? 1 : 0;
     const int groups = (trials[q] + G - 1) / G;
     for (int g = 0; g < groups; ++g) {
       const int live = std::min(G, trials[q] - g * G);
-      const double cost = static_cast<double>(p->n) * (sweeps[q] + 1) * ((live + 3) / 4);
+      const double cost = static_cast<double>(p->n) * (sweeps[q] + 1) * ((live + blk - 1) / blk);
       order.push_back({cost, ising::BatchUnit{q, g}});
     }
   }
@@ -237,14 +252,15 @@ struct FlowPlan {
 };
 
 // Stacks the rows of all trial groups and splits them over one CTA per SM,
-// weighted by the Philox quads of each row's group.  Fails with
+// weighted by the Philox blocks of each row's group.  Fails with
 // ISING_ERR_UNSUPPORTED when a CTA would touch more groups than the kernel
 // tracks or its rows would not fit in shared memory.
 int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp) {
   const int sms = num_sms_of(p->device);
   const int smem_max = max_smem_of(p->device);
   int G = p->cfg_group;
-  if (G == 0) G = T >= 32 ? 32 : ((T + 3) / 4) * 4;
+  if (G == 0) G = default_group(p, T);
+  const int blk = p->draw_bits == 16 ? 8 : 4;
   const int groups = (T + G - 1) / G;
   const long long RTl = static_cast<long long>(groups) * p->Y;
   if (RTl > (1LL << 30)) return ISING_ERR_UNSUPPORTED;
@@ -254,7 +270,7 @@ int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp) {
   for (int u = 0; u < RT; ++u) {
     const int g = u / p->Y;
     const int live = std::min(G, T - g * G);
-    cum[u + 1] = cum[u] + (live + 3) / 4;
+    cum[u + 1] = cum[u] + (live + blk - 1) / blk;
   }
   const long long total = cum[RT];
   std::vector<int32_t> split(static_cast<size_t>(P) + 1);
@@ -347,6 +363,7 @@ int run_flow(ising_problem* p, const FlowPlan& fp, int32_t trials, const std::ve
     a.status = p->d_status;
     a.spin_limit = p->wait_limit > 0 ? p->wait_limit : 4000000000LL;
     a.stall_test = p->stall_test;
+    a.u16 = p->draw_bits == 16 ? 1 : 0;
     e = ising::launch_flow(a, st);
   }
   const cudaError_t e2 = cudaFreeAsync(d, st);
@@ -492,6 +509,12 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
   return ISING_OK;
 }
 
+int ising_set_draw_bits(ising_problem* p, int32_t bits) {
+  if (!p || (bits != 32 && bits != 16)) return ISING_ERR_ARG;
+  p->draw_bits = bits;
+  return ISING_OK;
+}
+
 int ising_set_kernel(ising_problem* p, int32_t kind) {
   if (!p || kind < 0 || kind > 2) return ISING_ERR_ARG;
   p->cfg_kernel = kind;
@@ -536,9 +559,10 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
                  uint32_t sweep_offset, const int8_t* init_spins, int8_t* out_spins, int32_t* out_cuts,
                  void* cuda_stream) {
   if (!p || trials < 0 || S < 0 || (S > 0 && !betas)) return ISING_ERR_ARG;
+  if (p->draw_bits == 16 && p->cfg_group % 8) return ISING_ERR_ARG;
   std::vector<uint32_t> thr;
   try {
-    const int rc = make_thresholds(betas, S, thr);
+    const int rc = make_thresholds(betas, S, thr, p->draw_bits);
     if (rc != ISING_OK) return rc;
   } catch (const std::bad_alloc&) {
     return ISING_ERR_OOM;
@@ -595,6 +619,7 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
   a.C = sh.C;
   a.Rmax = sh.Rmax;
   a.neg_edges = p->neg_edges;
+  a.u16 = p->draw_bits == 16 ? 1 : 0;
   cudaError_t e = ising::launch_anneal(a, sh.threads, st);
   if (d_thr) {
     const cudaError_t e2 = cudaFreeAsync(d_thr, st);

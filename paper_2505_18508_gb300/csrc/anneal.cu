@@ -6,7 +6,7 @@
 namespace ising {
 namespace {
 
-template <bool kCluster>
+template <bool kCluster, bool kU16>
 __global__ void __launch_bounds__(1024, 1) anneal_strip_kernel(const __grid_constant__ AnnealArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   GroupJob job;
@@ -23,14 +23,15 @@ __global__ void __launch_bounds__(1024, 1) anneal_strip_kernel(const __grid_cons
   job.C = a.C; job.Rmax = a.Rmax;
   job.neg_edges = a.neg_edges;
   const int r = kCluster ? static_cast<int>(cluster_ctarank()) : 0;
-  anneal_group<kCluster>(job, blockIdx.y, r, smem);
+  anneal_group<kCluster, kU16>(job, blockIdx.y, r, smem);
 }
 
 }  // namespace
 
 size_t anneal_smem_bytes(int32_t H, int32_t Rmax) { return core_smem_bytes(H, Rmax); }
 
-cudaError_t launch_anneal(const AnnealArgs& a, int threads, cudaStream_t stream) {
+template <bool kU16>
+cudaError_t launch_strip(const AnnealArgs& a, int threads, cudaStream_t stream) {
   const size_t smem = anneal_smem_bytes(a.H, a.Rmax);
   const int groups = (a.T + a.G - 1) / a.G;
   cudaLaunchConfig_t cfg = {};
@@ -41,11 +42,11 @@ cudaError_t launch_anneal(const AnnealArgs& a, int threads, cudaStream_t stream)
   cudaLaunchAttribute attr[1];
   cudaError_t e;
   if (a.C > 1) {
-    e = cudaFuncSetAttribute(anneal_strip_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(anneal_strip_kernel<true, kU16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     if (a.C > 8) {
-      e = cudaFuncSetAttribute(anneal_strip_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      e = cudaFuncSetAttribute(anneal_strip_kernel<true, kU16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
     }
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -54,12 +55,16 @@ cudaError_t launch_anneal(const AnnealArgs& a, int threads, cudaStream_t stream)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, anneal_strip_kernel<true>, a);
+    return cudaLaunchKernelEx(&cfg, anneal_strip_kernel<true, kU16>, a);
   }
-  e = cudaFuncSetAttribute(anneal_strip_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(anneal_strip_kernel<false, kU16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  return cudaLaunchKernelEx(&cfg, anneal_strip_kernel<false>, a);
+  return cudaLaunchKernelEx(&cfg, anneal_strip_kernel<false, kU16>, a);
+}
+
+cudaError_t launch_anneal(const AnnealArgs& a, int threads, cudaStream_t stream) {
+  return a.u16 ? launch_strip<true>(a, threads, stream) : launch_strip<false>(a, threads, stream);
 }
 
 }  // namespace ising

@@ -16,7 +16,10 @@
 // the count m = e_L + e_R + e_U + e_D gives dE = 8 - 4m.  m >= 2: flip;
 // m = 1: flip iff u < T4; m = 0: flip iff u < T8.  The counts are bit-sliced
 // over the 32 trials of a word; the draws u come from Philox4x32-10 at
-// counter (i, k, t / 4, 0), word t mod 4.
+// counter (i, k, t / 4, 0), word t mod 4.  In the 16-bit draw mode (kU16)
+// one block serves eight trials: counter (i, k, t / 8, 0), the low (t even)
+// or high (t odd) half of word (t mod 8) / 2, against 16-bit thresholds that
+// the host stores shifted left by 16 bits.
 //
 // Philox sharing: in round 1 the site index i only meets multiplier M0 and the
 // quad index q only meets M1, and in round 2 the product M1 * c2 involves
@@ -160,7 +163,38 @@ __device__ __forceinline__ void quad_step(uint32_t& rej4, uint32_t& rej8, const 
   rej8 = shift_in_ge(rej8, u.x, T8);
 }
 
-// Metropolis update of one site word; returns the new word.
+// 16-bit draw mode: one Philox block for eight trials.  With thresholds
+// stored as T << 16, w >= T << 16 tests the high half and (w << 16) >= T << 16
+// the low half.  Trials 8j + 7 .. 8j are shifted in from the top: word w high,
+// word w low, ..., word x low.
+__device__ __forceinline__ void octet_step(uint32_t& rej4, uint32_t& rej8, const uint4 hd, uint32_t hi1, uint32_t lo1,
+                                           uint32_t lo0, uint32_t T4, uint32_t T8, const uint32_t* __restrict__ rk) {
+  const uint4 u = philox_rounds_3_to_10(hi1 ^ hd.x, lo1, hd.y ^ lo0, hd.z, rk);
+  const uint32_t w[4] = {u.w, u.z, u.y, u.x};
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    rej4 = shift_in_ge(rej4, w[m], T4);
+    rej4 = shift_in_ge(rej4, w[m] << 16, T4);
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    rej8 = shift_in_ge(rej8, w[m], T8);
+    rej8 = shift_in_ge(rej8, w[m] << 16, T8);
+  }
+}
+
+// Philox blocks per trial group of `live` trials, and the block index of the
+// group's first trial t0
+template <bool kU16>
+__host__ __device__ __forceinline__ int decision_blocks(int live) { return kU16 ? (live + 7) >> 3 : (live + 3) >> 2; }
+template <bool kU16>
+__host__ __device__ __forceinline__ uint32_t decision_block0(int t0) {
+  return kU16 ? static_cast<uint32_t>(t0) >> 3 : static_cast<uint32_t>(t0) >> 2;
+}
+
+// Metropolis update of one site word; returns the new word.  nq: Philox
+// blocks of the group (decision_blocks).
+template <bool kU16>
 __device__ __forceinline__ uint32_t update_word(uint32_t s, uint32_t nl, uint32_t nr, uint32_t nu, uint32_t nd,
                                                uint32_t f, uint32_t i, const uint4* head, int nq,
                                                uint32_t T4, uint32_t T8, const uint32_t* __restrict__ rk) {
@@ -177,11 +211,20 @@ __device__ __forceinline__ uint32_t update_word(uint32_t s, uint32_t nl, uint32_
   mulhilo(kPhiloxM0, i, hi0, lo0);
   mulhilo(kPhiloxM1, hi0 ^ rk[1], hi1, lo1);
   uint32_t rej4 = 0, rej8 = 0;   // bit set: draw at or above the threshold
-  if (nq == 8) {  // full groups: unrolled, so consecutive blocks can overlap
+  if constexpr (kU16) {
+    if (nq == 4) {
 #pragma unroll
-    for (int j = 7; j >= 0; --j) quad_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
+      for (int j = 3; j >= 0; --j) octet_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
+    } else {
+      for (int j = nq - 1; j >= 0; --j) octet_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
+    }
   } else {
-    for (int j = nq - 1; j >= 0; --j) quad_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
+    if (nq == 8) {  // full groups: unrolled, so consecutive blocks can overlap
+#pragma unroll
+      for (int j = 7; j >= 0; --j) quad_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
+    } else {
+      for (int j = nq - 1; j >= 0; --j) quad_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
+    }
   }
   return s ^ (ge2 | (eq1 & ~rej4) | (eq0 & ~rej8));
 }
@@ -189,7 +232,7 @@ __device__ __forceinline__ uint32_t update_word(uint32_t s, uint32_t nl, uint32_
 // Anneal trial group g (strip r of C) of job a.  All threads of the CTA (and
 // of the cluster when kCluster) must call it.  Ends with the CTA (cluster)
 // synchronised; shared memory may be reused after it returns.
-template <bool kCluster>
+template <bool kCluster, bool kU16>
 __device__ __forceinline__ void anneal_group(const GroupJob& a, const int g, const int r, unsigned char* smem) {
   const int C = a.C;
   const int rows = strip_rows(a.Y, C, r);
@@ -202,8 +245,10 @@ __device__ __forceinline__ void anneal_group(const GroupJob& a, const int g, con
 
   const int t0 = g * a.G;
   const int live = min(a.G, a.T - t0);
-  const int nq = (live + 3) >> 2;
-  const uint32_t q0 = static_cast<uint32_t>(t0) >> 2;
+  const int nq = decision_blocks<kU16>(live);       // Philox blocks per site word and sweep
+  const uint32_t q0 = decision_block0<kU16>(t0);
+  const int nqi = (live + 3) >> 2;                  // the starting spins use 32-bit quads
+  const uint32_t qi0 = static_cast<uint32_t>(t0) >> 2;
   const int tid = threadIdx.x, nt = blockDim.x;
 
   if (tid < 32) sm.part[tid] = 0;
@@ -232,8 +277,8 @@ __device__ __forceinline__ void anneal_group(const GroupJob& a, const int g, con
       for (int b = 0; b < live; ++b)
         w |= static_cast<uint32_t>(a.init[static_cast<size_t>(t0 + b) * a.n + i] > 0) << b;
     } else {
-      for (int j = 0; j < nq; ++j) {
-        const uint4 u = philox4x32_10(i, 0xFFFFFFFFu, q0 + j, 0u, a.key0, a.key1);
+      for (int j = 0; j < nqi; ++j) {
+        const uint4 u = philox4x32_10(i, 0xFFFFFFFFu, qi0 + j, 0u, a.key0, a.key1);
         w |= ((u.x >> 31) | ((u.y >> 31) << 1) | ((u.z >> 31) << 2) | ((u.w >> 31) << 3)) << (4 * j);
       }
     }
@@ -273,7 +318,7 @@ __device__ __forceinline__ void anneal_group(const GroupJob& a, const int g, con
         const int row = lr * H;
         const int hl = par ? h : (h == 0 ? H - 1 : h - 1);
         const int hr = par ? (h == H - 1 ? 0 : h + 1) : h;
-        const uint32_t ns = update_word(self[row + h], nb_plane[row + hl], nb_plane[row + hr],
+        const uint32_t ns = update_word<kU16>(self[row + h], nb_plane[row + hl], nb_plane[row + hr],
                                         nb_plane[row - H + h], nb_plane[row + H + h],
                                         fc[(lr - 1) * H + h], i, head, nq, T4, T8, a.rk);
         self[row + h] = ns;

@@ -48,7 +48,7 @@ struct FlowSmem {
   int32_t* meta;       // [8]: nown, nloc, nseg, ...
   int32_t* seg_g;      // [kMaxSeg] group of each segment
   int4* rowA;          // [LR] {up | dn << 16, xup, xdn, y*X}
-  int4* rowB;          // [LR] {seg | pub << 4 | (y & 1) << 5 | nq << 8, u, t0, 0}
+  int4* rowB;          // [LR] {seg | pub << 4 | (y & 1) << 5 | Philox blocks << 8, u, t0, 0}
   int32_t* ctab;       // [NC*32] lane item of each chunk: lr | h << 16, or -1
 };
 
@@ -123,6 +123,7 @@ __device__ __forceinline__ bool wait_count(const uint32_t* cnt, uint32_t need, c
   }
 }
 
+template <bool kU16>
 __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __grid_constant__ FlowArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int j = blockIdx.x;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
     const int u = sm.r_u[lr];
     const int g = u / Y, y = u - g * Y;
     const int t0 = g * a.G;
-    const int nq = (min(a.G, a.T - t0) + 3) >> 2;
+    const int nq = decision_blocks<kU16>(min(a.G, a.T - t0));
     sm.rowA[lr] = make_int4(sm.r_up[lr] | (sm.r_dn[lr] << 16), sm.r_xup[lr], sm.r_xdn[lr], y * a.X);
     sm.rowB[lr] = make_int4(sm.r_seg[lr] | (sm.r_pub[lr] << 4) | ((y & 1) << 5) | (nq << 8), u, t0, 0);
   }
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       __syncwarp();
       if (lane < nseg * 8) {
         const int s = lane >> 3, jq = lane & 7;
-        const uint32_t q = (static_cast<uint32_t>(sm.seg_g[s] * a.G) >> 2) + jq;
+        const uint32_t q = decision_block0<kU16>(sm.seg_g[s] * a.G) + jq;
         wh[lane] = philox_head_sweep_quad(a.k0 + static_cast<uint32_t>(kk), q, a.key0, a.key1);
       }
       __syncwarp();
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
                                                    : nb[up * H + h];
         const uint32_t nd = (xdn >= 0 && need > 0) ? __ldcg(a.gm + (static_cast<size_t>(2) * xdn + (1 - c)) * H + h)
                                                    : nb[dn * H + h];
-        const uint32_t ns = update_word(self[lr * H + h], nb[lr * H + hl], nb[lr * H + hr], nu, nd,
+        const uint32_t ns = update_word<kU16>(self[lr * H + h], nb[lr * H + hl], nb[lr * H + hr], nu, nd,
                                         sm.fl[(c * a.LRmax + lr) * H + h], i, wh + 8 * (rb.x & 15), rb.x >> 8, T4,
                                         T8, a.rk);
         sm.sp[(static_cast<size_t>(c) * a.LRmax + lr) * H + h] = ns;
@@ -439,9 +440,10 @@ size_t flow_smem_bytes(int32_t LR, int32_t H) {
 int flow_threads() { return kFlowThreads; }
 int flow_max_segments() { return kMaxSeg; }
 
-cudaError_t launch_flow(const FlowArgs& a, cudaStream_t stream) {
+template <bool kU16>
+cudaError_t launch_flow_mode(const FlowArgs& a, cudaStream_t stream) {
   const size_t smem = flow_smem_bytes(a.LRmax, a.H);
-  cudaError_t e = cudaFuncSetAttribute(anneal_flow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(anneal_flow_kernel<kU16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -454,14 +456,25 @@ cudaError_t launch_flow(const FlowArgs& a, cudaStream_t stream) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, anneal_flow_kernel, a);
+  return cudaLaunchKernelEx(&cfg, anneal_flow_kernel<kU16>, a);
+}
+
+cudaError_t launch_flow(const FlowArgs& a, cudaStream_t stream) {
+  return a.u16 ? launch_flow_mode<true>(a, stream) : launch_flow_mode<false>(a, stream);
 }
 
 cudaError_t flow_max_ctas(size_t smem, int* per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(anneal_flow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, anneal_flow_kernel, kFlowThreads, smem);
+  int both[2] = {0, 0};
+  for (int m = 0; m < 2; ++m) {
+    const void* fn = m ? reinterpret_cast<const void*>(anneal_flow_kernel<true>)
+                       : reinterpret_cast<const void*>(anneal_flow_kernel<false>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&both[m], fn, kFlowThreads, smem);
+    if (e != cudaSuccess) return e;
+  }
+  *per_sm = both[0] < both[1] ? both[0] : both[1];
+  return cudaSuccess;
 }
 
 }  // namespace ising

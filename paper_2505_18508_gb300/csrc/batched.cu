@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(1024, 1) batched_kernel(const BatchArgs a) {
     job.rk = s_rk;
     job.C = 1; job.Rmax = in.Y;
     job.neg_edges = in.neg_edges;
-    anneal_group<false>(job, un.group, 0, smem);
+    if (in.u16) anneal_group<false, true>(job, un.group, 0, smem);
+    else anneal_group<false, false>(job, un.group, 0, smem);
   }
 }
 

@@ -21,6 +21,7 @@ struct ising_problem {
   int32_t* d_status = nullptr;
   // launch overrides (0 = automatic) and the last shape used
   int32_t cfg_group = 0, cfg_strips = 0, cfg_threads = 0, cfg_kernel = 0;
+  int32_t draw_bits = 32;   // 32: the default decision stream; 16: the 16-bit draw mode
   int32_t last_group = 0, last_strips = 0, last_threads = 0, last_grid = 0, last_kernel = 0;
   // bounded-wait limit (cycles) and the forced-stall switch used by tests
   long long wait_limit = 0;
@@ -38,7 +39,7 @@ struct AnnealArgs {
   int32_t* out_cuts;        // [T] or null
   int32_t X, Y, H, n;
   int32_t T;                // trials
-  int32_t G;                // trials per group (multiple of 4, <= 32)
+  int32_t G;                // trials per group (multiple of 4, of 8 in the 16-bit mode; <= 32)
   int32_t S;                // sweeps in this call
   uint32_t k0;              // global index of the first sweep
   uint32_t key0, key1;      // Philox key
@@ -46,6 +47,7 @@ struct AnnealArgs {
   int32_t C;                // strips (CTAs) per group = cluster size
   int32_t Rmax;             // ceil(Y / C)
   int32_t neg_edges;
+  int32_t u16;              // 1: 16-bit draw mode (G a multiple of 8, thresholds stored << 16)
 };
 
 // Everything the persistent flow kernel reads (anneal_flow.cu).
@@ -71,6 +73,7 @@ struct FlowArgs {
   int32_t* status;          // the problem's status word
   long long spin_limit;     // cycles one wait may take
   int32_t stall_test;       // 1: the first chunk of CTA 0 waits for a count nothing reaches
+  int32_t u16;              // 1: 16-bit draw mode
 };
 size_t flow_smem_bytes(int32_t LR, int32_t H);
 int flow_threads();
@@ -129,6 +132,7 @@ struct BatchInst {                 // one instance of a batch (device-side descr
   uint32_t key0, key1;
   int32_t neg_edges;
   int32_t G;                       // trials per work unit for this instance
+  int32_t u16;                     // 1: 16-bit draw mode
 };
 struct BatchUnit {                 // one work item: one trial group of one instance
   int32_t inst;

@@ -48,13 +48,18 @@ int table_address(int device, uint32_t** out) {
 }
 
 // floor(exp(-beta dE) 2^32), clamped to 2^32 - 1, for dE = 4 and 8 (the same
-// acceptance thresholds as ising_anneal)
-int threshold_pair(double beta, uint32_t* t4, uint32_t* t8) {
+// acceptance thresholds as ising_anneal); in the 16-bit draw mode
+// floor(exp(-beta dE) 2^16), clamped to 2^16 - 1, shifted left by 16 bits
+int threshold_pair(double beta, int bits, uint32_t* t4, uint32_t* t8) {
   if (!(beta > 0.0)) return ISING_ERR_ARG;
-  const double v4 = std::floor(std::exp(-(beta * 4.0)) * 4294967296.0);
-  const double v8 = std::floor(std::exp(-(beta * 8.0)) * 4294967296.0);
-  *t4 = v4 >= 4294967295.0 ? 0xFFFFFFFFu : static_cast<uint32_t>(v4);
-  *t8 = v8 >= 4294967295.0 ? 0xFFFFFFFFu : static_cast<uint32_t>(v8);
+  const double scale = bits == 16 ? 65536.0 : 4294967296.0;
+  const double v4 = std::floor(std::exp(-(beta * 4.0)) * scale);
+  const double v8 = std::floor(std::exp(-(beta * 8.0)) * scale);
+  const uint32_t top = bits == 16 ? 0xFFFFu : 0xFFFFFFFFu;
+  const uint32_t a4 = v4 >= scale - 1.0 ? top : static_cast<uint32_t>(v4);
+  const uint32_t a8 = v8 >= scale - 1.0 ? top : static_cast<uint32_t>(v8);
+  *t4 = bits == 16 ? a4 << 16 : a4;
+  *t8 = bits == 16 ? a8 << 16 : a8;
   return ISING_OK;
 }
 
@@ -70,6 +75,7 @@ extern "C" int ising_anneal_noalloc(ising_problem* p, int32_t trials, const doub
                                     uint64_t seed, uint32_t sweep_offset, const int8_t* init_spins,
                                     int8_t* out_spins, int32_t* out_cuts, void* cuda_stream) {
   if (!p || trials < 0 || S < 0 || (S > 0 && !betas)) return ISING_ERR_ARG;
+  if (p->draw_bits == 16 && p->cfg_group % 8) return ISING_ERR_ARG;
   if (S > kNoAllocMaxSweeps) return ISING_ERR_UNSUPPORTED;
   for (int32_t k = 0; k < S; ++k)
     if (!(betas[k] > 0.0)) return ISING_ERR_ARG;
@@ -88,7 +94,8 @@ extern "C" int ising_anneal_noalloc(ising_problem* p, int32_t trials, const doub
   if (cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
       smem_max <= 0)
     smem_max = 227 * 1024;
-  int G = p->cfg_group ? p->cfg_group : (trials >= 32 ? 32 : ((trials + 3) / 4) * 4);
+  const int unit = p->draw_bits == 16 ? 8 : 4;   // trials per Philox block
+  int G = p->cfg_group ? p->cfg_group : (trials >= 32 ? 32 : ((trials + unit - 1) / unit) * unit);
   const int groups = (trials + G - 1) / G;
   int C = p->cfg_strips;
   if (C == 0) {
@@ -130,7 +137,7 @@ extern "C" int ising_anneal_noalloc(ising_problem* p, int32_t trials, const doub
   for (int32_t k0 = 0; k0 < S; k0 += kChunk) {
     const int32_t m = S - k0 < kChunk ? S - k0 : kChunk;
     for (int32_t j = 0; j < m; ++j) {
-      rc = threshold_pair(betas[k0 + j], &buf[2 * j], &buf[2 * j + 1]);
+      rc = threshold_pair(betas[k0 + j], p->draw_bits, &buf[2 * j], &buf[2 * j + 1]);
       if (rc != ISING_OK) return rc;
     }
     const cudaError_t e = cudaMemcpyAsync(table + 2 * static_cast<size_t>(k0), buf, sizeof(uint32_t) * 2 * m,
@@ -158,5 +165,6 @@ extern "C" int ising_anneal_noalloc(ising_problem* p, int32_t trials, const doub
   a.C = C;
   a.Rmax = Rmax;
   a.neg_edges = p->neg_edges;
+  a.u16 = p->draw_bits == 16 ? 1 : 0;
   return map_err(ising::launch_anneal(a, threads, st));
 }
