@@ -54,6 +54,9 @@ def lib():
         L.oracle_anneal.restype = ctypes.c_int
         L.oracle_anneal_bits.argtypes = L.oracle_anneal.argtypes + [ctypes.c_int32]   # + draw_bits
         L.oracle_anneal_bits.restype = ctypes.c_int
+        L.oracle_anneal_trace.argtypes = L.oracle_anneal_bits.argtypes + [
+            ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]   # trace_every, trace, best, best spins
+        L.oracle_anneal_trace.restype = ctypes.c_int
         L.oracle_thresholds16.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
         L.oracle_thresholds16.restype = ctypes.c_int
         L.oracle_draw.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32]
@@ -132,6 +135,34 @@ def anneal(inst, betas, seed, trials=None, t_begin=0, t_count=None, sweep_offset
     if rc != 0:
         raise ValueError(f"oracle_anneal failed with code {rc}")
     return spins, cuts
+
+
+def anneal_trace(inst, betas, seed, trace_every, t_begin=0, t_count=0, sweep_offset=0, init=None,
+                 draw_bits=32):
+    """The annealer with read-out along the trajectory: after every sweep j
+    (from 1) that is a multiple of trace_every, and after the last sweep, the
+    Eq. 1 cut of every trial; the best of those cuts per trial and the first
+    configuration reaching it.  Returns (spins, cuts, trace int32 [points,
+    t_count], best int32 [t_count], best_spins int8 [t_count, n])."""
+    n = int(inst["n"])
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    S = int(b.shape[0])
+    points = (S + trace_every - 1) // trace_every
+    spins = np.zeros((t_count, n), dtype=np.int8)
+    cuts = np.zeros(t_count, dtype=np.int32)
+    trace = np.zeros((points, t_count), dtype=np.int32)
+    best = np.zeros(t_count, dtype=np.int32)
+    best_spins = np.zeros((t_count, n), dtype=np.int8)
+    ini = None if init is None else np.ascontiguousarray(init, dtype=np.int8)
+    rc = lib().oracle_anneal_trace(n, _ptr(np.ascontiguousarray(inst["row_ptr"], dtype=np.int64)),
+                                   _ptr(np.ascontiguousarray(inst["col"], dtype=np.int32)),
+                                   _ptr(np.ascontiguousarray(inst["J"], dtype=np.int8)), int(inst["X"]),
+                                   int(t_begin), int(t_count), _ptr(b), S, int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                   int(sweep_offset) & 0xFFFFFFFF, _ptr(ini), _ptr(spins), _ptr(cuts), 0,
+                                   int(draw_bits), int(trace_every), _ptr(trace), _ptr(best), _ptr(best_spins))
+    if rc != 0:
+        raise ValueError(f"oracle_anneal_trace failed with code {rc}")
+    return spins, cuts, trace, best, best_spins
 
 
 def cut_csr(inst, spins):

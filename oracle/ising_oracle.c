@@ -205,15 +205,34 @@ int64_t oracle_energy(int32_t n, const int64_t* row_ptr, const int32_t* col,
 /* a mismatch).                                                              */
 /* Returns 0, -1 for bad arguments, -2 for a dE outside {-8,-4,0,4,8}.      */
 /* ------------------------------------------------------------------------ */
+/* Eq. 1 cut of the configuration s (+-1 ints) on the CSR graph */
+static int32_t cut_of(int32_t n, const int64_t* row_ptr, const int32_t* col, const int8_t* J, const int* s)
+{
+    int32_t cut = 0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (col[e] > i && s[i] != s[col[e]]) cut += -(int)J[e];
+    return cut;
+}
+
 /* draw_bits: 32 (the default stream) or 16 (the 16-bit draw mode).         */
-int oracle_anneal_bits(int32_t n, const int64_t* row_ptr, const int32_t* col, const int8_t* J,
-                       int32_t X, int32_t t_begin, int32_t t_count,
-                       const double* betas, int32_t S, uint64_t seed, uint32_t sweep_offset,
-                       const int8_t* init, int8_t* out_spins, int32_t* out_cuts,
-                       int32_t check_fields, int32_t draw_bits)
+/* Read-out along the trajectory (trace_every > 0): after sweep j of the    */
+/* call (counting from 1) with j a multiple of trace_every or j = S, the     */
+/* Eq. 1 cut goes to out_trace[p][tt] (p = 0, 1, ... in sweep order,         */
+/* ceil(S / trace_every) points), and the best of those cuts per trial to   */
+/* out_best[tt], with its configuration (the first one reaching it) in      */
+/* out_best_spins[tt][.] when that is not NULL.  With S = 0 there are no    */
+/* points; the best is then the cut of the starting configuration.          */
+int oracle_anneal_trace(int32_t n, const int64_t* row_ptr, const int32_t* col, const int8_t* J,
+                        int32_t X, int32_t t_begin, int32_t t_count,
+                        const double* betas, int32_t S, uint64_t seed, uint32_t sweep_offset,
+                        const int8_t* init, int8_t* out_spins, int32_t* out_cuts,
+                        int32_t check_fields, int32_t draw_bits,
+                        int32_t trace_every, int32_t* out_trace, int32_t* out_best, int8_t* out_best_spins)
 {
     if (n <= 0 || X <= 0 || n % X != 0 || t_begin < 0 || t_count < 0 || S < 0) return -1;
     if (draw_bits != 32 && draw_bits != 16) return -1;
+    if (trace_every < 0) return -1;
     uint32_t* T4 = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(S > 0 ? S : 1));
     uint32_t* T8 = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(S > 0 ? S : 1));
     int* s = (int*)malloc(sizeof(int) * (size_t)n);
@@ -241,6 +260,7 @@ int oracle_anneal_bits(int32_t n, const int64_t* row_ptr, const int32_t* col, co
             for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) acc += -(int)J[e] * s[col[e]];
             f[i] = acc;
         }
+        int32_t best = 0, have_best = 0;
         for (int32_t j = 0; j < S; ++j) {
             uint32_t k = sweep_offset + (uint32_t)j;
             for (int c = 0; c < 2; ++c) {
@@ -273,21 +293,43 @@ int oracle_anneal_bits(int32_t n, const int64_t* row_ptr, const int32_t* col, co
                     if (acc != f[i]) { rc = -3; goto done; }
                 }
             }
+            if (trace_every > 0 && ((j + 1) % trace_every == 0 || j + 1 == S)) {
+                int32_t c = cut_of(n, row_ptr, col, J, s);
+                if (out_trace) out_trace[(size_t)((j + 1 + trace_every - 1) / trace_every - 1) * t_count + tt] = c;
+                if (!have_best || c > best) {
+                    best = c;
+                    have_best = 1;
+                    if (out_best_spins)
+                        for (int32_t i = 0; i < n; ++i) out_best_spins[(size_t)tt * n + i] = (int8_t)s[i];
+                }
+            }
+        }
+        if (trace_every > 0) {
+            if (!have_best) {      /* no sweeps: the starting configuration */
+                best = cut_of(n, row_ptr, col, J, s);
+                if (out_best_spins)
+                    for (int32_t i = 0; i < n; ++i) out_best_spins[(size_t)tt * n + i] = (int8_t)s[i];
+            }
+            if (out_best) out_best[tt] = best;
         }
         for (int32_t i = 0; i < n; ++i) {
             if (out_spins) out_spins[(size_t)tt * n + i] = (int8_t)s[i];
         }
-        if (out_cuts) {
-            int32_t cut = 0;
-            for (int32_t i = 0; i < n; ++i)
-                for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-                    if (col[e] > i && s[i] != s[col[e]]) cut += -(int)J[e];
-            out_cuts[tt] = cut;
-        }
+        if (out_cuts) out_cuts[tt] = cut_of(n, row_ptr, col, J, s);
     }
 done:
     free(T4); free(T8); free(s); free(f); free(colour);
     return rc;
+}
+
+int oracle_anneal_bits(int32_t n, const int64_t* row_ptr, const int32_t* col, const int8_t* J,
+                       int32_t X, int32_t t_begin, int32_t t_count,
+                       const double* betas, int32_t S, uint64_t seed, uint32_t sweep_offset,
+                       const int8_t* init, int8_t* out_spins, int32_t* out_cuts,
+                       int32_t check_fields, int32_t draw_bits)
+{
+    return oracle_anneal_trace(n, row_ptr, col, J, X, t_begin, t_count, betas, S, seed, sweep_offset,
+                               init, out_spins, out_cuts, check_fields, draw_bits, 0, NULL, NULL, NULL);
 }
 
 int oracle_anneal(int32_t n, const int64_t* row_ptr, const int32_t* col, const int8_t* J,

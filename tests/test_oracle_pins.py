@@ -325,3 +325,47 @@ def test_repetitions_edge_cases():
     assert oracle.target_cut(14060) == 14046       # Table I: ">= 14045.94"
     assert oracle.target_cut(7008) == 7001          # ">= 7000.99"
     assert oracle.target_cut(9940) == 9931          # ">= 9930.06"
+
+
+# ---------------------------------------------------------------- trajectory read-out
+@pytest.mark.parametrize("S,every", [(30, 10), (31, 10), (7, 1), (5, 9)])
+def test_trace_points_equal_prefix_runs(S, every):
+    """Each traced cut is the Eq. 1 cut of the configuration a separate run of
+    the first j sweeps ends in; the best is their maximum, its configuration
+    the first reaching it."""
+    inst = synth.torus_instance(8, 6, 91)
+    edges = oracle.torus_edges(8, 6, inst["w_right"], inst["w_down"])
+    betas = synth.linear_betas(0.1, 2.5, S)
+    T = 9
+    spins, cuts, trace, best, bspins = oracle.anneal_trace(inst, betas, 5, every, t_count=T)
+    pts = list(range(every, S + 1, every))
+    if not pts or pts[-1] != S:
+        pts.append(S)
+    assert trace.shape == (len(pts), T)
+    prefix = []
+    for p, j in enumerate(pts):
+        sj, cj = oracle.anneal(inst, betas[:j], 5, t_count=T)
+        prefix.append(sj)
+        np.testing.assert_array_equal(trace[p], cj)
+        for t in range(T):
+            assert trace[p, t] == int(oracle.cut_eq1(edges, sj[t]))
+    np.testing.assert_array_equal(trace[-1], cuts)
+    np.testing.assert_array_equal(best, trace.max(axis=0))
+    first = trace.argmax(axis=0)
+    for t in range(T):
+        np.testing.assert_array_equal(bspins[t], prefix[first[t]][t])
+        assert int(oracle.cut_eq1(edges, bspins[t])) == best[t]
+
+
+def test_best_so_far_is_bounded_by_brute_force():
+    inst = synth.torus_instance(4, 4, 11)
+    edges = oracle.torus_edges(4, 4, inst["w_right"], inst["w_down"])
+    _, Cmax, _, _ = oracle.brute_force(edges, 16)
+    betas = synth.linear_betas(0.1, 3.0, 200)
+    _, cuts, _, best, _ = oracle.anneal_trace(inst, betas, 3, 7, t_count=40)
+    assert (best >= cuts).all() and (best <= Cmax).all()
+    # with no sweeps the best is the starting configuration's cut
+    s0, c0, tr, b0, bs0 = oracle.anneal_trace(inst, np.zeros(0), 3, 5, t_count=4)
+    assert tr.shape == (0, 4)
+    np.testing.assert_array_equal(b0, c0)
+    np.testing.assert_array_equal(bs0, s0)
