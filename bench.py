@@ -455,6 +455,12 @@ def main():
     batched = None
     if rank == 0 and not args.sweeps and not args.trials:
         batched = batched_leg()
+    campaign = None
+    if rank == 0 and not args.sweeps and not args.trials:
+        from paper_2505_18508_gb300.campaign import run_campaign
+        campaign = run_campaign(prob, (1000, 3000, 10000, 30000, 100000, 300000), 512, 4242)
+        campaign["workload"] = ("Fig. 1 style ladder on the headline instance (200x100, seed 2): 512 trials per "
+                                "budget, beta 0.1->3.0 over S sweeps, one anneal per budget")
     learned_cmp = None
     if rank == 0 and not args.no_learned and not args.sweeps and not args.trials:
         learned_cmp = learned_leg()
@@ -475,6 +481,7 @@ def main():
             "clocks": clk,
             "ttt_99_9": stats,
             "draw16_variant": draw16,
+            "campaign": campaign,
             "batched": batched,
             "learned_vs_plain": learned_cmp,
             "wall_s_timed": wall,

@@ -199,6 +199,31 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
 int ising_set_kernel(ising_problem* p, int32_t kind);
 
 /*
+ * ising_anneal_trace -- ising_anneal with read-out along the trajectory
+ * (Section III reads each trial out at its end; Fig. 1 plots the cut against
+ * sweeps).  After sweep j of the call (counting from 1) for every j that is a
+ * multiple of trace_every, and after the last sweep, the Eq. 1 cut of every
+ * trial is written to out_trace[p][t], p = 0 .. ceil(S / trace_every) - 1 in
+ * sweep order (device int32, points x trials, or NULL).  out_best[t] (device
+ * int32 [trials] or NULL) receives the largest of those cuts and
+ * out_best_spins[t][.] (device int8 [trials][n] or NULL, 4-byte aligned) the
+ * first configuration reaching it; with S = 0 the best is the starting
+ * configuration.  out_spins (required, 4-byte aligned) and out_cuts (or
+ * NULL) receive the final state as in ising_anneal; init_spins must not be
+ * out_spins.  The trajectory, and every other output, equals that of one
+ * ising_anneal call with the same arguments: the work runs as chunks of
+ * trace_every sweeps, each resuming from the previous one at its global
+ * sweep.  Asynchronous on cuda_stream; allocates one spin-sized scratch
+ * buffer in stream order.  Errors: ISING_ERR_ARG (trace_every <= 0, bad
+ * pointers or betas), and those of ising_anneal.  The paper has no such
+ * entry point.
+ */
+int ising_anneal_trace(ising_problem* p, int32_t trials, const double* betas, int32_t S, uint64_t seed,
+                       uint32_t sweep_offset, const int8_t* init_spins, int8_t* out_spins, int32_t* out_cuts,
+                       int32_t trace_every, int32_t* out_trace, int32_t* out_best, int8_t* out_best_spins,
+                       void* cuda_stream);
+
+/*
  * ising_set_draw_bits -- the decision stream of this handle's anneals
  * (ising_anneal, ising_anneal_noalloc and the batch entry points):
  *   32 (default): trial t at site i in sweep k draws word t mod 4 of the

@@ -22,7 +22,7 @@ import numpy as np
 from . import _abi
 from ._abi import IsingError, check, lib
 
-__all__ = ["Problem", "anneal", "cut", "anneal_batched", "BatchPlan", "IsingError", "lib"]
+__all__ = ["Problem", "anneal", "anneal_trace", "cut", "anneal_batched", "BatchPlan", "IsingError", "lib"]
 
 
 def _torch():
@@ -154,6 +154,33 @@ def anneal(prob, trials, betas, seed, sweep_offset=0, init=None, out_spins=None,
                             _dptr(out_spins) if want_spins else None, _dptr(out_cuts), _stream_ptr(stream))
     check(rc, "ising_anneal")
     return out_spins, out_cuts
+
+
+def anneal_trace(prob, trials, betas, seed, trace_every, sweep_offset=0, init=None, want_best_spins=True,
+                 stream=None):
+    """ising_anneal with read-out along the trajectory: returns (spins, cuts,
+    trace [points, trials], best [trials], best_spins [trials, n] or None) as
+    CUDA tensors; trace row p holds every trial's cut after sweep
+    min((p + 1) * trace_every, S) of the call."""
+    torch = _torch()
+    betas = np.ascontiguousarray(betas, dtype=np.float64)
+    S = int(betas.shape[0])
+    points = (S + int(trace_every) - 1) // int(trace_every) if trace_every > 0 else 0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spins = torch.empty((trials, prob.n), dtype=torch.int8, device=dev)
+    cuts = torch.empty((trials,), dtype=torch.int32, device=dev)
+    trace = torch.empty((max(points, 0), trials), dtype=torch.int32, device=dev)
+    best = torch.empty((trials,), dtype=torch.int32, device=dev)
+    best_spins = torch.empty((trials, prob.n), dtype=torch.int8, device=dev) if want_best_spins else None
+    if init is not None:
+        assert init.is_cuda and init.dtype == torch.int8 and init.shape == (trials, prob.n)
+        init = init.contiguous()
+    rc = lib().ising_anneal_trace(prob.handle, int(trials), betas.ctypes.data_as(ctypes.c_void_p), S,
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(sweep_offset) & 0xFFFFFFFF, _dptr(init),
+                                  _dptr(spins), _dptr(cuts), int(trace_every), _dptr(trace) if points else None,
+                                  _dptr(best), _dptr(best_spins), _stream_ptr(stream))
+    check(rc, "ising_anneal_trace")
+    return spins, cuts, trace, best, best_spins
 
 
 def cut(prob, spins, out=None, stream=None):

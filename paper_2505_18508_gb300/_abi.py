@@ -34,6 +34,8 @@ _SIGNATURES = {
     "ising_destroy": (None, [_vp]),
     "ising_anneal": (ctypes.c_int, [_vp, _i32, _vp, _i32, _u64, _u32, _vp, _vp, _vp, _vp]),
     "ising_cut": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
+    "ising_anneal_trace": (ctypes.c_int, [_vp, _i32, _vp, _i32, _u64, _u32, _vp, _vp, _vp, _i32, _vp, _vp, _vp,
+                                          _vp]),
     "ising_anneal_noalloc": (ctypes.c_int, [_vp, _i32, _vp, _i32, _u64, _u32, _vp, _vp, _vp, _vp]),
     "ising_anneal_batched": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "ising_batch_create": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _vp,
