@@ -57,6 +57,16 @@ def lib():
         L.oracle_anneal_trace.argtypes = L.oracle_anneal_bits.argtypes + [
             ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]   # trace_every, trace, best, best spins
         L.oracle_anneal_trace.restype = ctypes.c_int
+        L.oracle_greedy_colouring.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.oracle_greedy_colouring.restype = ctypes.c_int32
+        L.oracle_energy_h.argtypes = [ctypes.c_int32] + [ctypes.c_void_p] * 5
+        L.oracle_energy_h.restype = ctypes.c_int64
+        L.oracle_anneal_graph.argtypes = [
+            ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,   # n, rp, col, J, h
+            ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,                     # colour, ncol, t0, tc
+            ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32,                   # betas, S, seed, off
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]                   # init, spins, cuts, chk
+        L.oracle_anneal_graph.restype = ctypes.c_int
         L.oracle_thresholds16.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
         L.oracle_thresholds16.restype = ctypes.c_int
         L.oracle_draw.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32]
@@ -163,6 +173,60 @@ def anneal_trace(inst, betas, seed, trace_every, t_begin=0, t_count=0, sweep_off
     if rc != 0:
         raise ValueError(f"oracle_anneal_trace failed with code {rc}")
     return spins, cuts, trace, best, best_spins
+
+
+# --------------------------------------------------------------------------
+# General sparse graphs (integer J, fields h): Eq. 2 in full
+# --------------------------------------------------------------------------
+def _graph_arrays(g):
+    rp = np.ascontiguousarray(g["row_ptr"], dtype=np.int64)
+    col = np.ascontiguousarray(g["col"], dtype=np.int32)
+    J = np.ascontiguousarray(g["J"], dtype=np.int8)
+    h = None if g.get("h") is None else np.ascontiguousarray(g["h"], dtype=np.int8)
+    return rp, col, J, h
+
+
+def greedy_colouring(g):
+    """First-fit colouring in index order: (colour int32 [n], number of colours)."""
+    rp, col, _, _ = _graph_arrays(g)
+    colour = np.zeros(int(g["n"]), dtype=np.int32)
+    k = lib().oracle_greedy_colouring(int(g["n"]), _ptr(rp), _ptr(col), _ptr(colour))
+    if k < 0:
+        raise ValueError("colouring failed")
+    return colour, int(k)
+
+
+def energy_h(g, spins):
+    """Eq. 2 with fields: H = -sum_{i<j} J_ij s_i s_j - sum_i h_i s_i."""
+    rp, col, J, h = _graph_arrays(g)
+    s = np.ascontiguousarray(spins, dtype=np.int8)
+    return int(lib().oracle_energy_h(int(g["n"]), _ptr(rp), _ptr(col), _ptr(J), _ptr(h), _ptr(s)))
+
+
+def anneal_graph(g, betas, seed, t_count, t_begin=0, sweep_offset=0, init=None, colour=None,
+                 check_fields=False):
+    """The Metropolis annealer on a general graph, colour classes in order
+    (first-fit colouring unless given).  Returns (spins, cuts)."""
+    rp, col, J, h = _graph_arrays(g)
+    n = int(g["n"])
+    if colour is None:
+        colour, ncol = greedy_colouring(g)
+    else:
+        colour = np.ascontiguousarray(colour, dtype=np.int32)
+        ncol = int(colour.max()) + 1 if n else 0
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    spins = np.zeros((t_count, n), dtype=np.int8)
+    cuts = np.zeros(t_count, dtype=np.int32)
+    ini = None if init is None else np.ascontiguousarray(init, dtype=np.int8)
+    rc = lib().oracle_anneal_graph(n, _ptr(rp), _ptr(col), _ptr(J), _ptr(h), _ptr(colour), ncol,
+                                   int(t_begin), int(t_count), _ptr(b), int(b.shape[0]),
+                                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(sweep_offset) & 0xFFFFFFFF,
+                                   _ptr(ini), _ptr(spins), _ptr(cuts), 1 if check_fields else 0)
+    if rc == -3:
+        raise AssertionError("incremental local fields diverged from recomputed fields")
+    if rc != 0:
+        raise ValueError(f"oracle_anneal_graph failed with code {rc}")
+    return spins, cuts
 
 
 def cut_csr(inst, spins):

@@ -341,3 +341,145 @@ int oracle_anneal(int32_t n, const int64_t* row_ptr, const int32_t* col, const i
     return oracle_anneal_bits(n, row_ptr, col, J, X, t_begin, t_count, betas, S, seed, sweep_offset,
                               init, out_spins, out_cuts, check_fields, 32);
 }
+
+/* ======================================================================== */
+/* General sparse graphs (integer couplings J, fields h).                   */
+/*                                                                          */
+/* Eq. 2 in full: H(s) = -sum_{i<j} J_ij s_i s_j - sum_i h_i s_i.  Flipping */
+/* spin i changes it by dE_i = 2 s_i (sum_j J_ij s_j + h_i).  The sweep      */
+/* visits the colour classes of a proper colouring in order (colour 0, 1,   */
+/* ...), sites in increasing index within a class; sites of one class are   */
+/* never adjacent, so this equals updating a class at once.  Metropolis:    */
+/* flip when dE <= 0, otherwise when the 32-bit draw (same stream as on the */
+/* torus) is below T(dE) = min(floor(exp(-beta dE) 2^32), 2^32 - 1).        */
+/* ======================================================================== */
+
+/* First-fit colouring in index order: site i takes the smallest colour not */
+/* used by a neighbour j < i.  Returns the number of colours (or -1).       */
+int32_t oracle_greedy_colouring(int32_t n, const int64_t* row_ptr, const int32_t* col, int32_t* colour)
+{
+    if (n < 0) return -1;
+    int32_t ncol = 0;
+    int32_t cap = 64;
+    int* used = (int*)calloc((size_t)cap, sizeof(int));   /* used[c] == i + 1: taken for site i */
+    if (!used) return -1;
+    for (int32_t i = 0; i < n; ++i) {
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col[e];
+            if (j < i) {
+                int32_t c = colour[j];
+                if (c >= cap) {
+                    int32_t nc = cap * 2;
+                    while (nc <= c) nc *= 2;
+                    int* u2 = (int*)realloc(used, sizeof(int) * (size_t)nc);
+                    if (!u2) { free(used); return -1; }
+                    for (int32_t q = cap; q < nc; ++q) u2[q] = 0;
+                    used = u2;
+                    cap = nc;
+                }
+                used[c] = i + 1;
+            }
+        }
+        int32_t c = 0;
+        while (c < cap && used[c] == i + 1) ++c;
+        if (c >= cap) {
+            int* u2 = (int*)realloc(used, sizeof(int) * (size_t)(cap * 2));
+            if (!u2) { free(used); return -1; }
+            for (int32_t q = cap; q < cap * 2; ++q) u2[q] = 0;
+            used = u2;
+            cap *= 2;
+        }
+        colour[i] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(used);
+    return ncol;
+}
+
+/* Eq. 2 with fields: H = -sum_{i<j} J_ij s_i s_j - sum_i h_i s_i */
+int64_t oracle_energy_h(int32_t n, const int64_t* row_ptr, const int32_t* col, const int8_t* J,
+                        const int8_t* h, const int8_t* spins)
+{
+    int64_t H = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int si = spins[i] > 0 ? 1 : -1;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int32_t j = col[e];
+            if (j <= i) continue;
+            int sj = spins[j] > 0 ? 1 : -1;
+            H -= (int64_t)J[e] * si * sj;
+        }
+        if (h) H -= (int64_t)h[i] * si;
+    }
+    return H;
+}
+
+static uint32_t threshold_of(double beta, int dE)
+{
+    double fl = floor(exp(-(beta * (double)dE)) * 4294967296.0);
+    return fl >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)fl;
+}
+
+/* The annealer on a general graph.  colour: a proper colouring with ncol    */
+/* classes (the caller's, e.g. oracle_greedy_colouring).  h may be NULL.     */
+/* Outputs as oracle_anneal: spins, and the Eq. 1 cut sum_{i<j} w_ij         */
+/* [s_i != s_j] with w = -J.  Returns 0, -1 for bad arguments (including an  */
+/* improper colouring or a non-positive beta), -3 on a field mismatch.       */
+int oracle_anneal_graph(int32_t n, const int64_t* row_ptr, const int32_t* col, const int8_t* J,
+                        const int8_t* h, const int32_t* colour, int32_t ncol,
+                        int32_t t_begin, int32_t t_count, const double* betas, int32_t S, uint64_t seed,
+                        uint32_t sweep_offset, const int8_t* init, int8_t* out_spins, int32_t* out_cuts,
+                        int32_t check_fields)
+{
+    if (n <= 0 || ncol <= 0 || t_begin < 0 || t_count < 0 || S < 0) return -1;
+    for (int32_t k = 0; k < S; ++k)
+        if (!(betas[k] > 0.0)) return -1;
+    for (int32_t i = 0; i < n; ++i) {
+        if (colour[i] < 0 || colour[i] >= ncol) return -1;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (col[e] == i || colour[col[e]] == colour[i]) return -1;
+    }
+    int* s = (int*)malloc(sizeof(int) * (size_t)n);
+    int* f = (int*)malloc(sizeof(int) * (size_t)n);   /* f_i = sum_j J_ij s_j */
+    int rc = 0;
+    if (!s || !f) { rc = -1; goto out; }
+    for (int32_t tt = 0; tt < t_count; ++tt) {
+        int32_t t = t_begin + tt;
+        for (int32_t i = 0; i < n; ++i) {
+            if (init) s[i] = init[(size_t)tt * n + i] > 0 ? 1 : -1;
+            else s[i] = (draw((uint32_t)i, 0xFFFFFFFFu, t, seed) >> 31) ? 1 : -1;
+        }
+        for (int32_t i = 0; i < n; ++i) {
+            int acc = 0;
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) acc += (int)J[e] * s[col[e]];
+            f[i] = acc;
+        }
+        for (int32_t jj = 0; jj < S; ++jj) {
+            uint32_t k = sweep_offset + (uint32_t)jj;
+            for (int32_t c = 0; c < ncol; ++c) {
+                for (int32_t i = 0; i < n; ++i) {
+                    if (colour[i] != c) continue;
+                    int dE = 2 * s[i] * (f[i] + (h ? (int)h[i] : 0));
+                    int flip = dE <= 0 ? 1 : draw((uint32_t)i, k, t, seed) < threshold_of(betas[jj], dE);
+                    if (flip) {
+                        s[i] = -s[i];
+                        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) f[col[e]] += 2 * (int)J[e] * s[i];
+                    }
+                }
+            }
+            if (check_fields) {
+                for (int32_t i = 0; i < n; ++i) {
+                    int acc = 0;
+                    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) acc += (int)J[e] * s[col[e]];
+                    if (acc != f[i]) { rc = -3; goto out; }
+                }
+            }
+        }
+        if (out_spins)
+            for (int32_t i = 0; i < n; ++i) out_spins[(size_t)tt * n + i] = (int8_t)s[i];
+        if (out_cuts) out_cuts[tt] = cut_of(n, row_ptr, col, J, s);
+    }
+out:
+    free(s); free(f);
+    return rc;
+}

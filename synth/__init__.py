@@ -30,6 +30,8 @@ __all__ = [
     "random_spins",
     "batched_config",
     "cnn_init_params",
+    "random_graph",
+    "graph_from_edges",
 ]
 
 
@@ -134,3 +136,53 @@ def cnn_init_params(seed: int, scale: float = 1.0) -> np.ndarray:
             fan_in = shp[1] * shp[2] * shp[3]
             parts.append(rng.normal(0.0, scale * np.sqrt(2.0 / fan_in), size=shp))
     return np.concatenate([p.reshape(-1) for p in parts]).astype(np.float64)
+
+
+def graph_from_edges(n: int, i, j, w, h=None):
+    """Symmetric CSR of an undirected graph: edges (i[e], j[e]) with weight
+    w[e] (i != j, no repeats); returns a dict with n, row_ptr int64, col int32
+    (rows sorted by column), J int8 = -w (the Ising coupling of Eq. 2) and the
+    fields h (int8 [n] or None)."""
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    w = np.asarray(w, dtype=np.int64)
+    src = np.concatenate([i, j])
+    dst = np.concatenate([j, i])
+    ww = np.concatenate([w, w])
+    order = np.lexsort((dst, src))
+    src, dst, ww = src[order], dst[order], ww[order]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, src + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    return {"n": int(n), "row_ptr": row_ptr, "col": dst.astype(np.int32), "J": (-ww).astype(np.int8),
+            "h": None if h is None else np.asarray(h, dtype=np.int8), "w": ww.astype(np.int8)}
+
+
+def random_graph(n: int, m: int, seed: int, weights: str = "pm1", hmax: int = 0):
+    """A random simple graph with n vertices and m distinct edges (PCG64), in
+    the form of graph_from_edges.  weights: "pm1" (w = +-1, like the Gset
+    random and toroidal graphs), "one" (w = +1) or "int" (w in +-{1, 2, 3});
+    hmax > 0 adds integer fields h_i in [-hmax, hmax]."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    if m > n * (n - 1) // 2:
+        raise ValueError("too many edges")
+    seen = set()
+    ii, jj = [], []
+    while len(ii) < m:
+        a, b = (int(v) for v in rng.integers(0, n, size=2))
+        if a == b:
+            continue
+        key = (min(a, b), max(a, b))
+        if key in seen:
+            continue
+        seen.add(key)
+        ii.append(key[0])
+        jj.append(key[1])
+    if weights == "one":
+        w = np.ones(m, dtype=np.int64)
+    elif weights == "int":
+        w = rng.integers(1, 4, size=m) * (2 * rng.integers(0, 2, size=m) - 1)
+    else:
+        w = 2 * rng.integers(0, 2, size=m) - 1
+    h = rng.integers(-hmax, hmax + 1, size=n) if hmax > 0 else None
+    return graph_from_edges(n, ii, jj, w, h)

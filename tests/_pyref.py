@@ -75,3 +75,52 @@ def anneal_full_energy(X, Y, edges, betas, seed, trials, sweep_offset=0, init=No
                         s[i] = -s[i]
         out[t] = s
     return out
+
+
+def graph_energy(n, edges, h, s):
+    """Eq. 2 with fields from an edge list (i, j, J): -sum J s_i s_j - sum h s."""
+    i, j, Jv = edges
+    e = -sum(int(Jv[k]) * int(s[i[k]]) * int(s[j[k]]) for k in range(len(Jv)))
+    if h is not None:
+        e -= sum(int(h[q]) * int(s[q]) for q in range(n))
+    return e
+
+
+def first_fit_colouring(n, adj):
+    """Smallest colour not taken by an earlier neighbour, sites in index order."""
+    colour = [0] * n
+    for v in range(n):
+        taken = {colour[u] for u in adj[v] if u < v}
+        c = 0
+        while c in taken:
+            c += 1
+        colour[v] = c
+    return colour
+
+
+def anneal_graph_full_energy(n, edges, h, colour, betas, seed, trials, sweep_offset=0):
+    """The Metropolis sweep over colour classes in order, each flip judged by
+    the difference of whole-graph energies (Eq. 2 with fields)."""
+    out = np.zeros((trials, n), dtype=np.int8)
+    ncol = max(colour) + 1
+    for t in range(trials):
+        s = [1 if (draw(q, 0xFFFFFFFF, t, seed) >> 31) else -1 for q in range(n)]
+        for jj, beta in enumerate(betas):
+            k = (sweep_offset + jj) & MASK
+            for c in range(ncol):
+                for q in range(n):
+                    if colour[q] != c:
+                        continue
+                    e0 = graph_energy(n, edges, h, s)
+                    s[q] = -s[q]
+                    dE = graph_energy(n, edges, h, s) - e0
+                    s[q] = -s[q]
+                    if dE <= 0:
+                        flip = True
+                    else:
+                        thr = min(math.floor(math.exp(-beta * dE) * 2.0 ** 32), 2 ** 32 - 1)
+                        flip = draw(q, k, t, seed) < thr
+                    if flip:
+                        s[q] = -s[q]
+        out[t] = s
+    return out
