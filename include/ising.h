@@ -171,7 +171,9 @@ void ising_batch_destroy(ising_batch* b);
  * choice.
  * group_trials   trials packed per 32-bit word, multiple of 4 in [4, 32].
  * strips         CTAs that share one trial group as row strips (thread-block
- *                cluster of that size, 1..16), at most Y.
+ *                cluster of that size, 1..16), at most Y; for a general
+ *                graph handle the cluster that shares a 32-trial group,
+ *                1..8 (group_trials and threads do not apply there).
  * threads        threads per CTA, multiple of 32 in [64, 1024].
  * Errors: ISING_ERR_ARG.  Results do not depend on the shape.
  */
@@ -197,6 +199,44 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
  * Results do not depend on the kernel.  Errors: ISING_ERR_ARG.
  */
 int ising_set_kernel(ising_problem* p, int32_t kind);
+
+/*
+ * ising_graph_create -- a general sparse instance: any simple undirected
+ * graph as a symmetric CSR (host pointers, copied; row_ptr int64 [n+1],
+ * col_idx int32 [nnz], J int8 [nnz] with J_ij = J_ji, 1 <= |J| <= 127, no
+ * self loops or repeated neighbours) and integer fields h (int8 [n],
+ * |h| <= 127, or NULL).  Eq. 2 in full: H = -sum_{i<j} J_ij s_i s_j -
+ * sum_i h_i s_i; the Max-Cut weights are w = -J (Eq. 1).  n <= 2^24, and per
+ * site sum |J| + |h| <= 255.  The sweep visits the classes of the first-fit
+ * colouring (ising_greedy_colouring) in order; ising_anneal, ising_cut,
+ * ising_energy and ising_anneal_trace accept the handle (the batched, the
+ * 16-bit and the no-allocation paths return ISING_ERR_UNSUPPORTED).  One
+ * 32-trial group's spins must fit in shared memory (about 56,000 sites).
+ * Errors: ISING_ERR_ARG (malformed or asymmetric CSR), ISING_ERR_UNSUPPORTED,
+ * ISING_ERR_OOM, ISING_ERR_CUDA.  The paper frames the problem this way
+ * (Section II); its own runs use the toroidal instances only.
+ */
+int ising_graph_create(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, const int8_t* J,
+                       const int8_t* h, ising_problem** out);
+
+/*
+ * ising_greedy_colouring -- the colouring the general-graph sweep uses
+ * (host only, no GPU): site i takes the smallest colour no neighbour j < i
+ * holds.  colour: int32 [n] (host, caller-owned); *ncol: classes used.
+ */
+int ising_greedy_colouring(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t* colour,
+                           int32_t* ncol);
+
+/* ising_graph_info -- n, colour classes and the largest sum |J| + |h| of a
+ * general-graph handle (ISING_ERR_ARG for a torus handle). */
+int ising_graph_info(const ising_problem* p, int32_t* n, int32_t* ncol, int32_t* Dmax);
+
+/*
+ * ising_energy -- Eq. 2 of k configurations (device int8 [k][n]) into
+ * out_energies (device int64 [k]); asynchronous on cuda_stream.  For a torus
+ * handle H = W - 2 cut.  Errors: ISING_ERR_ARG, ISING_ERR_CUDA.
+ */
+int ising_energy(const ising_problem* p, const int8_t* spins, int32_t k, int64_t* out_energies, void* cuda_stream);
 
 /*
  * ising_anneal_trace -- ising_anneal with read-out along the trajectory

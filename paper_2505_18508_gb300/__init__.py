@@ -22,7 +22,8 @@ import numpy as np
 from . import _abi
 from ._abi import IsingError, check, lib
 
-__all__ = ["Problem", "anneal", "anneal_trace", "cut", "anneal_batched", "BatchPlan", "IsingError", "lib"]
+__all__ = ["Problem", "anneal", "anneal_trace", "cut", "energy", "greedy_colouring", "anneal_batched", "BatchPlan",
+           "IsingError", "lib"]
 
 
 def _torch():
@@ -42,11 +43,37 @@ def _dptr(t):
 
 
 class Problem:
-    """A validated toroidal instance packed on the current CUDA device."""
+    """A validated instance packed on the current CUDA device: a torus
+    (from_csr / from_instance) or a general sparse graph (from_graph)."""
 
-    def __init__(self, handle, X, Y):
+    def __init__(self, handle, X, Y, n=None):
         self._h = handle
-        self.X, self.Y, self.n = X, Y, X * Y
+        self.X, self.Y = X, Y
+        self.n = X * Y if n is None else int(n)
+
+    @classmethod
+    def from_graph(cls, g):
+        """From a dict with n, row_ptr, col, J and optional h (e.g. synth.random_graph)."""
+        row_ptr = np.ascontiguousarray(g["row_ptr"], dtype=np.int64)
+        col = np.ascontiguousarray(g["col"], dtype=np.int32)
+        J = np.ascontiguousarray(g["J"], dtype=np.int8)
+        h = g.get("h")
+        hp = None
+        if h is not None:
+            h = np.ascontiguousarray(h, dtype=np.int8)
+            hp = h.ctypes.data_as(ctypes.c_void_p)
+        out = ctypes.c_void_p()
+        rc = lib().ising_graph_create(int(g["n"]), row_ptr.ctypes.data_as(ctypes.c_void_p),
+                                      col.ctypes.data_as(ctypes.c_void_p), J.ctypes.data_as(ctypes.c_void_p),
+                                      hp, ctypes.byref(out))
+        check(rc, "ising_graph_create")
+        return cls(out, 0, 0, n=int(g["n"]))
+
+    def graph_info(self):
+        n, k, d = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib().ising_graph_info(self.handle, ctypes.byref(n), ctypes.byref(k), ctypes.byref(d)),
+              "ising_graph_info")
+        return {"n": n.value, "colours": k.value, "Dmax": d.value}
 
     @classmethod
     def from_csr(cls, n, row_ptr, col, J, X, Y, h=None):
@@ -181,6 +208,29 @@ def anneal_trace(prob, trials, betas, seed, trace_every, sweep_offset=0, init=No
                                   _dptr(best), _dptr(best_spins), _stream_ptr(stream))
     check(rc, "ising_anneal_trace")
     return spins, cuts, trace, best, best_spins
+
+
+def greedy_colouring(g):
+    """The first-fit colouring the general-graph sweep uses (host only)."""
+    row_ptr = np.ascontiguousarray(g["row_ptr"], dtype=np.int64)
+    col = np.ascontiguousarray(g["col"], dtype=np.int32)
+    colour = np.zeros(int(g["n"]), dtype=np.int32)
+    k = ctypes.c_int32()
+    check(lib().ising_greedy_colouring(int(g["n"]), row_ptr.ctypes.data_as(ctypes.c_void_p),
+                                       col.ctypes.data_as(ctypes.c_void_p), colour.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.byref(k)), "ising_greedy_colouring")
+    return colour, k.value
+
+
+def energy(prob, spins, out=None, stream=None):
+    """Eq. 2 (with fields) of each row of an int8 CUDA tensor [k, n] -> int64."""
+    torch = _torch()
+    spins = spins.contiguous()
+    k = spins.shape[0]
+    if out is None:
+        out = torch.empty((k,), dtype=torch.int64, device=spins.device)
+    check(lib().ising_energy(prob.handle, _dptr(spins), int(k), _dptr(out), _stream_ptr(stream)), "ising_energy")
+    return out
 
 
 def cut(prob, spins, out=None, stream=None):

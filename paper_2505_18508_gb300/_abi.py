@@ -47,6 +47,10 @@ _SIGNATURES = {
     "ising_problem_info": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "ising_set_kernel": (ctypes.c_int, [_vp, _i32]),
     "ising_set_draw_bits": (ctypes.c_int, [_vp, _i32]),
+    "ising_graph_create": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _vp]),
+    "ising_greedy_colouring": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp]),
+    "ising_graph_info": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "ising_energy": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
     "ising_last_kernel": (ctypes.c_int, [_vp, _i32p]),
     "ising_get_status": (ctypes.c_int, [_vp, _vp, _i32p]),
     "ising_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64, _i32]),

@@ -140,6 +140,7 @@ int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials,
   int device = 0;
   for (int32_t q = 0; q < m; ++q) {
     if (!probs[q] || trials[q] < 0 || sweeps[q] < 0 || (sweeps[q] > 0 && !betas[q])) return ISING_ERR_ARG;
+    if (probs[q]->graph) return ISING_ERR_UNSUPPORTED;
     if (q == 0) device = probs[q]->device;
     else if (probs[q]->device != device) return ISING_ERR_ARG;
   }
@@ -377,6 +378,105 @@ int run_flow(ising_problem* p, const FlowPlan& fp, int32_t trials, const std::ve
   return ISING_OK;
 }
 
+
+// ---------------------------------------------------------------- general graphs
+// First-fit colouring in index order: site i takes the smallest colour that
+// no neighbour j < i holds.  stamp[c] == i + 1 marks colour c as taken for i.
+int32_t first_fit(int32_t n, const int64_t* row_ptr, const int32_t* col, std::vector<int32_t>& colour) {
+  colour.assign(static_cast<size_t>(n), 0);
+  std::vector<int32_t> stamp(16, 0);
+  int32_t ncol = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int32_t j = col[e];
+      if (j >= i) continue;
+      const int32_t c = colour[j];
+      if (static_cast<size_t>(c) >= stamp.size()) stamp.resize(static_cast<size_t>(c) * 2 + 2, 0);
+      stamp[c] = i + 1;
+    }
+    int32_t c = 0;
+    while (static_cast<size_t>(c) < stamp.size() && stamp[c] == i + 1) ++c;
+    colour[i] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  return ncol;
+}
+
+ising::GraphArgs graph_args(const ising_problem* p) {
+  ising::GraphArgs a{};
+  a.nb = p->d_nb;
+  a.rowinfo = p->d_rowinfo;
+  a.sites = p->d_sites;
+  a.colour_off = p->d_colour_off;
+  a.n = p->n;
+  a.n_pad = (p->n + 3) & ~3;
+  a.thr_pad = (p->Dmax + 1 + 3) & ~3;
+  a.Dmax = p->Dmax;
+  a.planes = p->planes;
+  a.ncol = p->ncol;
+  return a;
+}
+
+int run_graph(ising_problem* p, int32_t trials, const double* betas, int32_t S, uint64_t seed,
+              uint32_t sweep_offset, const int8_t* init_spins, int8_t* out_spins, int32_t* out_cuts,
+              cudaStream_t st) {
+  if (p->draw_bits != 32) return ISING_ERR_UNSUPPORTED;
+  // T(dE) = min(floor(exp(-beta dE) 2^32), 2^32 - 1) for dE = 2q, q = 1 .. Dmax
+  std::vector<uint32_t> thr;
+  try {
+    thr.assign(static_cast<size_t>(S) * p->Dmax, 0u);
+  } catch (const std::bad_alloc&) {
+    return ISING_ERR_OOM;
+  }
+  for (int32_t k = 0; k < S; ++k) {
+    if (!(betas[k] > 0.0)) return ISING_ERR_ARG;
+    for (int32_t q = 1; q <= p->Dmax; ++q) {
+      const double v = std::floor(std::exp(-(betas[k] * (2.0 * q))) * 4294967296.0);
+      thr[static_cast<size_t>(k) * p->Dmax + (q - 1)] = v >= 4294967295.0 ? 0xFFFFFFFFu : static_cast<uint32_t>(v);
+    }
+  }
+  if (trials == 0) return ISING_OK;
+  const int sms = num_sms_of(p->device);
+  const int groups = (trials + 31) / 32;
+  if (groups > 65535) return ISING_ERR_UNSUPPORTED;
+  int C = p->cfg_strips;
+  if (C == 0) {
+    C = 1;
+    while (C < 8 && groups * (C * 2) <= sms) C *= 2;
+  }
+  if (C > 8) return ISING_ERR_UNSUPPORTED;
+  uint32_t* d_thr = nullptr;
+  const size_t bytes = thr.size() * sizeof(uint32_t);
+  if (bytes) {
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_thr), bytes, st);
+    if (e != cudaSuccess) return map_cuda(e);
+    e = cudaMemcpyAsync(d_thr, thr.data(), bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { cudaFreeAsync(d_thr, st); return map_cuda(e); }
+  }
+  ising::GraphArgs a = graph_args(p);
+  a.thr = d_thr;
+  a.init = init_spins;
+  a.out_spins = out_spins;
+  a.out_cuts = out_cuts;
+  a.T = trials;
+  a.S = S;
+  a.C = C;
+  a.k0 = sweep_offset;
+  a.key0 = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
+  a.key1 = static_cast<uint32_t>(seed >> 32);
+  cudaError_t e = ising::launch_graph(a, st);
+  if (d_thr) {
+    const cudaError_t e2 = cudaFreeAsync(d_thr, st);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e != cudaSuccess) return map_cuda(e);
+  p->last_kernel = 3;
+  p->last_group = 32;
+  p->last_strips = C;
+  p->last_threads = ising::graph_threads();
+  p->last_grid = C * groups;
+  return ISING_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -485,13 +585,17 @@ void ising_destroy(ising_problem* p) {
   cudaFree(p->d_flags);
   cudaFree(p->d_eflags);
   cudaFree(p->d_status);
+  cudaFree(p->d_nb);
+  cudaFree(p->d_rowinfo);
+  cudaFree(p->d_sites);
+  cudaFree(p->d_colour_off);
   delete p;
 }
 
 int ising_set_launch(ising_problem* p, int32_t group_trials, int32_t strips, int32_t threads) {
   if (!p) return ISING_ERR_ARG;
   if (group_trials != 0 && (group_trials < 4 || group_trials > 32 || group_trials % 4)) return ISING_ERR_ARG;
-  if (strips != 0 && (strips < 1 || strips > 16 || strips > p->Y)) return ISING_ERR_ARG;
+  if (strips != 0 && (strips < 1 || strips > 16 || (p->graph ? strips > 8 : strips > p->Y))) return ISING_ERR_ARG;
   if (threads != 0 && (threads < 64 || threads > 1024 || threads % 32)) return ISING_ERR_ARG;
   p->cfg_group = group_trials;
   p->cfg_strips = strips;
@@ -559,6 +663,9 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
                  uint32_t sweep_offset, const int8_t* init_spins, int8_t* out_spins, int32_t* out_cuts,
                  void* cuda_stream) {
   if (!p || trials < 0 || S < 0 || (S > 0 && !betas)) return ISING_ERR_ARG;
+  if (p->graph)
+    return run_graph(p, trials, betas, S, seed, sweep_offset, init_spins, out_spins, out_cuts,
+                     static_cast<cudaStream_t>(cuda_stream));
   if (p->draw_bits == 16 && p->cfg_group % 8) return ISING_ERR_ARG;
   std::vector<uint32_t> thr;
   try {
@@ -636,6 +743,9 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
 
 int ising_cut(const ising_problem* p, const int8_t* spins, int32_t k, int32_t* out_cuts, void* cuda_stream) {
   if (!p || k < 0 || (k > 0 && (!spins || !out_cuts))) return ISING_ERR_ARG;
+  if (p->graph)
+    return map_cuda(ising::launch_graph_measure(graph_args(p), spins, k, out_cuts, nullptr,
+                                                static_cast<cudaStream_t>(cuda_stream)));
   return map_cuda(ising::launch_cut(p, spins, k, out_cuts, static_cast<cudaStream_t>(cuda_stream)));
 }
 
@@ -742,6 +852,142 @@ int ising_batch_launch(ising_batch* b, void* cuda_stream) {
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   cudaError_t e = cudaGraphLaunch(b->exec, st);
   if (e == cudaSuccess) e = cudaEventRecord(b->done, st);
+  return map_cuda(e);
+}
+
+int ising_greedy_colouring(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t* colour,
+                           int32_t* ncol) {
+  if (n < 0 || (n > 0 && (!row_ptr || !col_idx || !colour)) || !ncol) return ISING_ERR_ARG;
+  std::vector<int32_t> c;
+  try {
+    *ncol = first_fit(n, row_ptr, col_idx, c);
+  } catch (const std::bad_alloc&) {
+    return ISING_ERR_OOM;
+  }
+  if (n > 0) std::memcpy(colour, c.data(), sizeof(int32_t) * static_cast<size_t>(n));
+  return ISING_OK;
+}
+
+int ising_graph_create(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, const int8_t* J,
+                       const int8_t* h, ising_problem** out) {
+  if (!row_ptr || !col_idx || !J || !out || n <= 0) return ISING_ERR_ARG;
+  if (n > (1 << 24)) return ISING_ERR_UNSUPPORTED;
+  if (row_ptr[0] != 0) return ISING_ERR_ARG;
+  for (int32_t i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return ISING_ERR_ARG;
+  const int64_t nnz = row_ptr[n];
+  if (nnz > (int64_t(1) << 31)) return ISING_ERR_UNSUPPORTED;
+  std::vector<uint32_t> nb;
+  std::vector<int4> rowinfo;
+  std::vector<int32_t> colour, sites, off;
+  int32_t Dmax = 0, ncol = 0;
+  int64_t wsum = 0;
+  try {
+    nb.resize(static_cast<size_t>(nnz));
+    rowinfo.resize(static_cast<size_t>(n));
+    // entries, self loops, repeats; per-row sorted copies for the symmetry test
+    std::vector<std::pair<int32_t, int8_t>> rows(static_cast<size_t>(nnz));
+    for (int32_t i = 0; i < n; ++i) {
+      int32_t D = 0;
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        const int32_t j = col_idx[e];
+        const int8_t v = J[e];
+        if (j < 0 || j >= n || j == i || v == 0 || v == -128) return ISING_ERR_ARG;
+        rows[e] = {j, v};
+        const int32_t mag = v < 0 ? -v : v;
+        D += mag;
+        nb[e] = static_cast<uint32_t>(j) | (v < 0 ? (1u << 24) : 0u) | (static_cast<uint32_t>(mag - 1) << 25);
+        if (j > i) wsum -= v;
+      }
+      std::sort(rows.begin() + row_ptr[i], rows.begin() + row_ptr[i + 1]);
+      for (int64_t e = row_ptr[i] + 1; e < row_ptr[i + 1]; ++e)
+        if (rows[e].first == rows[e - 1].first) return ISING_ERR_ARG;
+      int32_t hv = 0;
+      if (h) {
+        if (h[i] == -128) return ISING_ERR_ARG;
+        hv = h[i];
+      }
+      D += hv < 0 ? -hv : hv;
+      if (D > 255) return ISING_ERR_UNSUPPORTED;
+      Dmax = std::max(Dmax, D);
+      rowinfo[i] = make_int4(static_cast<int>(row_ptr[i]), static_cast<int>(row_ptr[i + 1] - row_ptr[i]), hv, D);
+    }
+    for (int32_t i = 0; i < n; ++i)
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        const int32_t j = rows[e].first;
+        const auto b = rows.begin() + row_ptr[j], en = rows.begin() + row_ptr[j + 1];
+        const auto it = std::lower_bound(b, en, std::make_pair(i, static_cast<int8_t>(-128)));
+        if (it == en || it->first != i || it->second != rows[e].second) return ISING_ERR_ARG;
+      }
+    ncol = first_fit(n, row_ptr, col_idx, colour);
+    off.assign(static_cast<size_t>(ncol) + 1, 0);
+    for (int32_t i = 0; i < n; ++i) ++off[colour[i] + 1];
+    for (int32_t c = 0; c < ncol; ++c) off[c + 1] += off[c];
+    sites.resize(static_cast<size_t>(n));
+    std::vector<int32_t> fill(off.begin(), off.end() - 1);
+    for (int32_t i = 0; i < n; ++i) sites[fill[colour[i]]++] = i;
+  } catch (const std::bad_alloc&) {
+    return ISING_ERR_OOM;
+  }
+  int planes = 1;
+  while ((1 << planes) <= Dmax) ++planes;
+  ising_problem* p = new (std::nothrow) ising_problem();
+  if (!p) return ISING_ERR_OOM;
+  p->graph = 1;
+  p->n = n;
+  p->nnz = nnz;
+  p->ncol = ncol;
+  p->Dmax = Dmax;
+  p->planes = planes;
+  p->weight_sum = static_cast<int32_t>(wsum);
+  if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return ISING_ERR_CUDA; }
+  if (ising::graph_smem_bytes(n, Dmax) > static_cast<size_t>(max_smem_of(p->device))) {
+    delete p;
+    return ISING_ERR_UNSUPPORTED;
+  }
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->d_status), sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int32_t));
+  if (e == cudaSuccess && nnz) e = cudaMalloc(reinterpret_cast<void**>(&p->d_nb), sizeof(uint32_t) * nnz);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_rowinfo), sizeof(int4) * n);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_sites), sizeof(int32_t) * n);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_colour_off), sizeof(int32_t) * (ncol + 1));
+  if (e == cudaSuccess && nnz)
+    e = cudaMemcpy(p->d_nb, nb.data(), sizeof(uint32_t) * nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_rowinfo, rowinfo.data(), sizeof(int4) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_sites, sites.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_colour_off, off.data(), sizeof(int32_t) * (ncol + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    ising_destroy(p);
+    return map_cuda(e);
+  }
+  *out = p;
+  return ISING_OK;
+}
+
+int ising_graph_info(const ising_problem* p, int32_t* n, int32_t* ncol, int32_t* Dmax) {
+  if (!p || !p->graph) return ISING_ERR_ARG;
+  if (n) *n = p->n;
+  if (ncol) *ncol = p->ncol;
+  if (Dmax) *Dmax = p->Dmax;
+  return ISING_OK;
+}
+
+int ising_energy(const ising_problem* p, const int8_t* spins, int32_t k, int64_t* out_energies, void* cuda_stream) {
+  if (!p || k < 0 || (k > 0 && (!spins || !out_energies))) return ISING_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (p->graph)
+    return map_cuda(ising::launch_graph_measure(graph_args(p), spins, k, nullptr,
+                                                reinterpret_cast<long long*>(out_energies), st));
+  // torus (h = 0): H = W - 2 cut
+  if (k == 0) return ISING_OK;
+  int32_t* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(int32_t) * k, st);
+  if (e != cudaSuccess) return map_cuda(e);
+  e = ising::launch_cut(p, spins, k, tmp, st);
+  if (e == cudaSuccess) e = ising::launch_energy_from_cut(tmp, p->weight_sum, k, out_energies, st);
+  const cudaError_t e2 = cudaFreeAsync(tmp, st);
+  if (e == cudaSuccess) e = e2;
   return map_cuda(e);
 }
 

@@ -26,6 +26,14 @@ struct ising_problem {
   // bounded-wait limit (cycles) and the forced-stall switch used by tests
   long long wait_limit = 0;
   int32_t stall_test = 0;
+  // general sparse graph (ising_graph_create); X = Y = 0 then
+  int32_t graph = 0;
+  int32_t ncol = 0, Dmax = 0, planes = 0;
+  int64_t nnz = 0;
+  uint32_t* d_nb = nullptr;        // [nnz] col | (J < 0) << 24 | (|J| - 1) << 25
+  int4* d_rowinfo = nullptr;       // [n] {first entry, degree, h, D = sum |J| + |h|}
+  int32_t* d_sites = nullptr;      // [n] sites by colour class, increasing index within a class
+  int32_t* d_colour_off = nullptr; // [ncol + 1]
 };
 
 namespace ising {
@@ -144,6 +152,28 @@ struct BatchArgs {
   int32_t n_units;
   uint32_t* counter;               // work-queue head, zero before the launch
 };
+// Everything the general-graph kernel reads (graph.cu).
+struct GraphArgs {
+  const uint32_t* nb;
+  const int4* rowinfo;
+  const int32_t* sites;
+  const int32_t* colour_off;
+  const uint32_t* thr;       // [S][Dmax]: entry q - 1 = T(dE = 2q)
+  const int8_t* init;        // [T][n] or null
+  int8_t* out_spins;         // [T][n] or null
+  int32_t* out_cuts;         // [T] or null
+  int32_t n, n_pad, thr_pad; // n and Dmax + 1, each rounded up to a multiple of 4
+  int32_t Dmax, planes, ncol;
+  int32_t T, S, C;           // trials, sweeps, CTAs per 32-trial group (cluster size)
+  uint32_t k0, key0, key1;
+};
+size_t graph_smem_bytes(int32_t n, int32_t Dmax);
+int graph_threads();
+cudaError_t launch_graph(const GraphArgs& a, cudaStream_t st);
+cudaError_t launch_graph_measure(const GraphArgs& a, const int8_t* spins, int32_t k, int32_t* cuts,
+                                 long long* energies, cudaStream_t st);
+cudaError_t launch_energy_from_cut(const int32_t* cuts, int32_t W, int32_t k, int64_t* out, cudaStream_t st);
+
 size_t batched_smem_bytes(int32_t H, int32_t Y);
 cudaError_t batched_prepare(size_t smem);
 cudaError_t launch_batched(const BatchArgs& a, int grid, int threads, size_t smem, cudaStream_t stream);

@@ -75,6 +75,7 @@ extern "C" int ising_anneal_noalloc(ising_problem* p, int32_t trials, const doub
                                     uint64_t seed, uint32_t sweep_offset, const int8_t* init_spins,
                                     int8_t* out_spins, int32_t* out_cuts, void* cuda_stream) {
   if (!p || trials < 0 || S < 0 || (S > 0 && !betas)) return ISING_ERR_ARG;
+  if (p->graph) return ISING_ERR_UNSUPPORTED;
   if (p->draw_bits == 16 && p->cfg_group % 8) return ISING_ERR_ARG;
   if (S > kNoAllocMaxSweeps) return ISING_ERR_UNSUPPORTED;
   for (int32_t k = 0; k < S; ++k)
