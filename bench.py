@@ -247,6 +247,45 @@ def learned_leg(budgets=(1000, 3000, 10000, 30000), every=100, tile=10, n_train=
             "per_seed": rows}
 
 
+def graph_leg(trials=1024, sweeps=2000, reps=3):
+    """General sparse graphs through the general-graph kernel (spins in
+    shared memory, colour classes in order): a G22-like random graph (2,000
+    vertices, 19,990 edges, w = +1), a random graph of the headline's size
+    (20,000 vertices, 40,000 edges, w = +-1) and the headline torus given as a
+    general graph."""
+    import torch
+    import paper_2505_18508_gb300 as ia
+    out = {}
+    inst = synth.torus_instance(200, 100, 2)
+    cases = {
+        "random_2000v_19990e_w1": synth.random_graph(2000, 19990, 22, weights="one"),
+        "random_20000v_40000e_pm1": synth.random_graph(20000, 40000, 81, weights="pm1"),
+        "torus_200x100_as_graph": {"n": inst["n"], "row_ptr": inst["row_ptr"], "col": inst["col"],
+                                   "J": inst["J"], "h": None},
+    }
+    betas = synth.linear_betas(0.1, 3.0, sweeps)
+    for name, g in cases.items():
+        prob = ia.Problem.from_graph(g)
+        cuts = torch.empty(trials, dtype=torch.int32, device="cuda")
+        ia.anneal(prob, trials, betas, 1, want_spins=False, out_cuts=cuts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for r in range(reps):
+            ia.anneal(prob, trials, betas, 2 + r, want_spins=False, out_cuts=cuts)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        info = prob.graph_info()
+        ups = trials * sweeps * g["n"]
+        out[name] = {"n": g["n"], "edges": int(len(g["col"]) // 2), "colours": info["colours"], "Dmax": info["Dmax"],
+                     "trials": trials, "sweeps": sweeps, "ms": ms, "value": ups / (ms / 1e3),
+                     "unit": "spin-updates/s", "best_cut": int(cuts.max().item()),
+                     "mean_cut": float(cuts.double().mean().item())}
+        prob.destroy()
+    return out
+
+
 def batched_leg(reps=2):
     """Config 3: the 96-instance uneven batch ({50,100,140,200}x100, 32-512
     trials, 2,000-20,000 sweeps) as one graph-replayed persistent launch."""
@@ -455,6 +494,9 @@ def main():
     batched = None
     if rank == 0 and not args.sweeps and not args.trials:
         batched = batched_leg()
+    graphs = None
+    if rank == 0 and not args.sweeps and not args.trials:
+        graphs = graph_leg()
     campaign = None
     if rank == 0 and not args.sweeps and not args.trials:
         from paper_2505_18508_gb300.campaign import run_campaign
@@ -482,6 +524,7 @@ def main():
             "ttt_99_9": stats,
             "draw16_variant": draw16,
             "campaign": campaign,
+            "general_graphs": graphs,
             "batched": batched,
             "learned_vs_plain": learned_cmp,
             "wall_s_timed": wall,
