@@ -317,10 +317,8 @@ def batched_leg(reps=2):
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2505_18508_gb300 import replicas
+    return replicas.env()
 
 
 def reference_arm(args):
@@ -396,8 +394,10 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
+    from paper_2505_18508_gb300 import replicas
+
     def seed_of(step):
-        return w["seed"] + 1_000_003 * rank + step
+        return replicas.rank_seed(w["seed"], rank, step)
 
     for i in range(args.warmup):
         ia.anneal(prob, T, betas, seed_of(-1 - i), out_spins=spins, out_cuts=cuts)
@@ -426,12 +426,8 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = float(np.mean(step_ms))
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * ups / (ms / 1e3)
+    ms = replicas.max_over_ranks(float(np.mean(step_ms)), dist, dev)
+    value = replicas.job_value(ws, ups, ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers: instance upload
     # (ising_create from the host CSR), host betas, device->host copy of all
@@ -466,7 +462,10 @@ def main():
                 "peak_source": f"{sms} SMs x {IMAD_LANES_PER_SM} IMAD lanes x "
                 f"{clk_mhz:.0f} MHz (sm_max_mhz of measured peaks file)"}
 
-    stats = ttt_stats(first_cuts.cpu().numpy(), ms / 1e3, T, S) if args.steps > 0 else None
+    stats = None
+    if args.steps > 0:   # over every rank's trials: the job ran ws * T trials in one step time
+        all_cuts = replicas.gather_cuts(first_cuts, dist)
+        stats = ttt_stats(all_cuts.cpu().numpy(), ms / 1e3, ws * T, S)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_throughput(w, inst)
