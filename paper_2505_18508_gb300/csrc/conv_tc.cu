@@ -143,7 +143,7 @@ __device__ __forceinline__ bool wait_mbar(uint32_t mbar, uint32_t phase) {
 // iteration to land.  256 threads: warp w drains TMEM lanes 32 (w mod 4) ..
 // and columns 16 (w / 4) .. of the accumulator.
 template <int kIn, int kOut>
-__global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(TcConvArgs a) {
+__global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) {
   constexpr int KC = kIn == 0 ? 2 : 4;          // 8-channel chunks of the input
   constexpr int N = kOut == 2 ? 16 : 32;         // output channels (padded)
   constexpr int NG = N / 8;
@@ -181,6 +181,10 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(TcConvArgs a) {
   const uint32_t tmem = *tslot;
   const uint32_t lane_off = static_cast<uint32_t>((warp & 3) * 32) << 16;
   const int half = warp >> 2;                    // which 16 of the 32 output channels
+  float bias_r[16];                              // this thread's output channels' biases
+#pragma unroll
+  for (int c = 0; c < 16; ++c) bias_r[c] = kOut == 0 ? __ldg(a.bias + half * 16 + c) : 0.f;
+  const float bias0 = kOut == 2 ? __ldg(a.bias) : 0.f;
 
   // stage unwrapped input row yu of image b into its ring slot
   auto stage = [&](int b, int yu) {
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(TcConvArgs a) {
       if (kOut == 2) {
         float v[1];
         tmem_ld<1>(col, v);
-        if (x < X) a.out_f32[p] = v[0] + a.bias[0];
+        if (x < X) a.out_f32[p] = v[0] + bias0;
         continue;
       }
       float v[16];
@@ -254,7 +258,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(TcConvArgs a) {
       __align__(16) __nv_bfloat16 o[16];
       if (kOut == 0) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16(fmaxf(v[c] + a.bias[half * 16 + c], 0.f));
+        for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16(fmaxf(v[c] + bias_r[c], 0.f));
       } else {
         const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * 32 + half * 16);
 #pragma unroll
@@ -329,6 +333,17 @@ __global__ void __launch_bounds__(kConvThreads) conv_tc_kernel(TcConvArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
+// CTAs of `threads` threads that the register file holds per SM (registers are
+// allocated per warp in units of 256)
+inline int regs_per_sm_limit(const void* fn, int threads) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess || fa.numRegs <= 0) return 1;
+  const int per_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+  const int warps = (threads + 31) / 32;
+  const int v = 65536 / (per_warp * warps);
+  return v > 0 ? v : 1;
+}
+
 template <int kIn, int kOut>
 size_t smem_bytes_for(int X) {
   constexpr int KC = kIn == 0 ? 2 : 4;
@@ -357,6 +372,7 @@ cudaError_t launch_one(const TcConvArgs& a, int sms, cudaStream_t st) {
   while (tc < cols) tc <<= 1;
   if (tc > 512) return cudaErrorInvalidConfiguration;
   per_sm = std::min(std::min(per_sm, 512 / tc), 8);
+  per_sm = std::min(per_sm, regs_per_sm_limit(reinterpret_cast<const void*>(conv_tc_kernel<kIn, kOut>), kConvThreads));
   const long long rows = static_cast<long long>(a.B) * a.Y;
   const long long grid = std::min<long long>(rows, static_cast<long long>(sms) * per_sm);
   conv_tc_kernel<kIn, kOut><<<static_cast<int>(grid), kConvThreads, sm, st>>>(a);
@@ -630,6 +646,7 @@ cudaError_t launch_wgrad_one(const TcWgradArgs& a, int sms, float* dW, float* db
   int per_sm = static_cast<int>(static_cast<size_t>(smem_sm) / (sm + static_cast<size_t>(reserved)));
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   per_sm = std::min(per_sm, kKind == 2 ? 16 : 4);   // tensor memory: 512 columns per SM
+  per_sm = std::min(per_sm, regs_per_sm_limit(reinterpret_cast<const void*>(wgrad_tc_kernel<kKind>), kTcThreads));
   const long long rows = static_cast<long long>(a.B) * a.Y;
   long long grid = std::min<long long>(rows, static_cast<long long>(sms) * per_sm);
   grid = std::min<long long>(grid, a.max_ctas);
