@@ -40,6 +40,11 @@ PEAK_HBM_GBS = float(json.load(open(PEAKS_FILE)).get("hbm_gbs", 6800.0)) if os.p
 IMAD_LANES_PER_SM = 64
 # Philox4x32-10 multiplies per spin update: 10 rounds x 2 products x 2 halves / 4 draws
 IMAD_OPS_PER_UPDATE = 10
+# DRAM bytes (read + write) of one launch of the persistent annealing kernel
+# on this workload, from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, --clock-control none) of the same launch
+# configuration: 680,192 + 124,416 bytes
+FLOW_TRAFFIC_BYTES = 680192 + 124416
 
 
 def updates_per_step(w):
@@ -457,7 +462,10 @@ def main():
     peak_tops = sms * IMAD_LANES_PER_SM * clk_mhz * 1e6 / 1e12
     achieved_tops = ups * IMAD_OPS_PER_UPDATE / (ms / 1e3) / 1e12 / 1.0
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (32-bit IMAD)",
-                "frac": achieved_tops / peak_tops, "traffic": None,
+                "frac": achieved_tops / peak_tops,
+                "traffic": FLOW_TRAFFIC_BYTES if prob.last_kernel() == 2 and (T, S, n) == (1024, 10000, 20000)
+                else None,
+                "traffic_note": "DRAM bytes per launch (ncu); the spins stay in L2, the path is integer-bound",
                 "kernel": {1: "anneal_strip_kernel", 2: "anneal_flow_kernel"}.get(prob.last_kernel(), "?"),
                 "peak_source": f"{sms} SMs x {IMAD_LANES_PER_SM} IMAD lanes x "
                 f"{clk_mhz:.0f} MHz (sm_max_mhz of measured peaks file)"}
