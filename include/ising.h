@@ -201,6 +201,39 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
 int ising_set_kernel(ising_problem* p, int32_t kind);
 
 /*
+ * ising_philox -- the library's Philox4x32-10 generator (Salmon et al.,
+ * SC'11), the source of every start spin and decision draw: for each of k
+ * counters ctr[j] (device uint32 [k][4], 16-byte aligned) writes the block
+ * out[j] (device uint32 [k][4], 16-byte aligned) under the key
+ * (seed mod 2^32, seed / 2^32).  Trial t at site i in sweep k draws word
+ * t mod 4 of the block at counter (i, k, t/4, 0); its start spin is bit 31 of
+ * word t mod 4 at counter (i, 0xFFFFFFFF, t/4, 0).  For reproducing
+ * individual draws.  Asynchronous on cuda_stream.  Errors: ISING_ERR_ARG.
+ */
+int ising_philox(const uint32_t* ctr, uint64_t seed, int32_t k, uint32_t* out, void* cuda_stream);
+
+/*
+ * ising_spins_to_hex / ising_hex_to_spins -- a configuration (host int8 [n],
+ * > 0 means +1) as hexadecimal digits, the form in which the paper prints its
+ * best cuts (App. C-E): digit d holds spins 4d .. 4d+3, the first of them in
+ * the most significant bit, bit 1 for +1 and 0 for -1, the last digit padded
+ * with 0 bits (the paper does not state the bit order; this reading is the
+ * library's).  to_hex writes ceil(n/4) digits and a terminating NUL into out
+ * (cap bytes, host).  from_hex skips whitespace and needs exactly ceil(n/4)
+ * digits with zero padding bits.  Errors: ISING_ERR_ARG.
+ */
+int ising_spins_to_hex(const int8_t* spins, int32_t n, char* out, int64_t cap);
+int ising_hex_to_spins(const char* hex, int32_t n, int8_t* out);
+
+/*
+ * ising_debug_fail_allocs -- a test hook: the next `count` device allocations
+ * the library makes report failure, so the calls that make them return
+ * ISING_ERR_OOM (host-side fault injection; nothing is done on the GPU).
+ * 0 clears it.  Errors: ISING_ERR_ARG (count < 0).
+ */
+int ising_debug_fail_allocs(int32_t count);
+
+/*
  * ising_graph_create -- a general sparse instance: any simple undirected
  * graph as a symmetric CSR (host pointers, copied; row_ptr int64 [n+1],
  * col_idx int32 [nnz], J int8 [nnz] with J_ij = J_ji, 1 <= |J| <= 127, no

@@ -23,7 +23,7 @@ from . import _abi
 from ._abi import IsingError, check, lib
 
 __all__ = ["Problem", "anneal", "anneal_trace", "cut", "energy", "greedy_colouring", "anneal_batched", "BatchPlan",
-           "IsingError", "lib"]
+           "IsingError", "lib", "spins_to_hex", "hex_to_spins", "philox"]
 
 
 def _torch():
@@ -220,6 +220,36 @@ def greedy_colouring(g):
                                        col.ctypes.data_as(ctypes.c_void_p), colour.ctypes.data_as(ctypes.c_void_p),
                                        ctypes.byref(k)), "ising_greedy_colouring")
     return colour, k.value
+
+
+def spins_to_hex(spins):
+    """A configuration (int8 [n], host) as hex digits (the paper's App. C-E form;
+    the first spin of each digit in its most significant bit, +1 -> 1)."""
+    s = np.ascontiguousarray(spins, dtype=np.int8).reshape(-1)
+    buf = ctypes.create_string_buffer((s.shape[0] + 3) // 4 + 1)
+    check(lib().ising_spins_to_hex(s.ctypes.data_as(ctypes.c_void_p), int(s.shape[0]), buf, len(buf)),
+          "ising_spins_to_hex")
+    return buf.value.decode()
+
+
+def hex_to_spins(hexstr, n):
+    """The inverse of spins_to_hex: int8 [n] in {-1, +1}."""
+    out = np.zeros(int(n), dtype=np.int8)
+    check(lib().ising_hex_to_spins(hexstr.encode(), int(n), out.ctypes.data_as(ctypes.c_void_p)),
+          "ising_hex_to_spins")
+    return out
+
+
+def philox(counters, seed, stream=None):
+    """The library's Philox4x32-10 blocks for uint32 counters [k, 4] (CUDA tensor or array)."""
+    torch = _torch()
+    c = counters if isinstance(counters, torch.Tensor) else torch.as_tensor(
+        np.ascontiguousarray(counters, dtype=np.uint32).view(np.int32))
+    c = c.to(device="cuda", dtype=torch.int32).contiguous()
+    out = torch.empty_like(c)
+    check(lib().ising_philox(_dptr(c), int(seed) & 0xFFFFFFFFFFFFFFFF, int(c.shape[0]), _dptr(out),
+                             _stream_ptr(stream)), "ising_philox")
+    return out
 
 
 def energy(prob, spins, out=None, stream=None):

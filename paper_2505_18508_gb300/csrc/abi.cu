@@ -4,6 +4,7 @@
 // Everything here is host code; the kernels live in anneal.cu, cut.cu and
 // batched.cu.  No C++ exception leaves an extern "C" function.
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -17,6 +18,15 @@
 namespace {
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// ISING_LOG >= 1: one line per anneal on stderr with the kernel and shape used
+void log_launch(const ising_problem* p, int32_t trials, int32_t S) {
+  if (ising::log_level() < 1) return;
+  static const char* names[4] = {"?", "strip", "persistent", "graph"};
+  std::fprintf(stderr, "ising: anneal n=%d trials=%d sweeps=%d kernel=%s group=%d strips=%d threads=%d grid=%d bits=%d\n",
+               p->n, trials, S, names[p->last_kernel & 3], p->last_group, p->last_strips, p->last_threads,
+               p->last_grid, p->draw_bits);
+}
 
 int map_cuda(cudaError_t e) {
   if (e == cudaSuccess) return ISING_OK;
@@ -329,7 +339,7 @@ int run_flow(ising_problem* p, const FlowPlan& fp, int32_t trials, const std::ve
   const size_t o_abort = o_done + 256;
   const size_t bytes = o_abort + 256;
   unsigned char* d = nullptr;
-  e = cudaMallocAsync(reinterpret_cast<void**>(&d), bytes, st);
+  e = ising::dev_malloc_async(reinterpret_cast<void**>(&d), bytes, st);
   if (e != cudaSuccess) return map_cuda(e);
   if (!thr.empty()) e = cudaMemcpyAsync(d + o_thr, thr.data(), thr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -375,6 +385,7 @@ int run_flow(ising_problem* p, const FlowPlan& fp, int32_t trials, const std::ve
   p->last_strips = 0;
   p->last_threads = ising::flow_threads();
   p->last_grid = fp.P;
+  log_launch(p, trials, S);
   return ISING_OK;
 }
 
@@ -448,7 +459,7 @@ int run_graph(ising_problem* p, int32_t trials, const double* betas, int32_t S, 
   uint32_t* d_thr = nullptr;
   const size_t bytes = thr.size() * sizeof(uint32_t);
   if (bytes) {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_thr), bytes, st);
+    cudaError_t e = ising::dev_malloc_async(reinterpret_cast<void**>(&d_thr), bytes, st);
     if (e != cudaSuccess) return map_cuda(e);
     e = cudaMemcpyAsync(d_thr, thr.data(), bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { cudaFreeAsync(d_thr, st); return map_cuda(e); }
@@ -475,6 +486,7 @@ int run_graph(ising_problem* p, int32_t trials, const double* betas, int32_t S, 
   p->last_strips = C;
   p->last_threads = ising::graph_threads();
   p->last_grid = C * groups;
+  log_launch(p, trials, S);
   return ISING_OK;
 }
 }  // namespace
@@ -563,9 +575,9 @@ int ising_create(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, cons
   p->neg_edges = neg;
   p->weight_sum = 2 * n - 2 * neg;
   if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return ISING_ERR_CUDA; }
-  cudaError_t e = cudaMalloc(&p->d_flags, n);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_eflags, n);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_status), sizeof(int32_t));
+  cudaError_t e = ising::dev_malloc(&p->d_flags, n);
+  if (e == cudaSuccess) e = ising::dev_malloc(&p->d_eflags, n);
+  if (e == cudaSuccess) e = ising::dev_malloc(reinterpret_cast<void**>(&p->d_status), sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemcpy(p->d_flags, flags.data(), n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_eflags, eflags.data(), n, cudaMemcpyHostToDevice);
@@ -701,7 +713,7 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
   uint32_t* d_thr = nullptr;
   const size_t thr_bytes = thr.size() * sizeof(uint32_t);
   if (thr_bytes) {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_thr), thr_bytes, st);
+    cudaError_t e = ising::dev_malloc_async(reinterpret_cast<void**>(&d_thr), thr_bytes, st);
     if (e != cudaSuccess) return map_cuda(e);
     e = cudaMemcpyAsync(d_thr, thr.data(), thr_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { cudaFreeAsync(d_thr, st); return map_cuda(e); }
@@ -738,6 +750,7 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
   p->last_strips = sh.C;
   p->last_threads = sh.threads;
   p->last_grid = sh.C * ((trials + sh.G - 1) / sh.G);
+  log_launch(p, trials, S);
   return ISING_OK;
 }
 
@@ -764,7 +777,7 @@ int ising_anneal_batched(ising_problem* const* probs, int32_t m, const int32_t* 
   unsigned char* d_arena = nullptr;
   cudaError_t e = ising::batched_prepare(hb.smem);
   if (e != cudaSuccess) return map_cuda(e);
-  e = cudaMallocAsync(reinterpret_cast<void**>(&d_arena), hb.bytes, st);
+  e = ising::dev_malloc_async(reinterpret_cast<void**>(&d_arena), hb.bytes, st);
   if (e != cudaSuccess) return map_cuda(e);
   std::vector<unsigned char> img;
   try {
@@ -815,7 +828,7 @@ int ising_batch_create(ising_problem* const* probs, int32_t m, const int32_t* tr
   ising_batch* b = new (std::nothrow) ising_batch();
   if (!b) return ISING_ERR_OOM;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_arena), hb.bytes);
+  cudaError_t e = ising::dev_malloc(reinterpret_cast<void**>(&b->d_arena), hb.bytes);
   std::vector<unsigned char> img;
   if (e == cudaSuccess) {
     try {
@@ -945,12 +958,12 @@ int ising_graph_create(int32_t n, const int64_t* row_ptr, const int32_t* col_idx
     delete p;
     return ISING_ERR_UNSUPPORTED;
   }
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->d_status), sizeof(int32_t));
+  cudaError_t e = ising::dev_malloc(reinterpret_cast<void**>(&p->d_status), sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int32_t));
-  if (e == cudaSuccess && nnz) e = cudaMalloc(reinterpret_cast<void**>(&p->d_nb), sizeof(uint32_t) * nnz);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_rowinfo), sizeof(int4) * n);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_sites), sizeof(int32_t) * n);
-  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&p->d_colour_off), sizeof(int32_t) * (ncol + 1));
+  if (e == cudaSuccess && nnz) e = ising::dev_malloc(reinterpret_cast<void**>(&p->d_nb), sizeof(uint32_t) * nnz);
+  if (e == cudaSuccess) e = ising::dev_malloc(reinterpret_cast<void**>(&p->d_rowinfo), sizeof(int4) * n);
+  if (e == cudaSuccess) e = ising::dev_malloc(reinterpret_cast<void**>(&p->d_sites), sizeof(int32_t) * n);
+  if (e == cudaSuccess) e = ising::dev_malloc(reinterpret_cast<void**>(&p->d_colour_off), sizeof(int32_t) * (ncol + 1));
   if (e == cudaSuccess && nnz)
     e = cudaMemcpy(p->d_nb, nb.data(), sizeof(uint32_t) * nnz, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_rowinfo, rowinfo.data(), sizeof(int4) * n, cudaMemcpyHostToDevice);
@@ -982,7 +995,7 @@ int ising_energy(const ising_problem* p, const int8_t* spins, int32_t k, int64_t
   // torus (h = 0): H = W - 2 cut
   if (k == 0) return ISING_OK;
   int32_t* tmp = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), sizeof(int32_t) * k, st);
+  cudaError_t e = ising::dev_malloc_async(reinterpret_cast<void**>(&tmp), sizeof(int32_t) * k, st);
   if (e != cudaSuccess) return map_cuda(e);
   e = ising::launch_cut(p, spins, k, tmp, st);
   if (e == cudaSuccess) e = ising::launch_energy_from_cut(tmp, p->weight_sum, k, out_energies, st);

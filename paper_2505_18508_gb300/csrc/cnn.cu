@@ -298,16 +298,16 @@ int ising_cnn_create(const float* params, ising_cnn** out) {
   if (!params || !out) return ISING_ERR_ARG;
   ising_cnn* net = new (std::nothrow) ising_cnn();
   if (!net) return ISING_ERR_OOM;
-  cudaError_t e = cudaMalloc(&net->master, NPARAM * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&net->adam_m, NPARAM * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&net->adam_v, NPARAM * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&net->w4r, 288 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&net->tc1, 9 * 16 * 32 * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) e = cudaMalloc(&net->tc2f, 9 * 32 * 32 * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) e = cudaMalloc(&net->tc3f, 9 * 32 * 32 * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) e = cudaMalloc(&net->tc2b, 9 * 32 * 32 * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) e = cudaMalloc(&net->tc3b, 9 * 32 * 32 * sizeof(__nv_bfloat16));
-  if (e == cudaSuccess) e = cudaMalloc(&net->tc4, 9 * 32 * 16 * sizeof(__nv_bfloat16));
+  cudaError_t e = ising::dev_malloc(&net->master, NPARAM * sizeof(float));
+  if (e == cudaSuccess) e = ising::dev_malloc(&net->adam_m, NPARAM * sizeof(float));
+  if (e == cudaSuccess) e = ising::dev_malloc(&net->adam_v, NPARAM * sizeof(float));
+  if (e == cudaSuccess) e = ising::dev_malloc(&net->w4r, 288 * sizeof(float));
+  if (e == cudaSuccess) e = ising::dev_malloc(&net->tc1, 9 * 16 * 32 * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = ising::dev_malloc(&net->tc2f, 9 * 32 * 32 * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = ising::dev_malloc(&net->tc3f, 9 * 32 * 32 * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = ising::dev_malloc(&net->tc2b, 9 * 32 * 32 * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = ising::dev_malloc(&net->tc3b, 9 * 32 * 32 * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = ising::dev_malloc(&net->tc4, 9 * 32 * 16 * sizeof(__nv_bfloat16));
   if (e == cudaSuccess) e = cudaMemcpy(net->master, params, NPARAM * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(net->adam_m, 0, NPARAM * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(net->adam_v, 0, NPARAM * sizeof(float));

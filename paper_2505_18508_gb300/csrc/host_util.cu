@@ -1,0 +1,123 @@
+// host_util.cu -- host-side services of the library: device allocation with
+// a test hook that makes allocations fail (fault injection on the host, never
+// on the GPU), the log level, hex import/export of configurations, and the
+// decision-stream generator as an entry point.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/ising.h"
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace {
+
+std::mutex g_alloc_mutex;
+int g_alloc_failures = 0;   // the next this many allocations fail
+
+bool take_failure() {
+  std::lock_guard<std::mutex> lock(g_alloc_mutex);
+  if (g_alloc_failures > 0) {
+    --g_alloc_failures;
+    return true;
+  }
+  return false;
+}
+
+__global__ void philox_kernel(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1, int32_t k,
+                              uint4* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < k) {
+    const uint4 c = ctr[t];
+    out[t] = ising::philox4x32_10(c.x, c.y, c.z, c.w, k0, k1);
+  }
+}
+
+int hex_value(char c) {
+  if (c >= '0' && c <= '9') return c - '0';
+  if (c >= 'a' && c <= 'f') return c - 'a' + 10;
+  if (c >= 'A' && c <= 'F') return c - 'A' + 10;
+  return -1;
+}
+
+}  // namespace
+
+namespace ising {
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (take_failure()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  if (take_failure()) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(p, bytes, st);
+}
+
+int log_level() {
+  static const int level = [] {
+    const char* v = std::getenv("ISING_LOG");
+    return v ? std::atoi(v) : 0;
+  }();
+  return level;
+}
+
+}  // namespace ising
+
+extern "C" {
+
+int ising_debug_fail_allocs(int32_t count) {
+  if (count < 0) return ISING_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_alloc_mutex);
+  g_alloc_failures = count;
+  return ISING_OK;
+}
+
+int ising_philox(const uint32_t* ctr, uint64_t seed, int32_t k, uint32_t* out, void* cuda_stream) {
+  if (k < 0 || (k > 0 && (!ctr || !out))) return ISING_ERR_ARG;
+  if (k == 0) return ISING_OK;
+  if (reinterpret_cast<uintptr_t>(ctr) % 16 || reinterpret_cast<uintptr_t>(out) % 16) return ISING_ERR_ARG;
+  philox_kernel<<<(k + 255) / 256, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+      reinterpret_cast<const uint4*>(ctr), static_cast<uint32_t>(seed & 0xFFFFFFFFull),
+      static_cast<uint32_t>(seed >> 32), k, reinterpret_cast<uint4*>(out));
+  return cudaGetLastError() == cudaSuccess ? ISING_OK : ISING_ERR_CUDA;
+}
+
+int ising_spins_to_hex(const int8_t* spins, int32_t n, char* out, int64_t cap) {
+  if (n < 0 || (n > 0 && !spins) || !out) return ISING_ERR_ARG;
+  const int64_t digits = (static_cast<int64_t>(n) + 3) / 4;
+  if (cap < digits + 1) return ISING_ERR_ARG;
+  static const char kHex[] = "0123456789ABCDEF";
+  for (int64_t d = 0; d < digits; ++d) {
+    int v = 0;
+    for (int b = 0; b < 4; ++b) {
+      const int64_t i = 4 * d + b;
+      v = (v << 1) | (i < n && spins[i] > 0 ? 1 : 0);
+    }
+    out[d] = kHex[v];
+  }
+  out[digits] = '\0';
+  return ISING_OK;
+}
+
+int ising_hex_to_spins(const char* hex, int32_t n, int8_t* out) {
+  if (!hex || n < 0 || (n > 0 && !out)) return ISING_ERR_ARG;
+  const int64_t digits = (static_cast<int64_t>(n) + 3) / 4;
+  int64_t d = 0;
+  for (const char* c = hex; *c; ++c) {
+    if (*c == ' ' || *c == '\n' || *c == '\r' || *c == '\t') continue;
+    const int v = hex_value(*c);
+    if (v < 0 || d >= digits) return ISING_ERR_ARG;
+    for (int b = 0; b < 4; ++b) {
+      const int64_t i = 4 * d + b;
+      const int bit = (v >> (3 - b)) & 1;
+      if (i < n) out[i] = bit ? 1 : -1;
+      else if (bit) return ISING_ERR_ARG;   // padding bits must be 0
+    }
+    ++d;
+  }
+  return d == digits ? ISING_OK : ISING_ERR_ARG;
+}
+
+}  // extern "C"

@@ -38,6 +38,20 @@ struct ising_problem {
 
 namespace ising {
 
+// host_util.cu: device allocations through a test hook (ising_debug_fail_allocs)
+// and the ISING_LOG level
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st);
+template <typename T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+template <typename T>
+inline cudaError_t dev_malloc_async(T** p, size_t bytes, cudaStream_t st) {
+  return dev_malloc_async(reinterpret_cast<void**>(p), bytes, st);
+}
+int log_level();
+
 // Everything the strip kernel reads; passed by value as the kernel parameter.
 struct AnnealArgs {
   const uint8_t* flags;     // plane-order site flags [n]

@@ -65,7 +65,7 @@ extern "C" int ising_anneal_trace(ising_problem* p, int32_t trials, const double
       (out_trace && points > 0) ? 0 : ((static_cast<size_t>(trials) * 4 + 255) & ~size_t(255));
   const size_t sbytes = (points > 1 ? ((spin_bytes + 255) & ~size_t(255)) : 0) + cut_bytes;
   if (sbytes) {
-    const cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), sbytes, st);
+    const cudaError_t e = ising::dev_malloc_async(reinterpret_cast<void**>(&scratch), sbytes, st);
     if (e != cudaSuccess) return map_err(e);
   }
   int8_t* other = points > 1 ? reinterpret_cast<int8_t*>(scratch) : nullptr;
