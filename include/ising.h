@@ -398,7 +398,11 @@ size_t ising_cnn_workspace_bytes(int32_t B, int32_t n, int32_t train);
  * spins    device [B][n] int8 (>0 is +1).
  * logits   device [B][n] float (site order y*X + x).
  * ws       device workspace of at least ising_cnn_workspace_bytes(B, n, 0).
- * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (X > 2,000), ISING_ERR_CUDA.
+ * The convolutions run on the tensor cores; a device-side wait on them that
+ * runs out (after about two seconds) leaves ISING_ERR_TIMEOUT in the
+ * handle's status word (ising_get_status).
+ * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (torus width above 640, or a
+ * general-graph handle), ISING_ERR_CUDA.
  */
 int ising_cnn_forward(const ising_cnn* net, const ising_problem* p, const int8_t* spins, int32_t B,
                       float* logits, void* ws, size_t ws_bytes, void* cuda_stream);
@@ -410,6 +414,9 @@ int ising_cnn_forward(const ising_cnn* net, const ising_problem* p, const int8_t
  * grad     device ISING_CNN_PARAMS floats (overwritten).
  * loss     device float (overwritten).
  * ws       device workspace of at least ising_cnn_workspace_bytes(B, n, 1).
+ * Device-side timeouts as in ising_cnn_forward.  Errors: ISING_ERR_ARG,
+ * ISING_ERR_UNSUPPORTED (torus width above 592, or a general-graph handle),
+ * ISING_ERR_CUDA.
  */
 int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* spins, const uint8_t* targets,
                    int32_t B, float* grad, float* loss, void* ws, size_t ws_bytes, void* cuda_stream);
@@ -429,6 +436,8 @@ int ising_cnn_adam_step(ising_cnn* net, const float* grad, float lr, float beta1
  * tile = 0: B = all sites with logit > 0 (whole-lattice proposal).
  * spins    device [B][n] int8, updated in place.
  * accepted device [B] int32 or NULL: proposals taken per configuration.
+ * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (a general-graph handle),
+ * ISING_ERR_CUDA.
  */
 int ising_propose(const ising_problem* p, int8_t* spins, int32_t B, const float* logits, int32_t tile,
                   int32_t* accepted, void* cuda_stream);

@@ -65,7 +65,7 @@ int default_group(const ising_problem* p, int32_t T) {
 
 int num_sms_of(int device) {
   int v = 0;
-  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 148;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 152;
   return v;
 }
 

@@ -196,7 +196,7 @@ int sm_count() {
   int dev = 0, v = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       v <= 0)
-    v = 148;
+    v = 152;
   return v;
 }
 
@@ -360,6 +360,7 @@ size_t ising_cnn_workspace_bytes(int32_t B, int32_t n, int32_t train) {
 int ising_cnn_forward(const ising_cnn* net, const ising_problem* p, const int8_t* spins, int32_t B, float* logits,
                       void* ws, size_t ws_bytes, void* cuda_stream) {
   if (!net || !p || B < 0 || (B > 0 && (!spins || !logits || !ws))) return ISING_ERR_ARG;
+  if (p->graph) return ISING_ERR_UNSUPPORTED;   // the network reads the torus layout
   if (B == 0) return ISING_OK;
   if (ws_bytes < ws_layout(B, p->n, 0, nullptr, nullptr)) return ISING_ERR_ARG;
   if (!tc_supported(p)) return ISING_ERR_UNSUPPORTED;
@@ -371,6 +372,7 @@ int ising_cnn_forward(const ising_cnn* net, const ising_problem* p, const int8_t
 int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* spins, const uint8_t* targets,
                    int32_t B, float* grad, float* loss, void* ws, size_t ws_bytes, void* cuda_stream) {
   if (!net || !p || B <= 0 || !spins || !targets || !grad || !loss || !ws) return ISING_ERR_ARG;
+  if (p->graph) return ISING_ERR_UNSUPPORTED;
   if (ws_bytes < ws_layout(B, p->n, 1, nullptr, nullptr)) return ISING_ERR_ARG;
   if (!tc_supported(p) || wgrad_tc_smem(1, p->X) > 227 * 1024) return ISING_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

@@ -91,7 +91,7 @@ extern "C" int ising_anneal_noalloc(ising_problem* p, int32_t trials, const doub
   // launch shape: the handle's fixed shape, else one trial group of 32 per
   // cluster of strips as wide as fits one CTA per SM (same rule as ising_anneal)
   int sms = 0, smem_max = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) sms = 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) sms = 152;
   if (cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
       smem_max <= 0)
     smem_max = 227 * 1024;

@@ -152,6 +152,7 @@ extern "C" int ising_flip_targets(const int8_t* spins, const int8_t* ref, int32_
 extern "C" int ising_propose(const ising_problem* p, int8_t* spins, int32_t B, const float* logits, int32_t tile,
                              int32_t* accepted, void* cuda_stream) {
   if (!p || B < 0 || tile < 0 || (B > 0 && (!spins || !logits))) return ISING_ERR_ARG;
+  if (p->graph) return ISING_ERR_UNSUPPORTED;   // tiles and boundaries of the torus
   if (B == 0) return ISING_OK;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   if (tile == 0) {

@@ -122,4 +122,15 @@ def test_graph_errors(ia):
     prob.set_draw_bits(32)
     with pytest.raises(ia.IsingError):
         ia.anneal_batched([prob], [8], [3], [np.ones(3)], [1])
+    # the learned stage needs the torus layout
+    import torch
+    from oracle import cnn as ocnn
+    net = ia.CNN(ocnn.init_params(1))
+    s = torch.ones((2, g["n"]), dtype=torch.int8, device="cuda")
+    with pytest.raises(ia.IsingError) as ei:
+        net.forward(prob, s)
+    assert ei.value.code == -7          # ISING_ERR_UNSUPPORTED
+    with pytest.raises(ia.IsingError):
+        ia.propose(prob, s, torch.zeros((2, g["n"]), device="cuda"), 0)
+    net.destroy()
     prob.destroy()
