@@ -129,7 +129,7 @@ def test_graph_errors(ia):
     s = torch.ones((2, g["n"]), dtype=torch.int8, device="cuda")
     with pytest.raises(ia.IsingError) as ei:
         net.forward(prob, s)
-    assert ei.value.code == -7          # ISING_ERR_UNSUPPORTED
+    assert ei.value.code == -8          # ISING_ERR_UNSUPPORTED
     with pytest.raises(ia.IsingError):
         ia.propose(prob, s, torch.zeros((2, g["n"]), device="cuda"), 0)
     net.destroy()
