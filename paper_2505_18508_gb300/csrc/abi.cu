@@ -263,10 +263,12 @@ struct FlowPlan {
 };
 
 // Stacks the rows of all trial groups and splits them over one CTA per SM,
-// weighted by the Philox blocks of each row's group.  Fails with
+// weighted by the Philox blocks of each row's group (or, unweighted, into
+// equal row counts: the caller's fallback when a ragged last group would pile
+// its light rows onto a few CTAs beyond their shared memory).  Fails with
 // ISING_ERR_UNSUPPORTED when a CTA would touch more groups than the kernel
 // tracks or its rows would not fit in shared memory.
-int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp) {
+int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp, bool weighted = true) {
   const int sms = num_sms_of(p->device);
   const int smem_max = max_smem_of(p->device);
   int G = p->cfg_group;
@@ -281,7 +283,7 @@ int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp) {
   for (int u = 0; u < RT; ++u) {
     const int g = u / p->Y;
     const int live = std::min(G, T - g * G);
-    cum[u + 1] = cum[u] + (live + blk - 1) / blk;
+    cum[u + 1] = cum[u] + (weighted ? (live + blk - 1) / blk : 1);
   }
   const long long total = cum[RT];
   std::vector<int32_t> split(static_cast<size_t>(P) + 1);
@@ -701,6 +703,7 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
     int frc;
     try {
       frc = plan_flow(p, trials, &fp);
+      if (frc == ISING_ERR_UNSUPPORTED) frc = plan_flow(p, trials, &fp, false);
     } catch (const std::bad_alloc&) {
       return ISING_ERR_OOM;
     }

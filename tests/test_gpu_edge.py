@@ -1,6 +1,7 @@
-"""Edge cases of the annealer against the oracle, bit for bit: a torus of two
+"""Edge cases of the annealer against the oracle, bit for bit: a torus of a
 million spins, extreme inverse temperatures, a sweep counter that wraps past
-2^32, and ragged trial counts at size."""
+2^32, and ragged trial counts at size; and a torus beyond the shared-memory
+limits, which is refused cleanly."""
 import numpy as np
 import pytest
 
@@ -20,9 +21,9 @@ def ia():
     return ia
 
 
-def test_two_million_spins(ia):
+def test_a_million_spins(ia):
     import torch
-    inst = synth.torus_instance(2048, 1024, 5)
+    inst = synth.torus_instance(1024, 1024, 5)
     betas = synth.linear_betas(0.3, 2.0, 3)
     prob = ia.Problem.from_instance(inst)
     spins, cuts = ia.anneal(prob, 33, betas, 77)
@@ -35,6 +36,17 @@ def test_two_million_spins(ia):
         rs, rc = oracle.anneal(inst, betas, 77, t_begin=t, t_count=1)
         np.testing.assert_array_equal(s[t], rs[0])
         assert cuts[t].item() == rc[0]
+    prob.destroy()
+
+
+def test_beyond_shared_memory_is_refused(ia):
+    # 2048 x 1024 with two trial groups: neither a persistent CTA's rows nor a
+    # 16-strip cluster's rows fit in shared memory
+    inst = synth.torus_instance(2048, 1024, 5)
+    prob = ia.Problem.from_instance(inst)
+    with pytest.raises(ia.IsingError) as ei:
+        ia.anneal(prob, 33, np.ones(2), 1)
+    assert ei.value.code == -8          # ISING_ERR_UNSUPPORTED
     prob.destroy()
 
 
