@@ -234,6 +234,29 @@ int ising_hex_to_spins(const char* hex, int32_t n, int8_t* out);
 int ising_debug_fail_allocs(int32_t count);
 
 /*
+ * ising_anneal_pt -- replica exchange (parallel tempering) on a torus handle:
+ * `temps` temperatures betas[0..temps-1] (host, positive, finite) times
+ * `chains` chains (a multiple of 32).  Slot t = r * chains + c holds chain c
+ * at temperature r.  Each of `rounds` rounds runs sweeps_per_round sweeps of
+ * every slot at its constant beta (global sweeps q L .. q L + L - 1; slot t
+ * keeps the decision stream of trial index t), then exchanges the pairs
+ * (r, r+1), r = q mod 2, q mod 2 + 2, ..., chain by chain: with
+ * d = E_r - E_{r+1} (Eq. 2, E = W - 2 cut) the swap is taken iff d <= 0 or
+ * u < min(floor(exp(-(beta_{r+1} - beta_r) d) 2^32), 2^32 - 1), u = word 0 of
+ * Philox4x32-10 at counter (c, q, r, 0xFFFFFFFD).  Start: the start spins of
+ * every slot.  out_spins (device int8 [temps*chains][n]) and out_cuts
+ * (device int32 [temps*chains]) receive the final slots; out_swaps (device
+ * int32 or NULL) the number of swaps taken.  Asynchronous on cuda_stream;
+ * allocates its tables and one spin-sized buffer in stream order.
+ * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (general-graph handle, 16-bit
+ * mode, no launch shape), ISING_ERR_OOM, ISING_ERR_CUDA.  The paper has no
+ * counterpart (its update rule is unpublished, Section III).
+ */
+int ising_anneal_pt(ising_problem* p, int32_t temps, const double* betas, int32_t chains, int32_t rounds,
+                    int32_t sweeps_per_round, uint64_t seed, int8_t* out_spins, int32_t* out_cuts, int32_t* out_swaps,
+                    void* cuda_stream);
+
+/*
  * ising_graph_create -- a general sparse instance: any simple undirected
  * graph as a symmetric CSR (host pointers, copied; row_ptr int64 [n+1],
  * col_idx int32 [nnz], J int8 [nnz] with J_ij = J_ji, 1 <= |J| <= 127, no

@@ -23,7 +23,7 @@ from . import _abi
 from ._abi import IsingError, check, lib
 
 __all__ = ["Problem", "anneal", "anneal_trace", "cut", "energy", "greedy_colouring", "anneal_batched", "BatchPlan",
-           "IsingError", "lib", "spins_to_hex", "hex_to_spins", "philox"]
+           "IsingError", "lib", "spins_to_hex", "hex_to_spins", "philox", "anneal_pt"]
 
 
 def _torch():
@@ -220,6 +220,22 @@ def greedy_colouring(g):
                                        col.ctypes.data_as(ctypes.c_void_p), colour.ctypes.data_as(ctypes.c_void_p),
                                        ctypes.byref(k)), "ising_greedy_colouring")
     return colour, k.value
+
+
+def anneal_pt(prob, betas, chains, rounds, sweeps_per_round, seed, stream=None):
+    """Replica exchange: returns (spins [R*C, n], cuts [R*C], swaps [1]) CUDA
+    tensors; slot r * chains + c is chain c at temperature betas[r]."""
+    torch = _torch()
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    R, T = int(b.shape[0]), int(b.shape[0]) * int(chains)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spins = torch.empty((T, prob.n), dtype=torch.int8, device=dev)
+    cuts = torch.empty((T,), dtype=torch.int32, device=dev)
+    swaps = torch.zeros((1,), dtype=torch.int32, device=dev)
+    check(lib().ising_anneal_pt(prob.handle, R, b.ctypes.data_as(ctypes.c_void_p), int(chains), int(rounds),
+                                int(sweeps_per_round), int(seed) & 0xFFFFFFFFFFFFFFFF, _dptr(spins), _dptr(cuts),
+                                _dptr(swaps), _stream_ptr(stream)), "ising_anneal_pt")
+    return spins, cuts, swaps
 
 
 def spins_to_hex(spins):

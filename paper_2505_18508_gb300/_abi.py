@@ -55,6 +55,7 @@ _SIGNATURES = {
     "ising_spins_to_hex": (ctypes.c_int, [_vp, _i32, _vp, ctypes.c_int64]),
     "ising_hex_to_spins": (ctypes.c_int, [ctypes.c_char_p, _i32, _vp]),
     "ising_debug_fail_allocs": (ctypes.c_int, [_i32]),
+    "ising_anneal_pt": (ctypes.c_int, [_vp, _i32, _vp, _i32, _i32, _i32, _u64, _vp, _vp, _vp, _vp]),
     "ising_last_kernel": (ctypes.c_int, [_vp, _i32p]),
     "ising_get_status": (ctypes.c_int, [_vp, _vp, _i32p]),
     "ising_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64, _i32]),

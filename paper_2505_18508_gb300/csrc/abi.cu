@@ -721,7 +721,7 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
     e = cudaMemcpyAsync(d_thr, thr.data(), thr_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { cudaFreeAsync(d_thr, st); return map_cuda(e); }
   }
-  ising::AnnealArgs a;
+  ising::AnnealArgs a{};
   a.flags = p->d_flags;
   a.thr = d_thr;
   a.init = init_spins;

@@ -11,7 +11,7 @@ __global__ void __launch_bounds__(1024, 1) anneal_strip_kernel(const __grid_cons
   extern __shared__ __align__(16) unsigned char smem[];
   GroupJob job;
   job.flags = a.flags;
-  job.thr = a.thr;
+  job.thr = a.thr + static_cast<size_t>(blockIdx.y) * a.thr_group_stride;
   job.init = a.init;
   job.out_spins = a.out_spins;
   job.out_cuts = a.out_cuts;

@@ -70,6 +70,7 @@ struct AnnealArgs {
   int32_t Rmax;             // ceil(Y / C)
   int32_t neg_edges;
   int32_t u16;              // 1: 16-bit draw mode (G a multiple of 8, thresholds stored << 16)
+  int32_t thr_group_stride; // words between the threshold tables of consecutive trial groups (0: one table)
 };
 
 // Everything the persistent flow kernel reads (anneal_flow.cu).

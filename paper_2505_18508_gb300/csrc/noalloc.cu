@@ -146,7 +146,7 @@ extern "C" int ising_anneal_noalloc(ising_problem* p, int32_t trials, const doub
     if (e != cudaSuccess) return map_err(e);
   }
 
-  ising::AnnealArgs a;
+  ising::AnnealArgs a{};
   a.flags = p->d_flags;
   a.thr = table;
   a.init = init_spins;
