@@ -291,6 +291,34 @@ def graph_leg(trials=1024, sweeps=2000, reps=3):
     return out
 
 
+def pt_leg(temps=8, chains=128, rounds=200, sweeps_per_round=50):
+    """Replica exchange on the headline instance at the headline's update
+    budget (temps x chains = 1,024 slots, rounds x sweeps = 10,000 sweeps):
+    throughput, and the coldest temperature's cuts against the plain
+    annealer's final cuts."""
+    import torch
+    import paper_2505_18508_gb300 as ia
+    inst = synth.torus_instance(200, 100, 2)
+    prob = ia.Problem.from_instance(inst)
+    betas = np.geomspace(0.5, 3.0, temps)
+    ia.anneal_pt(prob, betas, chains, 2, sweeps_per_round, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, cuts, swaps = ia.anneal_pt(prob, betas, chains, rounds, sweeps_per_round, 1002)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cold = cuts[(temps - 1) * chains:].cpu().numpy()
+    ups = temps * chains * rounds * sweeps_per_round * inst["n"]
+    out = {"workload": f"200x100 torus, {temps} temperatures (geometric 0.5..3.0) x {chains} chains, "
+                       f"{rounds} rounds x {sweeps_per_round} sweeps", "ms": ms, "value": ups / (ms / 1e3),
+           "unit": "spin-updates/s", "swaps": int(swaps.item()),
+           "coldest": {"best_cut": int(cold.max()), "mean_cut": float(cold.mean())}}
+    prob.destroy()
+    return out
+
+
 def batched_leg(reps=2):
     """Config 3: the 96-instance uneven batch ({50,100,140,200}x100, 32-512
     trials, 2,000-20,000 sweeps) as one graph-replayed persistent launch."""
@@ -502,8 +530,12 @@ def main():
     if rank == 0 and not args.sweeps and not args.trials:
         batched = batched_leg()
     graphs = None
+    pt = None
     if rank == 0 and not args.sweeps and not args.trials:
         graphs = graph_leg()
+        pt = pt_leg()
+        if stats is not None:
+            pt["plain_same_budget"] = {"best_cut": stats["best_cut"], "mean_cut": stats["cut_mean"]}
     campaign = None
     if rank == 0 and not args.sweeps and not args.trials:
         from paper_2505_18508_gb300.campaign import run_campaign
@@ -532,6 +564,7 @@ def main():
             "draw16_variant": draw16,
             "campaign": campaign,
             "general_graphs": graphs,
+            "replica_exchange": pt,
             "batched": batched,
             "learned_vs_plain": learned_cmp,
             "wall_s_timed": wall,
