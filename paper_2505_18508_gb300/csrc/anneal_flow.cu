@@ -279,24 +279,39 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
     const int lr = te & 0xFFFF, h = te >> 16;
     bool lane_ok = true;
     int4 ra = make_int4(0, -1, -1, 0), rb = make_int4(0, 0, 0, 0);
+    const uint32_t* rc = sm.rowcnt + (1 - c) * nloc;
+    int up = 0, dn = 0, xup = -1, xdn = -1;
+    bool ready = true;
     if (active) {
       ra = sm.rowA[lr];
       rb = sm.rowB[lr];
-      const uint32_t* rc = sm.rowcnt + (1 - c) * nloc;
-      const int up = ra.x & 0xFFFF, dn = ra.x >> 16;
-      const int xup = ra.y, xdn = ra.z;
-      // fast check of the three neighbour rows, bounded waits only when needed
+      up = ra.x & 0xFFFF;
+      dn = ra.x >> 16;
+      xup = ra.y;
+      xdn = ra.z;
+      // fast check of the three neighbour rows
       const uint32_t c_self = ld_volatile_shared(rc + lr);
       const uint32_t c_up = xup >= 0 ? (need == 0 ? 0u : ld_acquire_gpu(a.gcnt + 2 * xup + (1 - c)))
                                      : ld_volatile_shared(rc + up);
       const uint32_t c_dn = xdn >= 0 ? (need == 0 ? 0u : ld_acquire_gpu(a.gcnt + 2 * xdn + (1 - c)))
                                      : ld_volatile_shared(rc + dn);
-      if (c_self < need) lane_ok = wait_count<false>(rc + lr, need, a);
-      if (lane_ok && c_up < need)
-        lane_ok = xup >= 0 ? wait_count<true>(a.gcnt + 2 * xup + (1 - c), need, a) : wait_count<false>(rc + up, need, a);
-      if (lane_ok && c_dn < need)
-        lane_ok = xdn >= 0 ? wait_count<true>(a.gcnt + 2 * xdn + (1 - c), need, a) : wait_count<false>(rc + dn, need, a);
-      if (a.stall_test && j == 0 && m == 0) lane_ok = lane_ok && wait_count<false>(rc + lr, 0xFFFFFFFFu, a);
+      ready = c_self >= need && c_up >= need && c_dn >= need;
+    }
+    // one vote for the chunk: the bounded per-lane waits run only when some
+    // lane is not ready yet (the usual case needs none)
+    if (!__all_sync(0xFFFFFFFFu, ready) || a.stall_test) {
+      if (active) {
+        if (ld_volatile_shared(rc + lr) < need) lane_ok = wait_count<false>(rc + lr, need, a);
+        if (lane_ok)
+          lane_ok = xup >= 0 ? (need == 0 || wait_count<true>(a.gcnt + 2 * xup + (1 - c), need, a))
+                             : wait_count<false>(rc + up, need, a);
+        if (lane_ok)
+          lane_ok = xdn >= 0 ? (need == 0 || wait_count<true>(a.gcnt + 2 * xdn + (1 - c), need, a))
+                             : wait_count<false>(rc + dn, need, a);
+        if (a.stall_test && j == 0 && m == 0) lane_ok = lane_ok && wait_count<false>(rc + lr, 0xFFFFFFFFu, a);
+      }
+    }
+    if (active) {
       if (lane_ok) {
         __threadfence_block();
         const int par = ((rb.x >> 5) & 1) ^ c;
