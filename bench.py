@@ -43,8 +43,8 @@ IMAD_OPS_PER_UPDATE = 10
 # DRAM bytes (read + write) of one launch of the persistent annealing kernel
 # on this workload, from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, --clock-control none) of the same launch
-# configuration: 1,072,896 + 135,680 bytes
-FLOW_TRAFFIC_BYTES = 1072896 + 135680
+# configuration; None until the current kernel has been captured
+FLOW_TRAFFIC_BYTES = None
 
 
 def updates_per_step(w):

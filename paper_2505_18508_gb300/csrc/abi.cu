@@ -311,6 +311,8 @@ int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp, bool weighted = t
     if (nseg > ising::flow_max_segments()) return ISING_ERR_UNSUPPORTED;
     LRmax = std::max(LRmax, lr);
   }
+  // the kernel's tables hold shared-memory word indices in 16 bits
+  if (2LL * LRmax * p->H + 1 > 0xFFFF) return ISING_ERR_UNSUPPORTED;
   const size_t smem = ising::flow_smem_bytes(LRmax, p->H);
   if (smem > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
   fp->G = G;

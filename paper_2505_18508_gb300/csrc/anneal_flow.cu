@@ -29,13 +29,13 @@ namespace ising {
 namespace {
 
 constexpr int kMaxSeg = 4;        // row segments (groups touched) per CTA
-constexpr int kFlowThreads = 1024;
+constexpr int kFlowThreads = 640;
 constexpr int kFlowWarps = kFlowThreads / 32;
 
 struct FlowSmem {
-  uint32_t* sp;        // [2][LR][H] spin words (own rows and halo slots)
-  uint8_t* fl;         // [2][LR][H] site flags (own rows)
-  uint32_t* rowcnt;    // [2][LR] completed items per local row and colour
+  uint32_t* sp;        // [2][LR][H] spin words (own rows and halo slots), then one spare word
+  uint8_t* fl;         // [2][LR][H] site flags (own rows), then one spare byte
+  uint32_t* rowcnt;    // [2][LR + 1] completed items per local row and colour
   int32_t* r_u;        // [LR] global row of the local row (own or halo)
   int32_t* r_up;       // [LR] local row above (own row or halo slot)
   int32_t* r_dn;       // [LR] local row below
@@ -47,21 +47,25 @@ struct FlowSmem {
   uint4* whead;        // [warps][kMaxSeg][8] per-warp Philox heads
   int32_t* meta;       // [8]: nown, nloc, nseg, ...
   int32_t* seg_g;      // [kMaxSeg] group of each segment
-  int4* rowA;          // [LR] {up | dn << 16, xup, xdn, y*X}
-  int4* rowB;          // [LR] {seg | pub << 4 | (y & 1) << 5 | Philox blocks << 8, u, t0, 0}
-  int32_t* ctab;       // [NC*32] lane item of each chunk: lr | h << 16, or -1
+  int4* rowc;          // [2][LR + 1][2] per colour and local row: see the table build
+  int2* xtab;          // [NC*32] per item: see the table build
 };
+
+// items of the largest CTA, rounded up to whole chunks
+__host__ __device__ inline size_t flow_items_cap(int32_t LR, int32_t H) {
+  return (static_cast<size_t>(LR) * H + 31) / 32 * 32;
+}
 
 __host__ __device__ inline size_t flow_smem_layout(int32_t LR, int32_t H, size_t* off) {
   size_t o = 0;
-  off[0] = o; o += align16(static_cast<size_t>(2) * LR * H * 4);      // sp
-  off[1] = o; o += align16(static_cast<size_t>(2) * LR * H);          // fl
-  off[2] = o; o += align16(static_cast<size_t>(2) * LR * 4);          // rowcnt
-  off[3] = o; o += align16(static_cast<size_t>(8) * LR * 4);          // row tables (8 arrays)
-  off[4] = o; o += static_cast<size_t>(kFlowWarps) * kMaxSeg * 8 * 16; // whead
-  off[5] = o; o += 16 * 4;                                             // meta + seg_g
-  off[6] = o; o += static_cast<size_t>(2) * LR * 16;                   // rowA, rowB
-  off[7] = o; o += align16(static_cast<size_t>((LR * H + 31) / 32) * 32 * 4);  // ctab
+  off[0] = o; o += align16((static_cast<size_t>(2) * LR * H + 1) * 4);  // sp (+ spare word)
+  off[1] = o; o += align16(static_cast<size_t>(2) * LR * H + 1);        // fl (+ spare byte)
+  off[2] = o; o += align16(static_cast<size_t>(2) * (LR + 1) * 4);      // rowcnt
+  off[3] = o; o += align16(static_cast<size_t>(8) * LR * 4);            // row tables (8 arrays)
+  off[4] = o; o += static_cast<size_t>(kFlowWarps) * kMaxSeg * 8 * 16;   // whead
+  off[5] = o; o += 16 * 4;                                               // meta + seg_g
+  off[6] = o; o += static_cast<size_t>(2) * (LR + 1) * 2 * 16;          // rowc
+  off[7] = o; o += flow_items_cap(LR, H) * 8;                           // xtab
   return o;
 }
 
@@ -84,9 +88,8 @@ __device__ __forceinline__ FlowSmem flow_carve(unsigned char* smem, int32_t LR, 
   s.whead = reinterpret_cast<uint4*>(smem + off[4]);
   s.meta = reinterpret_cast<int32_t*>(smem + off[5]);
   s.seg_g = s.meta + 8;
-  s.rowA = reinterpret_cast<int4*>(smem + off[6]);
-  s.rowB = s.rowA + LR;
-  s.ctab = reinterpret_cast<int32_t*>(smem + off[7]);
+  s.rowc = reinterpret_cast<int4*>(smem + off[6]);
+  s.xtab = reinterpret_cast<int2*>(smem + off[7]);
   return s;
 }
 
@@ -96,21 +99,67 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
   return v;
 }
 
-__device__ __forceinline__ uint32_t ld_volatile_shared(const uint32_t* p) {
-  return *reinterpret_cast<const volatile uint32_t*>(p);
+// The hot loop addresses shared memory with 32-bit shared-window addresses
+// (no 64-bit generic pointer arithmetic per access).
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u8(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ int2 lds_v2(uint32_t addr) {
+  int2 v;
+  asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ int4 lds_v4(uint32_t addr) {
+  int4 v;
+  asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
-// Bounded wait for *cnt >= need (shared counter or, with kGlobal, a global
-// counter read with acquire semantics).  Returns false if the wait was
-// abandoned (limit reached, or another wait raised the abort flag).
+// acquire / release on the completion counters: a counter read with acquire
+// orders the reader's later loads after it, and a release increment orders
+// the writer's earlier stores (and, through the warp barrier before it, those
+// of the other lanes of its warp) before it
+__device__ __forceinline__ uint32_t ld_acquire_cta(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_cta(uint32_t addr, uint32_t v) {
+  asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_release_gpu(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait until a completion counter reaches `need`: the shared counter
+// at shared address `saddr`, or with kGlobal the global counter `gp`, read
+// with acquire semantics.  Returns false if the wait was abandoned (limit
+// reached, or another wait raised the abort flag).
 template <bool kGlobal>
-__device__ __forceinline__ bool wait_count(const uint32_t* cnt, uint32_t need, const FlowArgs& a) {
-  uint32_t v = kGlobal ? ld_acquire_gpu(cnt) : ld_volatile_shared(cnt);
+__device__ __forceinline__ uint32_t load_count(const uint32_t* gp, uint32_t saddr) {
+  return kGlobal ? ld_acquire_gpu(gp) : ld_acquire_cta(saddr);
+}
+
+template <bool kGlobal>
+__device__ __noinline__ bool wait_count(const uint32_t* gp, uint32_t saddr, uint32_t need, const FlowArgs& a) {
+  uint32_t v = load_count<kGlobal>(gp, saddr);
   if (v >= need) return true;
   const long long t0 = clock64();
   for (uint32_t it = 0;; ++it) {
     __nanosleep(64);   // keep the issue slots for the warps that have work
-    v = kGlobal ? ld_acquire_gpu(cnt) : ld_volatile_shared(cnt);
+    v = load_count<kGlobal>(gp, saddr);
     if (v >= need) return true;
     if ((it & 15u) == 15u) {
       if (*reinterpret_cast<const volatile uint32_t*>(a.abort_flag) != 0u) return false;
@@ -166,9 +215,16 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       }
       if (!whole) {
         sm.r_u[nloc] = g * Y + (ya + Y - 1) % Y;          // halo slot above
-        sm.r_seg[nloc] = nseg;
         sm.r_u[own0 + n] = g * Y + (yb % Y);              // halo slot below
-        sm.r_seg[own0 + n] = nseg;
+        for (int q = 0; q < 2; ++q) {
+          const int hl = q ? own0 + n : nloc;
+          sm.r_seg[hl] = nseg;
+          sm.r_up[hl] = hl;
+          sm.r_dn[hl] = hl;
+          sm.r_xup[hl] = -1;
+          sm.r_xdn[hl] = -1;
+          sm.r_pub[hl] = 0;
+        }
         nloc += n + 2;
       } else {
         nloc += n;
@@ -207,25 +263,64 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   const int nown = sm.meta[0], nloc = sm.meta[1], nseg = sm.meta[2];
   const int items = nown * H;
   const int NC = (items + 31) >> 5;
-  for (int lr = tid; lr < nloc; lr += kFlowThreads) {
-    const int u = sm.r_u[lr];
-    const int g = u / Y, y = u - g * Y;
-    const int t0 = g * a.G;
-    const int nq = decision_blocks<kU16>(min(a.G, a.T - t0));
-    sm.rowA[lr] = make_int4(sm.r_up[lr] | (sm.r_dn[lr] << 16), sm.r_xup[lr], sm.r_xdn[lr], y * a.X);
-    sm.rowB[lr] = make_int4(sm.r_seg[lr] | (sm.r_pub[lr] << 4) | ((y & 1) << 5) | (nq << 8), u, t0, 0);
-  }
-  for (int e = tid; e < NC * 32; e += kFlowThreads) {
-    int v = -1;
-    if (e < items) {
-      const int oi = e / H;
-      v = sm.order[oi] | ((e - oi * H) << 16);
+  const int NR = nloc + 1;                 // local rows, then the row of idle lanes
+  const int spare = 2 * a.LRmax * H;       // spin word that idle lanes update
+
+  // Row records, per colour c and local row lr (two int4):
+  //   A = {sp index of row `up` of colour 1-c | that of row `dn` << 16,
+  //        site index of the row's first colour-c site, Philox head offset
+  //        (segment * 8) | blocks << 8 | parity (y + c) & 1 << 16,
+  //        local row up | local row dn << 16}
+  //   B = {counter of the colour-(1-c) row above in the global mirror, or -1,
+  //        the same for the row below, mirror counter of this row's colour-c
+  //        words if another CTA reads them, or -1,
+  //        sp index of the row's colour-c words | that of its colour-(1-c) words << 16}
+  // The idle lanes' row has its own counters saturated, reads and writes the
+  // spare word and publishes nothing.
+  for (int idx = tid; idx < 2 * NR; idx += kFlowThreads) {
+    const int c = idx / NR, lr = idx - c * NR;
+    int4 A, B;
+    if (lr < nloc) {
+      const int u = sm.r_u[lr];
+      const int g = u / Y, y = u - g * Y;
+      const int nq = decision_blocks<kU16>(min(a.G, a.T - g * a.G));
+      const int up = sm.r_up[lr], dn = sm.r_dn[lr];
+      const int ownp = c * a.LRmax * H, nbp = (1 - c) * a.LRmax * H;
+      const int par = (y + c) & 1;
+      A = make_int4((nbp + up * H) | ((nbp + dn * H) << 16), y * a.X + par,
+                    sm.r_seg[lr] * 8 | (nq << 8) | (par << 16), up | (dn << 16));
+      const int xup = sm.r_xup[lr], xdn = sm.r_xdn[lr];
+      B = make_int4(xup >= 0 ? 2 * xup + (1 - c) : -1, xdn >= 0 ? 2 * xdn + (1 - c) : -1,
+                    sm.r_pub[lr] ? 2 * u + c : -1, (ownp + lr * H) | ((nbp + lr * H) << 16));
+    } else {
+      A = make_int4(spare | (spare << 16), 0, (1 << 8) | (1 << 16), nloc | (nloc << 16));
+      B = make_int4(-1, -1, -1, spare);   // left and right: words 0 and 1 of row 0 (read, never written)
     }
-    sm.ctab[e] = v;
+    sm.rowc[2 * idx] = A;
+    sm.rowc[2 * idx + 1] = B;
+    sm.rowcnt[idx] = lr < nloc ? 0u : 0xFFFFFFFFu;
+  }
+  // Item records (lane e % 32 of chunk e / 32): {local row | h << 16, run},
+  // where run > 0 marks the last lane of a run of items of one row within the
+  // chunk and counts the run's items (the completion counter's increment).
+  // Idle lanes take the idle row with h = 0: they update the spare word.
+  for (int e = tid; e < NC * 32; e += kFlowThreads) {
+    int2 v;
+    if (e < items) {
+      const int oi = e / H, h = e - oi * H;
+      const int ln = e & 31;
+      v = make_int2(sm.order[oi] | (h << 16), (ln == 31 || e + 1 == items || h == H - 1) ? min(ln, h) + 1 : 0);
+    } else {
+      v = make_int2(nloc, 0);
+    }
+    sm.xtab[e] = v;
+  }
+  if (tid == 0) {
+    sm.sp[spare] = 0u;
+    sm.fl[spare] = 0;
   }
 
   // ---- weights of own rows, starting spins of own rows and halo slots
-  for (int idx = tid; idx < 2 * nloc; idx += kFlowThreads) sm.rowcnt[idx] = 0u;
   for (int idx = tid; idx < 2 * nloc * H; idx += kFlowThreads) {
     const int c = idx / (nloc * H);
     const int rem = idx - c * nloc * H;
@@ -256,13 +351,15 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   // ---- the half-sweeps, chunk by chunk
   const long long M = 2LL * a.S * NC;
   uint4* wh = sm.whead + warp * (kMaxSeg * 8);
+  const uint32_t sp32 = smem_addr(sm.sp), fl32 = smem_addr(sm.fl), cnt32 = smem_addr(sm.rowcnt);
+  const uint32_t rowc32 = smem_addr(sm.rowc), xt32 = smem_addr(sm.xtab) + 8u * lane;
   int head_kk = -1;
-  bool ok = true;
+  uint32_t T4 = 0, T8 = 0;
   int hs = 0, k = warp;
   while (k >= NC && NC > 0) { k -= NC; ++hs; }
   for (long long m = warp; m < M; m += kFlowWarps) {
     const int kk = hs >> 1, c = hs & 1;
-    if (kk != head_kk) {   // Philox heads of this sweep for every segment's quads
+    if (kk != head_kk) {   // Philox heads and thresholds of this sweep
       __syncwarp();
       if (lane < nseg * 8) {
         const int s = lane >> 3, jq = lane & 7;
@@ -270,80 +367,77 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
         wh[lane] = philox_head_sweep_quad(a.k0 + static_cast<uint32_t>(kk), q, a.key0, a.key1);
       }
       __syncwarp();
+      T4 = __ldg(a.thr + 2 * kk);
+      T8 = __ldg(a.thr + 2 * kk + 1);
       head_kk = kk;
     }
-    const uint32_t T4 = __ldg(a.thr + 2 * kk), T8 = __ldg(a.thr + 2 * kk + 1);
     const uint32_t need = static_cast<uint32_t>(H) * static_cast<uint32_t>(kk + c);
-    const int te = sm.ctab[k * 32 + lane];
-    const bool active = te >= 0;
-    const int lr = te & 0xFFFF, h = te >> 16;
-    bool lane_ok = true;
-    int4 ra = make_int4(0, -1, -1, 0), rb = make_int4(0, 0, 0, 0);
-    const uint32_t* rc = sm.rowcnt + (1 - c) * nloc;
-    int up = 0, dn = 0, xup = -1, xdn = -1;
-    bool ready = true;
-    if (active) {
-      ra = sm.rowA[lr];
-      rb = sm.rowB[lr];
-      up = ra.x & 0xFFFF;
-      dn = ra.x >> 16;
-      xup = ra.y;
-      xdn = ra.z;
-      // fast check of the three neighbour rows
-      const uint32_t c_self = ld_volatile_shared(rc + lr);
-      const uint32_t c_up = xup >= 0 ? (need == 0 ? 0u : ld_acquire_gpu(a.gcnt + 2 * xup + (1 - c)))
-                                     : ld_volatile_shared(rc + up);
-      const uint32_t c_dn = xdn >= 0 ? (need == 0 ? 0u : ld_acquire_gpu(a.gcnt + 2 * xdn + (1 - c)))
-                                     : ld_volatile_shared(rc + dn);
-      ready = c_self >= need && c_up >= need && c_dn >= need;
+    const int2 it = lds_v2(xt32 + 256u * static_cast<uint32_t>(k));
+    const uint32_t lr = static_cast<uint32_t>(it.x) & 0xFFFFu, h = static_cast<uint32_t>(it.x) >> 16;
+    const uint32_t rrec = rowc32 + 32u * (static_cast<uint32_t>(c * NR) + lr);
+    const int4 A = lds_v4(rrec), B = lds_v4(rrec + 16u);
+    const uint32_t rc = cnt32 + 4u * static_cast<uint32_t>((1 - c) * NR);
+    const uint32_t c_self = rc + 4u * lr, c_up = rc + 4u * (static_cast<uint32_t>(A.w) & 0xFFFFu),
+                   c_dn = rc + 4u * (static_cast<uint32_t>(A.w) >> 16);
+    // the three colour-(1-c) rows this item reads must have finished the
+    // previous half-sweep.  Rows of another CTA are read from the mirror
+    // (except in the very first half-sweep, which reads the halo slots), and
+    // this CTA's rows that another CTA reads are published to it; one vote
+    // sends the chunks that touch neither (most of them) down a path of
+    // shared-memory operations only.
+    const bool gu = B.x >= 0 && need > 0, gd = B.y >= 0 && need > 0;
+    const bool mirror = __any_sync(0xFFFFFFFFu, gu || gd || B.z >= 0);
+    uint32_t v0, v1, v2;
+    if (!mirror) {
+      v0 = ld_acquire_cta(c_self);
+      v1 = ld_acquire_cta(c_up);
+      v2 = ld_acquire_cta(c_dn);
+    } else {
+      v0 = ld_acquire_cta(c_self);
+      v1 = gu ? ld_acquire_gpu(a.gcnt + B.x) : ld_acquire_cta(c_up);
+      v2 = gd ? ld_acquire_gpu(a.gcnt + B.y) : ld_acquire_cta(c_dn);
     }
+    const bool ready = v0 >= need && v1 >= need && v2 >= need;
     // one vote for the chunk: the bounded per-lane waits run only when some
     // lane is not ready yet (the usual case needs none)
     if (!__all_sync(0xFFFFFFFFu, ready) || a.stall_test) {
-      if (active) {
-        if (ld_volatile_shared(rc + lr) < need) lane_ok = wait_count<false>(rc + lr, need, a);
-        if (lane_ok)
-          lane_ok = xup >= 0 ? (need == 0 || wait_count<true>(a.gcnt + 2 * xup + (1 - c), need, a))
-                             : wait_count<false>(rc + up, need, a);
-        if (lane_ok)
-          lane_ok = xdn >= 0 ? (need == 0 || wait_count<true>(a.gcnt + 2 * xdn + (1 - c), need, a))
-                             : wait_count<false>(rc + dn, need, a);
-        if (a.stall_test && j == 0 && m == 0) lane_ok = lane_ok && wait_count<false>(rc + lr, 0xFFFFFFFFu, a);
-      }
+      bool lane_ok = true;
+      if (v0 < need) lane_ok = wait_count<false>(nullptr, c_self, need, a);
+      if (lane_ok && v1 < need)
+        lane_ok = gu ? wait_count<true>(a.gcnt + B.x, 0u, need, a) : wait_count<false>(nullptr, c_up, need, a);
+      if (lane_ok && v2 < need)
+        lane_ok = gd ? wait_count<true>(a.gcnt + B.y, 0u, need, a) : wait_count<false>(nullptr, c_dn, need, a);
+      if (a.stall_test && j == 0 && m == 0) lane_ok = lane_ok && wait_count<false>(nullptr, c_self, 0xFFFFFFFFu, a);
+      if (!__all_sync(0xFFFFFFFFu, lane_ok)) break;
     }
-    if (active) {
-      if (lane_ok) {
-        __threadfence_block();
-        const int par = ((rb.x >> 5) & 1) ^ c;
-        const uint32_t i = static_cast<uint32_t>(ra.w + 2 * h + par);
-        const uint32_t* self = sm.sp + static_cast<size_t>(c) * a.LRmax * H;
-        const uint32_t* nb = sm.sp + static_cast<size_t>(1 - c) * a.LRmax * H;
-        const int hl = par ? h : (h == 0 ? H - 1 : h - 1);
-        const int hr = par ? (h == H - 1 ? 0 : h + 1) : h;
-        const uint32_t nu = (xup >= 0 && need > 0) ? __ldcg(a.gm + (static_cast<size_t>(2) * xup + (1 - c)) * H + h)
-                                                   : nb[up * H + h];
-        const uint32_t nd = (xdn >= 0 && need > 0) ? __ldcg(a.gm + (static_cast<size_t>(2) * xdn + (1 - c)) * H + h)
-                                                   : nb[dn * H + h];
-        const uint32_t ns = update_word<kU16>(self[lr * H + h], nb[lr * H + hl], nb[lr * H + hr], nu, nd,
-                                        sm.fl[(c * a.LRmax + lr) * H + h], i, wh + 8 * (rb.x & 15), rb.x >> 8, T4,
-                                        T8, a.rk);
-        sm.sp[(static_cast<size_t>(c) * a.LRmax + lr) * H + h] = ns;
-        if ((rb.x >> 4) & 1) {
-          __stcg(a.gm + (static_cast<size_t>(2) * rb.y + c) * H + h, ns);
-          __threadfence();
-        }
-        __threadfence_block();
-      }
+    // the word, its left and right neighbours (the row's wrap at h = 0 / H - 1)
+    const uint32_t par = (static_cast<uint32_t>(A.z) >> 16) & 1u;
+    const uint32_t own = (static_cast<uint32_t>(B.w) & 0xFFFFu) + h;
+    const uint32_t nbr = static_cast<uint32_t>(B.w) >> 16;
+    const uint32_t hl = h + par == 0u ? static_cast<uint32_t>(H) - 1u : h + par - 1u;
+    const uint32_t hr = h + par == static_cast<uint32_t>(H) ? 0u : h + par;
+    const uint32_t nl = lds_u32(sp32 + 4u * (nbr + hl));
+    const uint32_t nr = lds_u32(sp32 + 4u * (nbr + hr));
+    const uint32_t a_up = sp32 + 4u * ((static_cast<uint32_t>(A.x) & 0xFFFFu) + h);
+    const uint32_t a_dn = sp32 + 4u * ((static_cast<uint32_t>(A.x) >> 16) + h);
+    uint32_t nu, nd;
+    if (!mirror) {
+      nu = lds_u32(a_up);
+      nd = lds_u32(a_dn);
+    } else {
+      nu = gu ? __ldcg(a.gm + static_cast<size_t>(B.x) * H + h) : lds_u32(a_up);
+      nd = gd ? __ldcg(a.gm + static_cast<size_t>(B.y) * H + h) : lds_u32(a_dn);
     }
-    ok = __all_sync(0xFFFFFFFFu, lane_ok);
-    if (!ok) break;
-    // completion counts: one atomic per distinct row of the chunk
-    const unsigned same = __match_any_sync(0xFFFFFFFFu, active ? lr : -1);
-    if (active && lane == __ffs(same) - 1) {
-      const uint32_t cnt = __popc(same);
-      atomicAdd(sm.rowcnt + c * nloc + lr, cnt);
-      if ((rb.x >> 4) & 1) atomicAdd(a.gcnt + 2 * rb.y + c, cnt);
+    const uint32_t ns = update_word<kU16>(lds_u32(sp32 + 4u * own), nl, nr, nu, nd, lds_u8(fl32 + own),
+                                          static_cast<uint32_t>(A.y) + 2u * h, wh + (A.z & 0xFF), (A.z >> 8) & 0xFF,
+                                          T4, T8, a.rk);
+    sts_u32(sp32 + 4u * own, ns);
+    if (mirror && B.z >= 0) {   // published row: mirror word, then count it at GPU scope
+      __stcg(a.gm + static_cast<size_t>(B.z) * H + h, ns);
+      red_release_gpu(a.gcnt + B.z, 1u);
     }
+    __syncwarp();
+    if (it.y) red_release_cta(cnt32 + 4u * (static_cast<uint32_t>(c * NR) + lr), static_cast<uint32_t>(it.y));
     k += kFlowWarps;
     while (k >= NC) { k -= NC; ++hs; }
   }
@@ -407,7 +501,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
           uint32_t sd;
           const int xdn = sm.r_xdn[lr];
           if (xdn >= 0 && a.S > 0) {
-            lok = wait_count<true>(a.gcnt + 2 * xdn + (1 - c), fin, a);
+            lok = wait_count<true>(a.gcnt + 2 * xdn + (1 - c), 0u, fin, a);
             sd = lok ? __ldcg(a.gm + (static_cast<size_t>(2) * xdn + (1 - c)) * H + h) : 0u;
           } else {
             sd = nb[sm.r_dn[lr] * H + h];
