@@ -262,10 +262,11 @@ struct FlowPlan {
   std::vector<int32_t> split;
 };
 
-// Stacks the rows of all trial groups and splits them over one CTA per SM,
-// weighted by the Philox blocks of each row's group (or, unweighted, into
-// equal row counts: the caller's fallback when a ragged last group would pile
-// its light rows onto a few CTAs beyond their shared memory).  Fails with
+// Stacks the rows of all trial groups and splits their site words over one
+// CTA per SM, weighted by the Philox blocks of each row's group (or,
+// unweighted, into equal word counts: the caller's fallback when a ragged last
+// group would pile its light rows onto a few CTAs beyond their shared
+// memory).  Fails with
 // ISING_ERR_UNSUPPORTED when a CTA would touch more groups than the kernel
 // tracks or its rows would not fit in shared memory.
 int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp, bool weighted = true) {
@@ -279,40 +280,64 @@ int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp, bool weighted = t
   if (RTl > (1LL << 30)) return ISING_ERR_UNSUPPORTED;
   const int RT = static_cast<int>(RTl);
   const int P = std::min(sms, RT);
-  std::vector<long long> cum(static_cast<size_t>(RT) + 1, 0);
+  const int H = p->H;
+  if (static_cast<long long>(RT) * H > (1LL << 30)) return ISING_ERR_UNSUPPORTED;
+  // Split the stacked site words (word w = row * H + h) into P ranges of
+  // equal weight (a word weighs the Philox blocks of its trial group, or 1).
+  // A range may start and end inside a row: such a row is shared by two CTAs,
+  // which then read it, and its neighbours, through the global mirror.  In
+  // the 16-bit draw mode, where a word's own work is cheaper, that costs more
+  // than the finer balance gains (measured on the 200 x 100 torus with 1,024
+  // trials), so there the ranges end at row boundaries.
+  const bool whole_rows = p->draw_bits == 16;
+  std::vector<long long> cum(static_cast<size_t>(RT) + 1, 0);   // weight of rows before u
+  std::vector<int> wrow(static_cast<size_t>(RT));
   for (int u = 0; u < RT; ++u) {
     const int g = u / p->Y;
     const int live = std::min(G, T - g * G);
-    cum[u + 1] = cum[u] + (weighted ? (live + blk - 1) / blk : 1);
+    wrow[u] = weighted ? (live + blk - 1) / blk : 1;
+    cum[u + 1] = cum[u] + wrow[u];
   }
-  const long long total = cum[RT];
+  const long long total = cum[RT] * H;
+  const int W = RT * H;
   std::vector<int32_t> split(static_cast<size_t>(P) + 1);
   split[0] = 0;
   int u = 0;
   for (int j = 1; j < P; ++j) {
     const long long target = (static_cast<long long>(j) * total + P / 2) / P;
-    while (u < RT && cum[u] < target) ++u;
-    int v = u;
-    if (v <= split[j - 1]) v = split[j - 1] + 1;
-    if (v > RT - (P - j)) v = RT - (P - j);
+    while (u < RT && cum[u + 1] * H <= target) ++u;
+    int v = W;
+    if (u < RT) {
+      const long long rem = target - cum[u] * H;   // weight still needed inside row u
+      const long long h = (rem + wrow[u] - 1) / wrow[u];
+      v = u * H + static_cast<int>(std::min<long long>(h, H));
+    }
+    if (whole_rows) v = (v + H - 1) / H * H;
+    const int unit = whole_rows ? H : 1;
+    if (v <= split[j - 1]) v = split[j - 1] + unit;
+    if (v > W - (P - j) * unit) v = W - (P - j) * unit;
     split[j] = v;
   }
-  split[P] = RT;
+  split[P] = W;
+  // local rows of each CTA: its rows (whole or shared) plus two halo slots
+  // per segment that is not a whole trial group
   int LRmax = 0;
   for (int j = 0; j < P; ++j) {
     int lr = 0, nseg = 0;
     for (int w = split[j]; w < split[j + 1];) {
-      const int g = w / p->Y, ya = w - g * p->Y;
-      const int n = std::min(p->Y - ya, split[j + 1] - w);
-      lr += n + (n == p->Y ? 0 : 2);
+      const int r = w / H, g = r / p->Y;
+      const int wend = std::min(split[j + 1], (g + 1) * p->Y * H);
+      const int n = (wend - 1) / H - r + 1;
+      const bool whole = wend - w == p->Y * H;
+      lr += n + (whole ? 0 : 2);
       ++nseg;
-      w += n;
+      w = wend;
     }
     if (nseg > ising::flow_max_segments()) return ISING_ERR_UNSUPPORTED;
     LRmax = std::max(LRmax, lr);
   }
   // the kernel's tables hold shared-memory word indices in 16 bits
-  if (2LL * LRmax * p->H + 1 > 0xFFFF) return ISING_ERR_UNSUPPORTED;
+  if (2LL * LRmax * H + 1 > 0xFFFF) return ISING_ERR_UNSUPPORTED;
   const size_t smem = ising::flow_smem_bytes(LRmax, p->H);
   if (smem > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
   fp->G = G;

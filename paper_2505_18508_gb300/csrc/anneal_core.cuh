@@ -192,12 +192,29 @@ __host__ __device__ __forceinline__ uint32_t decision_block0(int t0) {
   return kU16 ? static_cast<uint32_t>(t0) >> 3 : static_cast<uint32_t>(t0) >> 2;
 }
 
+// Where the per-sweep Philox heads of a word's decision blocks are read:
+// through a pointer, or from a 32-bit shared-memory address.
+struct HeadsAt {
+  const uint4* p;
+  __device__ __forceinline__ uint4 operator()(int j) const { return p[j]; }
+};
+struct HeadsShared {
+  uint32_t addr;
+  __device__ __forceinline__ uint4 operator()(int j) const {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr + 16u * static_cast<uint32_t>(j)));
+    return v;
+  }
+};
+
 // Metropolis update of one site word; returns the new word.  nq: Philox
-// blocks of the group (decision_blocks).
-template <bool kU16>
-__device__ __forceinline__ uint32_t update_word(uint32_t s, uint32_t nl, uint32_t nr, uint32_t nu, uint32_t nd,
-                                               uint32_t f, uint32_t i, const uint4* head, int nq,
-                                               uint32_t T4, uint32_t T8, const uint32_t* __restrict__ rk) {
+// blocks of the group (decision_blocks); heads(j): the head of block j.
+template <bool kU16, class Heads>
+__device__ __forceinline__ uint32_t update_word_h(uint32_t s, uint32_t nl, uint32_t nr, uint32_t nu, uint32_t nd,
+                                                 uint32_t f, uint32_t i, const Heads& heads, int nq,
+                                                 uint32_t T4, uint32_t T8, const uint32_t* __restrict__ rk) {
   const uint32_t mL = 0u - (f & 1u), mR = 0u - ((f >> 1) & 1u);
   const uint32_t mU = 0u - ((f >> 2) & 1u), mD = 0u - ((f >> 3) & 1u);
   const uint32_t eL = ~(s ^ nl ^ mL), eR = ~(s ^ nr ^ mR);
@@ -214,19 +231,26 @@ __device__ __forceinline__ uint32_t update_word(uint32_t s, uint32_t nl, uint32_
   if constexpr (kU16) {
     if (nq == 4) {
 #pragma unroll
-      for (int j = 3; j >= 0; --j) octet_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
+      for (int j = 3; j >= 0; --j) octet_step(rej4, rej8, heads(j), hi1, lo1, lo0, T4, T8, rk);
     } else {
-      for (int j = nq - 1; j >= 0; --j) octet_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
+      for (int j = nq - 1; j >= 0; --j) octet_step(rej4, rej8, heads(j), hi1, lo1, lo0, T4, T8, rk);
     }
   } else {
     if (nq == 8) {  // full groups: unrolled, so consecutive blocks can overlap
 #pragma unroll
-      for (int j = 7; j >= 0; --j) quad_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
+      for (int j = 7; j >= 0; --j) quad_step(rej4, rej8, heads(j), hi1, lo1, lo0, T4, T8, rk);
     } else {
-      for (int j = nq - 1; j >= 0; --j) quad_step(rej4, rej8, head[j], hi1, lo1, lo0, T4, T8, rk);
+      for (int j = nq - 1; j >= 0; --j) quad_step(rej4, rej8, heads(j), hi1, lo1, lo0, T4, T8, rk);
     }
   }
   return s ^ (ge2 | (eq1 & ~rej4) | (eq0 & ~rej8));
+}
+
+template <bool kU16>
+__device__ __forceinline__ uint32_t update_word(uint32_t s, uint32_t nl, uint32_t nr, uint32_t nu, uint32_t nd,
+                                               uint32_t f, uint32_t i, const uint4* head, int nq,
+                                               uint32_t T4, uint32_t T8, const uint32_t* __restrict__ rk) {
+  return update_word_h<kU16>(s, nl, nr, nu, nd, f, i, HeadsAt{head}, nq, T4, T8, rk);
 }
 
 // Anneal trial group g (strip r of C) of job a.  All threads of the CTA (and

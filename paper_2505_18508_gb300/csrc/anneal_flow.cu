@@ -5,20 +5,23 @@
 // organised so that every SM works and no CTA-wide barrier separates the
 // half-sweeps:
 //
-// * Rows of all trial groups are stacked (global row u = g*Y + y) and split
-//   into one contiguous range per CTA, weighted by the number of Philox quads
-//   of each row's group, over exactly one CTA per SM (cooperative launch, so
-//   all CTAs are resident together).
+// * Rows of all trial groups are stacked (global row u = g*Y + y), and their
+//   site words (u*H + h) are split into one contiguous range per CTA,
+//   weighted by the number of Philox quads of each row's group, over exactly
+//   one CTA per SM (cooperative launch, so all CTAs are resident together).
+//   A range may begin or end inside a row; such a row is shared by two CTAs.
 // * Inside a CTA, warps take 32-item chunks of the half-sweeps in one global
 //   order (half-sweep major), round robin.  A chunk of colour c only needs the
 //   colour-(1-c) words of its rows and of the rows above and below; per-row
 //   completion counters in shared memory say when those are final, so a warp
 //   waits for exactly its neighbours and never for the whole CTA.
-// * Rows whose neighbour belongs to another CTA ("published" rows) are also
-//   written to a global mirror, with a per-row completion counter in global
-//   memory; the neighbour CTA acquires that counter before reading the row.
-//   Published rows come first in each half-sweep, so the counters are usually
-//   complete long before anyone waits on them.
+// * Rows that another CTA reads ("published" rows: shared rows and the rows
+//   next to a shared or another CTA's row) are also written to a global
+//   mirror, with a per-row completion counter in global memory that all of
+//   the row's owners count into; a reader acquires that counter before it
+//   reads the row from the mirror.  Published rows come first in each
+//   half-sweep, so the counters are usually complete long before anyone
+//   waits on them.
 //
 // Every wait is bounded by a cycle limit.  A wait that runs out writes
 // ISING_ERR_TIMEOUT to the problem's status word and raises an abort flag that
@@ -44,6 +47,10 @@ struct FlowSmem {
   int32_t* r_pub;      // [LR] 1 if another CTA reads this own row
   int32_t* r_seg;      // [LR] segment of the row
   int32_t* order;      // [LR] own rows in processing order (published rows first)
+  int32_t* r_ha;       // [LR] own words of the row: h in [r_ha, r_hb)
+  int32_t* r_hb;
+  int32_t* r_xself;    // [LR] global row if another CTA owns some of its words, else -1
+  int32_t* oitem;      // [LR + 1] first item of the oi-th row of the processing order
   uint4* whead;        // [warps][kMaxSeg][8] per-warp Philox heads
   int32_t* meta;       // [8]: nown, nloc, nseg, ...
   int32_t* seg_g;      // [kMaxSeg] group of each segment
@@ -61,7 +68,7 @@ __host__ __device__ inline size_t flow_smem_layout(int32_t LR, int32_t H, size_t
   off[0] = o; o += align16((static_cast<size_t>(2) * LR * H + 1) * 4);  // sp (+ spare word)
   off[1] = o; o += align16(static_cast<size_t>(2) * LR * H + 1);        // fl (+ spare byte)
   off[2] = o; o += align16(static_cast<size_t>(2) * (LR + 1) * 4);      // rowcnt
-  off[3] = o; o += align16(static_cast<size_t>(8) * LR * 4);            // row tables (8 arrays)
+  off[3] = o; o += align16(static_cast<size_t>(12) * (LR + 1) * 4);     // row tables (12 arrays)
   off[4] = o; o += static_cast<size_t>(kFlowWarps) * kMaxSeg * 8 * 16;   // whead
   off[5] = o; o += 16 * 4;                                               // meta + seg_g
   off[6] = o; o += static_cast<size_t>(2) * (LR + 1) * 2 * 16;          // rowc
@@ -77,14 +84,19 @@ __device__ __forceinline__ FlowSmem flow_carve(unsigned char* smem, int32_t LR, 
   s.fl = smem + off[1];
   s.rowcnt = reinterpret_cast<uint32_t*>(smem + off[2]);
   int32_t* t = reinterpret_cast<int32_t*>(smem + off[3]);
+  const int L1 = LR + 1;
   s.r_u = t;
-  s.r_up = t + LR;
-  s.r_dn = t + 2 * LR;
-  s.r_xup = t + 3 * LR;
-  s.r_xdn = t + 4 * LR;
-  s.r_pub = t + 5 * LR;
-  s.r_seg = t + 6 * LR;
-  s.order = t + 7 * LR;
+  s.r_up = t + L1;
+  s.r_dn = t + 2 * L1;
+  s.r_xup = t + 3 * L1;
+  s.r_xdn = t + 4 * L1;
+  s.r_pub = t + 5 * L1;
+  s.r_seg = t + 6 * L1;
+  s.order = t + 7 * L1;
+  s.r_ha = t + 8 * L1;
+  s.r_hb = t + 9 * L1;
+  s.r_xself = t + 10 * L1;
+  s.oitem = t + 11 * L1;
   s.whead = reinterpret_cast<uint4*>(smem + off[4]);
   s.meta = reinterpret_cast<int32_t*>(smem + off[5]);
   s.seg_g = s.meta + 8;
@@ -179,17 +191,20 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int H = a.H, Y = a.Y;
   const FlowSmem sm = flow_carve(smem, a.LRmax, H);
-  const int r0 = a.split[j], r1 = a.split[j + 1];
+  const int w0 = a.split[j], w1 = a.split[j + 1];   // own words: stacked row * H + h in [w0, w1)
 
   // ---- local row tables (one thread; at most a few dozen rows)
   if (tid == 0) {
     int nloc = 0, nseg = 0;
     int seg_first[kMaxSeg], seg_n[kMaxSeg];
-    for (int u = r0; u < r1;) {
+    for (int w = w0; w < w1;) {
+      const int u = w / H;
       const int g = u / Y, ya = u - g * Y;
-      const int yb = min(Y, ya + (r1 - u));
-      const int n = yb - ya;
-      const bool whole = (n == Y);
+      const int wend = min(w1, (g + 1) * Y * H);   // this group's words within the range
+      const int ub = (wend - 1) / H;
+      const int n = ub - u + 1;
+      const int ha0 = w - u * H, hbl = wend - ub * H;
+      const bool whole = (wend - w == Y * H);
       sm.seg_g[nseg] = g;
       seg_n[nseg] = n;
       // layout: [halo top][own rows][halo bottom] (no halos for a whole group)
@@ -198,24 +213,34 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       for (int q = 0; q < n; ++q) {
         const int lr = own0 + q;
         const int y = ya + q;
+        const bool shared = (q == 0 && ha0 > 0) || (q == n - 1 && hbl < H);
+        const bool sh_up = q > 0 && ((q - 1 == 0 && ha0 > 0));
+        const bool sh_dn = q < n - 1 && ((q + 1 == n - 1 && hbl < H));
         sm.r_u[lr] = g * Y + y;
         sm.r_seg[lr] = nseg;
+        sm.r_ha[lr] = q == 0 ? ha0 : 0;
+        sm.r_hb[lr] = q == n - 1 ? hbl : H;
+        sm.r_xself[lr] = shared ? g * Y + y : -1;
         sm.r_xup[lr] = -1;
         sm.r_xdn[lr] = -1;
-        sm.r_pub[lr] = 0;
         if (whole) {
           sm.r_up[lr] = own0 + (q == 0 ? n - 1 : q - 1);
           sm.r_dn[lr] = own0 + (q == n - 1 ? 0 : q + 1);
         } else {
-          sm.r_up[lr] = lr - 1;            // halo slot above the first own row
-          sm.r_dn[lr] = lr + 1;            // halo slot below the last own row
-          if (q == 0) { sm.r_xup[lr] = g * Y + (ya + Y - 1) % Y; sm.r_pub[lr] = 1; }
-          if (q == n - 1) { sm.r_xdn[lr] = g * Y + (yb % Y); sm.r_pub[lr] = 1; }
+          // rows read through the global mirror: the halo rows (another
+          // CTA's) and the rows shared with another CTA
+          sm.r_up[lr] = lr - 1;
+          sm.r_dn[lr] = lr + 1;
+          if (q == 0 || sh_up) sm.r_xup[lr] = g * Y + (y + Y - 1) % Y;
+          if (q == n - 1 || sh_dn) sm.r_xdn[lr] = g * Y + (y + 1) % Y;
         }
+        // published: another CTA reads it (a shared row, or a neighbour of one
+        // or of a halo row)
+        sm.r_pub[lr] = shared || sm.r_xup[lr] >= 0 || sm.r_xdn[lr] >= 0;
       }
       if (!whole) {
-        sm.r_u[nloc] = g * Y + (ya + Y - 1) % Y;          // halo slot above
-        sm.r_u[own0 + n] = g * Y + (yb % Y);              // halo slot below
+        sm.r_u[nloc] = g * Y + (ya + Y - 1) % Y;              // halo slot above
+        sm.r_u[own0 + n] = g * Y + (ya + n) % Y;              // halo slot below
         for (int q = 0; q < 2; ++q) {
           const int hl = q ? own0 + n : nloc;
           sm.r_seg[hl] = nseg;
@@ -224,28 +249,31 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
           sm.r_xup[hl] = -1;
           sm.r_xdn[hl] = -1;
           sm.r_pub[hl] = 0;
+          sm.r_ha[hl] = 0;
+          sm.r_hb[hl] = 0;
+          sm.r_xself[hl] = -1;
         }
         nloc += n + 2;
       } else {
         nloc += n;
       }
       ++nseg;
-      u += n;
+      w = wend;
     }
-    // processing order: the published rows of every segment first, then the
-    // remaining rows of each segment from both ends towards the middle, the
-    // segments interleaved.  Every row's neighbours are then processed about
-    // one half-sweep before it needs them, never just before.
+    // processing order: the published rows of every segment first (from
+    // both ends), then the remaining rows of each segment from both ends
+    // towards the middle, the segments interleaved.  Every row's neighbours
+    // are then processed about one half-sweep before it needs them, never
+    // just before.
     int no = 0;
     int lo[kMaxSeg], hi[kMaxSeg];
     for (int s = 0; s < nseg; ++s) {
       lo[s] = seg_first[s];
       hi[s] = seg_first[s] + seg_n[s] - 1;
-      if (sm.r_pub[lo[s]]) {           // partial segment: first and last own row
-        sm.order[no++] = lo[s];
-        if (hi[s] != lo[s]) sm.order[no++] = hi[s];
-        ++lo[s];
-        --hi[s];
+      for (bool more = true; more;) {
+        more = false;
+        if (lo[s] <= hi[s] && sm.r_pub[lo[s]]) { sm.order[no++] = lo[s]++; more = true; }
+        if (lo[s] <= hi[s] && sm.r_pub[hi[s]]) { sm.order[no++] = hi[s]--; more = true; }
       }
     }
     for (bool more = true; more;) {
@@ -255,13 +283,20 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
         if (lo[s] <= hi[s]) { sm.order[no++] = hi[s]--; more = true; }
       }
     }
+    int items = 0;
+    for (int oi = 0; oi < no; ++oi) {
+      sm.oitem[oi] = items;
+      items += sm.r_hb[sm.order[oi]] - sm.r_ha[sm.order[oi]];
+    }
+    sm.oitem[no] = items;
     sm.meta[0] = no;
     sm.meta[1] = nloc;
     sm.meta[2] = nseg;
+    sm.meta[3] = items;
   }
   __syncthreads();
   const int nown = sm.meta[0], nloc = sm.meta[1], nseg = sm.meta[2];
-  const int items = nown * H;
+  const int items = sm.meta[3];
   const int NC = (items + 31) >> 5;
   const int NR = nloc + 1;                 // local rows, then the row of idle lanes
   const int spare = 2 * a.LRmax * H;       // spin word that idle lanes update
@@ -269,8 +304,10 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   // Row records, per colour c and local row lr (two int4):
   //   A = {sp index of row `up` of colour 1-c | that of row `dn` << 16,
   //        site index of the row's first colour-c site, Philox head offset
-  //        (segment * 8) | blocks << 8 | parity (y + c) & 1 << 16,
+  //        (segment * 8) | blocks << 8 | parity (y + c) & 1 << 16 | shared << 17,
   //        local row up | local row dn << 16}
+  // A shared row (some of its words belong to another CTA) is always
+  // published, so its colour-(1-c) mirror counter is B.z ^ 1.
   //   B = {counter of the colour-(1-c) row above in the global mirror, or -1,
   //        the same for the row below, mirror counter of this row's colour-c
   //        words if another CTA reads them, or -1,
@@ -288,7 +325,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       const int ownp = c * a.LRmax * H, nbp = (1 - c) * a.LRmax * H;
       const int par = (y + c) & 1;
       A = make_int4((nbp + up * H) | ((nbp + dn * H) << 16), y * a.X + par,
-                    sm.r_seg[lr] * 8 | (nq << 8) | (par << 16), up | (dn << 16));
+                    sm.r_seg[lr] * 8 | (nq << 8) | (par << 16) | ((sm.r_xself[lr] >= 0) << 17), up | (dn << 16));
       const int xup = sm.r_xup[lr], xdn = sm.r_xdn[lr];
       B = make_int4(xup >= 0 ? 2 * xup + (1 - c) : -1, xdn >= 0 ? 2 * xdn + (1 - c) : -1,
                     sm.r_pub[lr] ? 2 * u + c : -1, (ownp + lr * H) | ((nbp + lr * H) << 16));
@@ -307,9 +344,13 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   for (int e = tid; e < NC * 32; e += kFlowThreads) {
     int2 v;
     if (e < items) {
-      const int oi = e / H, h = e - oi * H;
+      int oi = 0;
+      while (sm.oitem[oi + 1] <= e) ++oi;
+      const int lr = sm.order[oi];
+      const int ha = sm.r_ha[lr];
+      const int h = ha + (e - sm.oitem[oi]);
       const int ln = e & 31;
-      v = make_int2(sm.order[oi] | (h << 16), (ln == 31 || e + 1 == items || h == H - 1) ? min(ln, h) + 1 : 0);
+      v = make_int2(lr | (h << 16), (ln == 31 || e + 1 == items || h == sm.r_hb[lr] - 1) ? min(ln, h - ha) + 1 : 0);
     } else {
       v = make_int2(nloc, 0);
     }
@@ -352,7 +393,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   const long long M = 2LL * a.S * NC;
   uint4* wh = sm.whead + warp * (kMaxSeg * 8);
   const uint32_t sp32 = smem_addr(sm.sp), fl32 = smem_addr(sm.fl), cnt32 = smem_addr(sm.rowcnt);
-  const uint32_t rowc32 = smem_addr(sm.rowc), xt32 = smem_addr(sm.xtab) + 8u * lane;
+  const uint32_t rowc32 = smem_addr(sm.rowc), xt32 = smem_addr(sm.xtab) + 8u * lane, wh32 = smem_addr(wh);
   int head_kk = -1;
   uint32_t T4 = 0, T8 = 0;
   int hs = 0, k = warp;
@@ -386,6 +427,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
     // sends the chunks that touch neither (most of them) down a path of
     // shared-memory operations only.
     const bool gu = B.x >= 0 && need > 0, gd = B.y >= 0 && need > 0;
+    const bool gs = ((A.z >> 17) & 1) && need > 0;
     const bool mirror = __any_sync(0xFFFFFFFFu, gu || gd || B.z >= 0);
     uint32_t v0, v1, v2;
     if (!mirror) {
@@ -393,7 +435,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       v1 = ld_acquire_cta(c_up);
       v2 = ld_acquire_cta(c_dn);
     } else {
-      v0 = ld_acquire_cta(c_self);
+      v0 = gs ? ld_acquire_gpu(a.gcnt + (B.z ^ 1)) : ld_acquire_cta(c_self);
       v1 = gu ? ld_acquire_gpu(a.gcnt + B.x) : ld_acquire_cta(c_up);
       v2 = gd ? ld_acquire_gpu(a.gcnt + B.y) : ld_acquire_cta(c_dn);
     }
@@ -402,7 +444,8 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
     // lane is not ready yet (the usual case needs none)
     if (!__all_sync(0xFFFFFFFFu, ready) || a.stall_test) {
       bool lane_ok = true;
-      if (v0 < need) lane_ok = wait_count<false>(nullptr, c_self, need, a);
+      if (v0 < need)
+        lane_ok = gs ? wait_count<true>(a.gcnt + (B.z ^ 1), 0u, need, a) : wait_count<false>(nullptr, c_self, need, a);
       if (lane_ok && v1 < need)
         lane_ok = gu ? wait_count<true>(a.gcnt + B.x, 0u, need, a) : wait_count<false>(nullptr, c_up, need, a);
       if (lane_ok && v2 < need)
@@ -416,21 +459,25 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
     const uint32_t nbr = static_cast<uint32_t>(B.w) >> 16;
     const uint32_t hl = h + par == 0u ? static_cast<uint32_t>(H) - 1u : h + par - 1u;
     const uint32_t hr = h + par == static_cast<uint32_t>(H) ? 0u : h + par;
-    const uint32_t nl = lds_u32(sp32 + 4u * (nbr + hl));
-    const uint32_t nr = lds_u32(sp32 + 4u * (nbr + hr));
     const uint32_t a_up = sp32 + 4u * ((static_cast<uint32_t>(A.x) & 0xFFFFu) + h);
     const uint32_t a_dn = sp32 + 4u * ((static_cast<uint32_t>(A.x) >> 16) + h);
-    uint32_t nu, nd;
+    uint32_t nl, nr, nu, nd;
     if (!mirror) {
+      nl = lds_u32(sp32 + 4u * (nbr + hl));
+      nr = lds_u32(sp32 + 4u * (nbr + hr));
       nu = lds_u32(a_up);
       nd = lds_u32(a_dn);
     } else {
+      const uint32_t* gself = a.gm + static_cast<size_t>(B.z ^ 1) * H;
+      nl = gs ? __ldcg(gself + hl) : lds_u32(sp32 + 4u * (nbr + hl));
+      nr = gs ? __ldcg(gself + hr) : lds_u32(sp32 + 4u * (nbr + hr));
       nu = gu ? __ldcg(a.gm + static_cast<size_t>(B.x) * H + h) : lds_u32(a_up);
       nd = gd ? __ldcg(a.gm + static_cast<size_t>(B.y) * H + h) : lds_u32(a_dn);
     }
-    const uint32_t ns = update_word<kU16>(lds_u32(sp32 + 4u * own), nl, nr, nu, nd, lds_u8(fl32 + own),
-                                          static_cast<uint32_t>(A.y) + 2u * h, wh + (A.z & 0xFF), (A.z >> 8) & 0xFF,
-                                          T4, T8, a.rk);
+    const uint32_t ns = update_word_h<kU16>(lds_u32(sp32 + 4u * own), nl, nr, nu, nd, lds_u8(fl32 + own),
+                                            static_cast<uint32_t>(A.y) + 2u * h,
+                                            HeadsShared{wh32 + 16u * (static_cast<uint32_t>(A.z) & 0xFFu)},
+                                            (A.z >> 8) & 0xFF, T4, T8, a.rk);
     sts_u32(sp32 + 4u * own, ns);
     if (mirror && B.z >= 0) {   // published row: mirror word, then count it at GPU scope
       __stcg(a.gm + static_cast<size_t>(B.z) * H + h, ns);
@@ -454,6 +501,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       const int oi = idx / a.X;
       const int x = idx - oi * a.X;
       const int lr = sm.order[oi];
+      if ((x >> 1) < sm.r_ha[lr] || (x >> 1) >= sm.r_hb[lr]) continue;   // another CTA's word
       const int u = sm.r_u[lr];
       const int g = u / Y, y = u - g * Y;
       const int t0 = g * a.G;
@@ -486,7 +534,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
           const int oi = rem / H;
           h = rem - oi * H;
           lr = sm.order[oi];
-          mine = sm.r_seg[lr] == s;
+          mine = sm.r_seg[lr] == s && h >= sm.r_ha[lr] && h < sm.r_hb[lr];
         }
         bool lok = true;
         if (mine) {
@@ -497,10 +545,17 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
           const uint32_t* nb = sm.sp + static_cast<size_t>(1 - c) * a.LRmax * H;
           const uint32_t sv = self[lr * H + h];
           const int hr = par ? (h == H - 1 ? 0 : h + 1) : h;
-          const uint32_t sr = nb[lr * H + hr];
+          uint32_t sr;
+          const int xs = sm.r_xself[lr];
+          if (xs >= 0 && a.S > 0) {   // a shared row: its final words are in the mirror
+            lok = wait_count<true>(a.gcnt + 2 * xs + (1 - c), 0u, fin, a);
+            sr = lok ? __ldcg(a.gm + (static_cast<size_t>(2) * xs + (1 - c)) * H + hr) : 0u;
+          } else {
+            sr = nb[lr * H + hr];
+          }
           uint32_t sd;
           const int xdn = sm.r_xdn[lr];
-          if (xdn >= 0 && a.S > 0) {
+          if (lok && xdn >= 0 && a.S > 0) {
             lok = wait_count<true>(a.gcnt + 2 * xdn + (1 - c), 0u, fin, a);
             sd = lok ? __ldcg(a.gm + (static_cast<size_t>(2) * xdn + (1 - c)) * H + h) : 0u;
           } else {

@@ -87,7 +87,7 @@ struct FlowArgs {
   int32_t P;                // CTAs (one per SM)
   int32_t LRmax;            // local rows (own rows and halo slots) of the largest CTA
   int32_t neg_edges;
-  const int32_t* split;     // [P+1] first stacked row of each CTA
+  const int32_t* split;     // [P+1] first stacked site word (row * H + h) of each CTA
   uint32_t* gm;             // [RT][2][H] mirror of rows read by another CTA
   uint32_t* gcnt;           // [RT][2] completed items of those rows (zeroed)
   int32_t* acc;             // [T] per-trial cut partial sums (zeroed)
