@@ -350,72 +350,136 @@ int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp, bool weighted = t
   return ISING_OK;
 }
 
-int run_flow(ising_problem* p, const FlowPlan& fp, int32_t trials, const std::vector<uint32_t>& thr, int32_t S,
-             uint64_t seed, uint32_t sweep_offset, const int8_t* init_spins, int8_t* out_spins, int32_t* out_cuts,
-             cudaStream_t st) {
-  int per_sm = 0;
-  cudaError_t e = ising::flow_max_ctas(fp.smem, &per_sm);
-  if (e != cudaSuccess) return map_cuda(e);
-  if (per_sm < 1 || fp.P > per_sm * num_sms_of(p->device)) return ISING_ERR_UNSUPPORTED;
-  // arena: thresholds | split | mirror | zeroed: counters, cut sums, done, abort
-  const size_t o_thr = 0;
-  const size_t o_split = o_thr + align256(thr.size() * sizeof(uint32_t));
-  const size_t o_gm = o_split + align256((fp.split.size()) * sizeof(int32_t));
-  const size_t o_zero = o_gm + align256(static_cast<size_t>(fp.RT) * 2 * p->H * sizeof(uint32_t));
-  const size_t o_gcnt = o_zero;
-  const size_t o_acc = o_gcnt + align256(static_cast<size_t>(fp.RT) * 2 * sizeof(uint32_t));
-  const size_t o_done = o_acc + align256(static_cast<size_t>(trials) * sizeof(int32_t));
-  const size_t o_abort = o_done + 256;
-  const size_t bytes = o_abort + 256;
+}  // namespace
+
+// A flow-kernel run prepared once for repeated launches: its plan and a
+// device arena of (optional) thresholds | split | mirror | zeroed: counters,
+// cut sums, done, abort.
+struct FlowRun {
+  ising_problem* p = nullptr;
+  FlowPlan fp;
+  int32_t trials = 0;
   unsigned char* d = nullptr;
-  e = ising::dev_malloc_async(reinterpret_cast<void**>(&d), bytes, st);
-  if (e != cudaSuccess) return map_cuda(e);
-  if (!thr.empty()) e = cudaMemcpyAsync(d + o_thr, thr.data(), thr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+  size_t o_split = 0, o_gm = 0, o_zero = 0, o_acc = 0, o_done = 0, o_abort = 0, bytes = 0;
+};
+
+namespace ising {
+
+int flow_run_create(ising_problem* p, int32_t trials, size_t thr_words, FlowRun** out, cudaStream_t st) {
+  *out = nullptr;
+  FlowRun* r = nullptr;
+  try {
+    r = new FlowRun();
+    int frc = plan_flow(p, trials, &r->fp);
+    if (frc == ISING_ERR_UNSUPPORTED) frc = plan_flow(p, trials, &r->fp, false);
+    if (frc != ISING_OK) { delete r; return frc; }
+  } catch (const std::bad_alloc&) {
+    delete r;
+    return ISING_ERR_OOM;
+  }
+  const FlowPlan& fp = r->fp;
+  int per_sm = 0;
+  cudaError_t e = flow_max_ctas(fp.smem, &per_sm);
+  if (e == cudaSuccess && (per_sm < 1 || fp.P > per_sm * num_sms_of(p->device))) {
+    delete r;
+    return ISING_ERR_UNSUPPORTED;
+  }
+  r->p = p;
+  r->trials = trials;
+  r->o_split = align256(thr_words * sizeof(uint32_t));
+  r->o_gm = r->o_split + align256(fp.split.size() * sizeof(int32_t));
+  r->o_zero = r->o_gm + align256(static_cast<size_t>(fp.RT) * 2 * p->H * sizeof(uint32_t));
+  r->o_acc = r->o_zero + align256(static_cast<size_t>(fp.RT) * 2 * sizeof(uint32_t));
+  r->o_done = r->o_acc + align256(static_cast<size_t>(trials) * sizeof(int32_t));
+  r->o_abort = r->o_done + 256;
+  r->bytes = r->o_abort + 256;
+  if (e == cudaSuccess) e = dev_malloc_async(reinterpret_cast<void**>(&r->d), r->bytes, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d + o_split, fp.split.data(), fp.split.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d + o_zero, 0, bytes - o_zero, st);
+    e = cudaMemcpyAsync(r->d + r->o_split, fp.split.data(), fp.split.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                        st);
+  if (e != cudaSuccess) {
+    if (r->d) cudaFreeAsync(r->d, st);
+    delete r;
+    return map_cuda(e);
+  }
+  *out = r;
+  return ISING_OK;
+}
+
+uint32_t* flow_run_thresholds(FlowRun* r) { return reinterpret_cast<uint32_t*>(r->d); }
+
+int flow_run_launch(FlowRun* r, const uint32_t* d_thr, int32_t thr_group_stride, int32_t S, uint32_t k0,
+                    uint64_t seed, const int8_t* init_spins, int8_t* out_spins, int32_t* out_cuts, cudaStream_t st) {
+  ising_problem* p = r->p;
+  const FlowPlan& fp = r->fp;
+  cudaError_t e = cudaMemsetAsync(r->d + r->o_zero, 0, r->bytes - r->o_zero, st);
   if (e == cudaSuccess) {
-    ising::FlowArgs a;
+    FlowArgs a;
     a.flags = p->d_flags;
-    a.thr = reinterpret_cast<const uint32_t*>(d + o_thr);
+    a.thr = d_thr;
+    a.thr_group_stride = thr_group_stride;
     a.init = init_spins;
     a.out_spins = out_spins;
     a.out_cuts = out_cuts;
     a.X = p->X; a.Y = p->Y; a.H = p->H; a.n = p->n;
-    a.T = trials; a.G = fp.G; a.S = S;
-    a.k0 = sweep_offset;
+    a.T = r->trials; a.G = fp.G; a.S = S;
+    a.k0 = k0;
     a.key0 = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
     a.key1 = static_cast<uint32_t>(seed >> 32);
-    for (uint32_t r = 0; r < 10; ++r) {
-      a.rk[2 * r] = a.key0 + r * 0x9E3779B9u;
-      a.rk[2 * r + 1] = a.key1 + r * 0xBB67AE85u;
+    for (uint32_t q = 0; q < 10; ++q) {
+      a.rk[2 * q] = a.key0 + q * 0x9E3779B9u;
+      a.rk[2 * q + 1] = a.key1 + q * 0xBB67AE85u;
     }
     a.RT = fp.RT;
     a.P = fp.P;
     a.LRmax = fp.LRmax;
     a.neg_edges = p->neg_edges;
-    a.split = reinterpret_cast<const int32_t*>(d + o_split);
-    a.gm = reinterpret_cast<uint32_t*>(d + o_gm);
-    a.gcnt = reinterpret_cast<uint32_t*>(d + o_gcnt);
-    a.acc = reinterpret_cast<int32_t*>(d + o_acc);
-    a.done = reinterpret_cast<uint32_t*>(d + o_done);
-    a.abort_flag = reinterpret_cast<uint32_t*>(d + o_abort);
+    a.split = reinterpret_cast<const int32_t*>(r->d + r->o_split);
+    a.gm = reinterpret_cast<uint32_t*>(r->d + r->o_gm);
+    a.gcnt = reinterpret_cast<uint32_t*>(r->d + r->o_zero);
+    a.acc = reinterpret_cast<int32_t*>(r->d + r->o_acc);
+    a.done = reinterpret_cast<uint32_t*>(r->d + r->o_done);
+    a.abort_flag = reinterpret_cast<uint32_t*>(r->d + r->o_abort);
     a.status = p->d_status;
     a.spin_limit = p->wait_limit > 0 ? p->wait_limit : 4000000000LL;
     a.stall_test = p->stall_test;
     a.u16 = p->draw_bits == 16 ? 1 : 0;
-    e = ising::launch_flow(a, st);
+    e = launch_flow(a, st);
   }
-  const cudaError_t e2 = cudaFreeAsync(d, st);
-  if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) return map_cuda(e);
   p->last_kernel = 2;
   p->last_group = fp.G;
   p->last_strips = 0;
-  p->last_threads = ising::flow_threads();
+  p->last_threads = flow_threads();
   p->last_grid = fp.P;
-  log_launch(p, trials, S);
   return ISING_OK;
+}
+
+void flow_run_destroy(FlowRun* r, cudaStream_t st) {
+  if (!r) return;
+  if (r->d) cudaFreeAsync(r->d, st);
+  delete r;
+}
+
+}  // namespace ising
+
+namespace {
+
+int run_flow(ising_problem* p, int32_t trials, const std::vector<uint32_t>& thr, int32_t S, uint64_t seed,
+             uint32_t sweep_offset, const int8_t* init_spins, int8_t* out_spins, int32_t* out_cuts, cudaStream_t st) {
+  FlowRun* r = nullptr;
+  int rc = ising::flow_run_create(p, trials, thr.size(), &r, st);
+  if (rc != ISING_OK) return rc;
+  cudaError_t e = cudaSuccess;
+  if (!thr.empty())
+    e = cudaMemcpyAsync(ising::flow_run_thresholds(r), thr.data(), thr.size() * sizeof(uint32_t),
+                        cudaMemcpyHostToDevice, st);
+  rc = e == cudaSuccess ? ising::flow_run_launch(r, ising::flow_run_thresholds(r), 0, S, sweep_offset, seed,
+                                                 init_spins, out_spins, out_cuts, st)
+                        : map_cuda(e);
+  ising::flow_run_destroy(r, st);
+  if (rc == ISING_OK) log_launch(p, trials, S);
+  return rc;
 }
 
 
@@ -726,16 +790,8 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
     kind = (p->cfg_strips == 0 && p->n >= 2048 && rows >= 4LL * num_sms_of(p->device)) ? 2 : 1;
   }
   if (kind == 2) {
-    FlowPlan fp;
-    int frc;
-    try {
-      frc = plan_flow(p, trials, &fp);
-      if (frc == ISING_ERR_UNSUPPORTED) frc = plan_flow(p, trials, &fp, false);
-    } catch (const std::bad_alloc&) {
-      return ISING_ERR_OOM;
-    }
-    if (frc == ISING_OK) return run_flow(p, fp, trials, thr, S, seed, sweep_offset, init_spins, out_spins, out_cuts, st);
-    if (p->cfg_kernel == 2) return frc;
+    const int frc = run_flow(p, trials, thr, S, seed, sweep_offset, init_spins, out_spins, out_cuts, st);
+    if (frc != ISING_ERR_UNSUPPORTED || p->cfg_kernel == 2) return frc;
   }
   Shape sh;
   const int rc = choose_shape(p, trials, &sh);

@@ -52,6 +52,7 @@ struct FlowSmem {
   int32_t* r_xself;    // [LR] global row if another CTA owns some of its words, else -1
   int32_t* oitem;      // [LR + 1] first item of the oi-th row of the processing order
   uint4* whead;        // [warps][kMaxSeg][8] per-warp Philox heads
+  uint2* wthr;         // [warps][kMaxSeg] per-warp (T4, T8) of each segment's group
   int32_t* meta;       // [8]: nown, nloc, nseg, ...
   int32_t* seg_g;      // [kMaxSeg] group of each segment
   int4* rowc;          // [2][LR + 1][2] per colour and local row: see the table build
@@ -69,7 +70,7 @@ __host__ __device__ inline size_t flow_smem_layout(int32_t LR, int32_t H, size_t
   off[1] = o; o += align16(static_cast<size_t>(2) * LR * H + 1);        // fl (+ spare byte)
   off[2] = o; o += align16(static_cast<size_t>(2) * (LR + 1) * 4);      // rowcnt
   off[3] = o; o += align16(static_cast<size_t>(12) * (LR + 1) * 4);     // row tables (12 arrays)
-  off[4] = o; o += static_cast<size_t>(kFlowWarps) * kMaxSeg * 8 * 16;   // whead
+  off[4] = o; o += static_cast<size_t>(kFlowWarps) * kMaxSeg * (8 * 16 + 8);   // whead, wthr
   off[5] = o; o += 16 * 4;                                               // meta + seg_g
   off[6] = o; o += static_cast<size_t>(2) * (LR + 1) * 2 * 16;          // rowc
   off[7] = o; o += flow_items_cap(LR, H) * 8;                           // xtab
@@ -98,6 +99,7 @@ __device__ __forceinline__ FlowSmem flow_carve(unsigned char* smem, int32_t LR, 
   s.r_xself = t + 10 * L1;
   s.oitem = t + 11 * L1;
   s.whead = reinterpret_cast<uint4*>(smem + off[4]);
+  s.wthr = reinterpret_cast<uint2*>(smem + off[4] + static_cast<size_t>(kFlowWarps) * kMaxSeg * 8 * 16);
   s.meta = reinterpret_cast<int32_t*>(smem + off[5]);
   s.seg_g = s.meta + 8;
   s.rowc = reinterpret_cast<int4*>(smem + off[6]);
@@ -158,7 +160,8 @@ __device__ __noinline__ bool wait_count(const uint32_t* gp, uint32_t saddr, uint
   }
 }
 
-template <bool kU16>
+// kGroupThr: every trial group has its own threshold table (a.thr_group_stride)
+template <bool kU16, bool kGroupThr>
 __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __grid_constant__ FlowArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int j = blockIdx.x;
@@ -366,6 +369,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   // ---- the half-sweeps, chunk by chunk
   const long long M = 2LL * a.S * NC;
   uint4* wh = sm.whead + warp * (kMaxSeg * 8);
+  uint2* wt = sm.wthr + warp * kMaxSeg;
   const uint32_t sp32 = smem_addr(sm.sp), fl32 = smem_addr(sm.fl), cnt32 = smem_addr(sm.rowcnt);
   const uint32_t rowc32 = smem_addr(sm.rowc), xt32 = smem_addr(sm.xtab) + 8u * lane, wh32 = smem_addr(wh);
   int head_kk = -1;
@@ -380,6 +384,12 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
         const int s = lane >> 3, jq = lane & 7;
         const uint32_t q = decision_block0<kU16>(sm.seg_g[s] * a.G) + jq;
         wh[lane] = philox_head_sweep_quad(a.k0 + static_cast<uint32_t>(kk), q, a.key0, a.key1);
+      }
+      if constexpr (kGroupThr) {
+        if (lane < nseg) {
+          const uint32_t* t = a.thr + static_cast<size_t>(sm.seg_g[lane]) * a.thr_group_stride + 2 * kk;
+          wt[lane] = make_uint2(__ldg(t), __ldg(t + 1));
+        }
       }
       __syncwarp();
       T4 = __ldg(a.thr + 2 * kk);
@@ -448,10 +458,12 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       nu = gu ? __ldcg(a.gm + static_cast<size_t>(B.x) * H + h) : lds_u32(a_up);
       nd = gd ? __ldcg(a.gm + static_cast<size_t>(B.y) * H + h) : lds_u32(a_dn);
     }
+    uint2 tq = make_uint2(T4, T8);
+    if constexpr (kGroupThr) tq = wt[(A.z & 0xFF) >> 3];
     const uint32_t ns = update_word_h<kU16>(lds_u32(sp32 + 4u * own), nl, nr, nu, nd, lds_u8(fl32 + own),
                                             static_cast<uint32_t>(A.y) + 2u * h,
                                             HeadsShared{wh32 + 16u * (static_cast<uint32_t>(A.z) & 0xFFu)},
-                                            (A.z >> 8) & 0xFF, T4, T8, a.rk);
+                                            (A.z >> 8) & 0xFF, tq.x, tq.y, a.rk);
     sts_u32(sp32 + 4u * own, ns);
     if (mirror && B.z >= 0) {   // published row: mirror word, then count it at GPU scope
       __stcg(a.gm + static_cast<size_t>(B.z) * H + h, ns);
@@ -578,11 +590,11 @@ size_t flow_smem_bytes(int32_t LR, int32_t H) {
 int flow_threads() { return kFlowThreads; }
 int flow_max_segments() { return kMaxSeg; }
 
-template <bool kU16>
+template <bool kU16, bool kGroupThr>
 cudaError_t launch_flow_mode(const FlowArgs& a, cudaStream_t stream) {
   const size_t smem = flow_smem_bytes(a.LRmax, a.H);
-  cudaError_t e = cudaFuncSetAttribute(anneal_flow_kernel<kU16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  cudaError_t e = cudaFuncSetAttribute(anneal_flow_kernel<kU16, kGroupThr>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.P, 1, 1);
@@ -594,24 +606,29 @@ cudaError_t launch_flow_mode(const FlowArgs& a, cudaStream_t stream) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, anneal_flow_kernel<kU16>, a);
+  return cudaLaunchKernelEx(&cfg, anneal_flow_kernel<kU16, kGroupThr>, a);
 }
 
 cudaError_t launch_flow(const FlowArgs& a, cudaStream_t stream) {
-  return a.u16 ? launch_flow_mode<true>(a, stream) : launch_flow_mode<false>(a, stream);
+  if (a.thr_group_stride > 0)
+    return a.u16 ? launch_flow_mode<true, true>(a, stream) : launch_flow_mode<false, true>(a, stream);
+  return a.u16 ? launch_flow_mode<true, false>(a, stream) : launch_flow_mode<false, false>(a, stream);
 }
 
 cudaError_t flow_max_ctas(size_t smem, int* per_sm) {
-  int both[2] = {0, 0};
-  for (int m = 0; m < 2; ++m) {
-    const void* fn = m ? reinterpret_cast<const void*>(anneal_flow_kernel<true>)
-                       : reinterpret_cast<const void*>(anneal_flow_kernel<false>);
+  const void* fns[4] = {reinterpret_cast<const void*>(anneal_flow_kernel<false, false>),
+                        reinterpret_cast<const void*>(anneal_flow_kernel<true, false>),
+                        reinterpret_cast<const void*>(anneal_flow_kernel<false, true>),
+                        reinterpret_cast<const void*>(anneal_flow_kernel<true, true>)};
+  *per_sm = 1 << 30;
+  for (const void* fn : fns) {
+    int v = 0;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&both[m], fn, kFlowThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn, kFlowThreads, smem);
     if (e != cudaSuccess) return e;
+    if (v < *per_sm) *per_sm = v;
   }
-  *per_sm = both[0] < both[1] ? both[0] : both[1];
   return cudaSuccess;
 }
 

@@ -97,12 +97,32 @@ struct FlowArgs {
   long long spin_limit;     // cycles one wait may take
   int32_t stall_test;       // 1: the first chunk of CTA 0 waits for a count nothing reaches
   int32_t u16;              // 1: 16-bit draw mode
+  int32_t thr_group_stride; // 0: one table for all groups; else group g's table at thr + g * stride
 };
 size_t flow_smem_bytes(int32_t LR, int32_t H);
 int flow_threads();
 int flow_max_segments();
 cudaError_t launch_flow(const FlowArgs& a, cudaStream_t stream);
 cudaError_t flow_max_ctas(size_t smem, int* per_sm);
+
+}  // namespace ising
+
+// A persistent flow-kernel run planned and allocated once for repeated
+// launches on one problem (abi.cu).
+struct FlowRun;
+
+namespace ising {
+
+// Plans the run for `trials` trials and allocates its device arena, with room
+// for `thr_words` threshold words (flow_run_thresholds).  Returns
+// ISING_ERR_UNSUPPORTED when the flow kernel cannot take the problem.
+int flow_run_create(ising_problem* p, int32_t trials, size_t thr_words, FlowRun** out, cudaStream_t st);
+uint32_t* flow_run_thresholds(FlowRun* r);
+// One launch: S sweeps from sweep k0 with the thresholds at d_thr (group g's
+// at d_thr + g * thr_group_stride when the stride is not 0).
+int flow_run_launch(FlowRun* r, const uint32_t* d_thr, int32_t thr_group_stride, int32_t S, uint32_t k0,
+                    uint64_t seed, const int8_t* init_spins, int8_t* out_spins, int32_t* out_cuts, cudaStream_t st);
+void flow_run_destroy(FlowRun* r, cudaStream_t st);
 
 // One 3x3 circular convolution layer on the tensor cores (conv_tc.cu).
 struct TcConvArgs {

@@ -146,6 +146,19 @@ extern "C" int ising_anneal_pt(ising_problem* p, int32_t temps, const double* be
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_sthr, sthr.data(), sthr.size() * 4, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && out_swaps) e = cudaMemsetAsync(out_swaps, 0, sizeof(int32_t), st);
 
+  // the persistent flow kernel (per-group threshold tables) when it takes
+  // the problem, as ising_anneal would choose it; else the strip kernel
+  FlowRun* fr = nullptr;
+  if (e == cudaSuccess && p->cfg_kernel != 1 && p->cfg_strips == 0 && (p->cfg_group == 0 || p->cfg_group == 32) &&
+      n >= 2048 && static_cast<long long>(groups) * p->Y >= 4LL * sms) {
+    const int rc = ising::flow_run_create(p, T, 0, &fr, st);
+    if (rc != ISING_OK && rc != ISING_ERR_UNSUPPORTED) {
+      cudaFreeAsync(d, st);
+      return rc;
+    }
+  }
+  const int32_t stride = 2 * (L > 0 ? L : 1);
+
   ising::AnnealArgs a{};
   a.flags = p->d_flags;
   a.thr = d_thr;
@@ -171,7 +184,12 @@ extern "C" int ising_anneal_pt(ising_problem* p, int32_t temps, const double* be
     a.out_spins = (rounds % 2 == 0) ? out_spins : other;
     a.S = 0;
     a.k0 = 0;
-    e = ising::launch_anneal(a, threads, st);
+    if (fr) {
+      const int rc = ising::flow_run_launch(fr, d_thr, stride, 0, 0, seed, nullptr, a.out_spins, out_cuts, st);
+      e = rc == ISING_OK ? cudaSuccess : cudaErrorUnknown;
+    } else {
+      e = ising::launch_anneal(a, threads, st);
+    }
     cur = a.out_spins;
   }
   for (int32_t q = 0; q < rounds && e == cudaSuccess; ++q) {
@@ -180,7 +198,12 @@ extern "C" int ising_anneal_pt(ising_problem* p, int32_t temps, const double* be
     a.out_spins = nxt;
     a.S = L;
     a.k0 = static_cast<uint32_t>(q) * static_cast<uint32_t>(L);
-    e = ising::launch_anneal(a, threads, st);
+    if (fr) {
+      const int rc = ising::flow_run_launch(fr, d_thr, stride, L, a.k0, seed, cur, nxt, out_cuts, st);
+      e = rc == ISING_OK ? cudaSuccess : cudaErrorUnknown;
+    } else {
+      e = ising::launch_anneal(a, threads, st);
+    }
     const int par = q & 1;
     const int npairs = temps - 1 > par ? (temps - 1 - par + 1) / 2 : 0;
     if (e == cudaSuccess && npairs > 0) {
@@ -190,6 +213,8 @@ extern "C" int ising_anneal_pt(ising_problem* p, int32_t temps, const double* be
     }
     cur = nxt;
   }
+  if (!fr && e == cudaSuccess) p->last_kernel = 1;
+  ising::flow_run_destroy(fr, st);
   const cudaError_t e2 = cudaFreeAsync(d, st);
   if (e == cudaSuccess) e = e2;
   return map_err(e);

@@ -26,6 +26,9 @@ CASES = [
     (16, 8, 3, [0.9], 32, 3, 7),                 # one temperature: no swaps
     (12, 10, 4, [0.5, 0.5, 0.5], 32, 4, 2),      # equal temperatures: every swap taken
     (40, 30, 5, [0.3, 0.8], 32, 0, 5),           # no rounds: the start
+    # large enough for the persistent kernel (per-group threshold tables)
+    (64, 48, 7, [0.3, 0.6, 1.1, 2.0], 128, 4, 6),
+    (64, 48, 8, [0.2, 0.35, 0.5, 0.7, 0.9, 1.2, 1.6, 2.4], 64, 5, 5),
 ]
 
 
@@ -53,4 +56,23 @@ def test_pt_arguments(ia):
         kw.update(bad)
         with pytest.raises(ia.IsingError):
             ia.anneal_pt(prob, kw["betas"], kw["chains"], 2, 2, 1)
+    prob.destroy()
+
+
+def test_pt_persistent_kernel_equals_strip_kernel(ia):
+    """The headline-sized exchange (200 x 100, 8 temperatures x 128 chains)
+    takes the persistent kernel; forcing the strip kernel gives the same
+    spins, cuts and swap count."""
+    import torch
+    inst = synth.torus_instance(200, 100, 9)
+    betas = list(np.geomspace(0.5, 3.0, 8))
+    prob = ia.Problem.from_instance(inst)
+    a = ia.anneal_pt(prob, betas, 128, 10, 20, 77)
+    torch.cuda.synchronize()
+    assert prob.last_kernel() == 2
+    prob.set_kernel(1)
+    b = ia.anneal_pt(prob, betas, 128, 10, 20, 77)
+    torch.cuda.synchronize()
+    assert prob.last_kernel() == 1
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and int(a[2].item()) == int(b[2].item())
     prob.destroy()
