@@ -201,6 +201,18 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
 int ising_set_kernel(ising_problem* p, int32_t kind);
 
 /*
+ * ising_set_graph_threads_per_site -- general-graph handles: how many
+ * threads share one site word's update in ising_anneal (Section II's general
+ * form; the sweep and its decisions are unchanged).  1: one thread counts the
+ * neighbours and draws all Philox blocks; 4 or 8: the threads split the
+ * neighbours and the blocks and combine their counts with warp shuffles, for
+ * graphs whose colour classes are too small to occupy the GPU one word per
+ * thread.  0 (default) chooses by the average class size.  Results do not
+ * depend on it.  Errors: ISING_ERR_ARG (NULL handle, other values).
+ */
+int ising_set_graph_threads_per_site(ising_problem* p, int32_t threads_per_site);
+
+/*
  * ising_philox -- the library's Philox4x32-10 generator (Salmon et al.,
  * SC'11), the source of every start spin and decision draw: for each of k
  * counters ctr[j] (device uint32 [k][4], 16-byte aligned) writes the block

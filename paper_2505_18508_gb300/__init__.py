@@ -120,6 +120,11 @@ class Problem:
         """0 automatic, 1 cluster-strip kernel, 2 persistent kernel."""
         check(lib().ising_set_kernel(self.handle, int(kind)), "ising_set_kernel")
 
+    def set_graph_threads_per_site(self, tpw):
+        """General graphs: threads that share one site word's update (1, 4 or
+        8; 0 automatic)."""
+        check(lib().ising_set_graph_threads_per_site(self.handle, int(tpw)), "ising_set_graph_threads_per_site")
+
     def last_kernel(self):
         v = ctypes.c_int32()
         check(lib().ising_last_kernel(self.handle, ctypes.byref(v)), "ising_last_kernel")

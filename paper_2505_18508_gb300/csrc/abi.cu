@@ -579,6 +579,15 @@ int run_graph(ising_problem* p, int32_t trials, const double* betas, int32_t S, 
   a.k0 = sweep_offset;
   a.key0 = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
   a.key1 = static_cast<uint32_t>(seed >> 32);
+  // threads per site word: a team of 8 or 4 when a CTA's share of an average
+  // colour class leaves most of its threads idle (small graphs), else 1
+  int tpw = p->cfg_graph_tpw;
+  if (tpw == 0) {
+    const double words = static_cast<double>(p->n) / (p->ncol > 0 ? p->ncol : 1) / C;
+    const double slots = 2.0 * ising::graph_threads();
+    tpw = words * 8 <= slots ? 8 : (words * 4 <= slots ? 4 : 1);
+  }
+  a.tpw = tpw;
   cudaError_t e = ising::launch_graph(a, st);
   if (d_thr) {
     const cudaError_t e2 = cudaFreeAsync(d_thr, st);
@@ -732,6 +741,13 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
 int ising_set_draw_bits(ising_problem* p, int32_t bits) {
   if (!p || (bits != 32 && bits != 16)) return ISING_ERR_ARG;
   p->draw_bits = bits;
+  return ISING_OK;
+}
+
+int ising_set_graph_threads_per_site(ising_problem* p, int32_t threads_per_site) {
+  if (!p || !(threads_per_site == 0 || threads_per_site == 1 || threads_per_site == 4 || threads_per_site == 8))
+    return ISING_ERR_ARG;
+  p->cfg_graph_tpw = threads_per_site;
   return ISING_OK;
 }
 

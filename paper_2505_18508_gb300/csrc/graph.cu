@@ -111,7 +111,68 @@ __device__ __forceinline__ uint32_t graph_update(const GraphArgs& a, const uint3
   return b ^ flip;
 }
 
-template <bool kCluster, int kP>
+// graph_update split over a team of kTPW consecutive lanes: lane r of the
+// team counts the neighbours e = r, r + kTPW, ... into its own bit-sliced
+// counter, the team adds the counters up (butterfly over xor shuffles; every
+// partial sum is at most the total, so kP planes hold it), and lane r draws
+// the decision blocks jq = r, r + kTPW, ...; the accepted trials are OR-ed
+// back together.  The decisions are those of graph_update.  Every lane of
+// the warp must call it (inactive teams with active = false).
+template <int kP, int kTPW>
+__device__ __forceinline__ uint32_t graph_update_team(const GraphArgs& a, const uint32_t* sp, const uint32_t* thr,
+                                                      uint32_t i, uint32_t k, uint32_t q0, int nq, int r,
+                                                      bool active) {
+  uint32_t b = 0u;
+  int4 ri = make_int4(0, 0, 0, 0);
+  if (active) {
+    b = sp[i];
+    ri = __ldg(a.rowinfo + i);
+  }
+  uint32_t pl[kP];
+#pragma unroll
+  for (int p = 0; p < kP; ++p) pl[p] = 0u;
+  for (int e = r; e < ri.y; e += kTPW) {
+    const uint32_t v = __ldg(a.nb + ri.x + e);
+    const uint32_t j = v & 0xFFFFFFu;
+    const uint32_t neg = 0u - ((v >> 24) & 1u);
+    add_weighted<kP>(pl, ~(b ^ sp[j]) ^ neg, (v >> 25) + 1u);
+  }
+  if (r == 0 && ri.z != 0) add_weighted<kP>(pl, ri.z > 0 ? b : ~b, static_cast<uint32_t>(ri.z > 0 ? ri.z : -ri.z));
+#pragma unroll
+  for (int off = 1; off < kTPW; off <<= 1) {
+    uint32_t carry = 0u;
+#pragma unroll
+    for (int p = 0; p < kP; ++p) {
+      const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, pl[p], off);
+      const uint32_t x = pl[p] ^ o;               // full adder, bit-sliced
+      const uint32_t c_out = (pl[p] & o) | (carry & x);
+      pl[p] = x ^ carry;
+      carry = c_out;
+    }
+  }
+  const uint32_t D = static_cast<uint32_t>(ri.w);
+  const uint32_t up = ge_const<kP>(pl, D / 2 + 1);   // 2a > D: uphill
+  uint32_t acc = 0u;
+  for (int jq = r; jq < nq; jq += kTPW) {
+    const uint32_t m4 = (up >> (4 * jq)) & 0xFu;
+    if (!m4) continue;
+    const uint4 u = philox4x32_10(i, k, q0 + jq, 0u, a.key0, a.key1);
+    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if ((m4 >> m) & 1u) {
+        const int t = 4 * jq + m;
+        const uint32_t q = 2u * lane_value<kP>(pl, t) - D;   // dE / 2, 1 .. D
+        if (uu[m] < thr[q]) acc |= 1u << t;
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < kTPW; off <<= 1) acc |= __shfl_xor_sync(0xFFFFFFFFu, acc, off);
+  return b ^ (~up | acc);
+}
+
+template <bool kCluster, int kP, int kTPW>
 __global__ void __launch_bounds__(kGraphThreads, 1) graph_anneal_kernel(const __grid_constant__ GraphArgs a) {
   extern __shared__ __align__(16) uint32_t gsm[];
   uint32_t* sp = gsm;                       // [n] spin words of the group
@@ -151,14 +212,35 @@ __global__ void __launch_bounds__(kGraphThreads, 1) graph_anneal_kernel(const __
       const int beg = __ldg(a.colour_off + c), len = __ldg(a.colour_off + c + 1) - beg;
       const int my0 = beg + static_cast<int>((static_cast<long long>(len) * rank) / C);
       const int my1 = beg + static_cast<int>((static_cast<long long>(len) * (rank + 1)) / C);
-      for (int idx = my0 + tid; idx < my1; idx += nt) {
-        const uint32_t i = static_cast<uint32_t>(__ldg(a.sites + idx));
-        const uint32_t w = graph_update<kP>(a, sp, thr, i, k, q0, nq);
-        sp[i] = w;
-        if constexpr (kCluster) {
-          const uint32_t addr = smem_addr(sp + i);
-          for (int r = 0; r < C; ++r)
-            if (r != static_cast<int>(rank)) st_cluster_u32(addr, static_cast<uint32_t>(r), w);
+      if constexpr (kTPW == 1) {
+        for (int idx = my0 + tid; idx < my1; idx += nt) {
+          const uint32_t i = static_cast<uint32_t>(__ldg(a.sites + idx));
+          const uint32_t w = graph_update<kP>(a, sp, thr, i, k, q0, nq);
+          sp[i] = w;
+          if constexpr (kCluster) {
+            const uint32_t addr = smem_addr(sp + i);
+            for (int r = 0; r < C; ++r)
+              if (r != static_cast<int>(rank)) st_cluster_u32(addr, static_cast<uint32_t>(r), w);
+          }
+        }
+      } else {
+        // teams of kTPW lanes per site word; the loop is warp-uniform so that
+        // every lane takes part in the team shuffles
+        constexpr int kWpw = 32 / kTPW;   // site words per warp and pass
+        const int lane = tid & 31, r = lane % kTPW;
+        for (int base = (tid >> 5) * kWpw; base < my1 - my0; base += (nt >> 5) * kWpw) {
+          const int wi = base + lane / kTPW;
+          const bool act = wi < my1 - my0;
+          const uint32_t i = act ? static_cast<uint32_t>(__ldg(a.sites + my0 + wi)) : 0u;
+          const uint32_t w = graph_update_team<kP, kTPW>(a, sp, thr, i, k, q0, nq, r, act);
+          if (act) {
+            if (r == 0) sp[i] = w;
+            if constexpr (kCluster) {
+              const uint32_t addr = smem_addr(sp + i);
+              for (int rr = r; rr < C; rr += kTPW)
+                if (rr != static_cast<int>(rank)) st_cluster_u32(addr, static_cast<uint32_t>(rr), w);
+            }
+          }
         }
       }
       if constexpr (kCluster) cluster_barrier();
@@ -244,8 +326,8 @@ __global__ void graph_measure_kernel(const GraphArgs a, const int8_t* __restrict
   }
 }
 
-template <int kP>
-cudaError_t launch_graph_p(const GraphArgs& a, cudaStream_t st) {
+template <int kP, int kTPW>
+cudaError_t launch_graph_pt(const GraphArgs& a, cudaStream_t st) {
   const size_t smem = graph_smem_bytes(a.n, a.Dmax);
   const int groups = (a.T + 31) / 32;
   cudaLaunchConfig_t cfg = {};
@@ -256,7 +338,7 @@ cudaError_t launch_graph_p(const GraphArgs& a, cudaStream_t st) {
   cudaLaunchAttribute attr[1];
   cudaError_t e;
   if (a.C > 1) {
-    e = cudaFuncSetAttribute(graph_anneal_kernel<true, kP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(graph_anneal_kernel<true, kP, kTPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -265,12 +347,21 @@ cudaError_t launch_graph_p(const GraphArgs& a, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, graph_anneal_kernel<true, kP>, a);
+    return cudaLaunchKernelEx(&cfg, graph_anneal_kernel<true, kP, kTPW>, a);
   }
-  e = cudaFuncSetAttribute(graph_anneal_kernel<false, kP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(graph_anneal_kernel<false, kP, kTPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem));
   if (e != cudaSuccess) return e;
-  return cudaLaunchKernelEx(&cfg, graph_anneal_kernel<false, kP>, a);
+  return cudaLaunchKernelEx(&cfg, graph_anneal_kernel<false, kP, kTPW>, a);
+}
+
+template <int kP>
+cudaError_t launch_graph_p(const GraphArgs& a, cudaStream_t st) {
+  switch (a.tpw) {
+    case 8: return launch_graph_pt<kP, 8>(a, st);
+    case 4: return launch_graph_pt<kP, 4>(a, st);
+    default: return launch_graph_pt<kP, 1>(a, st);
+  }
 }
 
 }  // namespace

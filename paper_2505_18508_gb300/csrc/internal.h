@@ -21,6 +21,7 @@ struct ising_problem {
   int32_t* d_status = nullptr;
   // launch overrides (0 = automatic) and the last shape used
   int32_t cfg_group = 0, cfg_strips = 0, cfg_threads = 0, cfg_kernel = 0;
+  int32_t cfg_graph_tpw = 0;       // general graphs: threads per site word (0: automatic)
   int32_t draw_bits = 32;   // 32: the default decision stream; 16: the 16-bit draw mode
   int32_t last_group = 0, last_strips = 0, last_threads = 0, last_grid = 0, last_kernel = 0;
   // bounded-wait limit (cycles) and the forced-stall switch used by tests
@@ -201,6 +202,7 @@ struct GraphArgs {
   int32_t Dmax, planes, ncol;
   int32_t T, S, C;           // trials, sweeps, CTAs per 32-trial group (cluster size)
   uint32_t k0, key0, key1;
+  int32_t tpw;               // threads per site word: 1, 4 or 8
 };
 size_t graph_smem_bytes(int32_t n, int32_t Dmax);
 int graph_threads();

@@ -134,3 +134,43 @@ def test_graph_errors(ia):
         ia.propose(prob, s, torch.zeros((2, g["n"]), device="cuda"), 0)
     net.destroy()
     prob.destroy()
+
+
+TEAM_CASES = [
+    # n, m, graph seed, weights, hmax, trials, sweeps, strips
+    (2000, 19990, 22, "one", 0, 96, 12, 0),    # G22-like: small colour classes
+    (600, 3000, 31, "int", 3, 70, 15, 2),      # fields, integer weights, ragged trials
+    (3000, 9000, 32, "pm1", 1, 33, 10, 8),
+]
+
+
+@pytest.mark.parametrize("tpw", [1, 4, 8])
+@pytest.mark.parametrize("n,m,gseed,weights,hmax,trials,S,C", TEAM_CASES)
+def test_graph_threads_per_site_parity(ia, n, m, gseed, weights, hmax, trials, S, C, tpw):
+    """A site word's update split over 1, 4 or 8 threads (neighbour counts
+    summed with shuffles, Philox blocks shared out) gives the oracle's
+    trajectory bit for bit."""
+    import torch
+    g = synth.random_graph(n, m, gseed, weights=weights, hmax=hmax)
+    betas = synth.linear_betas(0.1, 3.0, S)
+    seed = 0x7B0000 + gseed
+    prob = ia.Problem.from_graph(g)
+    if C:
+        prob.set_launch(0, C, 0)
+    prob.set_graph_threads_per_site(tpw)
+    spins, cuts = ia.anneal(prob, trials, betas, seed)
+    torch.cuda.synchronize()
+    sub = min(trials, 40)
+    rs, rc = oracle.anneal_graph(g, betas, seed, sub)
+    np.testing.assert_array_equal(spins.cpu().numpy()[:sub], rs)
+    np.testing.assert_array_equal(cuts.cpu().numpy()[:sub], rc)
+    prob.destroy()
+
+
+def test_graph_threads_per_site_arguments(ia):
+    g = synth.random_graph(50, 100, 33, weights="pm1")
+    prob = ia.Problem.from_graph(g)
+    for bad in (2, 3, 16, -1):
+        with pytest.raises(ia.IsingError):
+            prob.set_graph_threads_per_site(bad)
+    prob.destroy()
