@@ -515,6 +515,8 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_throughput(w, inst)
+        one = oracle_throughput(w, inst, sweeps=1000, procs=1)   # the oracle on a single host core
+        cpu["single_core"] = {"value": one["value"], "sample": one["sample"]}
     # ---- the 16-bit draw mode on the same workload (one Philox block per
     # eight trials): a variant line, not the headline stream
     draw16 = None
