@@ -131,8 +131,10 @@ def oracle_throughput(w, inst, sweeps=3000, trials_per_proc=1, procs=None):
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(procs) as pool:
-        pool.map(_oracle_slice, jobs)
+        times = pool.map(_oracle_slice, jobs)
     wall = time.perf_counter() - t0
+    if procs == 1:          # one core: the worker's own time, without the process start-up
+        wall = times[0]
     ups = procs * trials_per_proc * sweeps * w["X"] * w["Y"]
     return {"value": ups / wall, "unit": "spin-updates/s", "cores": procs, "kind": "oracle",
             "sample": f"{procs} processes x {trials_per_proc} trial(s) x first {sweeps} sweeps of the "
