@@ -95,3 +95,13 @@ def test_ragged_trials_at_size(ia, trials):
         np.testing.assert_array_equal(s[t], rs[0])
         assert cuts[t].item() == rc[0]
     prob.destroy()
+
+
+@pytest.mark.parametrize("kernel,bits", [(1, 32), (2, 32), (2, 16)])
+def test_sweep_by_sweep_no_divergence(ia, kernel, bits):
+    """The debugging aid that steps both sides one sweep at a time finds no
+    divergent sweep (and the chained one-sweep calls are themselves the
+    resume property, sweep by sweep)."""
+    from tests import first_divergence
+    X, Y, T = (64, 48, 96) if kernel == 2 else (8, 6, 37)
+    assert first_divergence.first_divergence(X, Y, 3, T, 6, 4242, kernel=kernel, draw_bits=bits) is None
