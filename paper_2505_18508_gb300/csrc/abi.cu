@@ -579,6 +579,10 @@ int run_graph(ising_problem* p, int32_t trials, const double* betas, int32_t S, 
   a.k0 = sweep_offset;
   a.key0 = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
   a.key1 = static_cast<uint32_t>(seed >> 32);
+  for (uint32_t r = 0; r < 10; ++r) {   // Philox round keys (Weyl sequence)
+    a.rk[2 * r] = a.key0 + r * 0x9E3779B9u;
+    a.rk[2 * r + 1] = a.key1 + r * 0xBB67AE85u;
+  }
   // threads per site word: a team of 8 or 4 when a CTA's share of an average
   // colour class leaves most of its threads idle (small graphs), else 1
   int tpw = p->cfg_graph_tpw;

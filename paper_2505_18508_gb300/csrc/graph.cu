@@ -23,8 +23,7 @@
 // shared memory, updates its share of each colour class and stores every new
 // word into all C copies (distributed shared memory); a cluster barrier
 // separates the classes.
-#include "device_common.cuh"
-#include "internal.h"
+#include "anneal_core.cuh"
 
 namespace ising {
 namespace {
@@ -76,7 +75,7 @@ __device__ __forceinline__ uint32_t lane_value(const uint32_t (&pl)[kP], int t) 
 
 template <int kP>
 __device__ __forceinline__ uint32_t graph_update(const GraphArgs& a, const uint32_t* sp, const uint32_t* thr,
-                                                 uint32_t i, uint32_t k, uint32_t q0, int nq) {
+                                                 const uint4* heads, uint32_t i, int nq) {
   const uint32_t b = sp[i];
   const int4 ri = __ldg(a.rowinfo + i);        // {first entry, degree, h, D}
   uint32_t pl[kP];
@@ -93,10 +92,16 @@ __device__ __forceinline__ uint32_t graph_update(const GraphArgs& a, const uint3
   const uint32_t up = ge_const<kP>(pl, D / 2 + 1);   // 2a > D: uphill
   uint32_t flip = ~up;
   if (up) {
+    // Philox4x32-10 at (i, k, q0 + jq, 0): the site's products of rounds 1-2
+    // here, the (sweep, block) part from the per-sweep heads
+    uint32_t hi0, lo0, hi1, lo1;
+    mulhilo(kPhiloxM0, i, hi0, lo0);
+    mulhilo(kPhiloxM1, hi0 ^ a.rk[1], hi1, lo1);
     for (int jq = 0; jq < nq; ++jq) {
       const uint32_t m4 = (up >> (4 * jq)) & 0xFu;
       if (!m4) continue;
-      const uint4 u = philox4x32_10(i, k, q0 + jq, 0u, a.key0, a.key1);
+      const uint4 hd = heads[jq];
+      const uint4 u = philox_rounds_3_to_10(hi1 ^ hd.x, lo1, hd.y ^ lo0, hd.z, a.rk);
       const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
@@ -120,8 +125,7 @@ __device__ __forceinline__ uint32_t graph_update(const GraphArgs& a, const uint3
 // the warp must call it (inactive teams with active = false).
 template <int kP, int kTPW>
 __device__ __forceinline__ uint32_t graph_update_team(const GraphArgs& a, const uint32_t* sp, const uint32_t* thr,
-                                                      uint32_t i, uint32_t k, uint32_t q0, int nq, int r,
-                                                      bool active) {
+                                                      const uint4* heads, uint32_t i, int nq, int r, bool active) {
   uint32_t b = 0u;
   int4 ri = make_int4(0, 0, 0, 0);
   if (active) {
@@ -153,10 +157,16 @@ __device__ __forceinline__ uint32_t graph_update_team(const GraphArgs& a, const 
   const uint32_t D = static_cast<uint32_t>(ri.w);
   const uint32_t up = ge_const<kP>(pl, D / 2 + 1);   // 2a > D: uphill
   uint32_t acc = 0u;
+  uint32_t hi0 = 0u, lo0 = 0u, hi1 = 0u, lo1 = 0u;
+  if (up) {
+    mulhilo(kPhiloxM0, i, hi0, lo0);
+    mulhilo(kPhiloxM1, hi0 ^ a.rk[1], hi1, lo1);
+  }
   for (int jq = r; jq < nq; jq += kTPW) {
     const uint32_t m4 = (up >> (4 * jq)) & 0xFu;
     if (!m4) continue;
-    const uint4 u = philox4x32_10(i, k, q0 + jq, 0u, a.key0, a.key1);
+    const uint4 hd = heads[jq];
+    const uint4 u = philox_rounds_3_to_10(hi1 ^ hd.x, lo1, hd.y ^ lo0, hd.z, a.rk);
     const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -178,6 +188,7 @@ __global__ void __launch_bounds__(kGraphThreads, 1) graph_anneal_kernel(const __
   uint32_t* sp = gsm;                       // [n] spin words of the group
   uint32_t* thr = gsm + a.n_pad;            // [Dmax + 1]: thr[q] = T(dE = 2q) of the current sweep
   uint32_t* part = thr + a.thr_pad;         // [32] cut partial sums (mod 2^32)
+  uint4* heads = reinterpret_cast<uint4*>(part + 32);   // [8] Philox heads of the current sweep
   const int C = kCluster ? a.C : 1;
   const uint32_t rank = kCluster ? cluster_ctarank() : 0u;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -207,6 +218,7 @@ __global__ void __launch_bounds__(kGraphThreads, 1) graph_anneal_kernel(const __
   for (int kk = 0; kk < a.S; ++kk) {
     const uint32_t k = a.k0 + static_cast<uint32_t>(kk);
     for (int q = tid; q < a.Dmax; q += nt) thr[q + 1] = __ldg(a.thr + static_cast<size_t>(kk) * a.Dmax + q);
+    if (tid < nq) heads[tid] = philox_head_sweep_quad(k, q0 + tid, a.key0, a.key1);
     __syncthreads();
     for (int c = 0; c < a.ncol; ++c) {
       const int beg = __ldg(a.colour_off + c), len = __ldg(a.colour_off + c + 1) - beg;
@@ -215,7 +227,7 @@ __global__ void __launch_bounds__(kGraphThreads, 1) graph_anneal_kernel(const __
       if constexpr (kTPW == 1) {
         for (int idx = my0 + tid; idx < my1; idx += nt) {
           const uint32_t i = static_cast<uint32_t>(__ldg(a.sites + idx));
-          const uint32_t w = graph_update<kP>(a, sp, thr, i, k, q0, nq);
+          const uint32_t w = graph_update<kP>(a, sp, thr, heads, i, nq);
           sp[i] = w;
           if constexpr (kCluster) {
             const uint32_t addr = smem_addr(sp + i);
@@ -232,7 +244,7 @@ __global__ void __launch_bounds__(kGraphThreads, 1) graph_anneal_kernel(const __
           const int wi = base + lane / kTPW;
           const bool act = wi < my1 - my0;
           const uint32_t i = act ? static_cast<uint32_t>(__ldg(a.sites + my0 + wi)) : 0u;
-          const uint32_t w = graph_update_team<kP, kTPW>(a, sp, thr, i, k, q0, nq, r, act);
+          const uint32_t w = graph_update_team<kP, kTPW>(a, sp, thr, heads, i, nq, r, act);
           if (act) {
             if (r == 0) sp[i] = w;
             if constexpr (kCluster) {
@@ -369,7 +381,7 @@ cudaError_t launch_graph_p(const GraphArgs& a, cudaStream_t st) {
 size_t graph_smem_bytes(int32_t n, int32_t Dmax) {
   const size_t n_pad = (static_cast<size_t>(n) + 3) & ~size_t(3);
   const size_t thr_pad = (static_cast<size_t>(Dmax) + 1 + 3) & ~size_t(3);
-  return (n_pad + thr_pad + 32) * sizeof(uint32_t);
+  return (n_pad + thr_pad + 32) * sizeof(uint32_t) + 8 * sizeof(uint4);
 }
 
 int graph_threads() { return kGraphThreads; }

@@ -203,6 +203,7 @@ struct GraphArgs {
   int32_t T, S, C;           // trials, sweeps, CTAs per 32-trial group (cluster size)
   uint32_t k0, key0, key1;
   int32_t tpw;               // threads per site word: 1, 4 or 8
+  uint32_t rk[20];           // Philox round keys: rk[2r] = key0 + r*W0, rk[2r+1] = key1 + r*W1
 };
 size_t graph_smem_bytes(int32_t n, int32_t Dmax);
 int graph_threads();
