@@ -73,6 +73,44 @@ __device__ __forceinline__ uint32_t lane_value(const uint32_t (&pl)[kP], int t) 
   return v;
 }
 
+// counter values of trials 8g .. 8g+7, one byte each (trials 8g .. 8g+3 in
+// .x, 8g+4 .. 8g+7 in .y): byte p of an 8 x 8 bit matrix holds plane p's bits
+// of the eight trials; transposing it (three delta swaps, Hacker's Delight
+// 7-3) leaves trial j's value in byte j
+template <int kP>
+__device__ __forceinline__ uint2 group_values(const uint32_t (&pl)[kP], int g) {
+  const uint32_t sel = static_cast<uint32_t>(g) | (static_cast<uint32_t>(g + 4) << 4);
+  auto plane = [&](int p) { return p < kP ? pl[p < kP ? p : 0] : 0u; };
+  const uint32_t lo = __byte_perm(__byte_perm(plane(0), plane(1), sel), __byte_perm(plane(2), plane(3), sel), 0x5410);
+  const uint32_t hi = kP > 4 ? __byte_perm(__byte_perm(plane(4), plane(5), sel), __byte_perm(plane(6), plane(7), sel),
+                                           0x5410)
+                             : 0u;
+  uint64_t x = (static_cast<uint64_t>(hi) << 32) | lo;
+  uint64_t t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+  x = x ^ t ^ (t << 7);
+  t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+  x = x ^ t ^ (t << 14);
+  t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+  x = x ^ t ^ (t << 28);
+  return make_uint2(static_cast<uint32_t>(x), static_cast<uint32_t>(x >> 32));
+}
+
+// the decisions of the uphill trials of quad jq (bits of m4): trial t's
+// value v = a from its byte of vq, dE / 2 = 2v - D indexes the threshold row
+__device__ __forceinline__ uint32_t quad_accepts(const uint4 u, uint32_t m4, uint32_t vq, uint32_t D,
+                                                 const uint32_t* thr, int jq) {
+  const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+  uint32_t acc = 0u;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    if ((m4 >> m) & 1u) {
+      const uint32_t q = 2u * ((vq >> (8 * m)) & 0xFFu) - D;   // dE / 2, 1 .. D
+      if (uu[m] < thr[q]) acc |= 1u << (4 * jq + m);
+    }
+  }
+  return acc;
+}
+
 template <int kP>
 __device__ __forceinline__ uint32_t graph_update(const GraphArgs& a, const uint32_t* sp, const uint32_t* thr,
                                                  const uint4* heads, uint32_t i, int nq) {
@@ -97,19 +135,19 @@ __device__ __forceinline__ uint32_t graph_update(const GraphArgs& a, const uint3
     uint32_t hi0, lo0, hi1, lo1;
     mulhilo(kPhiloxM0, i, hi0, lo0);
     mulhilo(kPhiloxM1, hi0 ^ a.rk[1], hi1, lo1);
-    for (int jq = 0; jq < nq; ++jq) {
-      const uint32_t m4 = (up >> (4 * jq)) & 0xFu;
-      if (!m4) continue;
-      const uint4 hd = heads[jq];
-      const uint4 u = philox_rounds_3_to_10(hi1 ^ hd.x, lo1, hd.y ^ lo0, hd.z, a.rk);
-      const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        if ((m4 >> m) & 1u) {
-          const int t = 4 * jq + m;
-          const uint32_t q = 2u * lane_value<kP>(pl, t) - D;   // dE / 2, 1 .. D
-          if (uu[m] < thr[q]) flip |= 1u << t;
-        }
+    for (int g = 0; g < 4; ++g) {
+      if (2 * g >= nq) break;
+      if (!((up >> (8 * g)) & 0xFFu)) continue;
+      const uint2 v = group_values<kP>(pl, g);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int jq = 2 * g + h;
+        const uint32_t m4 = (up >> (4 * jq)) & 0xFu;
+        if (jq >= nq || !m4) continue;
+        const uint4 hd = heads[jq];
+        const uint4 u = philox_rounds_3_to_10(hi1 ^ hd.x, lo1, hd.y ^ lo0, hd.z, a.rk);
+        flip |= quad_accepts(u, m4, h ? v.y : v.x, D, thr, jq);
       }
     }
   }
@@ -162,20 +200,15 @@ __device__ __forceinline__ uint32_t graph_update_team(const GraphArgs& a, const 
     mulhilo(kPhiloxM0, i, hi0, lo0);
     mulhilo(kPhiloxM1, hi0 ^ a.rk[1], hi1, lo1);
   }
-  for (int jq = r; jq < nq; jq += kTPW) {
+#pragma unroll
+  for (int s = 0; s < 8 / kTPW; ++s) {
+    const int jq = r + s * kTPW;
     const uint32_t m4 = (up >> (4 * jq)) & 0xFu;
-    if (!m4) continue;
+    if (jq >= nq || !m4) continue;
+    const uint2 v = group_values<kP>(pl, jq >> 1);
     const uint4 hd = heads[jq];
     const uint4 u = philox_rounds_3_to_10(hi1 ^ hd.x, lo1, hd.y ^ lo0, hd.z, a.rk);
-    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      if ((m4 >> m) & 1u) {
-        const int t = 4 * jq + m;
-        const uint32_t q = 2u * lane_value<kP>(pl, t) - D;   // dE / 2, 1 .. D
-        if (uu[m] < thr[q]) acc |= 1u << t;
-      }
-    }
+    acc |= quad_accepts(u, m4, (jq & 1) ? v.y : v.x, D, thr, jq);
   }
 #pragma unroll
   for (int off = 1; off < kTPW; off <<= 1) acc |= __shfl_xor_sync(0xFFFFFFFFu, acc, off);
