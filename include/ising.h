@@ -258,8 +258,12 @@ int ising_debug_fail_allocs(int32_t count);
  * Philox4x32-10 at counter (c, q, r, 0xFFFFFFFD).  Start: the start spins of
  * every slot.  out_spins (device int8 [temps*chains][n]) and out_cuts
  * (device int32 [temps*chains]) receive the final slots; out_swaps (device
- * int32 or NULL) the number of swaps taken.  Asynchronous on cuda_stream;
- * allocates its tables and one spin-sized buffer in stream order.
+ * int32 or NULL) the number of swaps taken.  The sweeps run on the kernel
+ * ising_anneal would choose for temps*chains trials (the persistent kernel
+ * with one threshold table per 32-slot group, else the strip kernel);
+ * ising_set_kernel(p, 1) forces the strip kernel.  Asynchronous on
+ * cuda_stream; allocates its tables, one spin-sized buffer and the persistent
+ * kernel's scratch in stream order.
  * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (general-graph handle, 16-bit
  * mode, no launch shape), ISING_ERR_OOM, ISING_ERR_CUDA.  The paper has no
  * counterpart (its update rule is unpublished, Section III).
