@@ -452,25 +452,13 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(TcWgradArgs a) {
             *reinterpret_cast<const uint4*>(f);
       }
     } else {
+      // asynchronous copies: every thread's share of the three rows is in
+      // flight at once, awaited once before the barrier
       const int total = 3 * X * 4;
-      for (int i0 = tid; i0 < total; i0 += 4 * kTcThreads) {
-        uint4 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = i0 + u * kTcThreads;
-          if (i < total) {
-            const int ky = i / (X * 4), rem = i - ky * X * 4, x = rem >> 2, ch = rem & 3;
-            v[u] = reinterpret_cast<const uint4*>(a.act + (ib + static_cast<size_t>(wrapi(y + ky - 1, Y)) * X + x) * 32)[ch];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = i0 + u * kTcThreads;
-          if (i < total) {
-            const int ky = i / (X * 4), rem = i - ky * X * 4, x = rem >> 2, ch = rem & 3;
-            *reinterpret_cast<uint4*>(sA + static_cast<size_t>(ky * 4 + ch) * blk + static_cast<size_t>(x) * 16) = v[u];
-          }
-        }
+      for (int i = tid; i < total; i += kTcThreads) {
+        const int ky = i / (X * 4), rem = i - ky * X * 4, x = rem >> 2, ch = rem & 3;
+        cp_async16(saddr(sA + static_cast<size_t>(ky * 4 + ch) * blk + static_cast<size_t>(x) * 16),
+                   a.act + (ib + static_cast<size_t>(wrapi(y + ky - 1, Y)) * X + x) * 32 + ch * 8);
       }
     }
     // ---- B: gradient row y at positions p = x + kx - 1 (mod X) of copy kx
@@ -505,6 +493,7 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(TcWgradArgs a) {
                                     static_cast<size_t>(wrapi(x + kx - 1, X)) * 16) = q;
       }
     }
+    if (kKind != 0) cp_async_commit_wait_all();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
