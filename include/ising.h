@@ -201,6 +201,27 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
 int ising_set_kernel(ising_problem* p, int32_t kind);
 
 /*
+ * ising_flow_split -- the persistent kernel's division of work, for
+ * inspection and tests (host only; no GPU, no handle).  The rows of all
+ * ceil(trials / group_trials) trial groups of a Y-row torus with H = X/2 site
+ * words per row and colour are stacked, and their words (row * H + h) split
+ * into ctas = min(sms, rows) contiguous ranges of equal weight: a word weighs
+ * its group's Philox blocks per sweep (ceil(live trials / 4), or / 8 with
+ * draw_bits 16) when `weighted`, else 1.  Ranges may start and end inside a
+ * row (a row then shared by two CTAs), except with draw_bits 16, where they
+ * end at row boundaries.  Writes the ctas + 1 range starts into split_out
+ * (host int32, cap entries), and, unless NULL, the most local rows (own rows,
+ * plus two halo rows per trial group not wholly owned) and the most trial
+ * groups any CTA touches.  ising_anneal refuses the persistent kernel when
+ * those exceed its shared memory or 4 groups.  Errors: ISING_ERR_ARG (bad
+ * sizes, draw_bits not 16 or 32, cap too small), ISING_ERR_UNSUPPORTED (more
+ * than 2^30 rows or words).
+ */
+int ising_flow_split(int32_t Y, int32_t H, int32_t trials, int32_t group_trials, int32_t draw_bits, int32_t sms,
+                     int32_t weighted, int32_t* split_out, int32_t cap, int32_t* ctas, int32_t* local_rows_max,
+                     int32_t* segments_max);
+
+/*
  * ising_set_graph_threads_per_site -- general-graph handles: how many
  * threads share one site word's update in ising_anneal (Section II's general
  * form; the sweep and its decisions are unchanged).  1: one thread counts the

@@ -261,6 +261,19 @@ def hex_to_spins(hexstr, n):
     return out
 
 
+def flow_split(Y, X, trials, group_trials=32, draw_bits=32, sms=152, weighted=True):
+    """The persistent kernel's division of the stacked site words over its
+    CTAs (host only): returns (split int32 [ctas + 1], most local rows of a
+    CTA, most trial groups a CTA touches)."""
+    cap = int(sms) + 1
+    out = np.zeros(cap, dtype=np.int32)
+    ctas, lr, seg = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(lib().ising_flow_split(int(Y), int(X) // 2, int(trials), int(group_trials), int(draw_bits), int(sms),
+                                 1 if weighted else 0, out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(ctas),
+                                 ctypes.byref(lr), ctypes.byref(seg)), "ising_flow_split")
+    return out[:ctas.value + 1].copy(), lr.value, seg.value
+
+
 def philox(counters, seed, stream=None):
     """The library's Philox4x32-10 blocks for uint32 counters [k, 4] (CUDA tensor or array)."""
     torch = _torch()

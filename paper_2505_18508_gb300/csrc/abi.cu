@@ -273,38 +273,31 @@ struct FlowPlan {
   std::vector<int32_t> split;
 };
 
-// Stacks the rows of all trial groups and splits their site words over one
-// CTA per SM, weighted by the Philox blocks of each row's group (or,
-// unweighted, into equal word counts: the caller's fallback when a ragged last
-// group would pile its light rows onto a few CTAs beyond their shared
-// memory).  Fails with
-// ISING_ERR_UNSUPPORTED when a CTA would touch more groups than the kernel
-// tracks or its rows would not fit in shared memory.
-int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp, bool weighted = true) {
-  const int sms = num_sms_of(p->device);
-  const int smem_max = max_smem_of(p->device);
-  int G = p->cfg_group;
-  if (G == 0) G = default_group(p, T);
-  const int blk = p->draw_bits == 16 ? 8 : 4;
+// The persistent kernel's split of the stacked site words (word w = row * H
+// + h, rows of all trial groups stacked) over P CTAs: ranges of equal weight,
+// a word weighing the Philox blocks of its trial group (weighted) or 1.  A
+// range may start and end inside a row: such a row is shared by two CTAs,
+// which then read it, and its neighbours, through the global mirror.  With
+// whole_rows the ranges end at row boundaries.  Fills split[0..P] and
+// returns the largest number of local rows (own rows, plus two halo slots per
+// segment that is not a whole trial group) and segments of any CTA.
+struct FlowSplit {
+  int P = 0, RT = 0, LRmax = 0, max_segments = 0;
+  std::vector<int32_t> split;
+};
+
+int flow_split(int32_t Y, int32_t H, int32_t T, int32_t G, int32_t blk, int32_t sms, bool weighted,
+               bool whole_rows, FlowSplit* fs) {
+  if (Y < 1 || H < 1 || T < 1 || G < 1 || blk < 1 || sms < 1) return ISING_ERR_ARG;
   const int groups = (T + G - 1) / G;
-  const long long RTl = static_cast<long long>(groups) * p->Y;
-  if (RTl > (1LL << 30)) return ISING_ERR_UNSUPPORTED;
+  const long long RTl = static_cast<long long>(groups) * Y;
+  if (RTl > (1LL << 30) || RTl * H > (1LL << 30)) return ISING_ERR_UNSUPPORTED;
   const int RT = static_cast<int>(RTl);
   const int P = std::min(sms, RT);
-  const int H = p->H;
-  if (static_cast<long long>(RT) * H > (1LL << 30)) return ISING_ERR_UNSUPPORTED;
-  // Split the stacked site words (word w = row * H + h) into P ranges of
-  // equal weight (a word weighs the Philox blocks of its trial group, or 1).
-  // A range may start and end inside a row: such a row is shared by two CTAs,
-  // which then read it, and its neighbours, through the global mirror.  In
-  // the 16-bit draw mode, where a word's own work is cheaper, that costs more
-  // than the finer balance gains (measured on the 200 x 100 torus with 1,024
-  // trials), so there the ranges end at row boundaries.
-  const bool whole_rows = p->draw_bits == 16;
   std::vector<long long> cum(static_cast<size_t>(RT) + 1, 0);   // weight of rows before u
   std::vector<int> wrow(static_cast<size_t>(RT));
   for (int u = 0; u < RT; ++u) {
-    const int g = u / p->Y;
+    const int g = u / Y;
     const int live = std::min(G, T - g * G);
     wrow[u] = weighted ? (live + blk - 1) / blk : 1;
     cum[u + 1] = cum[u] + wrow[u];
@@ -330,23 +323,52 @@ int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp, bool weighted = t
     split[j] = v;
   }
   split[P] = W;
-  // local rows of each CTA: its rows (whole or shared) plus two halo slots
-  // per segment that is not a whole trial group
-  int LRmax = 0;
+  int LRmax = 0, segmax = 0;
   for (int j = 0; j < P; ++j) {
     int lr = 0, nseg = 0;
     for (int w = split[j]; w < split[j + 1];) {
-      const int r = w / H, g = r / p->Y;
-      const int wend = std::min(split[j + 1], (g + 1) * p->Y * H);
+      const int r = w / H, g = r / Y;
+      const int wend = std::min(split[j + 1], (g + 1) * Y * H);
       const int n = (wend - 1) / H - r + 1;
-      const bool whole = wend - w == p->Y * H;
+      const bool whole = wend - w == Y * H;
       lr += n + (whole ? 0 : 2);
       ++nseg;
       w = wend;
     }
-    if (nseg > ising::flow_max_segments()) return ISING_ERR_UNSUPPORTED;
     LRmax = std::max(LRmax, lr);
+    segmax = std::max(segmax, nseg);
   }
+  fs->P = P;
+  fs->RT = RT;
+  fs->LRmax = LRmax;
+  fs->max_segments = segmax;
+  fs->split.swap(split);
+  return ISING_OK;
+}
+
+// Plans the persistent kernel's launch for T trials: the split above (the
+// caller falls back to the unweighted split when a ragged last group would
+// pile its light rows onto a few CTAs beyond their shared memory).  In the
+// 16-bit draw mode, where a word's own work is cheaper, the extra mirror
+// traffic of shared rows costs more than the finer balance gains (measured on
+// the 200 x 100 torus with 1,024 trials), so there the ranges end at row
+// boundaries.  Fails with ISING_ERR_UNSUPPORTED when a CTA would touch more
+// groups than the kernel tracks or its rows would not fit in shared memory.
+int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp, bool weighted = true) {
+  const int sms = num_sms_of(p->device);
+  const int smem_max = max_smem_of(p->device);
+  int G = p->cfg_group;
+  if (G == 0) G = default_group(p, T);
+  const int blk = p->draw_bits == 16 ? 8 : 4;
+  const int H = p->H;
+  FlowSplit fs;
+  const int rc = flow_split(p->Y, H, T, G, blk, sms, weighted, p->draw_bits == 16, &fs);
+  if (rc != ISING_OK) return rc;
+  if (fs.max_segments > ising::flow_max_segments()) return ISING_ERR_UNSUPPORTED;
+  const int LRmax = fs.LRmax;
+  const int groups = (T + G - 1) / G;
+  const int RT = fs.RT, P = fs.P;
+  std::vector<int32_t>& split = fs.split;
   // the kernel's tables hold shared-memory word indices in 16 bits
   if (2LL * LRmax * H + 1 > 0xFFFF) return ISING_ERR_UNSUPPORTED;
   const size_t smem = ising::flow_smem_bytes(LRmax, p->H);
@@ -745,6 +767,27 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
 int ising_set_draw_bits(ising_problem* p, int32_t bits) {
   if (!p || (bits != 32 && bits != 16)) return ISING_ERR_ARG;
   p->draw_bits = bits;
+  return ISING_OK;
+}
+
+int ising_flow_split(int32_t Y, int32_t H, int32_t trials, int32_t group_trials, int32_t draw_bits, int32_t sms,
+                     int32_t weighted, int32_t* split_out, int32_t cap, int32_t* ctas, int32_t* local_rows_max,
+                     int32_t* segments_max) {
+  if (!(draw_bits == 32 || draw_bits == 16) || group_trials < 1 || group_trials > 32 || !split_out || !ctas)
+    return ISING_ERR_ARG;
+  FlowSplit fs;
+  int rc;
+  try {
+    rc = flow_split(Y, H, trials, group_trials, draw_bits == 16 ? 8 : 4, sms, weighted != 0, draw_bits == 16, &fs);
+  } catch (const std::bad_alloc&) {
+    return ISING_ERR_OOM;
+  }
+  if (rc != ISING_OK) return rc;
+  if (cap < fs.P + 1) return ISING_ERR_ARG;
+  std::memcpy(split_out, fs.split.data(), sizeof(int32_t) * (fs.P + 1));
+  *ctas = fs.P;
+  if (local_rows_max) *local_rows_max = fs.LRmax;
+  if (segments_max) *segments_max = fs.max_segments;
   return ISING_OK;
 }
 

@@ -1,0 +1,95 @@
+"""Host logic of the persistent kernel's work split (ising_flow_split, no GPU):
+every stacked site word belongs to exactly one CTA, the ranges are balanced
+to within one word of weight, the 16-bit mode splits at row boundaries, and
+the local-row and segment counts match an independent count."""
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def ia():
+    import __graft_entry__
+    from paper_2505_18508_gb300 import build
+    build.build()
+    import paper_2505_18508_gb300 as ia
+    return ia
+
+
+def _weights(Y, T, G, blk, weighted):
+    groups = (T + G - 1) // G
+    w = []
+    for g in range(groups):
+        live = min(G, T - g * G)
+        w += [(live + blk - 1) // blk if weighted else 1] * Y
+    return np.array(w, dtype=np.int64)
+
+
+def _local_rows(split, Y, H):
+    lrmax = segmax = 0
+    for j in range(len(split) - 1):
+        lr = nseg = 0
+        rows = {}
+        for wd in range(split[j], split[j + 1]):
+            rows.setdefault(wd // H, 0)
+            rows[wd // H] += 1
+        groups = {}
+        for r in rows:
+            groups.setdefault(r // Y, []).append(r)
+        for g, rs in groups.items():
+            whole = len(rs) == Y and all(rows[r] == H for r in rs)
+            lr += len(rs) + (0 if whole else 2)
+            nseg += 1
+        lrmax, segmax = max(lrmax, lr), max(segmax, nseg)
+    return lrmax, segmax
+
+
+CASES = [
+    # X, Y, trials, group trials, draw bits, SMs, weighted
+    (200, 100, 1024, 32, 32, 152, True),
+    (200, 100, 1024, 32, 16, 152, True),
+    (100, 100, 1000, 32, 32, 152, True),
+    (8, 6, 37, 32, 32, 152, True),
+    (8, 6, 37, 32, 32, 152, False),
+    (24, 16, 3000, 8, 32, 152, True),
+    (50, 50, 64, 32, 32, 7, True),
+    (200, 100, 33, 32, 32, 152, True),
+    (64, 48, 96, 32, 16, 152, True),
+]
+
+
+@pytest.mark.parametrize("X,Y,T,G,bits,sms,weighted", CASES)
+def test_flow_split_invariants(ia, X, Y, T, G, bits, sms, weighted):
+    H = X // 2
+    split, lrmax, segmax = ia.flow_split(Y, X, T, G, bits, sms, weighted)
+    w = _weights(Y, T, G, 8 if bits == 16 else 4, weighted)
+    RT = w.shape[0]
+    P = min(sms, RT)
+    W = RT * H
+    assert split.shape[0] == P + 1 and split[0] == 0 and split[-1] == W
+    assert np.all(np.diff(split) > 0)                       # every CTA gets words, none twice
+    if bits == 16:
+        assert np.all(split % H == 0)                        # row boundaries in the 16-bit mode
+    # weight of each range against the ideal share (one word of slack per end;
+    # row-boundary splits may miss by up to a row)
+    word_w = np.repeat(w, H)
+    cumw = np.concatenate([[0], np.cumsum(word_w)])
+    share = cumw[-1] / P
+    slack = (H if bits == 16 else 1) * w.max() + w.max()
+    loads = cumw[split[1:]] - cumw[split[:-1]]
+    assert np.all(np.abs(loads - share) <= slack + 1e-9)
+    assert (lrmax, segmax) == _local_rows(split, Y, H)
+
+
+def test_flow_split_headline_balance(ia):
+    split, lrmax, segmax = ia.flow_split(100, 200, 1024)
+    sizes = np.diff(split)
+    assert split.shape[0] == 153 and set(sizes.tolist()) <= {2105, 2106}
+    assert segmax <= 2
+
+
+def test_flow_split_arguments(ia):
+    for kw in (dict(draw_bits=8), dict(group_trials=0), dict(group_trials=33)):
+        args = dict(Y=10, X=20, trials=64)
+        args.update(kw)
+        with pytest.raises(ia.IsingError):
+            ia.flow_split(**args)
