@@ -201,6 +201,25 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
 int ising_set_kernel(ising_problem* p, int32_t kind);
 
 /*
+ * ising_batch_schedule -- the schedule ising_batch_create / ising_anneal_batched
+ * would give m torus instances (host only; no GPU, no handles): X[q] x Y[q]
+ * tori (even, >= 4), trials[q] trials of sweeps[q] sweeps, all in the given
+ * draw mode (32 or 16).  group_trials and ctas_per_sm as in
+ * ising_anneal_batched (0: automatic); sms: the GPU's SMs; smem_per_cta_max:
+ * its shared memory per CTA (0: 227 KiB).  Writes the CTAs per SM and threads
+ * per CTA, G[q] (trials per work unit of instance q, host int32 [m]) and, if
+ * units is not NULL, the work units in the order the CTAs take them, as
+ * (instance, group) pairs (host int32 [cap][2]); *nunits receives their
+ * count.  Units are taken longest first (cost n (sweeps + 1) x Philox blocks).
+ * Errors: ISING_ERR_ARG (bad sizes, cap too small), ISING_ERR_UNSUPPORTED (a
+ * whole trial group does not fit in shared memory).
+ */
+int ising_batch_schedule(int32_t m, const int32_t* X, const int32_t* Y, const int32_t* trials, const int32_t* sweeps,
+                         int32_t draw_bits, int32_t group_trials, int32_t ctas_per_sm, int32_t sms,
+                         int32_t smem_per_cta_max, int32_t* per_sm, int32_t* threads, int32_t* G, int32_t* units,
+                         int32_t cap, int32_t* nunits);
+
+/*
  * ising_flow_split -- the persistent kernel's division of work, for
  * inspection and tests (host only; no GPU, no handle).  The rows of all
  * ceil(trials / group_trials) trial groups of a Y-row torus with H = X/2 site

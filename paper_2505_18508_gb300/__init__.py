@@ -274,6 +274,28 @@ def flow_split(Y, X, trials, group_trials=32, draw_bits=32, sms=152, weighted=Tr
     return out[:ctas.value + 1].copy(), lr.value, seg.value
 
 
+def batch_schedule(shapes, trials, sweeps, draw_bits=32, group_trials=0, ctas_per_sm=0, sms=152,
+                   smem_per_cta_max=0):
+    """The batched launch's schedule (host only) for tori shapes [(X, Y)]:
+    returns (CTAs per SM, threads per CTA, trials per unit [m], units
+    int32 [k, 2] of (instance, group) in the order the CTAs take them)."""
+    m = len(shapes)
+    X = np.ascontiguousarray([s[0] for s in shapes], dtype=np.int32)
+    Y = np.ascontiguousarray([s[1] for s in shapes], dtype=np.int32)
+    T = np.ascontiguousarray(trials, dtype=np.int32)
+    S = np.ascontiguousarray(sweeps, dtype=np.int32)
+    G = np.zeros(m, dtype=np.int32)
+    cap = int(sum((int(t) + 3) // 4 for t in T)) + 1
+    units = np.zeros((cap, 2), dtype=np.int32)
+    per_sm, threads, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)   # noqa: E731
+    check(lib().ising_batch_schedule(m, vp(X), vp(Y), vp(T), vp(S), int(draw_bits), int(group_trials),
+                                     int(ctas_per_sm), int(sms), int(smem_per_cta_max), ctypes.byref(per_sm),
+                                     ctypes.byref(threads), vp(G), vp(units), cap, ctypes.byref(k)),
+          "ising_batch_schedule")
+    return per_sm.value, threads.value, G, units[:k.value].copy()
+
+
 def philox(counters, seed, stream=None):
     """The library's Philox4x32-10 blocks for uint32 counters [k, 4] (CUDA tensor or array)."""
     torch = _torch()

@@ -48,6 +48,8 @@ _SIGNATURES = {
     "ising_set_kernel": (ctypes.c_int, [_vp, _i32]),
     "ising_set_graph_threads_per_site": (ctypes.c_int, [_vp, _i32]),
     "ising_flow_split": (ctypes.c_int, [_i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp]),
+    "ising_batch_schedule": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
+                                            _vp, _i32, _vp]),
     "ising_set_draw_bits": (ctypes.c_int, [_vp, _i32]),
     "ising_graph_create": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _vp]),
     "ising_greedy_colouring": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp]),

@@ -141,6 +141,83 @@ struct HostBatch {
 };
 
 
+// The batched launch's schedule (host only): CTAs per SM and threads, trials
+// per work unit of each instance, and the units (instance, group) in the
+// order the CTAs take them.  n, H, Y: each instance's spins, words per row and
+// rows; blk: its trials per Philox block (4, or 8 in the 16-bit mode).
+struct BatchSchedule {
+  int per_sm = 0, threads = 0;
+  size_t smem = 0;
+  std::vector<int> G;
+  std::vector<ising::BatchUnit> units;
+};
+
+int batch_schedule(int32_t m, const int32_t* n, const int32_t* H, const int32_t* Y, const int32_t* trials,
+                   const int32_t* sweeps, const int32_t* blk, int32_t group_trials, int32_t ctas_per_sm, int sms,
+                   int smem_max, BatchSchedule* bs) {
+  size_t max_smem = 0;
+  double total = 0.0;
+  for (int32_t q = 0; q < m; ++q) {
+    const size_t sb = ising::batched_smem_bytes(H[q], Y[q]);
+    if (trials[q] > 0 && sb > max_smem) max_smem = sb;
+    total += static_cast<double>(n[q]) * sweeps[q] * trials[q];
+  }
+  if (max_smem > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
+  // CTAs per SM: one of 1,024 threads when the work-weighted instance has
+  // enough site words per half-sweep to give every thread four or more
+  // (fewer, larger CTAs also let the units keep 32 trials, see below);
+  // otherwise two of 512 threads if shared memory allows.  On the
+  // 96-instance batch of {50,100,140,200}x100 tori one CTA per SM measured
+  // 1.72 s against 2.17 s for two.
+  int per_sm = ctas_per_sm;
+  if (per_sm == 0) {
+    double wwords = 0.0, wsum = 0.0;
+    for (int32_t q = 0; q < m; ++q) {
+      const double c = static_cast<double>(n[q]) * sweeps[q] * trials[q];
+      wwords += c * (n[q] / 2);
+      wsum += c;
+    }
+    per_sm = (wsum > 0.0 && wwords / wsum >= 4.0 * 1024) ? 1 : 2;
+    if (max_smem > 0 && static_cast<size_t>(per_sm) * (max_smem + 1024) > 228 * 1024) per_sm = 1;
+  }
+  if (max_smem > 0 && static_cast<size_t>(per_sm) * (max_smem + 1024) > 228 * 1024) return ISING_ERR_UNSUPPORTED;
+  const int grid = sms * per_sm;
+  bs->per_sm = per_sm;
+  bs->threads = 1024 / per_sm;
+  bs->smem = max_smem;
+  // trials per unit: 32 unless one such unit would exceed the average load of
+  // a CTA, then the largest multiple of the Philox block that fits (at least one block)
+  const double per_cta = total / (grid > 0 ? grid : 1);
+  bs->G.assign(static_cast<size_t>(m), 0);
+  std::vector<std::pair<double, ising::BatchUnit>> order;
+  for (int32_t q = 0; q < m; ++q) {
+    int G = group_trials;
+    if (G == 0) {
+      G = 32;
+      const double unit32 = static_cast<double>(n[q]) * sweeps[q] * 32.0;
+      if (unit32 > per_cta && per_cta > 0) {
+        G = blk[q] * static_cast<int>(per_cta / (blk[q] * static_cast<double>(n[q]) * (sweeps[q] > 0 ? sweeps[q] : 1)));
+        if (G < blk[q]) G = blk[q];
+        if (G > 32) G = 32;
+      }
+    }
+    bs->G[q] = G;
+    const int groups = (trials[q] + G - 1) / G;
+    for (int g = 0; g < groups; ++g) {
+      const int live = std::min(G, trials[q] - g * G);
+      const double cost = static_cast<double>(n[q]) * (sweeps[q] + 1) * ((live + blk[q] - 1) / blk[q]);
+      order.push_back({cost, ising::BatchUnit{q, g}});
+    }
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<double, ising::BatchUnit>& x, const std::pair<double, ising::BatchUnit>& y) {
+                     return x.first > y.first;
+                   });
+  bs->units.resize(order.size());
+  for (size_t u = 0; u < order.size(); ++u) bs->units[u] = order[u].second;
+  return ISING_OK;
+}
+
 int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials, const int32_t* sweeps,
                   const double* const* betas, const uint64_t* seeds, int8_t* const* out_spins,
                   int32_t* const* out_cuts, int32_t group_trials, int32_t ctas_per_sm, HostBatch& hb) {
@@ -156,8 +233,7 @@ int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials,
   }
   hb.inst.resize(m);
   hb.thr_off.resize(m);
-  size_t max_smem = 0;
-  double total = 0.0;
+  std::vector<int32_t> vn(m), vH(m), vY(m), vblk(m);
   for (int32_t q = 0; q < m; ++q) {
     std::vector<uint32_t> t;
     if (probs[q]->draw_bits == 16 && group_trials % 8) return ISING_ERR_ARG;
@@ -165,52 +241,20 @@ int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials,
     if (rc != ISING_OK) return rc;
     hb.thr_off[q] = hb.thr.size();
     hb.thr.insert(hb.thr.end(), t.begin(), t.end());
-    const ising_problem* p = probs[q];
-    const size_t sb = ising::batched_smem_bytes(p->H, p->Y);
-    if (trials[q] > 0 && sb > max_smem) max_smem = sb;
-    total += static_cast<double>(p->n) * sweeps[q] * trials[q];
+    vn[q] = probs[q]->n;
+    vH[q] = probs[q]->H;
+    vY[q] = probs[q]->Y;
+    vblk[q] = probs[q]->draw_bits == 16 ? 8 : 4;   // trials per Philox block
   }
-  const int smem_max = max_smem_of(device);
-  if (max_smem > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
-  const int sms = num_sms_of(device);
-  // CTAs per SM: one of 1,024 threads when the work-weighted instance has
-  // enough site words per half-sweep to give every thread four or more
-  // (fewer, larger CTAs also let the units keep 32 trials, see below);
-  // otherwise two of 512 threads if shared memory allows.  On the
-  // 96-instance batch of {50,100,140,200}x100 tori one CTA per SM measured
-  // 1.72 s against 2.17 s for two.
-  int per_sm = ctas_per_sm;
-  if (per_sm == 0) {
-    double wwords = 0.0, wsum = 0.0;
-    for (int32_t q = 0; q < m; ++q) {
-      const double c = static_cast<double>(probs[q]->n) * sweeps[q] * trials[q];
-      wwords += c * (probs[q]->n / 2);
-      wsum += c;
-    }
-    per_sm = (wsum > 0.0 && wwords / wsum >= 4.0 * 1024) ? 1 : 2;
-    if (max_smem > 0 && static_cast<size_t>(per_sm) * (max_smem + 1024) > 228 * 1024) per_sm = 1;
-  }
-  if (max_smem > 0 && static_cast<size_t>(per_sm) * (max_smem + 1024) > 228 * 1024) return ISING_ERR_UNSUPPORTED;
-  hb.grid = sms * per_sm;
-  hb.threads = 1024 / per_sm;
-  hb.smem = max_smem;
-  // trials per unit: 32 unless one such unit would exceed the average load of
-  // a CTA, then the largest multiple of 4 that fits (at least 4)
-  const double per_cta = total / (hb.grid > 0 ? hb.grid : 1);
-  std::vector<std::pair<double, ising::BatchUnit>> order;
+  BatchSchedule bs;
+  const int rc = batch_schedule(m, vn.data(), vH.data(), vY.data(), trials, sweeps, vblk.data(), group_trials,
+                                ctas_per_sm, num_sms_of(device), max_smem_of(device), &bs);
+  if (rc != ISING_OK) return rc;
+  hb.grid = num_sms_of(device) * bs.per_sm;
+  hb.threads = bs.threads;
+  hb.smem = bs.smem;
   for (int32_t q = 0; q < m; ++q) {
     const ising_problem* p = probs[q];
-    const int blk = p->draw_bits == 16 ? 8 : 4;   // trials per Philox block
-    int G = group_trials;
-    if (G == 0) {
-      G = 32;
-      const double unit32 = static_cast<double>(p->n) * sweeps[q] * 32.0;
-      if (unit32 > per_cta && per_cta > 0) {
-        G = blk * static_cast<int>(per_cta / (blk * static_cast<double>(p->n) * (sweeps[q] > 0 ? sweeps[q] : 1)));
-        if (G < blk) G = blk;
-        if (G > 32) G = 32;
-      }
-    }
     ising::BatchInst& in = hb.inst[q];
     in.flags = p->d_flags;
     in.thr = nullptr;  // patched once the arena address is known
@@ -221,21 +265,10 @@ int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials,
     in.key0 = static_cast<uint32_t>(seeds[q] & 0xFFFFFFFFull);
     in.key1 = static_cast<uint32_t>(seeds[q] >> 32);
     in.neg_edges = p->neg_edges;
-    in.G = G;
+    in.G = bs.G[q];
     in.u16 = p->draw_bits == 16 ? 1 : 0;
-    const int groups = (trials[q] + G - 1) / G;
-    for (int g = 0; g < groups; ++g) {
-      const int live = std::min(G, trials[q] - g * G);
-      const double cost = static_cast<double>(p->n) * (sweeps[q] + 1) * ((live + blk - 1) / blk);
-      order.push_back({cost, ising::BatchUnit{q, g}});
-    }
   }
-  std::stable_sort(order.begin(), order.end(),
-                   [](const std::pair<double, ising::BatchUnit>& x, const std::pair<double, ising::BatchUnit>& y) {
-                     return x.first > y.first;
-                   });
-  hb.units.resize(order.size());
-  for (size_t u = 0; u < order.size(); ++u) hb.units[u] = order[u].second;
+  hb.units.swap(bs.units);
   hb.off_inst = 0;
   hb.off_units = align256(sizeof(ising::BatchInst) * hb.inst.size());
   hb.off_counter = hb.off_units + align256(sizeof(ising::BatchUnit) * hb.units.size());
@@ -767,6 +800,44 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
 int ising_set_draw_bits(ising_problem* p, int32_t bits) {
   if (!p || (bits != 32 && bits != 16)) return ISING_ERR_ARG;
   p->draw_bits = bits;
+  return ISING_OK;
+}
+
+int ising_batch_schedule(int32_t m, const int32_t* X, const int32_t* Y, const int32_t* trials, const int32_t* sweeps,
+                         int32_t draw_bits, int32_t group_trials, int32_t ctas_per_sm, int32_t sms,
+                         int32_t smem_per_cta_max, int32_t* per_sm, int32_t* threads, int32_t* G, int32_t* units,
+                         int32_t cap, int32_t* nunits) {
+  if (m < 0 || (m > 0 && (!X || !Y || !trials || !sweeps || !G)) || !per_sm || !threads || !nunits ||
+      !(draw_bits == 32 || draw_bits == 16) || sms < 1 || ctas_per_sm < 0 || ctas_per_sm > 4)
+    return ISING_ERR_ARG;
+  if (group_trials != 0 && (group_trials < 4 || group_trials > 32 || group_trials % (draw_bits == 16 ? 8 : 4)))
+    return ISING_ERR_ARG;
+  std::vector<int32_t> n(m), H(m), blk(m, draw_bits == 16 ? 8 : 4);
+  for (int32_t q = 0; q < m; ++q) {
+    if (X[q] < 4 || Y[q] < 4 || X[q] % 2 || Y[q] % 2 || trials[q] < 0 || sweeps[q] < 0) return ISING_ERR_ARG;
+    n[q] = X[q] * Y[q];
+    H[q] = X[q] / 2;
+  }
+  BatchSchedule bs;
+  int rc;
+  try {
+    rc = batch_schedule(m, n.data(), H.data(), Y, trials, sweeps, blk.data(), group_trials, ctas_per_sm, sms,
+                        smem_per_cta_max > 0 ? smem_per_cta_max : 227 * 1024, &bs);
+  } catch (const std::bad_alloc&) {
+    return ISING_ERR_OOM;
+  }
+  if (rc != ISING_OK) return rc;
+  *per_sm = bs.per_sm;
+  *threads = bs.threads;
+  for (int32_t q = 0; q < m; ++q) G[q] = bs.G[q];
+  *nunits = static_cast<int32_t>(bs.units.size());
+  if (units) {
+    if (cap < *nunits) return ISING_ERR_ARG;
+    for (size_t u = 0; u < bs.units.size(); ++u) {
+      units[2 * u] = bs.units[u].inst;
+      units[2 * u + 1] = bs.units[u].group;
+    }
+  }
   return ISING_OK;
 }
 

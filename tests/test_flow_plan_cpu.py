@@ -93,3 +93,53 @@ def test_flow_split_arguments(ia):
         args.update(kw)
         with pytest.raises(ia.IsingError):
             ia.flow_split(**args)
+
+
+# ---------------------------------------------------------------- batched schedule
+
+def _batch_cfg():
+    import synth
+    cfg = synth.batched_config()
+    return [(c["X"], c["Y"]) for c in cfg], [c["trials"] for c in cfg], [c["sweeps"] for c in cfg]
+
+
+def test_batch_schedule_covers_every_group_longest_first(ia):
+    shapes, trials, sweeps = _batch_cfg()
+    per_sm, threads, G, units = ia.batch_schedule(shapes, trials, sweeps)
+    assert (per_sm, threads) == (1, 1024)        # large tori: one 1,024-thread CTA per SM
+    assert np.all(G % 4 == 0) and np.all((G >= 4) & (G <= 32))
+    want = {(q, g) for q in range(len(shapes)) for g in range((trials[q] + G[q] - 1) // G[q])}
+    got = [tuple(u) for u in units.tolist()]
+    assert len(got) == len(want) and set(got) == want
+    # longest first: n (S + 1) x Philox blocks of the unit, non-increasing
+    cost = []
+    Gi = [int(v) for v in G]
+    for q, g in got:
+        n = shapes[q][0] * shapes[q][1]
+        live = min(Gi[q], trials[q] - g * Gi[q])
+        cost.append(n * (sweeps[q] + 1) * ((live + 3) // 4))
+    assert all(a >= b for a, b in zip(cost, cost[1:]))
+    # no unit above a CTA's average share unless it is one Philox block
+    share = sum(x * y * s * t for (x, y), s, t in zip(shapes, sweeps, trials)) / (152 * per_sm)
+    for q in range(len(shapes)):
+        n = shapes[q][0] * shapes[q][1]
+        assert Gi[q] == 4 or n * sweeps[q] * Gi[q] <= share
+
+
+def test_batch_schedule_small_tori_take_two_ctas_per_sm(ia):
+    shapes = [(20, 20)] * 8
+    per_sm, threads, G, units = ia.batch_schedule(shapes, [64] * 8, [500] * 8)
+    assert (per_sm, threads) == (2, 512)
+    assert units.shape[0] == sum((64 + g - 1) // g for g in G)
+
+
+def test_batch_schedule_fixed_shapes_and_16_bit(ia):
+    shapes, trials, sweeps = _batch_cfg()
+    per_sm, threads, G, _ = ia.batch_schedule(shapes, trials, sweeps, group_trials=8, ctas_per_sm=2)
+    assert (per_sm, threads) == (2, 512) and np.all(G == 8)
+    _, _, G16, _ = ia.batch_schedule(shapes, trials, sweeps, draw_bits=16)
+    assert np.all(G16 % 8 == 0)
+    with pytest.raises(ia.IsingError):
+        ia.batch_schedule(shapes, trials, sweeps, draw_bits=16, group_trials=12)
+    with pytest.raises(ia.IsingError):
+        ia.batch_schedule([(5, 8)], [32], [10])
