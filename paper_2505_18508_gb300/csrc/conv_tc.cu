@@ -240,6 +240,26 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
                  : "memory");
   };
 
+  // kOut 1: the ReLU mask of the row the next epilogue drains, loaded while
+  // the MMAs run (the first two tiles; later tiles load in the epilogue)
+  uint4 m00 = make_uint4(0, 0, 0, 0), m01 = m00, m10 = m00, m11 = m00;   // [tile][half of 16 channels]
+  auto prefetch_mask = [&](int b, int y) {
+    if constexpr (kOut == 1) {
+      const int x0 = (warp & 3) * 32 + lane;
+      const size_t p = static_cast<size_t>(b) * n + static_cast<size_t>(y) * X + x0;
+      if (x0 < X) {
+        const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * 32 + half * 16);
+        m00 = mk[0];
+        m01 = mk[1];
+      }
+      if (ntile > 1 && x0 + 128 < X) {
+        const uint4* mk = reinterpret_cast<const uint4*>(a.mask + (p + 128) * 32 + half * 16);
+        m10 = mk[0];
+        m11 = mk[1];
+      }
+    }
+  };
+
   auto epilogue = [&](int b, int y, uint32_t buf) {
     if (kOut == 2 && half) return;               // one logit channel: the first warpgroup alone
     for (int t = 0; t < ntile; ++t) {
@@ -263,7 +283,7 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
         const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * 32 + half * 16);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const uint4 mv = mk[q];
+          const uint4 mv = t == 0 ? (q ? m01 : m00) : t == 1 ? (q ? m11 : m10) : mk[q];
           const __nv_bfloat16* m8 = reinterpret_cast<const __nv_bfloat16*>(&mv);
 #pragma unroll
           for (int e = 0; e < 8; ++e)
@@ -301,6 +321,7 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok) break;
       if (tid == 0) issue_mmas(y, static_cast<uint32_t>(y & 1));
+      if (y > ya) prefetch_mask(b, y - 1);
       bool prev = false;
       if (y > ya) {
         const uint32_t pb = static_cast<uint32_t>((y - 1) & 1);
@@ -315,6 +336,7 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
       if (kIn != 0) cp_async_wait_all_but_one();   // row y+2 has landed
     }
     if (ok) {
+      prefetch_mask(b, yb);
       const uint32_t lb = static_cast<uint32_t>(yb & 1);
       const bool last = wait_mbar(saddr(mbar + lb), (phases >> lb) & 1u);
       phases ^= 1u << lb;
