@@ -3,7 +3,7 @@
 
     python -m paper_2505_18508_gb300.probe.legs batched [--scale 0.1] [--ctas-per-sm 0]
     python -m paper_2505_18508_gb300.probe.legs pt [--rounds 200] [--sweeps-per-round 50]
-    python -m paper_2505_18508_gb300.probe.legs graph [--graph g22] [--sweeps 2000] [--threads-per-site 0]
+    python -m paper_2505_18508_gb300.probe.legs graph [--graph g22] [--sweeps 2000] [--threads-per-site 0] [--strips 0]
 
 * batched: the 96-instance uneven batch of {50,100,140,200}x100 tori
   (32-512 trials, 2,000-20,000 sweeps, each sweep count times --scale) as one
@@ -92,14 +92,15 @@ def graph(args):
         g = {"n": inst["n"], "row_ptr": inst["row_ptr"], "col": inst["col"], "J": inst["J"], "h": None}
     prob = ia.Problem.from_graph(g)
     prob.set_graph_threads_per_site(args.threads_per_site)
+    prob.set_launch(strips=args.strips)
     betas = synth.linear_betas(0.1, 3.0, args.sweeps)
     cuts = torch.empty(args.trials, dtype=torch.int32, device="cuda")
     ia.anneal(prob, args.trials, betas, 1, want_spins=False, out_cuts=cuts)
     ups = args.trials * args.sweeps * g["n"]
     for r in range(args.reps):
         ms = _time(lambda: ia.anneal(prob, args.trials, betas, 2 + r, want_spins=False, out_cuts=cuts))
-        print(json.dumps({"leg": "graph", "graph": args.graph, "threads_per_site": args.threads_per_site, "ms": ms,
-                          "updates_per_s": ups / (ms * 1e-3)}))
+        print(json.dumps({"leg": "graph", "graph": args.graph, "threads_per_site": args.threads_per_site,
+                          "strips": prob.last_launch().get("strips"), "ms": ms, "updates_per_s": ups / (ms * 1e-3)}))
     prob.destroy()
 
 
@@ -116,6 +117,7 @@ def main(argv=None):
     ap.add_argument("--trials", type=int, default=1024)
     ap.add_argument("--sweeps", type=int, default=2000)
     ap.add_argument("--threads-per-site", type=int, default=0, help="general graphs: 1, 4, 8 or 0 (automatic)")
+    ap.add_argument("--strips", type=int, default=0, help="general graphs: CTAs per trial group (1-8; 0: automatic)")
     args = ap.parse_args(argv)
     _setup()
     {"batched": batched, "pt": pt, "graph": graph}[args.leg](args)
