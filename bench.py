@@ -198,37 +198,57 @@ def learned_leg(budgets=(1000, 3000, 10000, 30000), every=100, tile=10, n_train=
            "note": "forward = 4 tcgen05 convolution launches; 389 algorithmic HBM bytes per site; "
                    "hbm_frac of measured copy bandwidth"}
     prob.destroy()
-    # forms: the plain annealer; the learned form with proposals every `every`
-    # sweeps over the whole schedule (config 5 as stated); and the same with
-    # proposals only in the last `end_window` sweeps, where the annealer has
-    # cooled and only coordinated block flips can still lower the energy
+    # forms, instance by instance: the plain annealer; the learned form with
+    # proposals every `every` sweeps over the whole schedule (config 5 as
+    # stated); and the same with proposals only in the last `end_window`
+    # sweeps, where the annealer has cooled and only coordinated block flips
+    # can still lower the energy.  Batched forms, all 8 instances at once: the
+    # plain annealer in one persistent launch, and learned_end with the sweeps
+    # before its window in one persistent launch.  A batched form's results
+    # equal its per-instance form's (checked below); only the wall time, shared
+    # by the 8 x T trials, differs.
     forms = ("plain", "learned", "learned_end")
-    rows = []
-    for q in range(8):
-        inst = synth.torus_instance(200, 100, 30000 + q)
-        prob = ia.Problem.from_instance(inst)
-        seed = 70000 + q
-        runs = {}
-        for S in budgets:
-            betas = synth.linear_betas(0.1, 3.0, S)
-            runs[S] = {}
+    bforms = {"plain_batched": "plain", "learned_end_batched": "learned_end"}
+    probs = [ia.Problem.from_instance(synth.torus_instance(200, 100, 30000 + q)) for q in range(8)]
+    seeds = [70000 + q for q in range(8)]
+    runs = [{S: {} for S in budgets} for _ in probs]
+    batched_same = True
+    for S in budgets:
+        betas = synth.linear_betas(0.1, 3.0, S)
+        end_start = max(0, S - end_window)
+        for q, (prob, seed) in enumerate(zip(probs, seeds)):
             for name in forms:
                 st = {}
                 torch.cuda.synchronize(); a = time.perf_counter()
                 if name == "plain":
                     _, c = ia.anneal(prob, T, betas, seed)
                 else:
-                    start = 0 if name == "learned" else max(0, S - end_window)
+                    start = 0 if name == "learned" else end_start
                     _, c = learned.anneal_learned(prob, net, T, betas, seed, every=every, tile=tile, stats=st,
                                                   start=start)
                 torch.cuda.synchronize(); b = time.perf_counter()
-                runs[S][name] = (c.cpu().numpy(), b - a, st.get("accepted_per_trial"))
-        best = int(max(max(v[f][0].max() for f in forms) for v in runs.values()))
+                runs[q][S][name] = (c.cpu().numpy(), b - a, st.get("accepted_per_trial"))
+        for name, base in bforms.items():
+            torch.cuda.synchronize(); a = time.perf_counter()
+            if name == "plain_batched":
+                _, cs = ia.anneal_batched(probs, [T] * 8, [S] * 8, [betas] * 8, seeds)
+            else:
+                _, cs = learned.anneal_learned_batched(probs, net, T, betas, seeds, every=every, tile=tile,
+                                                       start=end_start)
+            torch.cuda.synchronize(); b = time.perf_counter()
+            for q in range(8):
+                c = cs[q].cpu().numpy()
+                batched_same = batched_same and bool(np.array_equal(c, runs[q][S][base][0]))
+                runs[q][S][name] = (c, (b - a) / 8, None)   # the batch's wall time per instance
+    rows = []
+    allforms = forms + tuple(bforms)
+    for q in range(8):
+        best = int(max(max(v[f][0].max() for f in forms) for v in runs[q].values()))
         tgt = stats.target_cut(best)
         row = {"seed": 30000 + q, "best": best, "target": tgt}
         for S in budgets:
-            for name in forms:
-                cuts, wall, acc = runs[S][name]
+            for name in allforms:
+                cuts, wall, acc = runs[q][S][name]
                 Ps = stats.success_probability(cuts, tgt)
                 r = stats.repetitions(Ps)
                 e = {"P_s": Ps, "mean_cut": float(cuts.mean()), "wall_s": wall,
@@ -237,6 +257,7 @@ def learned_leg(budgets=(1000, 3000, 10000, 30000), every=100, tile=10, n_train=
                     e["accepted_per_trial"] = acc
                 row[f"{name}@{S}"] = e
         rows.append(row)
+    for prob in probs:
         prob.destroy()
     net.destroy()
 
@@ -246,21 +267,27 @@ def learned_leg(budgets=(1000, 3000, 10000, 30000), every=100, tile=10, n_train=
     ladder = {f"{name}@{S}": {"median_TTT_s": med(f"{name}@{S}"),
                               "reached": sum(r[f"{name}@{S}"]["TTT_s"] is not None for r in rows),
                               "mean_P_s": float(np.mean([r[f"{name}@{S}"]["P_s"] for r in rows]))}
-              for S in budgets for name in forms}
+              for S in budgets for name in allforms}
 
     def best_budget(prefix):
         c = [(v["median_TTT_s"], k) for k, v in ladder.items() if k.startswith(prefix) and v["median_TTT_s"]]
         return min(c) if c else (None, None)
-    bp, bl, be = best_budget("plain"), best_budget("learned@"), best_budget("learned_end")
+    bp, bl, be = best_budget("plain@"), best_budget("learned@"), best_budget("learned_end@")
+    bpb, beb = best_budget("plain_batched@"), best_budget("learned_end_batched@")
     return {"workload": "200x100 tori, seeds 30000-30007, 512 trials each, beta 0.1->3.0 over S sweeps, "
                         f"S in {list(budgets)}; proposals every {every} sweeps, tiles {tile}x{tile} "
-                        f"(learned: whole schedule; learned_end: last {end_window} sweeps)",
+                        f"(learned: whole schedule; learned_end: last {end_window} sweeps); *_batched: the 8 "
+                        "instances in one persistent launch (learned_end_batched: up to its window), wall time "
+                        "shared by all 8 x 512 trials",
+            "batched_results_equal_per_instance": batched_same,
             "train": {"instances": n_train, "snapshot_sweeps": train_sweeps, "steps": steps, "loss": losses,
                       "seconds": t_train},
             "cnn_forward": cnn,
             "ladder": ladder,
             "best_median_TTT_s": {"plain": bp[0], "plain_budget": bp[1], "learned": bl[0],
-                                  "learned_budget": bl[1], "learned_end": be[0], "learned_end_budget": be[1]},
+                                  "learned_budget": bl[1], "learned_end": be[0], "learned_end_budget": be[1],
+                                  "plain_batched": bpb[0], "plain_batched_budget": bpb[1],
+                                  "learned_end_batched": beb[0], "learned_end_batched_budget": beb[1]},
             "per_seed": rows}
 
 

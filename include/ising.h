@@ -210,7 +210,11 @@ int ising_set_kernel(ising_problem* p, int32_t kind);
  * per CTA, G[q] (trials per work unit of instance q, host int32 [m]) and, if
  * units is not NULL, the work units in the order the CTAs take them, as
  * (instance, group) pairs (host int32 [cap][2]); *nunits receives their
- * count.  Units are taken longest first (cost n (sweeps + 1) x Philox blocks).
+ * count.  A unit's cost is n (sweeps + 1) x (3 + its Philox blocks per site
+ * word); units are taken longest first.  An instance whose 32-trial unit fits
+ * in a CTA's average load keeps G = 32; the others share the multiple of the
+ * Philox block (32 down to one block) whose units finish first under that
+ * longest-first list schedule on sms x per_sm CTAs (ties: the wider).
  * Errors: ISING_ERR_ARG (bad sizes, cap too small), ISING_ERR_UNSUPPORTED (a
  * whole trial group does not fit in shared memory).
  */

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <algorithm>
+#include <functional>
 #include <utility>
 #include <vector>
 
@@ -185,34 +186,77 @@ int batch_schedule(int32_t m, const int32_t* n, const int32_t* H, const int32_t*
   bs->per_sm = per_sm;
   bs->threads = 1024 / per_sm;
   bs->smem = max_smem;
-  // trials per unit: 32 unless one such unit would exceed the average load of
-  // a CTA, then the largest multiple of the Philox block that fits (at least one block)
+  // Trials per unit.  A unit's cost is modelled as n (S + 1) (3 + its Philox
+  // blocks per site word): the word's own work (field count, loads, store)
+  // is about three blocks' worth.  An instance whose 32-trial unit fits in a
+  // CTA's average load keeps 32 trials per unit.  The others ("large") share
+  // one width G, a multiple of the Philox block from 32 down to one block:
+  // the G whose units give the shortest makespan when the CTAs take them
+  // longest first (list scheduling, as the kernel's atomic counter does).
+  // Ties go to the wider unit.  On 8 instances of 200x100 with 512 trials
+  // each, G = 28 gives 152 units for 152 CTAs (18 of 28 trials and one of 8
+  // per instance).
   const double per_cta = total / (grid > 0 ? grid : 1);
-  bs->G.assign(static_cast<size_t>(m), 0);
-  std::vector<std::pair<double, ising::BatchUnit>> order;
+  std::vector<char> large(static_cast<size_t>(m), 0);
+  bool any_large = false;
+  int blk_large = 4;
   for (int32_t q = 0; q < m; ++q) {
-    int G = group_trials;
-    if (G == 0) {
-      G = 32;
-      const double unit32 = static_cast<double>(n[q]) * sweeps[q] * 32.0;
-      if (unit32 > per_cta && per_cta > 0) {
-        G = blk[q] * static_cast<int>(per_cta / (blk[q] * static_cast<double>(n[q]) * (sweeps[q] > 0 ? sweeps[q] : 1)));
-        if (G < blk[q]) G = blk[q];
-        if (G > 32) G = 32;
-      }
-    }
-    bs->G[q] = G;
-    const int groups = (trials[q] + G - 1) / G;
-    for (int g = 0; g < groups; ++g) {
-      const int live = std::min(G, trials[q] - g * G);
-      const double cost = static_cast<double>(n[q]) * (sweeps[q] + 1) * ((live + blk[q] - 1) / blk[q]);
-      order.push_back({cost, ising::BatchUnit{q, g}});
+    const double unit32 = static_cast<double>(n[q]) * sweeps[q] * 32.0;
+    if (group_trials == 0 && trials[q] > 0 && unit32 > per_cta && per_cta > 0) {
+      large[q] = 1;
+      any_large = true;
+      if (blk[q] > blk_large) blk_large = blk[q];
     }
   }
-  std::stable_sort(order.begin(), order.end(),
-                   [](const std::pair<double, ising::BatchUnit>& x, const std::pair<double, ising::BatchUnit>& y) {
-                     return x.first > y.first;
-                   });
+  auto unit_cost = [&](int32_t q, int live) {
+    return static_cast<double>(n[q]) * (sweeps[q] + 1) * (3.0 + (live + blk[q] - 1) / blk[q]);
+  };
+  auto widths = [&](int g_large, std::vector<int>& G) {
+    G.assign(static_cast<size_t>(m), 32);
+    for (int32_t q = 0; q < m; ++q) {
+      if (group_trials != 0) G[q] = group_trials;
+      else if (large[q]) G[q] = g_large;
+    }
+  };
+  auto units_of = [&](const std::vector<int>& G, std::vector<std::pair<double, ising::BatchUnit>>& order) {
+    order.clear();
+    for (int32_t q = 0; q < m; ++q) {
+      const int groups = (trials[q] + G[q] - 1) / G[q];
+      for (int g = 0; g < groups; ++g) order.push_back({unit_cost(q, std::min(G[q], trials[q] - g * G[q])),
+                                                        ising::BatchUnit{q, g}});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<double, ising::BatchUnit>& x, const std::pair<double, ising::BatchUnit>& y) {
+                       return x.first > y.first;
+                     });
+  };
+  auto makespan = [&](const std::vector<std::pair<double, ising::BatchUnit>>& order) {
+    std::vector<double> busy(static_cast<size_t>(grid > 0 ? grid : 1), 0.0);   // min-heap of CTA finish times
+    for (const auto& u : order) {
+      std::pop_heap(busy.begin(), busy.end(), std::greater<double>());
+      busy.back() += u.first;
+      std::push_heap(busy.begin(), busy.end(), std::greater<double>());
+    }
+    return *std::max_element(busy.begin(), busy.end());
+  };
+  std::vector<std::pair<double, ising::BatchUnit>> order;
+  std::vector<int> G;
+  int g_best = 32;
+  if (any_large) {
+    double best = 0.0;
+    for (int g = 32; g >= blk_large; g -= blk_large) {
+      widths(g, G);
+      units_of(G, order);
+      const double ms = makespan(order);
+      if (g == 32 || ms < best) {
+        best = ms;
+        g_best = g;
+      }
+    }
+  }
+  widths(g_best, G);
+  units_of(G, order);
+  bs->G = G;
   bs->units.resize(order.size());
   for (size_t u = 0; u < order.size(); ++u) bs->units[u] = order[u].second;
   return ISING_OK;

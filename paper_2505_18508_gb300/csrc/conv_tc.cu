@@ -430,12 +430,11 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(TcWgradArgs a) {
   unsigned char* sB = smem + 12 * blk;               // NB blocks: [kx][chunk][pixel][16 B]
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + NB * blk);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-  float* sbias = reinterpret_cast<float*>(tslot + 4);   // [32]
+  float* sbias = reinterpret_cast<float*>(tslot + 4);   // [warps][32] per-warp bias sums
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   for (int i = tid; i < static_cast<int>((12 + NB) * blk / 16); i += kTcThreads)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
-  if (tid < 32) sbias[tid] = 0.f;
   constexpr uint32_t tcols = N <= 32 ? 32 : 128;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
@@ -550,15 +549,30 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(TcWgradArgs a) {
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
-  // ---- bias partial sums
+  // ---- bias partial sums, in a fixed order (so training is reproducible):
+  // a butterfly within each warp, then the warps' sums in turn
   if (kKind == 2) {
-    atomicAdd(&sbias[0], bsum[0]);
-  } else {
+    float v = bsum[0];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) atomicAdd(&sbias[(tid & 3) * 8 + e], bsum[e]);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    sbias[warp * 32 + lane] = lane == 0 ? v : 0.f;
+  } else {
+    // lanes with equal lane & 3 hold the same eight channels
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      float v = bsum[e];
+      v += __shfl_xor_sync(0xFFFFFFFFu, v, 4);
+      v += __shfl_xor_sync(0xFFFFFFFFu, v, 8);
+      v += __shfl_xor_sync(0xFFFFFFFFu, v, 16);
+      if (lane < 4) sbias[warp * 32 + lane * 8 + e] = v;
+    }
   }
   __syncthreads();
-  if (tid < 32) a.bpart[static_cast<size_t>(blockIdx.x) * 32 + tid] = sbias[tid];
+  if (tid < 32) {
+    float v = 0.f;
+    for (int w = 0; w < kTcThreads / 32; ++w) v += sbias[w * 32 + tid];
+    a.bpart[static_cast<size_t>(blockIdx.x) * 32 + tid] = v;
+  }
   // ---- accumulator rows (ky, c) = warp, lane; rows 96..127 are not used
   float* out = a.part + static_cast<size_t>(blockIdx.x) * 96 * N;
   if (ok && !first) {
@@ -640,7 +654,7 @@ template <int kKind>
 size_t wgrad_smem_for(int X) {
   constexpr int NB = kKind == 2 ? 4 : 12;
   const size_t RP = static_cast<size_t>((X + 15) / 16) * 16;
-  return (12 + NB) * RP * 16 + 32 + 32 * sizeof(float);
+  return (12 + NB) * RP * 16 + 32 + (kTcThreads / 32) * 32 * sizeof(float);
 }
 
 template <int kKind>

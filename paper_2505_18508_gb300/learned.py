@@ -6,10 +6,16 @@ ising_flip_targets, ising_cut), called through the C ABI.
 Learned anneal (per instance, T trials, schedule of S sweeps):
     s <- the Philox starting state (ising_anneal with no sweeps)
     optional warm start: logits = CNN(s); whole-lattice proposal
-    for every chunk of `every` sweeps:
+    the sweeps before the first chunk that ends past `start`: one ising_anneal
+    for every later chunk of `every` sweeps:
         s <- ising_anneal(the chunk's betas, sweep_offset = chunk start, init = s)
         logits = CNN(s); tile proposals (exact dE <= 0 acceptance)
     cuts <- ising_cut(s)
+The batched form runs the sweeps before the proposal window for all
+instances in one persistent launch (ising_anneal_batched), then the window
+instance by instance; its results equal the per-instance form's, since the
+random stream is keyed by site, sweep and trial and a resumed run continues
+exactly.
 Every proposal is judged by its exact integer energy change, so the plain
 annealer's moves are never undone by a bad proposal; with the proposals
 removed the loop is exactly the plain annealer (resume is bit-exact).
@@ -23,7 +29,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import CNN, Problem, anneal, cut, flip_targets, propose  # noqa: F401
+from . import CNN, Problem, anneal, anneal_batched, cut, flip_targets, propose  # noqa: F401
 
 
 def _torch():
@@ -98,9 +104,25 @@ def train(net, data, steps, batch=16, lr=2e-3, seed=0, log_every=0):
     return losses
 
 
+def first_proposal_sweep(S, every, start):
+    """Start of the first `every`-sweep chunk that ends past sweep `start`
+    (chunks begin at multiples of `every`); S if there is none."""
+    k = max(0, -(-(start - every + 1) // every) * every)
+    return min(k, S)
+
+
+def _proposal_window(prob, net, s, trials, betas, seed, k_first, every, tile, acc_total, logits):
+    for k0 in range(k_first, len(betas), every):
+        s, _ = anneal(prob, trials, betas[k0:k0 + every], seed, sweep_offset=k0, init=s)
+        net.forward(prob, s, out=logits)
+        acc_total += propose(prob, s, logits, tile).to(acc_total.dtype)
+    return s
+
+
 def anneal_learned(prob, net, trials, betas, seed, every=100, tile=10, warm=False, stats=None, start=0):
     """The learned form; returns (spins, cuts) on the device.  Proposal rounds
-    run after every chunk that ends past sweep `start`."""
+    run after every chunk that ends past sweep `start`; the sweeps before the
+    first such chunk run in one call."""
     torch = _torch()
     S = len(betas)
     s = initial_state(prob, trials, seed)
@@ -109,12 +131,36 @@ def anneal_learned(prob, net, trials, betas, seed, every=100, tile=10, warm=Fals
     if warm:
         net.forward(prob, s, out=logits)
         acc_total += propose(prob, s, logits, 0).to(torch.int64)
-    for k0 in range(0, S, every):
-        s, _ = anneal(prob, trials, betas[k0:k0 + every], seed, sweep_offset=k0, init=s)
-        if k0 + every > start:
-            net.forward(prob, s, out=logits)
-            acc_total += propose(prob, s, logits, tile).to(torch.int64)
+    k_first = first_proposal_sweep(S, every, start)
+    if k_first > 0:
+        s, _ = anneal(prob, trials, betas[:k_first], seed, init=s)
+    s = _proposal_window(prob, net, s, trials, betas, seed, k_first, every, tile, acc_total, logits)
     cuts = cut(prob, s)
     if stats is not None:
         stats["accepted_per_trial"] = float(acc_total.double().mean().item())
     return s, cuts
+
+
+def anneal_learned_batched(probs, net, trials, betas, seeds, every=100, tile=10, start=0):
+    """The learned form over several instances (the same trial count and
+    schedule, one seed each): the sweeps before the proposal window in one
+    persistent launch over all instances, then each instance's window.
+    Returns ([spins], [cuts]); instance q's results equal
+    anneal_learned(probs[q], net, trials, betas, seeds[q], every, tile,
+    start=start)."""
+    torch = _torch()
+    S = len(betas)
+    m = len(probs)
+    k_first = first_proposal_sweep(S, every, start)
+    if k_first > 0:
+        states, _ = anneal_batched(probs, [trials] * m, [k_first] * m, [betas[:k_first]] * m, list(seeds))
+    else:
+        states = [initial_state(p, trials, sd) for p, sd in zip(probs, seeds)]
+    spins, cuts = [], []
+    for p, sd, s in zip(probs, seeds, states):
+        acc_total = torch.zeros(trials, dtype=torch.int64, device=s.device)
+        logits = torch.empty((trials, p.n), dtype=torch.float32, device=s.device)
+        s = _proposal_window(p, net, s, trials, betas, sd, k_first, every, tile, acc_total, logits)
+        spins.append(s)
+        cuts.append(cut(p, s))
+    return spins, cuts

@@ -111,19 +111,63 @@ def test_batch_schedule_covers_every_group_longest_first(ia):
     want = {(q, g) for q in range(len(shapes)) for g in range((trials[q] + G[q] - 1) // G[q])}
     got = [tuple(u) for u in units.tolist()]
     assert len(got) == len(want) and set(got) == want
-    # longest first: n (S + 1) x Philox blocks of the unit, non-increasing
-    cost = []
+    # longest first: n (S + 1) x (3 + Philox blocks of the unit), non-increasing
     Gi = [int(v) for v in G]
-    for q, g in got:
-        n = shapes[q][0] * shapes[q][1]
-        live = min(Gi[q], trials[q] - g * Gi[q])
-        cost.append(n * (sweeps[q] + 1) * ((live + 3) // 4))
+    cost = [_unit_cost(shapes, sweeps, trials, Gi, q, g, 4) for q, g in got]
     assert all(a >= b for a, b in zip(cost, cost[1:]))
-    # no unit above a CTA's average share unless it is one Philox block
+    # every 32-trial unit of this batch fits in a CTA's average share: all 32
     share = sum(x * y * s * t for (x, y), s, t in zip(shapes, sweeps, trials)) / (152 * per_sm)
-    for q in range(len(shapes)):
-        n = shapes[q][0] * shapes[q][1]
-        assert Gi[q] == 4 or n * sweeps[q] * Gi[q] <= share
+    assert max(x * y * s * 32 for (x, y), s in zip(shapes, sweeps)) <= share
+    assert Gi == [32] * len(shapes)
+
+
+def _unit_cost(shapes, sweeps, trials, G, q, g, blk):
+    n = shapes[q][0] * shapes[q][1]
+    live = min(G[q], trials[q] - g * G[q])
+    return n * (sweeps[q] + 1) * (3 + (live + blk - 1) // blk)
+
+
+def _lpt_makespan(costs, ctas):
+    """List scheduling in the given order onto `ctas` identical CTAs."""
+    import heapq
+    busy = [0.0] * ctas
+    for c in costs:
+        heapq.heapreplace(busy, busy[0] + c)
+    return max(busy)
+
+
+@pytest.mark.parametrize("case", ["8x200x100", "mixed", "8x200x100_16bit"])
+def test_batch_schedule_unit_width_minimises_the_makespan(ia, case):
+    """Instances whose 32-trial unit exceeds a CTA's average share take the
+    unit width (a multiple of the Philox block) whose longest-first schedule
+    ends first, ties to the wider; the others keep 32.  Checked against a
+    separate list-scheduling simulation of every candidate width."""
+    draw_bits = 16 if case.endswith("16bit") else 32
+    blk = 8 if draw_bits == 16 else 4
+    if case.startswith("8x200x100"):
+        shapes, trials, sweeps = [(200, 100)] * 8, [512] * 8, [30000] * 8
+    else:
+        shapes = [(200, 100)] * 4 + [(50, 100)] * 20
+        trials, sweeps = [512] * 4 + [64] * 20, [20000] * 4 + [2000] * 20
+    per_sm, _, G, units = ia.batch_schedule(shapes, trials, sweeps, draw_bits=draw_bits)
+    ctas = 152 * per_sm
+    total = sum(x * y * s * t for (x, y), s, t in zip(shapes, sweeps, trials))
+    large = [x * y * s * 32 > total / ctas for (x, y), s in zip(shapes, sweeps)]
+    assert any(large)
+    spans = {}
+    for g in range(32, blk - 1, -blk):
+        Gc = [g if large[q] else 32 for q in range(len(shapes))]
+        cs = sorted((_unit_cost(shapes, sweeps, trials, Gc, q, k, blk)
+                     for q in range(len(shapes)) for k in range(-(-trials[q] // Gc[q]))), reverse=True)
+        spans[g] = _lpt_makespan(cs, ctas)
+    best = min(spans.values())
+    g_want = max(g for g, v in spans.items() if v == best)
+    Gi = [int(v) for v in G]
+    assert Gi == [g_want if large[q] else 32 for q in range(len(shapes))]
+    assert units.shape[0] == sum(-(-t // g) for t, g in zip(trials, Gi))
+    if case == "8x200x100":
+        assert g_want == 28 and units.shape[0] == 152        # 18 x 28 + 8 trials per instance
+        assert spans[28] < spans[32] < spans[24]
 
 
 def test_batch_schedule_small_tori_take_two_ctas_per_sm(ia):

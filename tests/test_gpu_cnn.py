@@ -81,6 +81,23 @@ def test_gradient_against_fp64(ia, X, Y, B):
     net.destroy(); prob.destroy()
 
 
+def test_gradient_is_reproducible(ia):
+    """Every reduction of the backward pass runs in a fixed order: the same
+    batch gives the same gradient, bit for bit (so training is reproducible),
+    on a batch large enough to spread over many CTAs."""
+    import torch
+    inst = synth.torus_instance(100, 100, 19)
+    prob = ia.Problem.from_instance(inst)
+    net = ia.CNN(_params(5))
+    s = torch.from_numpy(synth.random_spins(16, prob.n, 5)).cuda()
+    y = torch.from_numpy(ocnn.flip_targets(synth.random_spins(16, prob.n, 5),
+                                           synth.random_spins(16, prob.n, 6))).cuda()
+    grads = [net.grad(prob, s, y)[1].clone() for _ in range(3)]
+    torch.cuda.synchronize()
+    assert all(torch.equal(grads[0], g) for g in grads[1:])
+    net.destroy(); prob.destroy()
+
+
 def test_adam_step_matches_formula(ia):
     import torch
     params = _params(3).astype(np.float32)

@@ -96,3 +96,47 @@ def test_training_and_gain_at_proposal_points(ia):
     assert g_trained > 0.0
     assert g_trained > g_untrained
     net.destroy(); untrained.destroy()
+
+
+def test_window_and_batched_forms_equal_the_chunked_loop(ia):
+    """The learned form with a proposal window: the sweeps before the window
+    in one call (anneal_learned), or in one persistent launch over all
+    instances (anneal_learned_batched), give the spins and cuts of the loop
+    that runs every chunk on its own and proposes after the chunks that end
+    past `start`."""
+    import torch
+    from paper_2505_18508_gb300 import learned
+    S, every, tile, T, start = 400, 100, 2, 40, 250     # tiles per side: even (or one)
+    insts = [synth.torus_instance(20, 12, 81), synth.torus_instance(24, 16, 82)]
+    probs = [ia.Problem.from_instance(i) for i in insts]
+    betas = synth.linear_betas(0.1, 3.0, S)
+    seeds = [501, 502]
+    net = ia.CNN(ocnn.init_params(9, scale=0.8))
+    ref, n_acc = [], 0
+    for p, sd in zip(probs, seeds):
+        s = learned.initial_state(p, T, sd)
+        for k0 in range(0, S, every):
+            s, _ = ia.anneal(p, T, betas[k0:k0 + every], sd, sweep_offset=k0, init=s)
+            if k0 + every > start:
+                n_acc += int(ia.propose(p, s, net.forward(p, s), tile).sum().item())
+        ref.append((s, ia.cut(p, s)))
+    assert n_acc > 0
+    assert learned.first_proposal_sweep(S, every, start) == 200
+    for q, (p, sd) in enumerate(zip(probs, seeds)):
+        st = {}
+        s1, c1 = learned.anneal_learned(p, net, T, betas, sd, every=every, tile=tile, start=start, stats=st)
+        torch.cuda.synchronize()
+        assert torch.equal(s1, ref[q][0]) and torch.equal(c1, ref[q][1])
+    sb, cb = learned.anneal_learned_batched(probs, net, T, betas, seeds, every=every, tile=tile, start=start)
+    torch.cuda.synchronize()
+    for q in range(len(probs)):
+        assert torch.equal(sb[q], ref[q][0]) and torch.equal(cb[q], ref[q][1])
+    # no window at all: the batched form is the plain batched annealer
+    sp, cp = learned.anneal_learned_batched(probs, net, T, betas, seeds, every=every, tile=tile, start=S)
+    for q, (p, sd) in enumerate(zip(probs, seeds)):
+        s0, c0 = ia.anneal(p, T, betas, sd)
+        torch.cuda.synchronize()
+        assert torch.equal(sp[q], s0) and torch.equal(cp[q], c0)
+    net.destroy()
+    for p in probs:
+        p.destroy()
