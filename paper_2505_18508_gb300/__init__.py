@@ -42,6 +42,38 @@ def _dptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _device_tensor(t, dtype, shape, name, write=False):
+    """The C ABI takes raw device pointers: check that `t` is a tensor on the
+    current CUDA device with this dtype and shape (None: any), before any
+    pointer reaches a kernel.  Inputs are made contiguous; tensors the call
+    writes into (write=True) must already be.  Raises ValueError."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch.Tensor, got {type(t).__name__}")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be on the current CUDA device, got {t.device}")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: must be on the current CUDA device (cuda:{torch.cuda.current_device()}), "
+                         f"got {t.device}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if shape is not None and tuple(t.shape) != tuple(int(v) for v in shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(int(v) for v in shape)}")
+    if not t.is_contiguous():
+        if write:
+            raise ValueError(f"{name}: written in place, so it must be contiguous")
+        t = t.contiguous()
+    return t
+
+
+def _rows(t, name):
+    """Row count of a 2-D tensor argument (checked before use)."""
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.dim() != 2:
+        raise ValueError(f"{name}: expected a 2-D tensor [rows, sites]")
+    return int(t.shape[0])
+
+
 class Problem:
     """A validated instance packed on the current CUDA device: a torus
     (from_csr / from_instance) or a general sparse graph (from_graph)."""
@@ -175,11 +207,14 @@ def anneal(prob, trials, betas, seed, sweep_offset=0, init=None, out_spins=None,
     dev = torch.device("cuda", torch.cuda.current_device())
     if want_spins and out_spins is None:
         out_spins = torch.empty((trials, prob.n), dtype=torch.int8, device=dev)
+    elif want_spins:
+        out_spins = _device_tensor(out_spins, torch.int8, (trials, prob.n), "out_spins", write=True)
     if out_cuts is None:
         out_cuts = torch.empty((trials,), dtype=torch.int32, device=dev)
+    else:
+        out_cuts = _device_tensor(out_cuts, torch.int32, (trials,), "out_cuts", write=True)
     if init is not None:
-        assert init.is_cuda and init.dtype == torch.int8 and init.shape == (trials, prob.n)
-        init = init.contiguous()
+        init = _device_tensor(init, torch.int8, (trials, prob.n), "init")
     rc = lib().ising_anneal(prob.handle, int(trials), betas.ctypes.data_as(ctypes.c_void_p),
                             int(betas.shape[0]), int(seed) & 0xFFFFFFFFFFFFFFFF,
                             int(sweep_offset) & 0xFFFFFFFF, _dptr(init),
@@ -205,8 +240,7 @@ def anneal_trace(prob, trials, betas, seed, trace_every, sweep_offset=0, init=No
     best = torch.empty((trials,), dtype=torch.int32, device=dev)
     best_spins = torch.empty((trials, prob.n), dtype=torch.int8, device=dev) if want_best_spins else None
     if init is not None:
-        assert init.is_cuda and init.dtype == torch.int8 and init.shape == (trials, prob.n)
-        init = init.contiguous()
+        init = _device_tensor(init, torch.int8, (trials, prob.n), "init")
     rc = lib().ising_anneal_trace(prob.handle, int(trials), betas.ctypes.data_as(ctypes.c_void_p), S,
                                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(sweep_offset) & 0xFFFFFFFF, _dptr(init),
                                   _dptr(spins), _dptr(cuts), int(trace_every), _dptr(trace) if points else None,
@@ -311,10 +345,12 @@ def philox(counters, seed, stream=None):
 def energy(prob, spins, out=None, stream=None):
     """Eq. 2 (with fields) of each row of an int8 CUDA tensor [k, n] -> int64."""
     torch = _torch()
-    spins = spins.contiguous()
-    k = spins.shape[0]
+    k = _rows(spins, "spins")
+    spins = _device_tensor(spins, torch.int8, (k, prob.n), "spins")
     if out is None:
         out = torch.empty((k,), dtype=torch.int64, device=spins.device)
+    else:
+        out = _device_tensor(out, torch.int64, (k,), "out", write=True)
     check(lib().ising_energy(prob.handle, _dptr(spins), int(k), _dptr(out), _stream_ptr(stream)), "ising_energy")
     return out
 
@@ -322,10 +358,12 @@ def energy(prob, spins, out=None, stream=None):
 def cut(prob, spins, out=None, stream=None):
     """Exact Eq. 1 cut of each row of an int8 CUDA tensor [k, n]."""
     torch = _torch()
-    spins = spins.contiguous()
-    k = spins.shape[0]
+    k = _rows(spins, "spins")
+    spins = _device_tensor(spins, torch.int8, (k, prob.n), "spins")
     if out is None:
         out = torch.empty((k,), dtype=torch.int32, device=spins.device)
+    else:
+        out = _device_tensor(out, torch.int32, (k,), "out", write=True)
     check(lib().ising_cut(prob.handle, _dptr(spins), int(k), _dptr(out), _stream_ptr(stream)), "ising_cut")
     return out
 
@@ -432,10 +470,12 @@ class CNN:
 
     def forward(self, prob, spins, out=None, stream=None):
         torch = _torch()
-        spins = spins.contiguous()
-        B = spins.shape[0]
+        B = _rows(spins, "spins")
+        spins = _device_tensor(spins, torch.int8, (B, prob.n), "spins")
         if out is None:
             out = torch.empty((B, prob.n), dtype=torch.float32, device=spins.device)
+        else:
+            out = _device_tensor(out, torch.float32, (B, prob.n), "out", write=True)
         ws, need = self._workspace(B, prob.n, 0)
         check(lib().ising_cnn_forward(self._h, prob.handle, _dptr(spins), int(B), _dptr(out), _dptr(ws),
                                       ctypes.c_size_t(ws.numel()), _stream_ptr(stream)), "ising_cnn_forward")
@@ -443,9 +483,9 @@ class CNN:
 
     def grad(self, prob, spins, targets, stream=None):
         torch = _torch()
-        spins = spins.contiguous()
-        targets = targets.contiguous()
-        B = spins.shape[0]
+        B = _rows(spins, "spins")
+        spins = _device_tensor(spins, torch.int8, (B, prob.n), "spins")
+        targets = _device_tensor(targets, torch.uint8, (B, prob.n), "targets")
         g = torch.empty(CNN_PARAMS, dtype=torch.float32, device=spins.device)
         loss = torch.empty(1, dtype=torch.float32, device=spins.device)
         ws, need = self._workspace(B, prob.n, 1)
@@ -454,6 +494,7 @@ class CNN:
         return loss, g
 
     def adam_step(self, grad, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        grad = _device_tensor(grad, _torch().float32, (CNN_PARAMS,), "grad")
         check(lib().ising_cnn_adam_step(self._h, _dptr(grad), ctypes.c_float(lr), ctypes.c_float(beta1),
                                         ctypes.c_float(beta2), ctypes.c_float(eps), _stream_ptr(stream)),
               "ising_cnn_adam_step")
@@ -473,10 +514,14 @@ class CNN:
 def propose(prob, spins, logits, tile, accepted=None, stream=None):
     """Exact-acceptance proposals in place on spins (see ising_propose); returns accepted [B]."""
     torch = _torch()
-    B = spins.shape[0]
+    B = _rows(spins, "spins")
+    spins = _device_tensor(spins, torch.int8, (B, prob.n), "spins", write=True)
+    logits = _device_tensor(logits, torch.float32, (B, prob.n), "logits")
     if accepted is None:
         accepted = torch.zeros(B, dtype=torch.int32, device=spins.device)
-    check(lib().ising_propose(prob.handle, _dptr(spins), int(B), _dptr(logits.contiguous()), int(tile),
+    else:
+        accepted = _device_tensor(accepted, torch.int32, (B,), "accepted", write=True)
+    check(lib().ising_propose(prob.handle, _dptr(spins), int(B), _dptr(logits), int(tile),
                               _dptr(accepted), _stream_ptr(stream)), "ising_propose")
     return accepted
 
@@ -484,11 +529,14 @@ def propose(prob, spins, logits, tile, accepted=None, stream=None):
 def flip_targets(spins, ref, out=None, stream=None):
     """Gauge-aligned flip targets (ising_flip_targets): uint8 [B, n]."""
     torch = _torch()
-    spins = spins.contiguous()
-    ref = ref.contiguous()
-    B, n = spins.shape
+    B = _rows(spins, "spins")
+    n = int(spins.shape[1])
+    spins = _device_tensor(spins, torch.int8, (B, n), "spins")
+    ref = _device_tensor(ref, torch.int8, (B, n), "ref")
     if out is None:
         out = torch.empty((B, n), dtype=torch.uint8, device=spins.device)
+    else:
+        out = _device_tensor(out, torch.uint8, (B, n), "out", write=True)
     check(lib().ising_flip_targets(_dptr(spins), _dptr(ref), int(B), int(n), _dptr(out), _stream_ptr(stream)),
           "ising_flip_targets")
     return out
