@@ -33,6 +33,7 @@ import synth  # noqa: E402
 METRIC = "spin-updates/s; time-to-99.9%-cut on 200x100 +-1 torus, learned vs plain"
 WORKLOAD = {"X": 200, "Y": 100, "inst_seed": 2, "trials": 1024, "sweeps": 10000, "beta0": 0.1, "beta1": 3.0,
             "seed": 1002}
+WORKLOAD_NAME = "plain annealer, 200x100 +-1 torus (20,000 spins), 1,024 trials x 10,000 sweeps, beta 0.1->3.0"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PEAK_HBM_GBS = float(json.load(open(PEAKS_FILE)).get("hbm_gbs", 6800.0)) if os.path.exists(PEAKS_FILE) else 6800.0
 # Integer multiply lanes per SM per clock (32-bit IMAD; a 32x32->64 multiply
@@ -412,7 +413,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "spin-updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_ups / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": {"workload": "200x100 torus, oracle sample (CPU)", **w},
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, **w, "updates_per_step": updates_per_step(w)},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -592,8 +593,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "plain annealer, 200x100 +-1 torus (20,000 spins), 1,024 trials x "
-                                   "10,000 sweeps, beta 0.1->3.0", **w, "updates_per_step": ups,
+            "config": {"workload": WORKLOAD_NAME, **w, "updates_per_step": ups,
                        "l2": "flushed between steps (256 MB write)", "launch": shape},
             "e2e": {"value": ws * ups / (e2e_step_ms / 1e3), "unit": "spin-updates/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step_ms},
