@@ -4,12 +4,17 @@
     python -m paper_2505_18508_gb300.probe.legs batched [--scale 0.1] [--ctas-per-sm 0]
     python -m paper_2505_18508_gb300.probe.legs pt [--rounds 200] [--sweeps-per-round 50]
     python -m paper_2505_18508_gb300.probe.legs graph [--graph g22] [--sweeps 2000] [--threads-per-site 0] [--strips 0]
+    python -m paper_2505_18508_gb300.probe.legs trace [--trace-every 100]
 
 * batched: the 96-instance uneven batch of {50,100,140,200}x100 tori
   (32-512 trials, 2,000-20,000 sweeps, each sweep count times --scale) as one
   graph-replayed persistent launch;
 * pt: replica exchange on the 200x100 torus, 8 temperatures (geometric
   0.5..3.0) x 128 chains;
+* trace: the 200x100 torus, 1,024 trials x 10,000 sweeps, read out along
+  the trajectory (ising_anneal_trace: every trial's cut after every
+  --trace-every sweeps, best-so-far cut and configuration) against the same
+  anneal read out at the end only;
 * graph: 1,024 trials on a general graph: g22 (2,000 vertices, 19,990 edges,
   w = +1), r20k (20,000 vertices, 40,000 edges, w = +-1) or the 200x100 torus
   given as a graph.
@@ -104,9 +109,26 @@ def graph(args):
     prob.destroy()
 
 
+def trace(args):
+    import synth
+    import paper_2505_18508_gb300 as ia
+    inst = synth.torus_instance(200, 100, 2)
+    prob = ia.Problem.from_instance(inst)
+    betas = synth.linear_betas(0.1, 3.0, 10000)
+    ups = 1024 * 10000 * inst["n"]
+    ia.anneal(prob, 1024, betas, 1)
+    ia.anneal_trace(prob, 1024, betas, 1, args.trace_every)
+    for r in range(args.reps):
+        ms_plain = _time(lambda: ia.anneal(prob, 1024, betas, 1002 + r))
+        ms_trace = _time(lambda: ia.anneal_trace(prob, 1024, betas, 1002 + r, args.trace_every))
+        print(json.dumps({"leg": "trace", "trace_every": args.trace_every, "ms_plain": ms_plain, "ms_trace": ms_trace,
+                          "updates_per_s_trace": ups / (ms_trace * 1e-3), "overhead": ms_trace / ms_plain - 1.0}))
+    prob.destroy()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("leg", choices=["batched", "pt", "graph"])
+    ap.add_argument("leg", choices=["batched", "pt", "graph", "trace"])
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--group-trials", type=int, default=0)
@@ -116,11 +138,12 @@ def main(argv=None):
     ap.add_argument("--graph", default="g22", choices=["g22", "r20k", "torus"])
     ap.add_argument("--trials", type=int, default=1024)
     ap.add_argument("--sweeps", type=int, default=2000)
+    ap.add_argument("--trace-every", type=int, default=100)
     ap.add_argument("--threads-per-site", type=int, default=0, help="general graphs: 1, 4, 8 or 0 (automatic)")
     ap.add_argument("--strips", type=int, default=0, help="general graphs: CTAs per trial group (1-8; 0: automatic)")
     args = ap.parse_args(argv)
     _setup()
-    {"batched": batched, "pt": pt, "graph": graph}[args.leg](args)
+    {"batched": batched, "pt": pt, "graph": graph, "trace": trace}[args.leg](args)
     return 0
 
 
