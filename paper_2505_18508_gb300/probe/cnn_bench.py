@@ -8,7 +8,10 @@ Prints one JSON line: milliseconds per call (CUDA events, after warm-up),
 useful TFLOP/s (2 * 9 * (3*32 + 32*32*2 + 32*1) flops per site per forward)
 and the forward's algorithmic HBM bytes per site: spins in (1 B), the three
 BF16 activation maps written and read once each (3 * 2 * 64 B) and FP32
-logits out (4 B) = 389 B.  Inputs are seeded synthetic tori and spins.
+logits out (4 B) = 389 B.  Also the tile proposals on those logits
+(ising_propose, 10 x 10 tiles, exact dE <= 0 acceptance; timed last, in
+place): 6 algorithmic HBM bytes per site (spins read and written, FP32 logits
+read).  Inputs are seeded synthetic tori and spins.
 """
 import argparse
 import json
@@ -17,6 +20,7 @@ import sys
 
 FLOP_PER_SITE = 2 * 9 * (3 * 32 + 32 * 32 * 2 + 32 * 1)
 BYTES_PER_SITE = 1 + 3 * 2 * 64 + 4
+PROPOSE_BYTES_PER_SITE = 1 + 4 + 1
 
 
 def main(argv=None):
@@ -57,6 +61,7 @@ def main(argv=None):
 
     fwd_ms = timed(lambda: net.forward(prob, s, out=z), args.reps)
     grad_ms = timed(lambda: net.grad(prob, s, y), max(1, args.reps // 4))
+    prop_ms = timed(lambda: ia.propose(prob, s, z, 10), args.reps)
     sites = B * X * Y
     out = {
         "workload": f"{B} x {X}x{Y} spin configurations",
@@ -65,6 +70,8 @@ def main(argv=None):
         "forward_gbs": BYTES_PER_SITE * sites / (fwd_ms * 1e-3) / 1e9,
         "grad_ms": grad_ms,
         "grad_status": prob.get_status(),
+        "propose_ms": prop_ms,
+        "propose_gbs": PROPOSE_BYTES_PER_SITE * sites / (prop_ms * 1e-3) / 1e9,
     }
     print(json.dumps(out), flush=True)
     net.destroy()
