@@ -224,6 +224,22 @@ int ising_batch_schedule(int32_t m, const int32_t* X, const int32_t* Y, const in
                          int32_t cap, int32_t* nunits);
 
 /*
+ * ising_thresholds -- the acceptance thresholds every annealing call of this
+ * library uploads for its schedule (host only; no GPU, no handle).  The
+ * Metropolis rule accepts an uphill move of dE > 0 with probability
+ * exp(-beta dE) (the paper leaves its own rule unpublished, Section III; on
+ * the +-1 torus dE is 4 or 8, from Eq. 2 with J = -w, h = 0): a draw u is
+ * accepted iff u < T_dE.  betas: host double [S], each > 0 (+inf allowed).
+ * out: host uint32 [S][2] receives (T_4, T_8) per sweep, with
+ * T_d = min(floor(exp(-beta d) 2^32), 2^32 - 1); with draw_bits 16,
+ * min(floor(exp(-beta d) 2^16), 2^16 - 1) stored shifted left by 16 bits
+ * (the form the kernels compare against).  exp is the host C library's, in
+ * double precision.  Errors: ISING_ERR_ARG (S < 0, a NULL pointer with
+ * S > 0, draw_bits not 16 or 32, a beta that is not > 0), ISING_ERR_OOM.
+ */
+int ising_thresholds(const double* betas, int32_t S, int32_t draw_bits, uint32_t* out);
+
+/*
  * ising_flow_split -- the persistent kernel's division of work, for
  * inspection and tests (host only; no GPU, no handle).  The rows of all
  * ceil(trials / group_trials) trial groups of a Y-row torus with H = X/2 site

@@ -23,7 +23,7 @@ from . import _abi
 from ._abi import IsingError, check, lib
 
 __all__ = ["Problem", "anneal", "anneal_trace", "cut", "energy", "greedy_colouring", "anneal_batched", "BatchPlan",
-           "IsingError", "lib", "spins_to_hex", "hex_to_spins", "philox", "anneal_pt"]
+           "IsingError", "lib", "spins_to_hex", "hex_to_spins", "philox", "anneal_pt", "thresholds"]
 
 
 def _torch():
@@ -328,6 +328,17 @@ def batch_schedule(shapes, trials, sweeps, draw_bits=32, group_trials=0, ctas_pe
                                      ctypes.byref(threads), vp(G), vp(units), cap, ctypes.byref(k)),
           "ising_batch_schedule")
     return per_sm.value, threads.value, G, units[:k.value].copy()
+
+
+def thresholds(betas, draw_bits=32):
+    """The library's acceptance thresholds for a schedule (ising_thresholds,
+    host only): uint32 [S, 2] of (T_4, T_8) per sweep; in the 16-bit mode
+    shifted left by 16 bits, as the kernels compare them."""
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    out = np.zeros((b.shape[0], 2), dtype=np.uint32)
+    check(lib().ising_thresholds(b.ctypes.data_as(ctypes.c_void_p), int(b.shape[0]), int(draw_bits),
+                                 out.ctypes.data_as(ctypes.c_void_p)), "ising_thresholds")
+    return out
 
 
 def philox(counters, seed, stream=None):

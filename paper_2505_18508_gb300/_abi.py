@@ -47,6 +47,7 @@ _SIGNATURES = {
     "ising_problem_info": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "ising_set_kernel": (ctypes.c_int, [_vp, _i32]),
     "ising_set_graph_threads_per_site": (ctypes.c_int, [_vp, _i32]),
+    "ising_thresholds": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
     "ising_flow_split": (ctypes.c_int, [_i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp, _i32, _vp, _vp, _vp]),
     "ising_batch_schedule": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp,
                                             _vp, _i32, _vp]),

@@ -885,6 +885,19 @@ int ising_batch_schedule(int32_t m, const int32_t* X, const int32_t* Y, const in
   return ISING_OK;
 }
 
+int ising_thresholds(const double* betas, int32_t S, int32_t draw_bits, uint32_t* out) {
+  if (S < 0 || (S > 0 && (!betas || !out)) || (draw_bits != 32 && draw_bits != 16)) return ISING_ERR_ARG;
+  std::vector<uint32_t> t;
+  try {
+    const int rc = make_thresholds(betas, S, t, draw_bits);
+    if (rc != ISING_OK) return rc;
+  } catch (const std::bad_alloc&) {
+    return ISING_ERR_OOM;
+  }
+  if (!t.empty()) std::memcpy(out, t.data(), t.size() * sizeof(uint32_t));
+  return ISING_OK;
+}
+
 int ising_flow_split(int32_t Y, int32_t H, int32_t trials, int32_t group_trials, int32_t draw_bits, int32_t sms,
                      int32_t weighted, int32_t* split_out, int32_t cap, int32_t* ctas, int32_t* local_rows_max,
                      int32_t* segments_max) {
