@@ -243,9 +243,15 @@ int batch_schedule(int32_t m, const int32_t* n, const int32_t* H, const int32_t*
   std::vector<int> G;
   int g_best = 32;
   if (any_large) {
+    // narrower units only add units: stop before a simulation would take
+    // more than ~2^20 of them (such batches keep 32 trials per unit)
+    constexpr size_t kMaxSimUnits = size_t(1) << 20;
     double best = 0.0;
     for (int g = 32; g >= blk_large; g -= blk_large) {
       widths(g, G);
+      size_t count = 0;
+      for (int32_t q = 0; q < m; ++q) count += static_cast<size_t>((trials[q] + G[q] - 1) / G[q]);
+      if (count > kMaxSimUnits) break;
       units_of(G, order);
       const double ms = makespan(order);
       if (g == 32 || ms < best) {
