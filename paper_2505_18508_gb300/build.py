@@ -73,5 +73,29 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+def build_program(src: str, exe: str, flags=("-O3", "-lineinfo"), force: bool = False) -> str:
+    """Compile a stand-alone CUDA program (one .cu file) for sm_103a into
+    `exe`, unless it is newer than its source."""
+    if not force and os.path.exists(exe) and os.path.getmtime(exe) >= os.path.getmtime(src):
+        return exe
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    tmp = f"{exe}.tmp{os.getpid()}"
+    r = subprocess.run([nvcc(), *ARCH, *flags, "-o", tmp, src], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, exe)
+    return exe
+
+
+PROBE_SRC = os.path.join(HERE, "probe", "alu_peak.cu")
+PROBE_EXE = os.path.join(OUT_DIR, "alu_peak")
+
+
+def build_probe(force: bool = False) -> str:
+    """The integer-pipe peak probe (probe/alu_peak.cu)."""
+    return build_program(PROBE_SRC, PROBE_EXE, force=force)
+
+
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+    print(build_probe(force=True))

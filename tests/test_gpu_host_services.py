@@ -5,7 +5,6 @@ ISING_LOG launch line."""
 import os
 import subprocess
 import sys
-import tempfile
 
 import numpy as np
 import pytest
@@ -38,9 +37,9 @@ def test_philox_matches_oracle(ia):
 
 
 def test_philox_matches_curand(ia):
-    from paper_2505_18508_gb300.build import ARCH, nvcc
-    exe = os.path.join(tempfile.mkdtemp(), "curand_philox")
-    subprocess.run([nvcc(), *ARCH, "-O2", "-o", exe, os.path.join(ROOT, "tests", "curand_philox.cu")], check=True)
+    import __graft_entry__
+    from paper_2505_18508_gb300.build import build_program
+    exe = build_program(__graft_entry__.CURAND_CHECK_SRC, __graft_entry__.CURAND_CHECK_EXE, ("-O2",))
     for seed, sub in ((0x1234_5678_9ABC_DEF0, 7), (42, 0x1_0000_0003), (0, 0)):
         out = subprocess.run([exe, hex(seed), hex(sub), "6"], capture_output=True, text=True, check=True).stdout
         cur = [[int(w, 16) for w in line.split()] for line in out.strip().splitlines()]
