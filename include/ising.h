@@ -56,7 +56,7 @@ extern "C" {
 #define ISING_ERR_OOM           -5  /* host or device allocation failed */
 #define ISING_ERR_CUDA          -6  /* a CUDA runtime call or kernel launch failed */
 #define ISING_ERR_TIMEOUT       -7  /* a bounded device-side wait ran out */
-#define ISING_ERR_UNSUPPORTED   -8  /* valid input beyond what this build handles */
+#define ISING_ERR_UNSUPPORTED   -8  /* valid input beyond what this library handles */
 
 typedef struct ising_problem ising_problem;
 

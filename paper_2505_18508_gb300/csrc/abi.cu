@@ -725,7 +725,7 @@ const char* ising_strerror(int code) {
     case ISING_ERR_OOM: return "out of memory";
     case ISING_ERR_CUDA: return "CUDA error";
     case ISING_ERR_TIMEOUT: return "bounded device wait timed out";
-    case ISING_ERR_UNSUPPORTED: return "valid input outside what this build supports";
+    case ISING_ERR_UNSUPPORTED: return "valid input outside what this library supports";
     default: return "unknown status code";
   }
 }
