@@ -187,3 +187,14 @@ def test_batch_schedule_fixed_shapes_and_16_bit(ia):
         ia.batch_schedule(shapes, trials, sweeps, draw_bits=16, group_trials=12)
     with pytest.raises(ia.IsingError):
         ia.batch_schedule([(5, 8)], [32], [10])
+
+
+def test_batch_schedule_degenerate_batches(ia):
+    per_sm, threads, G, units = ia.batch_schedule([], [], [])
+    assert G.shape == (0,) and units.shape == (0, 2)
+    _, _, G, units = ia.batch_schedule([(8, 8)], [0], [10])            # no trials: no units
+    assert units.shape == (0, 2)
+    _, _, G, units = ia.batch_schedule([(8, 8), (200, 100)], [0, 5], [10, 0])
+    assert [tuple(u) for u in units.tolist()] == [(1, 0)]             # 5 trials, no sweeps: one unit
+    _, _, G, units = ia.batch_schedule([(200, 100)], [3], [100])
+    assert G.tolist() == [32] and units.tolist() == [[0, 0]]           # every width gives one unit: the widest
