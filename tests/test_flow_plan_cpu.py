@@ -59,6 +59,27 @@ CASES = [
 
 @pytest.mark.parametrize("X,Y,T,G,bits,sms,weighted", CASES)
 def test_flow_split_invariants(ia, X, Y, T, G, bits, sms, weighted):
+    _check_split(ia, X, Y, T, G, bits, sms, weighted)
+
+
+def test_flow_split_invariants_random_shapes(ia):
+    """The same invariants on 120 random shapes: even sides 4..400, every
+    group width and both draw modes, 1..160 SMs, and up to 5,000 trials
+    (capped so a case stacks at most 60,000 site words)."""
+    rng = np.random.default_rng(2026)
+    for _ in range(120):
+        bits = int(rng.choice([32, 16]))
+        blk = 8 if bits == 16 else 4
+        X = 2 * int(rng.integers(2, 201))
+        Y = 2 * int(rng.integers(2, 201))
+        G = blk * int(rng.integers(1, 32 // blk + 1))
+        groups_max = max(1, 60000 // (Y * (X // 2)))
+        T = int(rng.integers(1, min(5000, groups_max * G) + 1))
+        sms = int(rng.integers(1, 161))
+        _check_split(ia, X, Y, T, G, bits, sms, bool(rng.integers(0, 2)))
+
+
+def _check_split(ia, X, Y, T, G, bits, sms, weighted):
     H = X // 2
     split, lrmax, segmax = ia.flow_split(Y, X, T, G, bits, sms, weighted)
     w = _weights(Y, T, G, 8 if bits == 16 else 4, weighted)
