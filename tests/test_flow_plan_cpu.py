@@ -219,3 +219,39 @@ def test_batch_schedule_degenerate_batches(ia):
     assert [tuple(u) for u in units.tolist()] == [(1, 0)]             # 5 trials, no sweeps: one unit
     _, _, G, units = ia.batch_schedule([(200, 100)], [3], [100])
     assert G.tolist() == [32] and units.tolist() == [[0, 0]]           # every width gives one unit: the widest
+
+
+def test_batch_schedule_random_batches(ia):
+    """40 random uneven batches (1-20 tori of even sides 4..200, 1-600
+    trials, 1-3,000 sweeps, both draw modes): every unit once, longest first
+    under the cost model, and each large instance's width the one whose
+    list schedule ends first (ties to the wider), per a separate simulation."""
+    rng = np.random.default_rng(11)
+    for _ in range(40):
+        m = int(rng.integers(1, 21))
+        bits = int(rng.choice([32, 16]))
+        blk = 8 if bits == 16 else 4
+        shapes = [(2 * int(rng.integers(2, 101)), 2 * int(rng.integers(2, 101))) for _ in range(m)]
+        trials = [int(rng.integers(1, 601)) for _ in range(m)]
+        sweeps = [int(rng.integers(1, 3001)) for _ in range(m)]
+        per_sm, _, G, units = ia.batch_schedule(shapes, trials, sweeps, draw_bits=bits)
+        Gi = [int(v) for v in G]
+        got = [tuple(u) for u in units.tolist()]
+        assert sorted(got) == sorted((q, g) for q in range(m) for g in range(-(-trials[q] // Gi[q])))
+        cost = [_unit_cost(shapes, sweeps, trials, Gi, q, g, blk) for q, g in got]
+        assert all(a >= b for a, b in zip(cost, cost[1:]))
+        ctas = 152 * per_sm
+        total = sum(x * y * s * t for (x, y), s, t in zip(shapes, sweeps, trials))
+        large = [x * y * s * 32 > total / ctas for (x, y), s in zip(shapes, sweeps)]
+        if not any(large):
+            assert Gi == [32] * m
+            continue
+        spans = {}
+        for g in range(32, blk - 1, -blk):
+            Gc = [g if large[q] else 32 for q in range(m)]
+            cs = sorted((_unit_cost(shapes, sweeps, trials, Gc, q, k, blk)
+                         for q in range(m) for k in range(-(-trials[q] // Gc[q]))), reverse=True)
+            spans[g] = _lpt_makespan(cs, ctas)
+        best = min(spans.values())
+        g_want = max(g for g, v in spans.items() if v == best)
+        assert Gi == [g_want if large[q] else 32 for q in range(m)]
