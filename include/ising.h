@@ -161,8 +161,11 @@ int ising_batch_create(ising_problem* const* probs, int32_t m, const int32_t* tr
                        const uint64_t* seeds, int8_t* const* out_spins,
                        int32_t* const* out_cuts, int32_t group_trials,
                        int32_t ctas_per_sm, void* cuda_stream, ising_batch** out);
+/* ising_batch_launch -- replay the plan on cuda_stream (asynchronous).
+ * Errors: ISING_ERR_ARG (NULL plan), ISING_ERR_CUDA. */
 int ising_batch_launch(ising_batch* b, void* cuda_stream);
-/* Frees the plan; waits for the plan's last launch to finish first. */
+/* Frees the plan; waits for the plan's last launch to finish first (NULL is
+ * a no-op). */
 void ising_batch_destroy(ising_batch* b);
 
 /*
@@ -482,6 +485,8 @@ typedef struct ising_cnn ising_cnn;
 /* ising_cnn_create -- copy ISING_CNN_PARAMS host floats to a new network on
  * the current device (Adam state zeroed).  Errors: ISING_ERR_ARG, _OOM, _CUDA. */
 int ising_cnn_create(const float* params, ising_cnn** out);
+/* ising_cnn_destroy -- free the network's device memory (NULL is a no-op);
+ * the caller must not destroy it while work that uses it is still queued. */
 void ising_cnn_destroy(ising_cnn* net);
 /* host copy of the FP32 master parameters */
 int ising_cnn_get_params(const ising_cnn* net, float* params);
