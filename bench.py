@@ -6,11 +6,15 @@ instance seed 2), 1,024 trials x 10,000 Metropolis sweeps, beta linear
 produced on the device.  A step is T*S*n = 2.048e11 spin updates.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --leg NAME [leg options]      # one secondary workload alone
 
 N > 1 (torchrun): every rank runs the full workload with its own seeds
 (independent trials, weak scaling), no collective on the data path.
 
-Prints one JSON line (rank 0).
+Output (rank 0): one JSON line per secondary workload ("leg": draw16,
+batched, graph, pt, campaign, learned), each with its full detail, then the
+headline as the LAST line: a compact object with the metric, the roofline,
+the CPU baseline, the clocks and a one-number summary of every leg.
 """
 from __future__ import annotations
 
@@ -34,10 +38,15 @@ METRIC = "spin-updates/s; time-to-99.9%-cut on 200x100 +-1 torus, learned vs pla
 WORKLOAD = {"X": 200, "Y": 100, "inst_seed": 2, "trials": 1024, "sweeps": 10000, "beta0": 0.1, "beta1": 3.0,
             "seed": 1002}
 WORKLOAD_NAME = "plain annealer, 200x100 +-1 torus (20,000 spins), 1,024 trials x 10,000 sweeps, beta 0.1->3.0"
+# the small 50x50 workload (64 trials x 1,000 sweeps, instance seed 1, seed 1001)
+SMALL = {"X": 50, "Y": 50, "inst_seed": 1, "trials": 64, "sweeps": 1000, "beta0": 0.1, "beta1": 3.0,
+         "seed": 1001}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 PEAK_HBM_GBS = float(json.load(open(PEAKS_FILE)).get("hbm_gbs", 6800.0)) if os.path.exists(PEAKS_FILE) else 6800.0
 # Integer multiply lanes per SM per clock (32-bit IMAD; a 32x32->64 multiply
-# counts as two) on this part: 4 sub-partitions x 16 lanes.
+# counts as two): 4 sub-partitions x 16 lanes.  The integer-pipe probe
+# (tests/alu_peak.cu, run by tests/test_gpu_alu_peak.py) measured 64.07
+# mad.lo per clock per SM on the GB300.
 IMAD_LANES_PER_SM = 64
 # Philox4x32-10 multiplies per spin update: 10 rounds x 2 products x 2 halves / 4 draws
 IMAD_OPS_PER_UPDATE = 10
@@ -46,6 +55,15 @@ IMAD_OPS_PER_UPDATE = 10
 # dram__bytes_write.sum, --clock-control none) of the same launch
 # configuration: 427,008 + 360,704 bytes
 FLOW_TRAFFIC_BYTES = 427008 + 360704
+# the headline line stays well inside what a log tail keeps
+HEADLINE_MAX_BYTES = 4096
+HEADLINE_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                 "scaling", "vs_baseline", "dtype", "data", "config", "e2e", "gpu_launches", "roofline",
+                 "cpu_baseline", "clocks")
+
+CNN_FLOP_PER_SITE = 2 * 9 * (3 * 32 + 32 * 32 * 2 + 32 * 1)
+CNN_BYTES_PER_SITE = 1 + 3 * 2 * 64 + 4   # spins in, three BF16 maps written and read, FP32 logits out
+PROPOSE_BYTES_PER_SITE = 1 + 4 + 1        # spins read and written, FP32 logits read
 
 
 def updates_per_step(w):
@@ -106,40 +124,95 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-CNN_FLOP_PER_SITE = 2 * 9 * (3 * 32 + 32 * 32 * 2 + 32 * 1)
-CNN_BYTES_PER_SITE = 1 + 3 * 2 * 64 + 4   # spins in, three BF16 maps written and read, FP32 logits out
+def _cuda_time(fn, reps=1):
+    """Milliseconds per call of fn(), CUDA events on the current stream."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
 
 # ------------------------------------------------------------------ CPU oracle
-def _oracle_slice(args):
-    import oracle  # test infrastructure: the CPU baseline leg only
-    inst, betas, seed, t_begin, t_count = args
+def _oracle_job(args):
+    import oracle  # test infrastructure: the CPU baseline legs only
+    inst, betas, seed, t_begin, t_count, sweep_offset = args
     t = time.perf_counter()
-    oracle.anneal(inst, betas, seed, t_begin=t_begin, t_count=t_count)
-    return time.perf_counter() - t
+    _, cuts = oracle.anneal(inst, betas, seed, t_begin=t_begin, t_count=t_count, sweep_offset=sweep_offset)
+    return time.perf_counter() - t, cuts
 
 
-def oracle_throughput(w, inst, sweeps=3000, trials_per_proc=1, procs=None):
-    """The CPU oracle, as it stands, on a bounded sample of the workload:
-    `procs` processes (default: every host core), each running
-    `trials_per_proc` trials of the first `sweeps` sweeps of the schedule."""
+def _oracle_pool(jobs, procs):
+    """Run oracle jobs in `procs` spawned processes; (wall seconds, results)."""
     import multiprocessing as mp
     import oracle
-    oracle.lib()  # build before forking workers
-    procs = procs or os.cpu_count() or 1
-    betas = synth.linear_betas(w["beta0"], w["beta1"], w["sweeps"])[:sweeps]
-    jobs = [(inst, betas, w["seed"], p * trials_per_proc, trials_per_proc) for p in range(procs)]
+    oracle.lib()  # build before starting workers
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(procs) as pool:
-        times = pool.map(_oracle_slice, jobs)
-    wall = time.perf_counter() - t0
+        res = pool.map(_oracle_job, jobs)
+    return time.perf_counter() - t0, res
+
+
+def oracle_sample_jobs(w, inst, procs, sweeps):
+    """A bounded, stratified sample of the workload: process p runs trial p
+    over `sweeps` consecutive sweeps of the schedule starting at sweep
+    p * S / procs (from that trial's start spins), so that the sample covers
+    the whole temperature range."""
+    betas = synth.linear_betas(w["beta0"], w["beta1"], w["sweeps"])
+    jobs = []
+    for p in range(procs):
+        k0 = min(w["sweeps"] - sweeps, (p * w["sweeps"]) // procs)
+        jobs.append((inst, betas[k0:k0 + sweeps], w["seed"], p, 1, k0))
+    return jobs
+
+
+def oracle_throughput(w, inst, sweeps=2000, procs=None):
+    """The CPU oracle, as it stands, on a bounded sample of the workload
+    (oracle_sample_jobs), one spawned process per host core."""
+    procs = procs or os.cpu_count() or 1
+    jobs = oracle_sample_jobs(w, inst, procs, sweeps)
+    wall, res = _oracle_pool(jobs, procs)
     if procs == 1:          # one core: the worker's own time, without the process start-up
-        wall = times[0]
-    ups = procs * trials_per_proc * sweeps * w["X"] * w["Y"]
-    return {"value": ups / wall, "unit": "spin-updates/s", "cores": procs, "kind": "oracle",
-            "sample": f"{procs} processes x {trials_per_proc} trial(s) x first {sweeps} sweeps of the "
-                      f"{w['X']}x{w['Y']} workload ({ups:.3g} updates, {wall:.1f} s wall)"}
+        wall = res[0][0]
+    ups = procs * sweeps * w["X"] * w["Y"]
+    return {"value": ups / wall, "unit": "spin-updates/s", "cores": procs, "kind": "oracle", "updates": ups,
+            "wall_s": wall,
+            "sample": f"{procs} processes x 1 trial x {sweeps} sweeps of the {w['X']}x{w['Y']} workload, "
+                      f"process p from sweep p*{w['sweeps']}/{procs} ({ups:.3g} updates)"}
+
+
+def oracle_ttt(w, inst, seed, procs, trials=None, target=None, r_gpu=None):
+    """Time-to-target of the oracle on the host cores (Eq. 3-5): `trials`
+    whole trials (default: all of the workload's) of the full schedule with
+    seed `seed`, split over `procs` spawned processes.  t_trial = wall /
+    trials (throughput form).  Without a target the oracle's own best cut
+    sets it; with one (from the GPU run of the same seed), the repetitions r
+    come from the GPU's full distribution, which the oracle's trials
+    reproduce bit for bit (their cuts are returned for that check)."""
+    from paper_2505_18508_gb300 import stats
+    trials = trials or w["trials"]
+    procs = min(procs, trials)
+    betas = synth.linear_betas(w["beta0"], w["beta1"], w["sweeps"])
+    per = [trials // procs + (1 if p < trials % procs else 0) for p in range(procs)]
+    jobs, t0 = [], 0
+    for c in per:
+        jobs.append((inst, betas, seed, t0, c, 0))
+        t0 += c
+    wall, res = _oracle_pool(jobs, procs)
+    cuts = np.concatenate([c for _, c in res])
+    if target is None:
+        target = stats.target_cut(int(cuts.max()))
+        Ps = stats.success_probability(cuts, target)
+        r = stats.repetitions(Ps)
+    else:
+        r = r_gpu
+    t_trial = wall / trials
+    return {"trials": trials, "processes": procs, "wall_s": wall, "t_trial_s": t_trial, "target": int(target),
+            "r": r, "TTT_s": t_trial * r if math.isfinite(r) else None}, cuts
 
 
 # ------------------------------------------------------------------ helpers
@@ -156,7 +229,226 @@ def ttt_stats(cuts, t_step_s, trials, sweeps, quality=0.999):
             "cut_mean": float(cuts.mean()), "cut_min": int(cuts.min())}
 
 
-def learned_leg(budgets=(1000, 3000, 10000, 30000), every=100, tile=10, n_train=256, train_sweeps=1000,
+def _round(v, nd=4):
+    if isinstance(v, float):
+        if not math.isfinite(v):
+            return None
+        return float(f"{v:.{nd}g}")
+    if isinstance(v, dict):
+        return {k: _round(x, nd) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [_round(x, nd) for x in v]
+    return v
+
+
+# ------------------------------------------------------------------ secondary legs
+def draw16_leg(args, prob=None, inst=None):
+    """The headline workload in the 16-bit draw mode (one Philox block per
+    eight trials), 3 timed steps with an L2 flush between them."""
+    import torch
+    import paper_2505_18508_gb300 as ia
+    w = dict(WORKLOAD)
+    own = prob is None
+    if own:
+        inst = synth.torus_instance(w["X"], w["Y"], w["inst_seed"])
+        prob = ia.Problem.from_instance(inst)
+    T, S, n = w["trials"], w["sweeps"], inst["n"]
+    betas = synth.linear_betas(w["beta0"], w["beta1"], S)
+    spins = torch.empty((T, n), dtype=torch.int8, device="cuda")
+    cuts = torch.empty((T,), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    prob.set_draw_bits(16)
+    for i in range(2):
+        ia.anneal(prob, T, betas, 3000 + i, out_spins=spins, out_cuts=cuts)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    stream = torch.cuda.current_stream()
+    for i, (e0, e1) in enumerate(ev):
+        flush.zero_()
+        e0.record(stream)
+        ia.anneal(prob, T, betas, 3100 + i, out_spins=spins, out_cuts=cuts)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    prob.set_draw_bits(32)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ups = updates_per_step(w)
+    peak = _imad_peak_tops()
+    a16 = ups * (IMAD_OPS_PER_UPDATE / 2) / (ms / 1e3) / 1e12
+    if own:
+        prob.destroy()
+    return {"workload": "the headline workload with 16-bit draws (the 16-bit decision stream)",
+            "value": ups / (ms / 1e3), "unit": "spin-updates/s", "ms_per_step": ms,
+            "roofline": {"bound": "alu", "achieved": a16, "peak": peak, "frac": a16 / peak,
+                         "unit": "Tops/s (32-bit IMAD)", "ops_per_update": IMAD_OPS_PER_UPDATE / 2}}
+
+
+def batched_leg(args):
+    """The 96-instance uneven batch ({50,100,140,200}x100, 32-512 trials,
+    2,000-20,000 sweeps, each sweep count times --scale) as one graph-replayed
+    persistent launch."""
+    import paper_2505_18508_gb300 as ia
+    cfg = synth.batched_config()
+    insts = [synth.torus_instance(c["X"], c["Y"], c["inst_seed"]) for c in cfg]
+    probs = [ia.Problem.from_instance(i) for i in insts]
+    trials = [c["trials"] for c in cfg]
+    sweeps = [max(1, int(c["sweeps"] * args.scale)) for c in cfg]
+    betas = [synth.linear_betas(0.1, 3.0, S) for S in sweeps]
+    seeds = [c["seed"] for c in cfg]
+    plan = ia.BatchPlan(probs, trials, sweeps, betas, seeds, group_trials=args.group_trials,
+                        ctas_per_sm=args.ctas_per_sm)
+    plan.launch()
+    ms = _cuda_time(plan.launch, args.reps)
+    ups = sum(t * s * i["n"] for t, s, i in zip(trials, sweeps, insts))
+    plan.destroy()
+    for p in probs:
+        p.destroy()
+    return {"workload": "96 tori {50,100,140,200}x100, 32-512 trials, 2,000-20,000 sweeps"
+                        + (f" x {args.scale}" if args.scale != 1.0 else "") + ", one CUDA-graph replay",
+            "updates": ups, "ms_per_replay": ms, "value": ups / (ms / 1e3), "unit": "spin-updates/s"}
+
+
+GRAPHS = ("g22", "r20k", "torus")
+
+
+def _graph_case(name):
+    if name == "g22":
+        return "random_2000v_19990e_w1", synth.random_graph(2000, 19990, 22, weights="one")
+    if name == "r20k":
+        return "random_20000v_40000e_pm1", synth.random_graph(20000, 40000, 81, weights="pm1")
+    inst = synth.torus_instance(200, 100, 2)
+    return "torus_200x100_as_graph", {"n": inst["n"], "row_ptr": inst["row_ptr"], "col": inst["col"],
+                                      "J": inst["J"], "h": None}
+
+
+def graph_leg(args):
+    """General sparse graphs through the general-graph kernel (spins in
+    shared memory, colour classes in order): a G22-like random graph (2,000
+    vertices, 19,990 edges, w = +1), a random graph of the headline's size
+    (20,000 vertices, 40,000 edges, w = +-1) and the headline torus given as a
+    general graph."""
+    import torch
+    import paper_2505_18508_gb300 as ia
+    out = {}
+    betas = synth.linear_betas(0.1, 3.0, args.sweeps)
+    for gname in ([args.graph] if args.graph != "all" else GRAPHS):
+        name, g = _graph_case(gname)
+        prob = ia.Problem.from_graph(g)
+        prob.set_graph_threads_per_site(args.threads_per_site)
+        prob.set_launch(strips=args.strips)
+        cuts = torch.empty(args.trials, dtype=torch.int32, device="cuda")
+        ia.anneal(prob, args.trials, betas, 1, want_spins=False, out_cuts=cuts)
+        torch.cuda.synchronize()
+        ms = _cuda_time(lambda: ia.anneal(prob, args.trials, betas, 2, want_spins=False, out_cuts=cuts), args.reps)
+        info = prob.graph_info()
+        ups = args.trials * args.sweeps * g["n"]
+        out[name] = {"n": g["n"], "edges": int(len(g["col"]) // 2), "colours": info["colours"], "Dmax": info["Dmax"],
+                     "trials": args.trials, "sweeps": args.sweeps, "ms": ms, "value": ups / (ms / 1e3),
+                     "unit": "spin-updates/s", "best_cut": int(cuts.max().item()),
+                     "mean_cut": float(cuts.double().mean().item())}
+        prob.destroy()
+    return out
+
+
+def pt_leg(args, temps=8, chains=128):
+    """Replica exchange on the headline instance at the headline's update
+    budget (temps x chains = 1,024 slots, rounds x sweeps = 10,000 sweeps):
+    throughput, and the coldest temperature's cuts."""
+    import torch
+    import paper_2505_18508_gb300 as ia
+    inst = synth.torus_instance(200, 100, 2)
+    prob = ia.Problem.from_instance(inst)
+    betas = np.geomspace(0.5, 3.0, temps)
+    ia.anneal_pt(prob, betas, chains, 2, args.sweeps_per_round, 1)
+    torch.cuda.synchronize()
+    res = {}
+
+    def run():
+        res["out"] = ia.anneal_pt(prob, betas, chains, args.rounds, args.sweeps_per_round, 1002)
+    ms = _cuda_time(run)
+    _, cuts, swaps = res["out"]
+    cold = cuts[(temps - 1) * chains:].cpu().numpy()
+    ups = temps * chains * args.rounds * args.sweeps_per_round * inst["n"]
+    out = {"workload": f"200x100 torus, {temps} temperatures (geometric 0.5..3.0) x {chains} chains, "
+                       f"{args.rounds} rounds x {args.sweeps_per_round} sweeps", "ms": ms, "value": ups / (ms / 1e3),
+           "unit": "spin-updates/s", "swaps": int(swaps.item()), "kernel": prob.last_kernel(),
+           "coldest": {"best_cut": int(cold.max()), "mean_cut": float(cold.mean())}}
+    prob.destroy()
+    return out
+
+
+def trace_leg(args):
+    """The headline workload read out along the trajectory (every trial's cut
+    after every --trace-every sweeps, best-so-far cut and configuration)
+    against the same anneal read out at the end only."""
+    import paper_2505_18508_gb300 as ia
+    w = WORKLOAD
+    inst = synth.torus_instance(w["X"], w["Y"], w["inst_seed"])
+    prob = ia.Problem.from_instance(inst)
+    betas = synth.linear_betas(w["beta0"], w["beta1"], w["sweeps"])
+    ups = updates_per_step(w)
+    T = w["trials"]
+    ia.anneal(prob, T, betas, 1)
+    ia.anneal_trace(prob, T, betas, 1, args.trace_every)
+    ms_plain = _cuda_time(lambda: ia.anneal(prob, T, betas, 1002), args.reps)
+    ms_trace = _cuda_time(lambda: ia.anneal_trace(prob, T, betas, 1002, args.trace_every), args.reps)
+    prob.destroy()
+    return {"trace_every": args.trace_every, "ms_plain": ms_plain, "ms_trace": ms_trace,
+            "value": ups / (ms_trace * 1e-3), "unit": "spin-updates/s", "overhead": ms_trace / ms_plain - 1.0}
+
+
+def cnn_leg(args):
+    """The learned stage's network on --batch seeded random configurations of
+    an --X x --Y torus: one forward pass (logits), one gradient (forward,
+    loss, input and weight gradients) and the tile proposals on those logits
+    (10 x 10 tiles, exact dE <= 0 acceptance), through the C ABI.  Forward:
+    2 * 9 * (3*32 + 32*32*2 + 32*1) useful flops and 389 algorithmic HBM bytes
+    per site (spins in, three BF16 activation maps written and read, FP32
+    logits out); proposals: 6 bytes per site."""
+    import torch
+    import paper_2505_18508_gb300 as ia
+    X, Y, B = args.X, args.Y, args.batch
+    prob = ia.Problem.from_instance(synth.torus_instance(X, Y, 3))
+    net = ia.CNN(synth.cnn_init_params(1, scale=0.7))
+    s = torch.from_numpy(synth.random_spins(B, X * Y, 5)).cuda()
+    y = torch.from_numpy(synth.random_spins(B, X * Y, 6)).cuda().gt(0).to(torch.uint8)
+    z = torch.empty((B, X * Y), dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        return _cuda_time(fn, reps)
+
+    fwd_ms = timed(lambda: net.forward(prob, s, out=z), args.reps)
+    grad_ms = timed(lambda: net.grad(prob, s, y), max(1, args.reps // 4))
+    prop_ms = timed(lambda: ia.propose(prob, s, z, 10), args.reps)
+    sites = B * X * Y
+    fwd_gbs = CNN_BYTES_PER_SITE * sites / (fwd_ms * 1e-3) / 1e9
+    out = {"workload": f"{B} x {X}x{Y} spin configurations", "forward_ms": fwd_ms,
+           "forward_tflops": CNN_FLOP_PER_SITE * sites / (fwd_ms * 1e-3) / 1e12,
+           "forward_gbs": fwd_gbs, "forward_hbm_frac": fwd_gbs / PEAK_HBM_GBS,
+           "grad_ms": grad_ms, "grad_status": prob.get_status(), "propose_ms": prop_ms,
+           "propose_gbs": PROPOSE_BYTES_PER_SITE * sites / (prop_ms * 1e-3) / 1e9}
+    net.destroy()
+    prob.destroy()
+    return out
+
+
+def campaign_leg(args):
+    """Fig. 1 style ladder on the headline instance: --campaign-trials trials
+    per budget, beta 0.1 -> 3.0 over S sweeps, one anneal per budget."""
+    import paper_2505_18508_gb300 as ia
+    from paper_2505_18508_gb300.campaign import run_campaign
+    inst = synth.torus_instance(200, 100, 2)
+    prob = ia.Problem.from_instance(inst)
+    budgets = [int(float(b)) for b in args.budgets.split(",")]
+    out = run_campaign(prob, budgets, args.campaign_trials, 4242)
+    prob.destroy()
+    out["workload"] = (f"Fig. 1 style ladder on the 200x100 instance (seed 2): {args.campaign_trials} trials per "
+                       "budget, beta 0.1->3.0 over S sweeps, one anneal per budget")
+    return out
+
+
+def learned_leg(args, budgets=(1000, 3000, 10000, 30000), every=100, tile=10, n_train=256, train_sweeps=1000,
                 steps=800, end_window=500):
     """Config 5 of the workload set: 200x100 tori, 8 seeds x 512 trials, the
     plain annealer against the learned form (network trained on 20,000-spin
@@ -275,7 +567,15 @@ def learned_leg(budgets=(1000, 3000, 10000, 30000), every=100, tile=10, n_train=
         return min(c) if c else (None, None)
     bp, bl, be = best_budget("plain@"), best_budget("learned@"), best_budget("learned_end@")
     bpb, beb = best_budget("plain_batched@"), best_budget("learned_end_batched@")
-    return {"workload": "200x100 tori, seeds 30000-30007, 512 trials each, beta 0.1->3.0 over S sweeps, "
+    best_med = {"plain": bp[0], "learned": bl[0], "learned_end": be[0], "plain_batched": bpb[0],
+                "learned_end_batched": beb[0]}
+    best_med_full = {"plain": bp, "learned": bl, "learned_end": be, "plain_batched": bpb, "learned_end_batched": beb}
+    summary = {"median_TTT_s": {k: best_med[k] for k in ("plain", "plain_batched", "learned_end",
+                                                          "learned_end_batched", "learned")},
+               "mean_P_s@30000": {f: ladder[f"{f}@30000"]["mean_P_s"] for f in allforms if f"{f}@30000" in ladder},
+               "seeds": len(rows)}
+    return {"summary": summary,
+            "workload": "200x100 tori, seeds 30000-30007, 512 trials each, beta 0.1->3.0 over S sweeps, "
                         f"S in {list(budgets)}; proposals every {every} sweeps, tiles {tile}x{tile} "
                         f"(learned: whole schedule; learned_end: last {end_window} sweeps); *_batched: the 8 "
                         "instances in one persistent launch (learned_end_batched: up to its window), wall time "
@@ -285,108 +585,53 @@ def learned_leg(budgets=(1000, 3000, 10000, 30000), every=100, tile=10, n_train=
                       "seconds": t_train},
             "cnn_forward": cnn,
             "ladder": ladder,
-            "best_median_TTT_s": {"plain": bp[0], "plain_budget": bp[1], "learned": bl[0],
-                                  "learned_budget": bl[1], "learned_end": be[0], "learned_end_budget": be[1],
-                                  "plain_batched": bpb[0], "plain_batched_budget": bpb[1],
-                                  "learned_end_batched": beb[0], "learned_end_batched_budget": beb[1]},
+            "best_median_TTT_s": best_med_full,
             "per_seed": rows}
 
 
-def graph_leg(trials=1024, sweeps=2000, reps=3):
-    """General sparse graphs through the general-graph kernel (spins in
-    shared memory, colour classes in order): a G22-like random graph (2,000
-    vertices, 19,990 edges, w = +1), a random graph of the headline's size
-    (20,000 vertices, 40,000 edges, w = +-1) and the headline torus given as a
-    general graph."""
-    import torch
-    import paper_2505_18508_gb300 as ia
-    out = {}
-    inst = synth.torus_instance(200, 100, 2)
-    cases = {
-        "random_2000v_19990e_w1": synth.random_graph(2000, 19990, 22, weights="one"),
-        "random_20000v_40000e_pm1": synth.random_graph(20000, 40000, 81, weights="pm1"),
-        "torus_200x100_as_graph": {"n": inst["n"], "row_ptr": inst["row_ptr"], "col": inst["col"],
-                                   "J": inst["J"], "h": None},
-    }
-    betas = synth.linear_betas(0.1, 3.0, sweeps)
-    for name, g in cases.items():
-        prob = ia.Problem.from_graph(g)
-        cuts = torch.empty(trials, dtype=torch.int32, device="cuda")
-        ia.anneal(prob, trials, betas, 1, want_spins=False, out_cuts=cuts)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for r in range(reps):
-            ia.anneal(prob, trials, betas, 2 + r, want_spins=False, out_cuts=cuts)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        info = prob.graph_info()
-        ups = trials * sweeps * g["n"]
-        out[name] = {"n": g["n"], "edges": int(len(g["col"]) // 2), "colours": info["colours"], "Dmax": info["Dmax"],
-                     "trials": trials, "sweeps": sweeps, "ms": ms, "value": ups / (ms / 1e3),
-                     "unit": "spin-updates/s", "best_cut": int(cuts.max().item()),
-                     "mean_cut": float(cuts.double().mean().item())}
-        prob.destroy()
-    return out
+LEGS = {"draw16": draw16_leg, "batched": batched_leg, "graph": graph_leg, "pt": pt_leg, "trace": trace_leg,
+        "cnn": cnn_leg, "campaign": campaign_leg, "learned": learned_leg}
+# legs the default run adds after the headline's timed region
+DEFAULT_LEGS = ("draw16", "batched", "graph", "pt", "campaign", "learned")
 
 
-def pt_leg(temps=8, chains=128, rounds=200, sweeps_per_round=50):
-    """Replica exchange on the headline instance at the headline's update
-    budget (temps x chains = 1,024 slots, rounds x sweeps = 10,000 sweeps):
-    throughput, and the coldest temperature's cuts against the plain
-    annealer's final cuts."""
-    import torch
-    import paper_2505_18508_gb300 as ia
-    inst = synth.torus_instance(200, 100, 2)
-    prob = ia.Problem.from_instance(inst)
-    betas = np.geomspace(0.5, 3.0, temps)
-    ia.anneal_pt(prob, betas, chains, 2, sweeps_per_round, 1)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    _, cuts, swaps = ia.anneal_pt(prob, betas, chains, rounds, sweeps_per_round, 1002)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    cold = cuts[(temps - 1) * chains:].cpu().numpy()
-    ups = temps * chains * rounds * sweeps_per_round * inst["n"]
-    out = {"workload": f"200x100 torus, {temps} temperatures (geometric 0.5..3.0) x {chains} chains, "
-                       f"{rounds} rounds x {sweeps_per_round} sweeps", "ms": ms, "value": ups / (ms / 1e3),
-           "unit": "spin-updates/s", "swaps": int(swaps.item()),
-           "coldest": {"best_cut": int(cold.max()), "mean_cut": float(cold.mean())}}
-    prob.destroy()
-    return out
+def leg_summary(name, d):
+    """One or two numbers per leg for the headline line."""
+    if d is None:
+        return None
+    if "error" in d:
+        return {"error": d["error"][:200]}
+    if name == "draw16":
+        return {"value": d["value"], "frac": d["roofline"]["frac"]}
+    if name in ("batched", "trace"):
+        return {"value": d["value"]}
+    if name == "pt":
+        return {"value": d["value"], "coldest_best_cut": d["coldest"]["best_cut"]}
+    if name == "graph":
+        return {k: v["value"] for k, v in d.items()}
+    if name == "campaign":
+        return {"sweeps": [b["sweeps"] for b in d["budgets"]], "highest": [b["highest"] for b in d["budgets"]]}
+    if name == "learned":
+        return d.get("summary")
+    if name == "cnn":
+        return {"forward_ms": d["forward_ms"], "forward_hbm_frac": d["forward_hbm_frac"]}
+    return None
 
 
-def batched_leg(reps=2):
-    """Config 3: the 96-instance uneven batch ({50,100,140,200}x100, 32-512
-    trials, 2,000-20,000 sweeps) as one graph-replayed persistent launch."""
-    import torch
-    import paper_2505_18508_gb300 as ia
-    cfg = synth.batched_config()
-    insts = [synth.torus_instance(c["X"], c["Y"], c["inst_seed"]) for c in cfg]
-    probs = [ia.Problem.from_instance(i) for i in insts]
-    trials = [c["trials"] for c in cfg]
-    sweeps = [c["sweeps"] for c in cfg]
-    betas = [synth.linear_betas(0.1, 3.0, S) for S in sweeps]
-    seeds = [c["seed"] for c in cfg]
-    plan = ia.BatchPlan(probs, trials, sweeps, betas, seeds)
-    plan.launch()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        plan.launch()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    ups = sum(t * s * i["n"] for t, s, i in zip(trials, sweeps, insts))
-    plan.destroy()
-    for p in probs:
-        p.destroy()
-    return {"workload": "96 tori {50,100,140,200}x100, 32-512 trials, 2,000-20,000 sweeps, one CUDA-graph replay",
-            "updates": ups, "ms_per_replay": ms, "value": ups / (ms / 1e3), "unit": "spin-updates/s"}
+def headline_line(base, legs):
+    """The last stdout line: the contract's keys, with every number rounded,
+    and a one-number summary per leg.  Raises if a key is missing or the line
+    outgrows HEADLINE_MAX_BYTES."""
+    line = {k: base[k] for k in HEADLINE_KEYS}
+    for k in ("ttt_99_9",):
+        if k in base:
+            line[k] = base[k]
+    line["legs"] = {name: leg_summary(name, d) for name, d in legs.items()}
+    line = _round(line)
+    text = json.dumps(line, separators=(",", ":"))
+    if len(text) > HEADLINE_MAX_BYTES:
+        raise ValueError(f"headline line is {len(text)} bytes (limit {HEADLINE_MAX_BYTES})")
+    return text
 
 
 def dist_env():
@@ -394,34 +639,49 @@ def dist_env():
     return replicas.env()
 
 
+def _imad_peak_tops(sms=None):
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    if sms is None:
+        import torch
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return sms * IMAD_LANES_PER_SM * clk_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ reference arm
 def reference_arm(args):
+    """The oracle as it stands on the host cores: each step is the bounded,
+    stratified sample of the headline workload that oracle_sample_jobs
+    describes; the line states that sample and its own updates per step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     w = dict(WORKLOAD)
     inst = synth.torus_instance(w["X"], w["Y"], w["inst_seed"])
     sweeps = 1000
-    vals = []
     for _ in range(args.warmup):
         oracle_throughput(w, inst, sweeps=sweeps)
-    for _ in range(args.steps):
-        vals.append(oracle_throughput(w, inst, sweeps=sweeps))
-    v = float(np.mean([x["value"] for x in vals]))
-    cb = dict(vals[-1])
+    vals = [oracle_throughput(w, inst, sweeps=sweeps) for _ in range(args.steps)]
+    wall = float(np.mean([x["wall_s"] for x in vals]))
+    step_ups = vals[-1]["updates"]
+    v = step_ups / wall
+    cb = {k: vals[-1][k] for k in ("unit", "cores", "kind", "sample")}
     cb["value"] = v
-    step_ups = vals[-1]["cores"] * sweeps * w["X"] * w["Y"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "spin-updates/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_ups / v,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, **w, "updates_per_step": updates_per_step(w)},
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, **w, "updates_per_step": step_ups,
+                       "sample": vals[-1]["sample"],
+                       "note": "each step is the stated sample of the workload, not all of its 2.048e11 updates"},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "spin-updates/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(_round(line, 6)), flush=True)
     return 0
 
 
 # ------------------------------------------------------------------ main arm
-def main():
+def _parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -432,18 +692,52 @@ def main():
     ap.add_argument("--sweeps", type=int, default=None, help="override (profiling runs only)")
     ap.add_argument("--trials", type=int, default=None, help="override (profiling runs only)")
     ap.add_argument("--launch", default=None, help="G,C,threads launch shape (default: automatic)")
-    ap.add_argument("--no-learned", action="store_true", help="skip the learned-vs-plain comparison")
-    args = ap.parse_args()
+    ap.add_argument("--legs", default=",".join(DEFAULT_LEGS), help="secondary legs after the headline ('' = none)")
+    ap.add_argument("--leg", default=None, choices=sorted(LEGS), help="run one secondary leg alone and exit")
+    # leg options
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--scale", type=float, default=1.0, help="batched: sweep counts x scale")
+    ap.add_argument("--group-trials", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--rounds", type=int, default=200)
+    ap.add_argument("--sweeps-per-round", type=int, default=50)
+    ap.add_argument("--graph", default="all", choices=("all",) + GRAPHS)
+    ap.add_argument("--leg-trials", dest="leg_trials", type=int, default=1024)
+    ap.add_argument("--leg-sweeps", dest="leg_sweeps", type=int, default=2000)
+    ap.add_argument("--trace-every", type=int, default=100)
+    ap.add_argument("--threads-per-site", type=int, default=0, help="general graphs: 1, 4, 8 or 0 (automatic)")
+    ap.add_argument("--strips", type=int, default=0, help="general graphs: CTAs per trial group (1-8; 0: automatic)")
+    ap.add_argument("--X", type=int, default=100)
+    ap.add_argument("--Y", type=int, default=100)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--budgets", default="1000,3000,10000,30000,100000,300000")
+    ap.add_argument("--campaign-trials", type=int, default=512)
+    ap.add_argument("--learned-seeds", type=int, default=16)
+    return ap
+
+
+def run_leg(name, args):
+    a = argparse.Namespace(**vars(args))
+    a.trials, a.sweeps = args.leg_trials, args.leg_sweeps
+    return LEGS[name](a)
+
+
+def main(argv=None):
+    args = _parser().parse_args(argv)
     if args.impl == "reference":
         return reference_arm(args)
 
     import torch
     import paper_2505_18508_gb300 as ia
     from paper_2505_18508_gb300 import build as lib_build
+    from paper_2505_18508_gb300 import replicas
 
     ws, rank, local = dist_env()
     lib_build.build()
     torch.cuda.set_device(local)
+    if args.leg:
+        print(json.dumps({"leg": args.leg, **run_leg(args.leg, args)}), flush=True)
+        return 0
     dist = None
     if ws > 1:
         import torch.distributed as dist
@@ -467,8 +761,6 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    from paper_2505_18508_gb300 import replicas
-
     def seed_of(step):
         return replicas.rank_seed(w["seed"], rank, step)
 
@@ -476,6 +768,7 @@ def main():
         ia.anneal(prob, T, betas, seed_of(-1 - i), out_spins=spins, out_cuts=cuts)
     torch.cuda.synchronize()
     shape = prob.last_launch()
+    kernel = {1: "anneal_strip_kernel", 2: "anneal_flow_kernel"}.get(prob.last_kernel(), "?")
 
     clocks = ClockSampler(local)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -523,73 +816,66 @@ def main():
     d2h = T * n + 4 * T
 
     # ---- roofline: integer-multiply pipe (Philox multiplies per update vs IMAD lanes)
-    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-    props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
-    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tops = sms * IMAD_LANES_PER_SM * clk_mhz * 1e6 / 1e12
-    achieved_tops = ups * IMAD_OPS_PER_UPDATE / (ms / 1e3) / 1e12 / 1.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tops = _imad_peak_tops(sms)
+    achieved_tops = ups * IMAD_OPS_PER_UPDATE / (ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (32-bit IMAD)",
                 "frac": achieved_tops / peak_tops,
-                "traffic": FLOW_TRAFFIC_BYTES if prob.last_kernel() == 2 and (T, S, n) == (1024, 10000, 20000)
+                "traffic": FLOW_TRAFFIC_BYTES if kernel == "anneal_flow_kernel" and (T, S, n) == (1024, 10000, 20000)
                 else None,
-                "traffic_note": "DRAM bytes per launch (ncu); the spins stay in L2, the path is integer-bound",
-                "kernel": {1: "anneal_strip_kernel", 2: "anneal_flow_kernel"}.get(prob.last_kernel(), "?"),
-                "peak_source": f"{sms} SMs x {IMAD_LANES_PER_SM} IMAD lanes x "
-                f"{clk_mhz:.0f} MHz (sm_max_mhz of measured peaks file)"}
+                "kernel": kernel,
+                "peak_source": f"{sms} SMs x {IMAD_LANES_PER_SM} IMAD lanes x sm_max_mhz (measured peaks file)"}
 
     stats = None
     if args.steps > 0:   # over every rank's trials: the job ran ws * T trials in one step time
         all_cuts = replicas.gather_cuts(first_cuts, dist)
         stats = ttt_stats(all_cuts.cpu().numpy(), ms / 1e3, ws * T, S)
+
+    # ---- the CPU oracle on the host cores (rank 0 of a 1-GPU run only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
         cpu = oracle_throughput(w, inst)
-        one = oracle_throughput(w, inst, sweeps=1000, procs=1)   # the oracle on a single host core
+        one = oracle_throughput(w, inst, sweeps=1000, procs=1)
         cpu["single_core"] = {"value": one["value"], "sample": one["sample"]}
-    # ---- the 16-bit draw mode on the same workload (one Philox block per
-    # eight trials): a variant line, not the headline stream
-    draw16 = None
-    if args.steps > 0:
-        prob.set_draw_bits(16)
-        for i in range(2):
-            ia.anneal(prob, T, betas, seed_of(-10 - i), out_spins=spins, out_cuts=cuts)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
-        for i, (e0, e1) in enumerate(ev):
-            flush.zero_()
-            e0.record(stream)
-            ia.anneal(prob, T, betas, seed_of(200 + i), out_spins=spins, out_cuts=cuts)
-            e1.record(stream)
-        torch.cuda.synchronize()
-        ms16 = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-        prob.set_draw_bits(32)
-        a16 = ups * (IMAD_OPS_PER_UPDATE / 2) / (ms16 / 1e3) / 1e12
-        draw16 = {"value": ws * ups / (ms16 / 1e3), "unit": "spin-updates/s", "ms_per_step": ms16,
-                  "workload": "same as the headline, 16-bit draws (decision stream of the 16-bit mode)",
-                  "roofline": {"bound": "alu", "achieved": a16, "peak": peak_tops, "frac": a16 / peak_tops,
-                               "unit": "Tops/s (32-bit IMAD)", "ops_per_update": IMAD_OPS_PER_UPDATE / 2}}
-    batched = None
+        cpu.pop("wall_s")
+        cpu.pop("updates")
+        ttt = {}
+        if stats is not None and (T, S) == (1024, 10000):
+            # the headline's step-0 trials 0 .. cores-1 on the oracle: their
+            # cuts equal the GPU's bit for bit, and r is the GPU's
+            o, oc = oracle_ttt(w, inst, seed_of(0), cores, trials=cores, target=stats["target"], r_gpu=stats["r"])
+            o["parity_trials_equal"] = bool(np.array_equal(oc, first_cuts[:cores].cpu().numpy()))
+            o["gpu_TTT_s"] = stats["TTT_s_throughput_form"]
+            ttt["200x100"] = o
+        # the 50x50 workload: all 64 trials on the oracle and on the GPU
+        inst1 = synth.torus_instance(SMALL["X"], SMALL["Y"], SMALL["inst_seed"])
+        o1, oc1 = oracle_ttt(SMALL, inst1, SMALL["seed"], cores)
+        p1 = ia.Problem.from_instance(inst1)
+        b1 = synth.linear_betas(SMALL["beta0"], SMALL["beta1"], SMALL["sweeps"])
+        ia.anneal(p1, SMALL["trials"], b1, SMALL["seed"])
+        res = {}
+        g_ms = _cuda_time(lambda: res.setdefault("c", ia.anneal(p1, SMALL["trials"], b1, SMALL["seed"])[1]))
+        p1.destroy()
+        o1["parity_trials_equal"] = bool(np.array_equal(oc1, res["c"].cpu().numpy()))
+        o1["gpu_t_trial_s"] = g_ms / 1e3 / SMALL["trials"]
+        o1["gpu_TTT_s"] = o1["gpu_t_trial_s"] * o1["r"] if math.isfinite(o1["r"]) else None
+        ttt["50x50"] = o1
+        cpu["ttt_99_9"] = ttt
+
+    # ---- secondary legs, each printed on its own line before the headline
+    legs = {}
     if rank == 0 and not args.sweeps and not args.trials:
-        batched = batched_leg()
-    graphs = None
-    pt = None
-    if rank == 0 and not args.sweeps and not args.trials:
-        graphs = graph_leg()
-        pt = pt_leg()
-        if stats is not None:
-            pt["plain_same_budget"] = {"best_cut": stats["best_cut"], "mean_cut": stats["cut_mean"]}
-    campaign = None
-    if rank == 0 and not args.sweeps and not args.trials:
-        from paper_2505_18508_gb300.campaign import run_campaign
-        campaign = run_campaign(prob, (1000, 3000, 10000, 30000, 100000, 300000), 512, 4242)
-        campaign["workload"] = ("Fig. 1 style ladder on the headline instance (200x100, seed 2): 512 trials per "
-                                "budget, beta 0.1->3.0 over S sweeps, one anneal per budget")
-    learned_cmp = None
-    if rank == 0 and not args.no_learned and not args.sweeps and not args.trials:
-        learned_cmp = learned_leg()
+        for name in [x for x in args.legs.split(",") if x]:
+            try:
+                d = run_leg(name, args) if name != "draw16" else draw16_leg(args, prob, inst)
+            except Exception as ex:        # a failed leg is reported, the headline still prints
+                d = {"error": f"{type(ex).__name__}: {ex}"}
+            legs[name] = d
+            print(json.dumps({"leg": name, **_round(d, 6)}), flush=True)
 
     if rank == 0:
-        line = {
+        base = {
             "metric": METRIC, "value": value, "unit": "spin-updates/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -602,16 +888,8 @@ def main():
             "cpu_baseline": cpu,
             "clocks": clk,
             "ttt_99_9": stats,
-            "draw16_variant": draw16,
-            "campaign": campaign,
-            "general_graphs": graphs,
-            "replica_exchange": pt,
-            "batched": batched,
-            "learned_vs_plain": learned_cmp,
-            "wall_s_timed": wall,
-            "step_ms": step_ms,
         }
-        print(json.dumps(line), flush=True)
+        print(headline_line(base, legs), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     prob.destroy()

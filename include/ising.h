@@ -446,19 +446,28 @@ int ising_problem_info(const ising_problem* p, int32_t* X, int32_t* Y, int32_t* 
  * device memory while they run (for example an application whose framework
  * has already reserved the device memory it may use, or a loop that must not
  * enter the CUDA allocator once started).  The paper has no counterpart; this
- * is an interface variant of ising_anneal, with the same arguments, results
- * and errors.
+ * is an interface variant of ising_anneal, with the same arguments and
+ * results, bit for bit, for the same launch shape.
  *
  * The call allocates nothing: the per-sweep threshold table goes into one
  * fixed array inside the library's device image, at most 32,768 sweeps
  * (256 KiB, held by every GPU that loads the library until the process
- * exits).  S above that limit returns ISING_ERR_UNSUPPORTED before anything
- * is queued.  The first call on a device looks up that array's device address
- * (with the problem's device current, which must also be the current device
- * at every call, else ISING_ERR_ARG); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents:
- * calls whose work overlaps on the GPU (unordered streams) race on it.
- * Nothing in the array needs to start at zero.
+ * exits).  The table reaches that array through the parameters of small
+ * copy kernels queued on cuda_stream ahead of the anneal (one per 1,024
+ * sweeps), so no host buffer has to outlive the call.  The anneal itself
+ * always runs on the cluster-strip kernel (the persistent kernel needs a
+ * per-call work area).  The first call on a device looks up that array's
+ * device address, with the problem's device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents: calls whose work overlaps on the GPU (unordered
+ * streams) race on it.  Nothing in the array needs to start at zero.
+ *
+ * Errors: those of ising_anneal, with three differences:
+ *   ISING_ERR_UNSUPPORTED  S > 32,768, or a general-graph handle
+ *                          (ising_graph_create), which ising_anneal accepts;
+ *   ISING_ERR_ARG          the current device is not the problem's device.
+ * Each is returned before anything is queued.  The launch this call used is
+ * what ising_last_launch and ising_last_kernel then report.
  */
 int ising_anneal_noalloc(ising_problem* p, int32_t trials, const double* betas, int32_t S,
                          uint64_t seed, uint32_t sweep_offset, const int8_t* init_spins,

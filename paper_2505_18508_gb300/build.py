@@ -87,15 +87,5 @@ def build_program(src: str, exe: str, flags=("-O3", "-lineinfo"), force: bool = 
     return exe
 
 
-PROBE_SRC = os.path.join(HERE, "probe", "alu_peak.cu")
-PROBE_EXE = os.path.join(OUT_DIR, "alu_peak")
-
-
-def build_probe(force: bool = False) -> str:
-    """The integer-pipe peak probe (probe/alu_peak.cu)."""
-    return build_program(PROBE_SRC, PROBE_EXE, force=force)
-
-
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
-    print(build_probe(force=True))

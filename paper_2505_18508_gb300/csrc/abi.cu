@@ -35,26 +35,11 @@ int map_cuda(cudaError_t e) {
   return ISING_ERR_CUDA;
 }
 
-// T_d = min(floor(exp(-beta d) 2^32), 2^32 - 1) for d = 4 and 8: the
-// Metropolis acceptance probability min(1, exp(-beta dE)) of an uphill move,
-// as an integer threshold for a uniform 32-bit draw (accept iff u < T).  In
-// the 16-bit draw mode T_d = min(floor(exp(-beta d) 2^16), 2^16 - 1), stored
-// shifted left by 16 bits (the kernels compare draws placed in the top half).
+// The table of ising_anneal: (T4_k, T8_k) for every sweep k (reading R3,
+// ising::threshold_table).
 int make_thresholds(const double* betas, int32_t S, std::vector<uint32_t>& out, int bits = 32) {
   out.assign(static_cast<size_t>(2) * (S > 0 ? S : 0), 0u);
-  const double scale = bits == 16 ? 65536.0 : 4294967296.0;
-  const double top = scale - 1.0;
-  for (int32_t k = 0; k < S; ++k) {
-    const double beta = betas[k];
-    if (!(beta > 0.0)) return ISING_ERR_ARG;
-    for (int d = 0; d < 2; ++d) {
-      const double dE = d == 0 ? 4.0 : 8.0;
-      const double v = std::floor(std::exp(-(beta * dE)) * scale);
-      const uint32_t T = v >= top ? static_cast<uint32_t>(top) : static_cast<uint32_t>(v);
-      out[2 * static_cast<size_t>(k) + d] = bits == 16 ? T << 16 : T;
-    }
-  }
-  return ISING_OK;
+  return S > 0 ? ising::threshold_table(betas, S, bits, out.data()) : ISING_OK;
 }
 
 // trials per group when the handle does not fix it: 32, or all trials rounded
@@ -77,9 +62,35 @@ int max_smem_of(int device) {
   return v;
 }
 
-struct Shape {
-  int G, C, threads, Rmax;
-};
+using Shape = ising::StripShape;
+
+}  // namespace
+
+// ---------------------------------------------------------------- shared host rules
+namespace ising {
+
+// Reading R3: T = min(floor(exp(-x) 2^B), 2^B - 1) for the exponent x =
+// beta dE of an uphill move, the Metropolis acceptance probability
+// min(1, exp(-beta dE)) as an integer threshold for a uniform B-bit draw
+// (accept iff u < T).  B = 16 stores T shifted left by 16 bits: the kernels
+// compare draws placed in the top half of a word.
+uint32_t accept_threshold(double x, int bits) {
+  const double scale = bits == 16 ? 65536.0 : 4294967296.0;
+  const double top = scale - 1.0;
+  const double v = std::floor(std::exp(-x) * scale);
+  const uint32_t T = v >= top ? static_cast<uint32_t>(top) : static_cast<uint32_t>(v);
+  return bits == 16 ? T << 16 : T;
+}
+
+int threshold_table(const double* betas, int32_t S, int bits, uint32_t* out) {
+  for (int32_t k = 0; k < S; ++k) {
+    const double beta = betas[k];
+    if (!(beta > 0.0)) return ISING_ERR_ARG;
+    out[2 * static_cast<size_t>(k)] = accept_threshold(beta * 4.0, bits);
+    out[2 * static_cast<size_t>(k) + 1] = accept_threshold(beta * 8.0, bits);
+  }
+  return ISING_OK;
+}
 
 // threads per CTA: many warps hide the Philox dependency chains, so take
 // the multiple of 32 in [768, 1024] that leaves the fewest idle item slots
@@ -99,10 +110,10 @@ int pick_threads(int items) {
   return best;
 }
 
-int choose_shape(const ising_problem* p, int32_t T, Shape* out) {
+int strip_shape(const ising_problem* p, int32_t T, int32_t G, StripShape* out) {
   const int sms = num_sms_of(p->device);
   const int smem_max = max_smem_of(p->device);
-  int G = p->cfg_group;
+  if (G == 0) G = p->cfg_group;
   if (G == 0) G = default_group(p, T);
   if (G < 4) G = 4;
   const int groups = (T + G - 1) / G;
@@ -112,13 +123,13 @@ int choose_shape(const ising_problem* p, int32_t T, Shape* out) {
     // CTA per SM), with at least two rows per strip
     C = 1;
     while (C < 8 && groups * (C * 2) <= sms && p->Y / (C * 2) >= 2) C *= 2;
-    while (C < 16 && ising::anneal_smem_bytes(p->H, (p->Y + C - 1) / C) > static_cast<size_t>(smem_max) &&
+    while (C < 16 && anneal_smem_bytes(p->H, (p->Y + C - 1) / C) > static_cast<size_t>(smem_max) &&
            (C * 2) <= p->Y)
       C *= 2;
   }
   if (C > p->Y) return ISING_ERR_UNSUPPORTED;
   const int Rmax = (p->Y + C - 1) / C;
-  if (ising::anneal_smem_bytes(p->H, Rmax) > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
+  if (anneal_smem_bytes(p->H, Rmax) > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
   if (groups > 65535) return ISING_ERR_UNSUPPORTED;
   int threads = p->cfg_threads;
   if (threads == 0) threads = pick_threads(Rmax * p->H);
@@ -128,6 +139,21 @@ int choose_shape(const ising_problem* p, int32_t T, Shape* out) {
   out->Rmax = Rmax;
   return ISING_OK;
 }
+
+void record_strip_launch(ising_problem* p, int32_t trials, int32_t S, const StripShape& sh) {
+  p->last_kernel = 1;
+  p->last_group = sh.G;
+  p->last_strips = sh.C;
+  p->last_threads = sh.threads;
+  p->last_grid = sh.C * ((trials + sh.G - 1) / sh.G);
+  log_launch(p, trials, S);
+}
+
+}  // namespace ising
+
+namespace {
+
+int choose_shape(const ising_problem* p, int32_t T, Shape* out) { return ising::strip_shape(p, T, 0, out); }
 
 // ---------------------------------------------------------------- batches
 struct HostBatch {
@@ -1039,12 +1065,7 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
     if (e == cudaSuccess) e = e2;
   }
   if (e != cudaSuccess) return map_cuda(e);
-  p->last_kernel = 1;
-  p->last_group = sh.G;
-  p->last_strips = sh.C;
-  p->last_threads = sh.threads;
-  p->last_grid = sh.C * ((trials + sh.G - 1) / sh.G);
-  log_launch(p, trials, S);
+  ising::record_strip_launch(p, trials, S, sh);
   return ISING_OK;
 }
 

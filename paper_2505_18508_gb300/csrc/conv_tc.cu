@@ -19,12 +19,14 @@
 // 8 pixels = 128 bytes) >> 4, version 1.  Instruction: kind::f16, BF16 A and
 // B, FP32 D, both K-major, M = 128, N = 16 or 32.
 //
-// Persistent CTAs of 128 threads walk consecutive output rows, keeping a ring
-// of three staged input rows, so each new output row stages one input row.
-// Per row: stage -> fence.proxy.async -> one thread issues the MMAs of every
-// 128-pixel tile of the row (9 taps x K/16 each) and commits to an mbarrier
-// -> all threads wait (bounded) -> tcgen05.ld of their pixel's accumulator ->
-// fused epilogue -> store.
+// Persistent CTAs of 256 threads (two warpgroups) walk consecutive output
+// rows, keeping a ring of five staged input rows (each new output row stages
+// one input row, three iterations ahead) and two TMEM accumulator buffers.
+// Per row: one thread issues the MMAs of every 128-pixel tile of the row
+// (9 taps x K/16 each) and commits to the buffer's mbarrier; meanwhile all
+// threads wait (bounded) for the previous row's MMAs, tcgen05.ld its
+// accumulator and run the fused epilogue.  The weight-gradient kernel below
+// uses 128 threads.
 #include <cuda_bf16.h>
 
 #include <algorithm>

@@ -159,6 +159,27 @@ size_t wgrad_tc_smem(int kind, int X);
 cudaError_t launch_wgrad_tc(int kind, const TcWgradArgs& a, int sms, float* dW, float* db, cudaStream_t st);
 cudaError_t launch_conv_tc(int kind, const TcConvArgs& a, int sms, cudaStream_t st);
 
+// Reading R3 (abi.cu): T = min(floor(exp(-x) 2^bits), 2^bits - 1) for the
+// exponent x = beta dE of an uphill move, stored shifted left by 16 bits when
+// bits = 16.  Every table the library uploads (annealing, replica exchange,
+// the no-allocation entry point) is built from this one function.
+uint32_t accept_threshold(double x, int bits);
+// (T4_k, T8_k) = (accept_threshold(4 beta_k), accept_threshold(8 beta_k)) into
+// out[2k], out[2k + 1] for k < S; ISING_ERR_ARG when some beta_k is not > 0.
+int threshold_table(const double* betas, int32_t S, int bits, uint32_t* out);
+
+// Launch shape of the strip kernel (abi.cu): trials per group G (0: the
+// handle's, else 32 or all trials rounded up to a Philox block), strips per
+// cluster C, threads per CTA and rows per strip.  ISING_ERR_UNSUPPORTED when
+// no strip width fits shared memory or the grid is too tall.
+struct StripShape {
+  int G, C, threads, Rmax;
+};
+int strip_shape(const ising_problem* p, int32_t T, int32_t G, StripShape* out);
+// Records a strip-kernel launch in the handle (ising_last_launch,
+// ising_last_kernel) and logs it at ISING_LOG >= 1.
+void record_strip_launch(ising_problem* p, int32_t trials, int32_t S, const StripShape& sh);
+
 size_t anneal_smem_bytes(int32_t H, int32_t Rmax);
 // grid = (C, ceil(T/G)); cluster (C,1,1) when C > 1
 cudaError_t launch_anneal(const AnnealArgs& a, int threads, cudaStream_t stream);

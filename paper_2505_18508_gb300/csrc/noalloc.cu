@@ -14,7 +14,6 @@
 // device share it and it keeps the last call's contents; two calls whose work
 // overlaps on the GPU (different streams, no ordering between them) race on
 // it, so order such calls on one stream or with events.
-#include <cmath>
 #include <mutex>
 
 #include "../../include/ising.h"
@@ -25,8 +24,8 @@ namespace {
 constexpr int32_t kNoAllocMaxSweeps = 32768;
 constexpr int kMaxDevices = 64;
 
-// (T4_k, T8_k) for every sweep of the current call; written by the host
-// through its device address before each launch, read by the kernel.
+// (T4_k, T8_k) for every sweep of the current call; written by the fill
+// kernels queued ahead of the annealing launch, read by that launch.
 static __device__ __align__(256) uint32_t g_noalloc_thresholds[2 * kNoAllocMaxSweeps];
 
 std::mutex g_setup_mutex;
@@ -47,20 +46,16 @@ int table_address(int device, uint32_t** out) {
   return ISING_OK;
 }
 
-// floor(exp(-beta dE) 2^32), clamped to 2^32 - 1, for dE = 4 and 8 (the same
-// acceptance thresholds as ising_anneal); in the 16-bit draw mode
-// floor(exp(-beta dE) 2^16), clamped to 2^16 - 1, shifted left by 16 bits
-int threshold_pair(double beta, int bits, uint32_t* t4, uint32_t* t8) {
-  if (!(beta > 0.0)) return ISING_ERR_ARG;
-  const double scale = bits == 16 ? 65536.0 : 4294967296.0;
-  const double v4 = std::floor(std::exp(-(beta * 4.0)) * scale);
-  const double v8 = std::floor(std::exp(-(beta * 8.0)) * scale);
-  const uint32_t top = bits == 16 ? 0xFFFFu : 0xFFFFFFFFu;
-  const uint32_t a4 = v4 >= scale - 1.0 ? top : static_cast<uint32_t>(v4);
-  const uint32_t a8 = v8 >= scale - 1.0 ? top : static_cast<uint32_t>(v8);
-  *t4 = bits == 16 ? a4 << 16 : a4;
-  *t8 = bits == 16 ? a8 << 16 : a8;
-  return ISING_OK;
+// Copies one slice of the threshold table into the fixed array.  The words
+// travel inside the kernel's parameters, which the launch copies when it is
+// queued, so no host buffer has to outlive the call and no pageable
+// host-to-device copy is involved.
+constexpr int kFillWords = 2048;   // 1,024 sweeps (8 KiB of parameters) per launch
+struct FillSlice {
+  uint32_t w[kFillWords];
+};
+__global__ void fill_table_kernel(uint32_t* __restrict__ dst, const FillSlice slice, int32_t words) {
+  for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = slice.w[i];
 }
 
 int map_err(cudaError_t e) {
@@ -88,61 +83,20 @@ extern "C" int ising_anneal_noalloc(ising_problem* p, int32_t trials, const doub
   int rc = table_address(device, &table);
   if (rc != ISING_OK) return rc;
 
-  // launch shape: the handle's fixed shape, else one trial group of 32 per
-  // cluster of strips as wide as fits one CTA per SM (same rule as ising_anneal)
-  int sms = 0, smem_max = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) sms = 152;
-  if (cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
-      smem_max <= 0)
-    smem_max = 227 * 1024;
-  const int unit = p->draw_bits == 16 ? 8 : 4;   // trials per Philox block
-  int G = p->cfg_group ? p->cfg_group : (trials >= 32 ? 32 : ((trials + unit - 1) / unit) * unit);
-  const int groups = (trials + G - 1) / G;
-  int C = p->cfg_strips;
-  if (C == 0) {
-    C = 1;
-    while (C < 8 && groups * (C * 2) <= sms && p->Y / (C * 2) >= 2) C *= 2;
-    while (C < 16 && ising::anneal_smem_bytes(p->H, (p->Y + C - 1) / C) > static_cast<size_t>(smem_max) &&
-           C * 2 <= p->Y)
-      C *= 2;
-  }
-  if (C > p->Y || groups > 65535) return ISING_ERR_UNSUPPORTED;
-  const int Rmax = (p->Y + C - 1) / C;
-  if (ising::anneal_smem_bytes(p->H, Rmax) > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
-  int threads = p->cfg_threads;
-  if (threads == 0) {
-    const int items = Rmax * p->H;
-    threads = 1024;
-    if (items <= 768) {
-      threads = ((items + 31) / 32) * 32;
-      if (threads < 64) threads = 64;
-    } else {
-      double best = -1.0;
-      for (int t = 768; t <= 1024; t += 32) {
-        const int it = (items + t - 1) / t;
-        const double eff = static_cast<double>(items) / (static_cast<double>(it) * t);
-        if (eff > best + 1e-9 || (std::fabs(eff - best) <= 1e-9 && t > threads)) {
-          best = eff;
-          threads = t;
-        }
-      }
-    }
-  }
+  // the launch shape ising_anneal gives the strip kernel
+  ising::StripShape sh;
+  rc = ising::strip_shape(p, trials, 0, &sh);
+  if (rc != ISING_OK) return rc;
 
-  // thresholds into the fixed table, through a small host buffer on the stack
-  // (pageable host-to-device copies are staged before cudaMemcpyAsync returns,
-  // so the buffer can be refilled right away)
+  // thresholds into the fixed table, one slice per fill launch
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  constexpr int32_t kChunk = 512;
-  uint32_t buf[2 * kChunk];
-  for (int32_t k0 = 0; k0 < S; k0 += kChunk) {
-    const int32_t m = S - k0 < kChunk ? S - k0 : kChunk;
-    for (int32_t j = 0; j < m; ++j) {
-      rc = threshold_pair(betas[k0 + j], p->draw_bits, &buf[2 * j], &buf[2 * j + 1]);
-      if (rc != ISING_OK) return rc;
-    }
-    const cudaError_t e = cudaMemcpyAsync(table + 2 * static_cast<size_t>(k0), buf, sizeof(uint32_t) * 2 * m,
-                                          cudaMemcpyHostToDevice, st);
+  FillSlice slice;
+  for (int32_t k0 = 0; k0 < S; k0 += kFillWords / 2) {
+    const int32_t m = S - k0 < kFillWords / 2 ? S - k0 : kFillWords / 2;
+    rc = ising::threshold_table(betas + k0, m, p->draw_bits, slice.w);
+    if (rc != ISING_OK) return rc;
+    fill_table_kernel<<<1, 256, 0, st>>>(table + 2 * static_cast<size_t>(k0), slice, 2 * m);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return map_err(e);
   }
 
@@ -154,7 +108,7 @@ extern "C" int ising_anneal_noalloc(ising_problem* p, int32_t trials, const doub
   a.out_cuts = out_cuts;
   a.X = p->X; a.Y = p->Y; a.H = p->H; a.n = p->n;
   a.T = trials;
-  a.G = G;
+  a.G = sh.G;
   a.S = S;
   a.k0 = sweep_offset;
   a.key0 = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
@@ -163,9 +117,12 @@ extern "C" int ising_anneal_noalloc(ising_problem* p, int32_t trials, const doub
     a.rk[2 * r] = a.key0 + r * 0x9E3779B9u;
     a.rk[2 * r + 1] = a.key1 + r * 0xBB67AE85u;
   }
-  a.C = C;
-  a.Rmax = Rmax;
+  a.C = sh.C;
+  a.Rmax = sh.Rmax;
   a.neg_edges = p->neg_edges;
   a.u16 = p->draw_bits == 16 ? 1 : 0;
-  return map_err(ising::launch_anneal(a, threads, st));
+  const cudaError_t e = ising::launch_anneal(a, sh.threads, st);
+  if (e != cudaSuccess) return map_err(e);
+  ising::record_strip_launch(p, trials, S, sh);
+  return ISING_OK;
 }

@@ -68,11 +68,6 @@ int map_err(cudaError_t e) {
   return ISING_ERR_CUDA;
 }
 
-uint32_t threshold32(double x) {   // min(floor(exp(-x) 2^32), 2^32 - 1)
-  const double v = std::floor(std::exp(-x) * 4294967296.0);
-  return v >= 4294967295.0 ? 0xFFFFFFFFu : static_cast<uint32_t>(v);
-}
-
 }  // namespace
 
 extern "C" int ising_anneal_pt(ising_problem* p, int32_t temps, const double* betas, int32_t chains, int32_t rounds,
@@ -97,41 +92,27 @@ extern "C" int ising_anneal_pt(ising_problem* p, int32_t temps, const double* be
     for (int32_t g = 0; g < groups; ++g) {
       const double beta = betas[g * 32 / chains];
       for (int32_t k = 0; k < (L > 0 ? L : 1); ++k) {
-        thr[(static_cast<size_t>(g) * (L > 0 ? L : 1) + k) * 2 + 0] = threshold32(beta * 4.0);
-        thr[(static_cast<size_t>(g) * (L > 0 ? L : 1) + k) * 2 + 1] = threshold32(beta * 8.0);
+        thr[(static_cast<size_t>(g) * (L > 0 ? L : 1) + k) * 2 + 0] = ising::accept_threshold(beta * 4.0, 32);
+        thr[(static_cast<size_t>(g) * (L > 0 ? L : 1) + k) * 2 + 1] = ising::accept_threshold(beta * 8.0, 32);
       }
     }
     sthr.resize(static_cast<size_t>(temps > 1 ? temps - 1 : 1) * half_range);
     for (int32_t r = 0; r + 1 < temps; ++r) {
       const double db = betas[r + 1] - betas[r];
       for (int32_t h = 1; h <= half_range; ++h)
-        sthr[static_cast<size_t>(r) * half_range + (h - 1)] = threshold32(db * (2.0 * h));
+        sthr[static_cast<size_t>(r) * half_range + (h - 1)] = ising::accept_threshold(db * (2.0 * h), 32);
     }
   } catch (const std::bad_alloc&) {
     return ISING_ERR_OOM;
   }
 
   // launch shape of the strip kernel with 32-trial groups
-  int sms = 0, smem_max = 0, dev = p->device;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-  if (cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-    smem_max = 227 * 1024;
-  int Cs = p->cfg_strips;
-  if (Cs == 0) {
-    Cs = 1;
-    while (Cs < 8 && groups * (Cs * 2) <= sms && p->Y / (Cs * 2) >= 2) Cs *= 2;
-    while (Cs < 16 && ising::anneal_smem_bytes(p->H, (p->Y + Cs - 1) / Cs) > static_cast<size_t>(smem_max) &&
-           Cs * 2 <= p->Y)
-      Cs *= 2;
-  }
-  const int Rmax = (p->Y + Cs - 1) / Cs;
-  if (Cs > p->Y || groups > 65535 || ising::anneal_smem_bytes(p->H, Rmax) > static_cast<size_t>(smem_max))
-    return ISING_ERR_UNSUPPORTED;
-  int threads = p->cfg_threads;
-  if (threads == 0) {
-    const int items = Rmax * p->H;
-    threads = items <= 768 ? std::max(64, ((items + 31) / 32) * 32) : 1024;
-  }
+  ising::StripShape sh;
+  const int src = ising::strip_shape(p, T, 32, &sh);
+  if (src != ISING_OK) return src;
+  const int Cs = sh.C, Rmax = sh.Rmax, threads = sh.threads;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || sms <= 0) sms = 152;
 
   // device scratch: thresholds, swap tables, the other spin buffer
   const size_t b_thr = ((thr.size() * 4 + 255) / 256) * 256, b_sthr = ((sthr.size() * 4 + 255) / 256) * 256;

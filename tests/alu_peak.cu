@@ -1,4 +1,5 @@
-// alu_peak.cu -- measures the integer-pipe peaks the annealer's roofline uses:
+// alu_peak.cu -- test program (tests/test_gpu_alu_peak.py): measures the
+// integer-pipe peaks the annealer's roofline uses:
 // per-SM throughput of 32-bit multiply-add (mad.lo), 32x32->64 multiply
 // (mul.wide), three-input logic (lop3) and whole Philox4x32-10 blocks.
 // One CTA of 1024 threads per SM; each CTA counts its own SM cycles with

@@ -5,7 +5,9 @@ while they run (their device memory is already reserved by the host
 framework, or their loop must stay out of the allocator).  It keeps the
 threshold table in a fixed array inside the library instead of allocating
 one per call; its results must be the same bits as the allocating call.
-Two calls in a row check that the shared array is rewritten correctly.
+Two calls in a row check that the shared array is rewritten correctly, and
+a chained pair of calls (the second resuming from the first one's spins at
+its global sweep) must equal one allocating call over both stretches.
 """
 import ctypes
 
@@ -46,11 +48,37 @@ def test_noalloc_matches_allocating_entry_point_twice():
         betas = synth.linear_betas(b0, b1, S)
         rc, s_na, c_na = _noalloc(ia, prob, trials, betas, seed)
         assert rc == 0, ia.lib().ising_strerror(rc)
+        shape_na, kernel_na = prob.last_launch(), prob.last_kernel()
         s_ref, c_ref = ia.anneal(prob, trials, betas, seed)
+        # the handle reports the launch the call used: the strip kernel in the
+        # shape ising_anneal picks for the same trials
+        assert kernel_na == 1 and prob.last_kernel() == 1
+        assert shape_na == prob.last_launch()
         torch.cuda.synchronize()
         assert torch.equal(s_na, s_ref)
         assert torch.equal(c_na, c_ref)
     # beyond the fixed capacity: rejected before anything is queued
     rc, _, _ = _noalloc(ia, prob, 4, np.ones(40000), 1)
     assert rc == -8
+    prob.destroy()
+
+
+def test_noalloc_chained_calls_match_one_allocating_call():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2505_18508_gb300 as ia
+    torch.cuda.set_device(0)
+    inst = synth.torus_instance(60, 40, 5)
+    prob = ia.Problem.from_instance(inst)
+    trials, S1, S2, seed = 72, 1500, 900, 4321     # S1 crosses a 1,024-sweep copy slice
+    betas = synth.linear_betas(0.1, 3.0, S1 + S2)
+    rc, s1, _ = _noalloc(ia, prob, trials, betas[:S1], seed)
+    assert rc == 0, ia.lib().ising_strerror(rc)
+    rc, s2, c2 = _noalloc(ia, prob, trials, betas[S1:], seed, sweep_offset=S1, init=s1)
+    assert rc == 0, ia.lib().ising_strerror(rc)
+    s_ref, c_ref = ia.anneal(prob, trials, betas, seed)
+    torch.cuda.synchronize()
+    assert torch.equal(s2, s_ref)
+    assert torch.equal(c2, c_ref)
     prob.destroy()
