@@ -534,6 +534,20 @@ int ising_cnn_forward(const ising_cnn* net, const ising_problem* p, const int8_t
 int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* spins, const uint8_t* targets,
                    int32_t B, float* grad, float* loss, void* ws, size_t ws_bytes, void* cuda_stream);
 
+/*
+ * ising_cnn_set_wait_limit -- cycles one device-side wait of the network's
+ * tensor-core kernels (for the completion of its MMAs) may take before the
+ * CTA gives up (0 restores the default of about two seconds), and a test
+ * switch: stall_test = 1 makes CTA 0 of every tensor-core launch of this
+ * network wait once, with that limit, on an mbarrier nothing arrives at, so
+ * the wait runs out on purpose.  A CTA whose wait ran out stops its work,
+ * still waits for the MMAs it has committed before it frees its tensor
+ * memory, and leaves ISING_ERR_TIMEOUT in the problem's status word
+ * (ising_get_status); that call's results are undefined.  This project's
+ * failure detection; the paper has no counterpart.  Errors: ISING_ERR_ARG.
+ */
+int ising_cnn_set_wait_limit(ising_cnn* net, int64_t cycles, int32_t stall_test);
+
 /* ising_cnn_adam_step -- one Adam update of the FP32 master parameters with
  * the device gradient `grad`, then refresh the BF16 copies. */
 int ising_cnn_adam_step(ising_cnn* net, const float* grad, float lr, float beta1, float beta2, float eps,

@@ -77,7 +77,8 @@ def _torch():
 
 
 def forward(params, spins, w_right, w_down, return_all=False):
-    """Logits [B, Y, X] (float64)."""
+    """Logits [B, Y, X] (float64).  return_all: also the input features, the
+    hidden pre-activations p1..p3 and activations h1..h3."""
     torch = _torch()
     F = torch.nn.functional
     p = {k: torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)) for k, v in unflatten(params).items()}
@@ -86,12 +87,16 @@ def forward(params, spins, w_right, w_down, return_all=False):
     def conv(t, W, b):
         return F.conv2d(F.pad(t, (1, 1, 1, 1), mode="circular"), W, b)
 
-    h1 = torch.relu(conv(x, p["W1"], p["b1"]))
-    h2 = torch.relu(conv(h1, p["W2"], p["b2"]))
-    h3 = torch.relu(conv(h2, p["W3"], p["b3"]))
+    p1 = conv(x, p["W1"], p["b1"])
+    h1 = torch.relu(p1)
+    p2 = conv(h1, p["W2"], p["b2"])
+    h2 = torch.relu(p2)
+    p3 = conv(h2, p["W3"], p["b3"])
+    h3 = torch.relu(p3)
     z = conv(h3, p["W4"], p["b4"])[:, 0]
     if return_all:
-        return {"x": x.numpy(), "h1": h1.numpy(), "h2": h2.numpy(), "h3": h3.numpy(), "z": z.numpy()}
+        return {"x": x.numpy(), "p1": p1.numpy(), "h1": h1.numpy(), "p2": p2.numpy(), "h2": h2.numpy(),
+                "p3": p3.numpy(), "h3": h3.numpy(), "z": z.numpy()}
     return z.numpy()
 
 

@@ -504,6 +504,9 @@ class CNN:
                                    _dptr(ws), ctypes.c_size_t(ws.numel()), _stream_ptr(stream)), "ising_cnn_grad")
         return loss, g
 
+    def set_wait_limit(self, cycles=0, stall_test=0):
+        check(lib().ising_cnn_set_wait_limit(self._h, int(cycles), int(stall_test)), "ising_cnn_set_wait_limit")
+
     def adam_step(self, grad, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         grad = _device_tensor(grad, _torch().float32, (CNN_PARAMS,), "grad")
         check(lib().ising_cnn_adam_step(self._h, _dptr(grad), ctypes.c_float(lr), ctypes.c_float(beta1),

@@ -71,6 +71,7 @@ _SIGNATURES = {
     "ising_cnn_workspace_bytes": (ctypes.c_size_t, [_i32, _i32, _i32]),
     "ising_cnn_forward": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp, ctypes.c_size_t, _vp]),
     "ising_cnn_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "ising_cnn_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64, _i32]),
     "ising_cnn_adam_step": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                            ctypes.c_float, _vp]),
     "ising_propose": (ctypes.c_int, [_vp, _vp, _i32, _vp, _i32, _vp, _vp]),

@@ -172,6 +172,8 @@ struct ising_cnn {
   __nv_bfloat16* tc3b = nullptr;
   __nv_bfloat16* tc4 = nullptr;
   int64_t step = 0;
+  long long wait_limit = 0;   // cycles one tensor-core wait may take (0: about two seconds)
+  int32_t stall_test = 0;     // 1: CTA 0 of every tensor-core launch waits once on a barrier nothing arrives at
 };
 
 namespace {
@@ -200,13 +202,15 @@ int sm_count() {
   return v;
 }
 
-TcConvArgs tc_args(const ising_problem* p, int32_t B) {
+TcConvArgs tc_args(const ising_cnn* net, const ising_problem* p, int32_t B) {
   TcConvArgs a{};
   a.X = p->X;
   a.Y = p->Y;
   a.B = B;
   a.eflags = p->d_eflags;
   a.status = p->d_status;
+  a.wait_limit = net->wait_limit;
+  a.stall_test = net->stall_test;
   return a;
 }
 
@@ -258,14 +262,14 @@ size_t ws_layout(int32_t B, int32_t n, int train, WS* w, unsigned char* base) {
 cudaError_t forward_pass(const ising_cnn* net, const ising_problem* p, const int8_t* spins, int32_t B, float* z,
                          const WS& w, cudaStream_t st) {
   const int sms = sm_count();
-  TcConvArgs a = tc_args(p, B);
+  TcConvArgs a = tc_args(net, p, B);
   a.spins = spins;
   a.wt = net->tc1;
   a.bias = net->master + OFF_B1;
   a.out_bf16 = w.h1;
   cudaError_t e = launch_conv_tc(0, a, sms, st);
   if (e != cudaSuccess) return e;
-  a = tc_args(p, B);
+  a = tc_args(net, p, B);
   a.in = w.h1;
   a.wt = net->tc2f;
   a.bias = net->master + OFF_B2;
@@ -278,7 +282,7 @@ cudaError_t forward_pass(const ising_cnn* net, const ising_problem* p, const int
   a.out_bf16 = w.h3;
   e = launch_conv_tc(1, a, sms, st);
   if (e != cudaSuccess) return e;
-  a = tc_args(p, B);
+  a = tc_args(net, p, B);
   a.in = w.h3;
   a.wt = net->tc4;
   a.bias = net->master + OFF_B4;
@@ -388,7 +392,7 @@ int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* s
   loss_kernel<<<blocks, 256, 0, st>>>(w.z, targets, N, w.dz, loss);
   layer4_back_kernel<<<static_cast<int>((4 * N + 255) / 256), 256, 0, st>>>(w.dz, w.h3, B, X, Y, net->w4r, w.g3);
   {
-    TcConvArgs a = tc_args(p, B);
+    TcConvArgs a = tc_args(net, p, B);
     a.in = w.g3;
     a.wt = net->tc3b;
     a.mask = w.h2;
@@ -413,6 +417,8 @@ int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* s
     a.bpart = w.bpart;
     a.status = p->d_status;
     a.max_ctas = w.max_ctas;
+    a.wait_limit = net->wait_limit;
+    a.stall_test = net->stall_test;
     const int sms = sm_count();
     a.act = w.h3;
     a.g = w.dz;
@@ -437,6 +443,13 @@ int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* s
     if (e != cudaSuccess) return cnn_map(e);
   }
   return cnn_map(cudaGetLastError());
+}
+
+int ising_cnn_set_wait_limit(ising_cnn* net, int64_t cycles, int32_t stall_test) {
+  if (!net || cycles < 0 || stall_test < 0 || stall_test > 1) return ISING_ERR_ARG;
+  net->wait_limit = cycles;
+  net->stall_test = stall_test;
+  return ISING_OK;
 }
 
 int ising_cnn_adam_step(ising_cnn* net, const float* grad, float lr, float beta1, float beta2, float eps,

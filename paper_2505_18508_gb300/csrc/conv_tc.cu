@@ -114,8 +114,9 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Bounded wait on an mbarrier phase by the calling thread.
-__device__ __forceinline__ bool wait_mbar(uint32_t mbar, uint32_t phase) {
+// Bounded wait on an mbarrier phase by the calling thread: false when `limit`
+// cycles pass first.
+__device__ __forceinline__ bool wait_mbar(uint32_t mbar, uint32_t phase, long long limit) {
   uint32_t done = 0;
   const long long t_start = clock64();
   while (!done) {
@@ -124,7 +125,7 @@ __device__ __forceinline__ bool wait_mbar(uint32_t mbar, uint32_t phase) {
         : "=r"(done)
         : "r"(mbar), "r"(phase)
         : "memory");
-    if (!done && clock64() - t_start > kWaitCycles) break;   // about two seconds
+    if (!done && clock64() - t_start > limit) break;
   }
   return done != 0;
 }
@@ -157,8 +158,10 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
   unsigned char* sw = smem;                                        // weights [9][KC][NG][8][16B]
   unsigned char* srow = smem + wbytes;                              // kRing slots x [KC][RP][16B]
   const size_t slot_bytes = static_cast<size_t>(KC) * RP * 16;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(srow + kRing * slot_bytes);   // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  // [0], [1]: MMA completion of accumulator buffers 0, 1; [2]: a spare barrier
+  // nothing arrives at (the stall test waits on it)
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(srow + kRing * slot_bytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   for (int i = tid; i < static_cast<int>(wbytes / 16); i += kConvThreads)
@@ -176,6 +179,7 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar + 1)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar + 2)));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -300,7 +304,10 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
 
   const long long R = static_cast<long long>(a.B) * Y;
   const long long r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
-  uint32_t phases = 0;   // bit j: parity to wait for on mbar[j]
+  const long long limit = a.wait_limit > 0 ? a.wait_limit : kWaitCycles;
+  uint32_t phases = 0;    // bit j: parity to wait for on mbar[j]
+  uint32_t pending = 0;   // bit j: MMAs committed to mbar[j] and not yet awaited
+  bool stall = a.stall_test != 0 && blockIdx.x == 0;
   bool ok = true;
   for (long long row = r0; row < r1 && ok;) {
     const int b = static_cast<int>(row / Y);
@@ -323,14 +330,23 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok) break;
       if (tid == 0) issue_mmas(y, static_cast<uint32_t>(y & 1));
+      pending |= 1u << (y & 1);
+      if (stall) {   // test switch: a bounded wait on the barrier nothing arrives at
+        stall = false;
+        if (!wait_mbar(saddr(mbar + 2), 0u, limit)) ok = false;
+      }
       if (y > ya) prefetch_mask(b, y - 1);
       bool prev = false;
-      if (y > ya) {
+      if (ok && y > ya) {
         const uint32_t pb = static_cast<uint32_t>((y - 1) & 1);
-        prev = wait_mbar(saddr(mbar + pb), (phases >> pb) & 1u);
-        phases ^= 1u << pb;
+        prev = wait_mbar(saddr(mbar + pb), (phases >> pb) & 1u, limit);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!prev) ok = false;
+        if (prev) {
+          phases ^= 1u << pb;
+          pending &= ~(1u << pb);
+        } else {
+          ok = false;
+        }
       }
       if (ok && y + 3 <= yb + 1) stage(b, y + 3);
       if (kIn != 0) cp_async_commit();       // (possibly empty) group of row y+3
@@ -340,11 +356,15 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
     if (ok) {
       prefetch_mask(b, yb);
       const uint32_t lb = static_cast<uint32_t>(yb & 1);
-      const bool last = wait_mbar(saddr(mbar + lb), (phases >> lb) & 1u);
-      phases ^= 1u << lb;
+      const bool last = wait_mbar(saddr(mbar + lb), (phases >> lb) & 1u, limit);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (last) epilogue(b, yb, lb);
-      else ok = false;
+      if (last) {
+        phases ^= 1u << lb;
+        pending &= ~(1u << lb);
+        epilogue(b, yb, lb);
+      } else {
+        ok = false;
+      }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     ok = __syncthreads_and(ok) != 0;
@@ -352,8 +372,15 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
     row = seg_end;
   }
   if (!ok && tid == 0) atomicExch(a.status, ISING_ERR_TIMEOUT);
+  // MMAs still committed but not awaited (the work ended early) finish before
+  // their tensor memory is freed
+  for (uint32_t j = 0; j < 2; ++j)
+    if (pending & (1u << j)) wait_mbar(saddr(mbar + j), (phases >> j) & 1u, kWaitCycles);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (kIn != 0) cp_async_commit_wait_all();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
@@ -430,8 +457,8 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(TcWgradArgs a) {
   const size_t blk = static_cast<size_t>(RP) * 16;   // bytes per block row
   unsigned char* sA = smem;                          // 12 blocks: [ky][chunk][pixel][16 B]
   unsigned char* sB = smem + 12 * blk;               // NB blocks: [kx][chunk][pixel][16 B]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + NB * blk);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + NB * blk);   // [0] MMA completion, [1] spare (stall test)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   float* sbias = reinterpret_cast<float*>(tslot + 4);   // [warps][32] per-warp bias sums
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -443,11 +470,16 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(TcWgradArgs a) {
                  "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)));
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar + 1)));
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
+  const long long limit = a.wait_limit > 0 ? a.wait_limit : kWaitCycles;
+  bool stall = a.stall_test != 0 && blockIdx.x == 0;
 
   const long long R = static_cast<long long>(a.B) * Y;
   const long long r0 = R * blockIdx.x / gridDim.x, r1 = R * (blockIdx.x + 1) / gridDim.x;
@@ -532,19 +564,16 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(TcWgradArgs a) {
                    : "memory");
     }
     first = false;
-    // the next row's staging overwrites what these MMAs read: wait for them
-    uint32_t done = 0;
-    const long long t_start = clock64();
-    while (!done) {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(done)
-          : "r"(saddr(mbar)), "r"(phase)
-          : "memory");
-      if (!done && clock64() - t_start > kWaitCycles) break;
+    bool stalled = false;
+    if (stall) {   // test switch: a bounded wait on the barrier nothing arrives at
+      stall = false;
+      stalled = !wait_mbar(saddr(mbar + 1), 0u, limit);
     }
+    // the next row's staging overwrites what these MMAs read: wait for them
+    // (also after a stall, so that they finish before tensor memory is freed)
+    uint32_t done = wait_mbar(saddr(mbar), phase, limit) ? 1u : 0u;
     phase ^= 1u;
-    done = __syncthreads_and(done);
+    done = __syncthreads_and(done && !stalled);
     if (!done) {
       if (tid == 0) atomicExch(a.status, ISING_ERR_TIMEOUT);
       ok = false;

@@ -137,6 +137,8 @@ struct TcConvArgs {
   float* out_f32;               // [B*n] (kind 3)
   int32_t* status;              // bounded-wait failures
   int X, Y, B;
+  long long wait_limit;         // cycles one mbarrier wait may take (0: about two seconds)
+  int32_t stall_test;           // 1: CTA 0 waits once on a barrier nothing arrives at
 };
 size_t conv_tc_smem(int kind, int X);
 
@@ -153,6 +155,8 @@ struct TcWgradArgs {
   int32_t* status;
   int X, Y, B;
   int max_ctas;
+  long long wait_limit;         // as TcConvArgs
+  int32_t stall_test;
 };
 constexpr int kWgradMaxCtas = 640;
 size_t wgrad_tc_smem(int kind, int X);

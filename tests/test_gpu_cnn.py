@@ -1,7 +1,11 @@
 """GPU parity for the learned proposal stage against the FP64 CPU oracle.
 
 * logits within 2e-2 absolute of the FP64 forward (BF16 weights/activations);
-* gradients within 3e-2 of the FP64 gradient, per parameter tensor, in norm;
+* gradients element by element against the FP64 gradient, on parameters
+  built so that every hidden ReLU mask is unambiguous (see
+  _unambiguous_params), and within 3e-2 per parameter tensor in norm on
+  random parameters;
+* flip targets (ising_flip_targets) equal to the oracle's, ties included;
 * Adam: the update of the device master weights equals the Adam formula;
 * proposals: bit-exact against the oracle fed with the same logits.
 """
@@ -79,6 +83,138 @@ def test_gradient_against_fp64(ia, X, Y, B):
     for name, e in errs.items():
         assert e <= (6e-2 if name in ("W1", "b1") else 3e-2), errs
     net.destroy(); prob.destroy()
+
+
+def _bf16_exact(a):
+    a32 = np.asarray(a, dtype=np.float32)
+    return np.array_equal(a32.view(np.uint32) & 0xFFFF, np.zeros(a32.shape, np.uint32))
+
+
+def _abs_conv(h, W):
+    """(|W| conv |h|) on the torus: per element the sum of |w| |a| over the
+    terms of a pre-activation."""
+    import torch
+    F = torch.nn.functional
+    t = torch.from_numpy(np.abs(h))
+    return F.conv2d(F.pad(t, (1, 1, 1, 1), mode="circular"), torch.from_numpy(np.abs(W))).numpy()
+
+
+def _unambiguous_params(inst, s, seed):
+    """Parameters whose hidden ReLU masks are the same on the GPU as in FP64,
+    asserted on the oracle's side.
+
+    Layers 1 and 2 compute exactly on the GPU: the features are +-1, W1 holds
+    multiples of 1/8 (|W1| <= 1/2) and b1 odd multiples of 1/16, so every
+    layer-1 pre-activation is an odd multiple of 1/16 (|p1| >= 1/16) and every
+    h1 = j/16 with j < 256 is exact in BF16; W2 holds multiples of 1/32
+    (|W2| <= 1/4), so p2 - b2 is a multiple of 1/512 and its FP32 sums are
+    exact, and b2 is an odd multiple of 1/1024 placed at the median of its
+    channel (|p2| >= 1/1024, both signs occur).  h2 is rounded to BF16 (at
+    most 2^-8 relative), so layer 3's pre-activations carry an error of at
+    most e3 = 2^-8 (|W3| conv |h2|); each layer-3 channel is put entirely on
+    or off with |p3| >= 2 e3 everywhere.  W3, W4 hold multiples of 1/64."""
+    rng = np.random.default_rng(seed)
+    P = {"W1": rng.integers(-4, 5, (32, 3, 3, 3)) / 8.0,
+         "b1": (2 * rng.integers(-8, 8, 32) + 1) / 16.0,
+         "W2": rng.integers(-8, 9, (32, 32, 3, 3)) / 32.0, "b2": np.zeros(32),
+         "W3": rng.integers(-8, 9, (32, 32, 3, 3)) / 64.0, "b3": np.zeros(32),
+         "W4": rng.integers(-8, 9, (1, 32, 3, 3)) / 64.0, "b4": np.array([-0.25])}
+
+    def flat():
+        return np.concatenate([P[name].reshape(-1) for name, _ in ocnn.SHAPES])
+
+    def fwd():
+        return ocnn.forward(flat(), s, inst["w_right"], inst["w_down"], return_all=True)
+
+    v = fwd()["p2"]                       # b2 = 0: p2 - b2
+    for o in range(32):
+        med = np.median(v[:, o])
+        P["b2"][o] = (2 * np.floor(-med * 512.0) + 1) / 1024.0
+    f = fwd()
+    v, e3 = f["p3"], 2.0 ** -8 * _abs_conv(f["h2"], P["W3"])
+    for o in range(32):
+        m = 2 * e3[:, o].max() + 2 ** -6
+        P["b3"][o] = (-v[:, o].min() + m) if o % 2 == 0 else (-v[:, o].max() - m)
+    P["b3"] = P["b3"].astype(np.float32).astype(np.float64)
+    f = fwd()
+    # the margins, on the oracle's side
+    p1 = f["p1"]
+    assert np.all(np.abs(p1) >= 1.0 / 16) and np.all((p1 * 16) % 2 == 1)
+    assert np.all(f["h1"] * 16 < 256) and _bf16_exact(f["h1"])
+    p2 = f["p2"]
+    assert np.all(np.abs(p2) >= 1.0 / 1024) and np.all((p2 * 1024) % 2 == 1) and np.all(np.abs(p2) < 2 ** 14)
+    for o in range(32):                    # both signs in every layer-2 channel
+        assert (p2[:, o] > 0).any() and (p2[:, o] < 0).any()
+    e3 = 2.0 ** -8 * _abs_conv(f["h2"], P["W3"])
+    assert np.all(np.abs(f["p3"]) >= 2 * e3)
+    params = flat()
+    assert _bf16_exact(np.concatenate([P[k].reshape(-1) for k in ("W1", "W2", "W3", "W4")]))
+    assert np.array_equal(params.astype(np.float32).astype(np.float64), params)
+    return params
+
+
+@pytest.mark.parametrize("X,Y,B,seed", [(12, 8, 3, 1), (20, 10, 2, 2), (34, 6, 2, 3)])
+def test_gradient_elementwise_against_fp64(ia, X, Y, B, seed):
+    """Every gradient element against FP64 autograd, with all ReLU masks
+    fixed (above).  What remains is BF16 storage of h2, h3 and of the three
+    backward activation gradients, each at most 2^-8 relative: a term passing
+    six such roundings moves by < 6 * 2^-8 = 2.3e-2 of itself, hence
+    |g - g64| <= 3e-2 |g64| + 1e-2 max|g64 of the tensor| (the absolute part
+    covers elements whose terms cancel)."""
+    import torch
+    inst = synth.torus_instance(X, Y, 40 + seed)
+    s = synth.random_spins(B, X * Y, 60 + seed)
+    y = ocnn.flip_targets(s, synth.random_spins(B, X * Y, 80 + seed))
+    params = _unambiguous_params(inst, s, seed)
+    prob = ia.Problem.from_instance(inst)
+    net = ia.CNN(params)
+    loss, g = net.grad(prob, torch.from_numpy(s).cuda(), torch.from_numpy(y).cuda())
+    torch.cuda.synchronize()
+    rl, rg = ocnn.loss_and_grad(params, s, y, inst["w_right"], inst["w_down"])
+    assert abs(loss.item() - rl) <= 1e-2 * abs(rl)
+    gg = g.cpu().numpy().astype(np.float64)
+    worst = {}
+    for name, sl in _tensor_slices():
+        d = np.abs(gg[sl] - rg[sl])
+        tol = 3e-2 * np.abs(rg[sl]) + 1e-2 * np.abs(rg[sl]).max()
+        worst[name] = float((d / tol).max())
+        bad = np.nonzero(d > tol)[0]
+        assert bad.size == 0, (name, bad[:8], gg[sl][bad[:8]], rg[sl][bad[:8]])
+    print(worst)
+    net.destroy(); prob.destroy()
+
+
+def test_flip_targets_against_oracle_with_ties(ia):
+    """ising_flip_targets equals the oracle's flip_targets, including rows with
+    exactly n/2 differing sites, with site 0 equal and with site 0 different."""
+    import torch
+    rng = np.random.default_rng(12)
+    n = 200
+    s = synth.random_spins(12, n, 13)
+    r = synth.random_spins(12, n, 14)
+    for row in range(4, 12):                 # exact ties
+        idx = rng.permutation(n)[: n // 2]
+        if row % 2 == 0:
+            idx = idx[idx != 0]
+            idx = np.concatenate([idx, [next(i for i in range(1, n) if i not in set(idx))]])
+        elif 0 not in idx:
+            idx[0] = 0
+        r[row] = s[row]
+        r[row, idx] = -s[row, idx]
+        assert (r[row] != s[row]).sum() == n // 2
+        assert (r[row, 0] != s[row, 0]) == (row % 2 == 1)
+    got = ia.flip_targets(torch.from_numpy(s).cuda(), torch.from_numpy(r).cuda())
+    torch.cuda.synchronize()
+    ref = ocnn.flip_targets(s, r)
+    np.testing.assert_array_equal(got.cpu().numpy(), ref)
+    assert (ref[4:, 0] == 0).all()
+    # odd n and a single site
+    for nn in (7, 1):
+        s1 = synth.random_spins(5, nn, 15)
+        r1 = synth.random_spins(5, nn, 16)
+        got = ia.flip_targets(torch.from_numpy(s1).cuda(), torch.from_numpy(r1).cuda())
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(got.cpu().numpy(), ocnn.flip_targets(s1, r1))
 
 
 def test_gradient_is_reproducible(ia):
@@ -181,3 +317,42 @@ def test_bad_tile_counts_are_rejected(ia):
     with pytest.raises(ia.IsingError):
         ia.propose(prob, s, torch.zeros((1, 96), device="cuda"), 4)
     prob.destroy()
+
+
+def test_tensor_core_wait_timeout_is_reported_and_next_call_is_exact(ia):
+    """The test switch makes CTA 0 of every tensor-core launch wait on an
+    mbarrier nothing arrives at, with a ~1 ms limit: the wait must run out,
+    the kernel must still await its committed MMAs before freeing tensor
+    memory, the status word must read ISING_ERR_TIMEOUT, and the next calls
+    (forward and gradient) on the same context must be exact again."""
+    import torch
+    X, Y, B = 20, 10, 3
+    inst = synth.torus_instance(X, Y, 5)
+    params = _params(1)
+    s = synth.random_spins(B, X * Y, 7)
+    y = ocnn.flip_targets(s, synth.random_spins(B, X * Y, 8))
+    prob = ia.Problem.from_instance(inst)
+    net = ia.CNN(params)
+    sd, yd = torch.from_numpy(s).cuda(), torch.from_numpy(y).cuda()
+    ref_z = net.forward(prob, sd).clone()
+    ref_loss, ref_g = net.grad(prob, sd, yd)
+    ref_g = ref_g.clone()
+    torch.cuda.synchronize()
+    assert prob.get_status() == 0
+    net.set_wait_limit(2_000_000, stall_test=1)            # about 1 ms of cycles
+    net.forward(prob, sd)
+    assert prob.get_status() == -7                          # ISING_ERR_TIMEOUT
+    assert prob.get_status() == 0                           # read-and-clear
+    net.grad(prob, sd, yd)
+    assert prob.get_status() == -7
+    net.set_wait_limit(0, 0)
+    z = net.forward(prob, sd)
+    loss, g = net.grad(prob, sd, yd)
+    torch.cuda.synchronize()
+    assert prob.get_status() == 0
+    assert torch.equal(z, ref_z)                             # the same kernels, the same bits
+    assert torch.equal(g, ref_g)                             # fixed-order reductions
+    assert abs(loss.item() - ref_loss.item()) <= 1e-6 * abs(ref_loss.item())
+    err = np.abs(z.cpu().numpy() - ocnn.forward(params, s, inst["w_right"], inst["w_down"]).reshape(B, -1)).max()
+    assert err <= 2e-2
+    net.destroy(); prob.destroy()

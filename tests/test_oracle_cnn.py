@@ -95,6 +95,28 @@ def test_flip_targets_are_gauge_invariant():
     assert (a.sum(axis=1) <= 25).all()
 
 
+def test_flip_target_tie_rule_on_hand_built_states():
+    """Exactly n/2 sites differ: r and -r are equally close to s, and the
+    reading keeps the aligned reference that agrees with s at site 0, so the
+    target never asks to flip site 0 on a tie, and r and -r give the same
+    targets.  Hand-built: n = 4 and n = 6, site 0 equal and different."""
+    s = np.array([[1, 1, 1, 1]], dtype=np.int8)
+    r_keep = np.array([[1, 1, -1, -1]], dtype=np.int8)      # site 0 equal: r itself is used
+    r_flip = np.array([[-1, -1, 1, 1]], dtype=np.int8)      # site 0 differs: -r is used
+    np.testing.assert_array_equal(cnn.flip_targets(s, r_keep), [[0, 0, 1, 1]])
+    np.testing.assert_array_equal(cnn.flip_targets(s, r_flip), [[0, 0, 1, 1]])
+    np.testing.assert_array_equal(cnn.flip_targets(s, -r_keep), [[0, 0, 1, 1]])
+    np.testing.assert_array_equal(cnn.flip_targets(s, -r_flip), [[0, 0, 1, 1]])
+    s6 = np.array([[1, -1, 1, -1, 1, -1], [-1, -1, 1, 1, -1, 1]], dtype=np.int8)
+    r6 = np.array([[-1, 1, 1, -1, -1, -1], [-1, 1, -1, 1, -1, 1]], dtype=np.int8)
+    # row 0: sites 0, 1, 4 differ (a tie, site 0 differs) -> flip r: targets = sites 2, 3, 5
+    # row 1: sites 1, 2 differ (2 < 3, no tie) -> keep r: targets = sites 1, 2
+    np.testing.assert_array_equal(cnn.flip_targets(s6, r6), [[0, 0, 1, 1, 0, 1], [0, 1, 1, 0, 0, 0]])
+    # away from ties the targets are the Hamming-nearer gauge copy's differences
+    assert cnn.flip_targets(np.ones((1, 5), np.int8), np.array([[1, -1, -1, -1, 1]], np.int8)).tolist() == \
+        [[1, 0, 0, 0, 1]]
+
+
 def _energy(inst, s):
     return oracle.energy_csr(inst, s)
 
