@@ -378,6 +378,7 @@ ising::BatchArgs batch_args(const HostBatch& hb, unsigned char* d_arena) {
 // ---------------------------------------------------------------- flow kernel plan
 struct FlowPlan {
   int G = 0, groups = 0, RT = 0, P = 0, LRmax = 0;
+  int cap = 0, use_rec = 0;   // items per colour of the largest CTA (multiple of 32); fast-path records
   size_t smem = 0;
   std::vector<int32_t> split;
 };
@@ -480,13 +481,25 @@ int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp, bool weighted = t
   std::vector<int32_t>& split = fs.split;
   // the kernel's tables hold shared-memory word indices in 16 bits
   if (2LL * LRmax * H + 1 > 0xFFFF) return ISING_ERR_UNSUPPORTED;
-  const size_t smem = ising::flow_smem_bytes(LRmax, p->H);
+  // the kernel's fast path keeps two 16-byte records per item and colour and
+  // a 16-bit byte offset of each local row's counter: used when they fit
+  int items_max = 0;
+  for (int q = 0; q < P; ++q) items_max = std::max(items_max, split[q + 1] - split[q]);
+  const int cap = (items_max + 31) / 32 * 32;
+  int use_rec = 1;
+  size_t smem = ising::flow_smem_bytes(LRmax, p->H, cap, 1);
+  if (smem > static_cast<size_t>(smem_max) || 8LL * (LRmax + 2) >= 65536) {
+    use_rec = 0;
+    smem = ising::flow_smem_bytes(LRmax, p->H, cap, 0);
+  }
   if (smem > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
   fp->G = G;
   fp->groups = groups;
   fp->RT = RT;
   fp->P = P;
   fp->LRmax = LRmax;
+  fp->cap = cap;
+  fp->use_rec = use_rec;
   fp->smem = smem;
   fp->split.swap(split);
   return ISING_OK;
@@ -586,6 +599,8 @@ int flow_run_launch(FlowRun* r, const uint32_t* d_thr, int32_t thr_group_stride,
     a.spin_limit = p->wait_limit > 0 ? p->wait_limit : 4000000000LL;
     a.stall_test = p->stall_test;
     a.u16 = p->draw_bits == 16 ? 1 : 0;
+    a.cap = fp.cap;
+    a.use_rec = fp.use_rec;
     e = launch_flow(a, st);
   }
   if (e != cudaSuccess) return map_cuda(e);

@@ -209,14 +209,15 @@ struct HeadsShared {
   }
 };
 
-// Metropolis update of one site word; returns the new word.  nq: Philox
-// blocks of the group (decision_blocks); heads(j): the head of block j.
+// Metropolis update of one site word; returns the new word.  mL..mD: all
+// ones where the edge to the left / right / upper / lower neighbour has
+// w = -1, else zero.  nq: Philox blocks of the group (decision_blocks);
+// heads(j): the head of block j.
 template <bool kU16, class Heads>
-__device__ __forceinline__ uint32_t update_word_h(uint32_t s, uint32_t nl, uint32_t nr, uint32_t nu, uint32_t nd,
-                                                 uint32_t f, uint32_t i, const Heads& heads, int nq,
-                                                 uint32_t T4, uint32_t T8, const uint32_t* __restrict__ rk) {
-  const uint32_t mL = 0u - (f & 1u), mR = 0u - ((f >> 1) & 1u);
-  const uint32_t mU = 0u - ((f >> 2) & 1u), mD = 0u - ((f >> 3) & 1u);
+__device__ __forceinline__ uint32_t update_word_m(uint32_t s, uint32_t nl, uint32_t nr, uint32_t nu, uint32_t nd,
+                                                 uint32_t mL, uint32_t mR, uint32_t mU, uint32_t mD, uint32_t i,
+                                                 const Heads& heads, int nq, uint32_t T4, uint32_t T8,
+                                                 const uint32_t* __restrict__ rk) {
   const uint32_t eL = ~(s ^ nl ^ mL), eR = ~(s ^ nr ^ mR);
   const uint32_t eU = ~(s ^ nu ^ mU), eD = ~(s ^ nd ^ mD);
   const uint32_t any = eL | eR | eU | eD;
@@ -244,6 +245,25 @@ __device__ __forceinline__ uint32_t update_word_h(uint32_t s, uint32_t nl, uint3
     }
   }
   return s ^ (ge2 | (eq1 & ~rej4) | (eq0 & ~rej8));
+}
+
+// The same with the edge signs as the flag byte f (bit 0: left edge has
+// w = -1, bit 1 right, bit 2 up, bit 3 down).
+template <bool kU16, class Heads>
+__device__ __forceinline__ uint32_t update_word_h(uint32_t s, uint32_t nl, uint32_t nr, uint32_t nu, uint32_t nd,
+                                                 uint32_t f, uint32_t i, const Heads& heads, int nq,
+                                                 uint32_t T4, uint32_t T8, const uint32_t* __restrict__ rk) {
+  return update_word_m<kU16>(s, nl, nr, nu, nd, 0u - (f & 1u), 0u - ((f >> 1) & 1u), 0u - ((f >> 2) & 1u),
+                             0u - ((f >> 3) & 1u), i, heads, nq, T4, T8, rk);
+}
+
+// All ones if byte b of x has its top bit set, else zero (prmt with sign
+// replication of one byte into all four)
+template <int b>
+__device__ __forceinline__ uint32_t byte_sign_mask(uint32_t x) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, 0, %2;" : "=r"(r) : "r"(x), "n"((8 + b) * 0x1111));
+  return r;
 }
 
 template <bool kU16>

@@ -23,6 +23,15 @@
 //   half-sweep, so the counters are usually complete long before anyone
 //   waits on them.
 //
+// * Fast path: when its records fit in shared memory, every item has two
+//   16-byte records with the shared addresses of its word and neighbours,
+//   its site index, edge signs and counter offsets, and every chunk a list of
+//   the completion counters it waits for (one per lane).  Chunks that touch
+//   no mirror row then cost two record loads, one acquire per lane and the
+//   word update; the others take the general path, which decodes the row
+//   and item tables.  A published row's mirror counter is released once per
+//   run of its items in a chunk, after a warp barrier.
+//
 // Every wait is bounded by a cycle limit.  A wait that runs out writes
 // ISING_ERR_TIMEOUT to the problem's status word and raises an abort flag that
 // ends all other waits at once; the kernel then returns without results.
@@ -57,14 +66,13 @@ struct FlowSmem {
   int32_t* seg_g;      // [kMaxSeg] group of each segment
   int4* rowc;          // [2][LR + 1][2] per colour and local row: see the table build
   int2* xtab;          // [NC*32] per item: see the table build
+  uint4* rec;          // [2][2][cap] per colour and item: the fast path's records (see their build)
+  uint32_t* ccnt;      // [2][cap / 32][32] per colour and chunk: the counters the chunk waits for
 };
 
-// items of the largest CTA, rounded up to whole chunks
-__host__ __device__ inline size_t flow_items_cap(int32_t LR, int32_t H) {
-  return (static_cast<size_t>(LR) * H + 31) / 32 * 32;
-}
-
-__host__ __device__ inline size_t flow_smem_layout(int32_t LR, int32_t H, size_t* off) {
+// cap: items (own site words per colour) of the largest CTA, rounded up to
+// whole chunks; rec: room for the fast path's item and chunk records
+__host__ __device__ inline size_t flow_smem_layout(int32_t LR, int32_t H, int32_t cap, int32_t rec, size_t* off) {
   size_t o = 0;
   off[0] = o; o += align16((static_cast<size_t>(2) * LR * H + 1) * 4);  // sp (+ spare word)
   off[1] = o; o += align16(static_cast<size_t>(2) * LR * H + 1);        // fl (+ spare byte)
@@ -73,13 +81,15 @@ __host__ __device__ inline size_t flow_smem_layout(int32_t LR, int32_t H, size_t
   off[4] = o; o += static_cast<size_t>(kFlowWarps) * kMaxSeg * (8 * 16 + 8);   // whead, wthr
   off[5] = o; o += 16 * 4;                                               // meta + seg_g
   off[6] = o; o += static_cast<size_t>(2) * (LR + 1) * 2 * 16;          // rowc
-  off[7] = o; o += flow_items_cap(LR, H) * 8;                           // xtab
+  off[7] = o; o += static_cast<size_t>(cap) * 8;                        // xtab
+  off[8] = o; o += rec ? static_cast<size_t>(2) * 2 * cap * 16 : 0;     // item records
+  off[9] = o; o += rec ? static_cast<size_t>(2) * cap * 4 : 0;          // chunk counter records
   return o;
 }
 
-__device__ __forceinline__ FlowSmem flow_carve(unsigned char* smem, int32_t LR, int32_t H) {
-  size_t off[8];
-  flow_smem_layout(LR, H, off);
+__device__ __forceinline__ FlowSmem flow_carve(unsigned char* smem, int32_t LR, int32_t H, int32_t cap, int32_t rec) {
+  size_t off[10];
+  flow_smem_layout(LR, H, cap, rec, off);
   FlowSmem s;
   s.sp = reinterpret_cast<uint32_t*>(smem + off[0]);
   s.fl = smem + off[1];
@@ -104,6 +114,8 @@ __device__ __forceinline__ FlowSmem flow_carve(unsigned char* smem, int32_t LR, 
   s.seg_g = s.meta + 8;
   s.rowc = reinterpret_cast<int4*>(smem + off[6]);
   s.xtab = reinterpret_cast<int2*>(smem + off[7]);
+  s.rec = reinterpret_cast<uint4*>(smem + off[8]);
+  s.ccnt = reinterpret_cast<uint32_t*>(smem + off[9]);
   return s;
 }
 
@@ -167,7 +179,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   const int j = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int H = a.H, Y = a.Y;
-  const FlowSmem sm = flow_carve(smem, a.LRmax, H);
+  const FlowSmem sm = flow_carve(smem, a.LRmax, H, a.cap, a.use_rec);
   const int w0 = a.split[j], w1 = a.split[j + 1];   // own words: stacked row * H + h in [w0, w1)
 
   // ---- local row tables (one thread; at most a few dozen rows)
@@ -366,12 +378,85 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   }
   __syncthreads();
 
+  // ---- records of the fast path (when they fit in shared memory).  Per
+  // colour c and item e, two uint4 with everything the item's update reads,
+  // decoded once from the row and item tables:
+  //   R0 = {shared byte address of the word, of its left, right and upper
+  //         neighbours (colour 1-c)},
+  //   R1 = {address of the lower neighbour, site index i, the edge signs as
+  //         bytes (0x80: w = -1) left, right, up, down,
+  //         run | mirror << 8 | segment << 9 | blocks << 11 | byte offset of
+  //         the own row's colour-c counter << 16},
+  // where run is the item's increment of that counter (see the item table)
+  // and mirror marks rows that exchange words with another CTA through the
+  // global mirror (their chunks take the general path).  Per colour and
+  // chunk, 32 counter addresses: the colour-(1-c) counters of every row the
+  // chunk's items read (own, above, below), then the idle row's saturated
+  // counter; ~0 when they are more than 32 (the chunk then takes the general
+  // path).
+  const uint32_t cap = static_cast<uint32_t>(a.cap);
+  const uint32_t sp32 = smem_addr(sm.sp), cnt32 = smem_addr(sm.rowcnt);
+  if (a.use_rec) {
+    for (int idx = tid; idx < 2 * NC * 32; idx += kFlowThreads) {
+      const int c = idx / (NC * 32), e = idx - c * NC * 32;
+      const int2 it = sm.xtab[e];
+      const uint32_t lr = static_cast<uint32_t>(it.x) & 0xFFFFu, h = static_cast<uint32_t>(it.x) >> 16;
+      const int4 A = sm.rowc[2 * (c * NR + lr)], B = sm.rowc[2 * (c * NR + lr) + 1];
+      const uint32_t par = (static_cast<uint32_t>(A.z) >> 16) & 1u;
+      const uint32_t own = (static_cast<uint32_t>(B.w) & 0xFFFFu) + h;
+      const uint32_t nbr = static_cast<uint32_t>(B.w) >> 16;
+      const uint32_t hl = h + par == 0u ? static_cast<uint32_t>(H) - 1u : h + par - 1u;
+      const uint32_t hr = h + par == static_cast<uint32_t>(H) ? 0u : h + par;
+      const uint32_t f = sm.fl[own];
+      const uint32_t fb = ((f & 1u) << 7) | ((f & 2u) << 14) | ((f & 4u) << 21) | ((f & 8u) << 28);
+      const uint32_t mir = (B.x >= 0 || B.y >= 0 || B.z >= 0) ? 1u : 0u;
+      const uint32_t seg = (static_cast<uint32_t>(A.z) & 0xFFu) >> 3, nq = (static_cast<uint32_t>(A.z) >> 8) & 0xFFu;
+      const uint32_t slot = static_cast<uint32_t>(c) * cap + static_cast<uint32_t>(e);
+      sm.rec[slot] = make_uint4(sp32 + 4u * own, sp32 + 4u * (nbr + hl), sp32 + 4u * (nbr + hr),
+                                sp32 + 4u * ((static_cast<uint32_t>(A.x) & 0xFFFFu) + h));
+      sm.rec[2 * cap + slot] = make_uint4(sp32 + 4u * ((static_cast<uint32_t>(A.x) >> 16) + h),
+                                          static_cast<uint32_t>(A.y) + 2u * h, fb,
+                                          static_cast<uint32_t>(it.y) | (mir << 8) | (seg << 9) | (nq << 11) |
+                                              ((4u * (static_cast<uint32_t>(c * NR) + lr)) << 16));
+    }
+    for (int idx = tid; idx < 2 * NC; idx += kFlowThreads) {
+      const int c = idx / NC, kc = idx - c * NC;
+      const uint32_t base = static_cast<uint32_t>((1 - c) * NR);
+      uint32_t list[32];
+      int nl = 0;
+      bool over = false;
+      int prev = -1;
+      for (int l = 0; l < 32; ++l) {
+        const int lr = sm.xtab[kc * 32 + l].x & 0xFFFF;
+        if (lr == prev) continue;
+        prev = lr;
+        const int4 A = sm.rowc[2 * (c * NR + lr)];
+        const uint32_t rows[3] = {static_cast<uint32_t>(lr), static_cast<uint32_t>(A.w) & 0xFFFFu,
+                                  static_cast<uint32_t>(A.w) >> 16};
+        for (int q = 0; q < 3; ++q) {
+          const uint32_t ci = base + rows[q];
+          bool seen = false;
+          for (int t = 0; t < nl; ++t) seen = seen || list[t] == ci;
+          if (seen) continue;
+          if (nl < 32) list[nl++] = ci;
+          else over = true;
+        }
+      }
+      uint32_t* out = sm.ccnt + (static_cast<size_t>(c) * (cap >> 5) + kc) * 32;
+      for (int l = 0; l < 32; ++l)
+        out[l] = (over && l == 31) ? 0xFFFFFFFFu : cnt32 + 4u * (l < nl ? list[l] : base + static_cast<uint32_t>(nloc));
+    }
+  }
+  __syncthreads();
+
   // ---- the half-sweeps, chunk by chunk
   const long long M = 2LL * a.S * NC;
   uint4* wh = sm.whead + warp * (kMaxSeg * 8);
   uint2* wt = sm.wthr + warp * kMaxSeg;
-  const uint32_t sp32 = smem_addr(sm.sp), fl32 = smem_addr(sm.fl), cnt32 = smem_addr(sm.rowcnt);
+  const uint32_t fl32 = smem_addr(sm.fl);
   const uint32_t rowc32 = smem_addr(sm.rowc), xt32 = smem_addr(sm.xtab) + 8u * lane, wh32 = smem_addr(wh);
+  const uint32_t rec32 = smem_addr(sm.rec) + 16u * lane, rstride = 32u * cap;
+  const uint32_t cc32 = smem_addr(sm.ccnt) + 4u * lane;
   int head_kk = -1;
   uint32_t T4 = 0, T8 = 0;
   int hs = 0, k = warp;
@@ -397,80 +482,102 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       head_kk = kk;
     }
     const uint32_t need = static_cast<uint32_t>(H) * static_cast<uint32_t>(kk + c);
-    const int2 it = lds_v2(xt32 + 256u * static_cast<uint32_t>(k));
-    const uint32_t lr = static_cast<uint32_t>(it.x) & 0xFFFFu, h = static_cast<uint32_t>(it.x) >> 16;
-    const uint32_t rrec = rowc32 + 32u * (static_cast<uint32_t>(c * NR) + lr);
-    const int4 A = lds_v4(rrec), B = lds_v4(rrec + 16u);
-    const uint32_t rc = cnt32 + 4u * static_cast<uint32_t>((1 - c) * NR);
-    const uint32_t c_self = rc + 4u * lr, c_up = rc + 4u * (static_cast<uint32_t>(A.w) & 0xFFFFu),
-                   c_dn = rc + 4u * (static_cast<uint32_t>(A.w) >> 16);
-    // the three colour-(1-c) rows this item reads must have finished the
-    // previous half-sweep.  Rows of another CTA are read from the mirror
-    // (except in the very first half-sweep, which reads the halo slots), and
-    // this CTA's rows that another CTA reads are published to it; one vote
-    // sends the chunks that touch neither (most of them) down a path of
-    // shared-memory operations only.
-    const bool gu = B.x >= 0 && need > 0, gd = B.y >= 0 && need > 0;
-    const bool gs = ((A.z >> 17) & 1) && need > 0;
-    const bool mirror = __any_sync(0xFFFFFFFFu, gu || gd || B.z >= 0);
-    uint32_t v0, v1, v2;
-    if (!mirror) {
-      v0 = ld_acquire_cta(c_self);
-      v1 = ld_acquire_cta(c_up);
-      v2 = ld_acquire_cta(c_dn);
-    } else {
-      v0 = gs ? ld_acquire_gpu(a.gcnt + (B.z ^ 1)) : ld_acquire_cta(c_self);
-      v1 = gu ? ld_acquire_gpu(a.gcnt + B.x) : ld_acquire_cta(c_up);
-      v2 = gd ? ld_acquire_gpu(a.gcnt + B.y) : ld_acquire_cta(c_dn);
+    const uint32_t ck = static_cast<uint32_t>(c) * (cap >> 5) + static_cast<uint32_t>(k);
+    bool fast = false;
+    uint4 R1;
+    uint32_t caddr = 0;
+    if (a.use_rec) {
+      R1 = lds_v4u(rec32 + rstride + 512u * ck);
+      caddr = lds_u32(cc32 + 128u * ck);
+      fast = !__any_sync(0xFFFFFFFFu, ((R1.w >> 8) & 1u) || caddr == 0xFFFFFFFFu);
     }
-    const bool ready = v0 >= need && v1 >= need && v2 >= need;
-    // one vote for the chunk: the bounded per-lane waits run only when some
-    // lane is not ready yet (the usual case needs none)
-    if (!__all_sync(0xFFFFFFFFu, ready) || a.stall_test) {
-      bool lane_ok = true;
-      if (v0 < need)
-        lane_ok = gs ? wait_count<true>(a.gcnt + (B.z ^ 1), 0u, need, a) : wait_count<false>(nullptr, c_self, need, a);
-      if (lane_ok && v1 < need)
-        lane_ok = gu ? wait_count<true>(a.gcnt + B.x, 0u, need, a) : wait_count<false>(nullptr, c_up, need, a);
-      if (lane_ok && v2 < need)
-        lane_ok = gd ? wait_count<true>(a.gcnt + B.y, 0u, need, a) : wait_count<false>(nullptr, c_dn, need, a);
-      if (a.stall_test && j == 0 && m == 0) lane_ok = lane_ok && wait_count<false>(nullptr, c_self, 0xFFFFFFFFu, a);
-      if (!__all_sync(0xFFFFFFFFu, lane_ok)) break;
-    }
-    // the word, its left and right neighbours (the row's wrap at h = 0 / H - 1)
-    const uint32_t par = (static_cast<uint32_t>(A.z) >> 16) & 1u;
-    const uint32_t own = (static_cast<uint32_t>(B.w) & 0xFFFFu) + h;
-    const uint32_t nbr = static_cast<uint32_t>(B.w) >> 16;
-    const uint32_t hl = h + par == 0u ? static_cast<uint32_t>(H) - 1u : h + par - 1u;
-    const uint32_t hr = h + par == static_cast<uint32_t>(H) ? 0u : h + par;
-    const uint32_t a_up = sp32 + 4u * ((static_cast<uint32_t>(A.x) & 0xFFFFu) + h);
-    const uint32_t a_dn = sp32 + 4u * ((static_cast<uint32_t>(A.x) >> 16) + h);
-    uint32_t nl, nr, nu, nd;
-    if (!mirror) {
-      nl = lds_u32(sp32 + 4u * (nbr + hl));
-      nr = lds_u32(sp32 + 4u * (nbr + hr));
-      nu = lds_u32(a_up);
-      nd = lds_u32(a_dn);
+    if (fast) {
+      // ---- fast path: the chunk reads and writes this CTA's shared memory
+      // only; each lane acquires one of the counters the chunk waits for
+      const uint4 R0 = lds_v4u(rec32 + 512u * ck);
+      const uint32_t v = ld_acquire_cta(caddr);
+      if (!__all_sync(0xFFFFFFFFu, v >= need) || a.stall_test) {
+        bool lane_ok = v >= need || wait_count<false>(nullptr, caddr, need, a);
+        if (a.stall_test && j == 0 && m == 0) lane_ok = lane_ok && wait_count<false>(nullptr, caddr, 0xFFFFFFFFu, a);
+        if (!__all_sync(0xFFFFFFFFu, lane_ok)) break;
+      }
+      __syncwarp();   // every lane's reads after all lanes' acquires
+      const uint32_t misc = R1.w;
+      const uint32_t seg = (misc >> 9) & 3u;
+      uint2 tq = make_uint2(T4, T8);
+      if constexpr (kGroupThr) tq = wt[seg];
+      const uint32_t fb = R1.z;
+      const uint32_t ns = update_word_m<kU16>(lds_u32(R0.x), lds_u32(R0.y), lds_u32(R0.z), lds_u32(R0.w),
+                                              lds_u32(R1.x), byte_sign_mask<0>(fb), byte_sign_mask<1>(fb),
+                                              byte_sign_mask<2>(fb), byte_sign_mask<3>(fb), R1.y,
+                                              HeadsShared{wh32 + 128u * seg}, static_cast<int>((misc >> 11) & 15u),
+                                              tq.x, tq.y, a.rk);
+      sts_u32(R0.x, ns);
+      __syncwarp();
+      const uint32_t run = misc & 0xFFu;
+      if (run) red_release_cta(cnt32 + (misc >> 16), run);
     } else {
+      // ---- general path: some lane reads or publishes words of the global mirror
+      const int2 it = lds_v2(xt32 + 256u * static_cast<uint32_t>(k));
+      const uint32_t lr = static_cast<uint32_t>(it.x) & 0xFFFFu, h = static_cast<uint32_t>(it.x) >> 16;
+      const uint32_t rrec = rowc32 + 32u * (static_cast<uint32_t>(c * NR) + lr);
+      const int4 A = lds_v4(rrec), B = lds_v4(rrec + 16u);
+      const uint32_t rc = cnt32 + 4u * static_cast<uint32_t>((1 - c) * NR);
+      const uint32_t c_self = rc + 4u * lr, c_up = rc + 4u * (static_cast<uint32_t>(A.w) & 0xFFFFu),
+                     c_dn = rc + 4u * (static_cast<uint32_t>(A.w) >> 16);
+      // the three colour-(1-c) rows this item reads must have finished the
+      // previous half-sweep.  Rows of another CTA are read from the mirror
+      // (except in the very first half-sweep, which reads the halo slots),
+      // and this CTA's rows that another CTA reads are published to it.
+      const bool gu = B.x >= 0 && need > 0, gd = B.y >= 0 && need > 0;
+      const bool gs = ((A.z >> 17) & 1) && need > 0;
+      const uint32_t v0 = gs ? ld_acquire_gpu(a.gcnt + (B.z ^ 1)) : ld_acquire_cta(c_self);
+      const uint32_t v1 = gu ? ld_acquire_gpu(a.gcnt + B.x) : ld_acquire_cta(c_up);
+      const uint32_t v2 = gd ? ld_acquire_gpu(a.gcnt + B.y) : ld_acquire_cta(c_dn);
+      const bool ready = v0 >= need && v1 >= need && v2 >= need;
+      // one vote for the chunk: the bounded per-lane waits run only when some
+      // lane is not ready yet (the usual case needs none)
+      if (!__all_sync(0xFFFFFFFFu, ready) || a.stall_test) {
+        bool lane_ok = true;
+        if (v0 < need)
+          lane_ok = gs ? wait_count<true>(a.gcnt + (B.z ^ 1), 0u, need, a) : wait_count<false>(nullptr, c_self, need, a);
+        if (lane_ok && v1 < need)
+          lane_ok = gu ? wait_count<true>(a.gcnt + B.x, 0u, need, a) : wait_count<false>(nullptr, c_up, need, a);
+        if (lane_ok && v2 < need)
+          lane_ok = gd ? wait_count<true>(a.gcnt + B.y, 0u, need, a) : wait_count<false>(nullptr, c_dn, need, a);
+        if (a.stall_test && j == 0 && m == 0) lane_ok = lane_ok && wait_count<false>(nullptr, c_self, 0xFFFFFFFFu, a);
+        if (!__all_sync(0xFFFFFFFFu, lane_ok)) break;
+      }
+      // the word, its left and right neighbours (the row's wrap at h = 0 / H - 1)
+      const uint32_t par = (static_cast<uint32_t>(A.z) >> 16) & 1u;
+      const uint32_t own = (static_cast<uint32_t>(B.w) & 0xFFFFu) + h;
+      const uint32_t nbr = static_cast<uint32_t>(B.w) >> 16;
+      const uint32_t hl = h + par == 0u ? static_cast<uint32_t>(H) - 1u : h + par - 1u;
+      const uint32_t hr = h + par == static_cast<uint32_t>(H) ? 0u : h + par;
       const uint32_t* gself = a.gm + static_cast<size_t>(B.z ^ 1) * H;
-      nl = gs ? __ldcg(gself + hl) : lds_u32(sp32 + 4u * (nbr + hl));
-      nr = gs ? __ldcg(gself + hr) : lds_u32(sp32 + 4u * (nbr + hr));
-      nu = gu ? __ldcg(a.gm + static_cast<size_t>(B.x) * H + h) : lds_u32(a_up);
-      nd = gd ? __ldcg(a.gm + static_cast<size_t>(B.y) * H + h) : lds_u32(a_dn);
+      const uint32_t nl = gs ? __ldcg(gself + hl) : lds_u32(sp32 + 4u * (nbr + hl));
+      const uint32_t nr = gs ? __ldcg(gself + hr) : lds_u32(sp32 + 4u * (nbr + hr));
+      const uint32_t nu = gu ? __ldcg(a.gm + static_cast<size_t>(B.x) * H + h)
+                             : lds_u32(sp32 + 4u * ((static_cast<uint32_t>(A.x) & 0xFFFFu) + h));
+      const uint32_t nd = gd ? __ldcg(a.gm + static_cast<size_t>(B.y) * H + h)
+                             : lds_u32(sp32 + 4u * ((static_cast<uint32_t>(A.x) >> 16) + h));
+      uint2 tq = make_uint2(T4, T8);
+      if constexpr (kGroupThr) tq = wt[(A.z & 0xFF) >> 3];
+      const uint32_t ns = update_word_h<kU16>(lds_u32(sp32 + 4u * own), nl, nr, nu, nd, lds_u8(fl32 + own),
+                                              static_cast<uint32_t>(A.y) + 2u * h,
+                                              HeadsShared{wh32 + 16u * (static_cast<uint32_t>(A.z) & 0xFFu)},
+                                              (A.z >> 8) & 0xFF, tq.x, tq.y, a.rk);
+      sts_u32(sp32 + 4u * own, ns);
+      if (B.z >= 0) __stcg(a.gm + static_cast<size_t>(B.z) * H + h, ns);   // published row: its mirror word
+      __syncwarp();
+      // the last lane of each run of one row's items counts the run, in the
+      // CTA's counter and, for a published row, at GPU scope in the mirror's
+      // (the warp barrier orders the other lanes' stores before the release)
+      if (it.y) {
+        red_release_cta(cnt32 + 4u * (static_cast<uint32_t>(c * NR) + lr), static_cast<uint32_t>(it.y));
+        if (B.z >= 0) red_release_gpu(a.gcnt + B.z, static_cast<uint32_t>(it.y));
+      }
     }
-    uint2 tq = make_uint2(T4, T8);
-    if constexpr (kGroupThr) tq = wt[(A.z & 0xFF) >> 3];
-    const uint32_t ns = update_word_h<kU16>(lds_u32(sp32 + 4u * own), nl, nr, nu, nd, lds_u8(fl32 + own),
-                                            static_cast<uint32_t>(A.y) + 2u * h,
-                                            HeadsShared{wh32 + 16u * (static_cast<uint32_t>(A.z) & 0xFFu)},
-                                            (A.z >> 8) & 0xFF, tq.x, tq.y, a.rk);
-    sts_u32(sp32 + 4u * own, ns);
-    if (mirror && B.z >= 0) {   // published row: mirror word, then count it at GPU scope
-      __stcg(a.gm + static_cast<size_t>(B.z) * H + h, ns);
-      red_release_gpu(a.gcnt + B.z, 1u);
-    }
-    __syncwarp();
-    if (it.y) red_release_cta(cnt32 + 4u * (static_cast<uint32_t>(c * NR) + lr), static_cast<uint32_t>(it.y));
     k += kFlowWarps;
     while (k >= NC) { k -= NC; ++hs; }
   }
@@ -582,9 +689,9 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
 
 }  // namespace
 
-size_t flow_smem_bytes(int32_t LR, int32_t H) {
-  size_t off[8];
-  return flow_smem_layout(LR, H, off);
+size_t flow_smem_bytes(int32_t LR, int32_t H, int32_t cap, int32_t rec) {
+  size_t off[10];
+  return flow_smem_layout(LR, H, cap, rec, off);
 }
 
 int flow_threads() { return kFlowThreads; }
@@ -592,7 +699,7 @@ int flow_max_segments() { return kMaxSeg; }
 
 template <bool kU16, bool kGroupThr>
 cudaError_t launch_flow_mode(const FlowArgs& a, cudaStream_t stream) {
-  const size_t smem = flow_smem_bytes(a.LRmax, a.H);
+  const size_t smem = flow_smem_bytes(a.LRmax, a.H, a.cap, a.use_rec);
   cudaError_t e = cudaFuncSetAttribute(anneal_flow_kernel<kU16, kGroupThr>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;

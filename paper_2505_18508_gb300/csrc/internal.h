@@ -99,8 +99,10 @@ struct FlowArgs {
   int32_t stall_test;       // 1: the first chunk of CTA 0 waits for a count nothing reaches
   int32_t u16;              // 1: 16-bit draw mode
   int32_t thr_group_stride; // 0: one table for all groups; else group g's table at thr + g * stride
+  int32_t cap;              // own site words per colour of the largest CTA, rounded up to a multiple of 32
+  int32_t use_rec;          // 1: the fast path's records fit in shared memory
 };
-size_t flow_smem_bytes(int32_t LR, int32_t H);
+size_t flow_smem_bytes(int32_t LR, int32_t H, int32_t cap, int32_t rec);
 int flow_threads();
 int flow_max_segments();
 cudaError_t launch_flow(const FlowArgs& a, cudaStream_t stream);
