@@ -203,3 +203,83 @@ def propose_global(spins, logits, w_right, w_down):
             s[b] = cand
             acc[b] = 1
     return s.reshape(s.shape[0], -1), acc
+
+
+# ---------------------------------------------------------------- clusters
+def _energy_grid(s, w_right, w_down):
+    """H = sum over the 2n torus edges of w_ij s_i s_j (Eq. 2 with J = -w, h = 0)."""
+    t = np.asarray(s, dtype=np.int64)
+    return int((w_right * t * np.roll(t, -1, axis=1)).sum() + (w_down * t * np.roll(t, -1, axis=0)).sum())
+
+
+def torus_components(mask):
+    """Connected components of the True sites of mask [Y, X] under 4-neighbour
+    adjacency on the torus: a list of lists of (y, x), found by breadth-first
+    search from each unvisited site in increasing index order."""
+    Y, X = mask.shape
+    seen = np.zeros_like(mask, dtype=bool)
+    comps = []
+    for y0 in range(Y):
+        for x0 in range(X):
+            if not mask[y0, x0] or seen[y0, x0]:
+                continue
+            comp, queue = [], [(y0, x0)]
+            seen[y0, x0] = True
+            while queue:
+                y, x = queue.pop()
+                comp.append((y, x))
+                for yy, xx in ((y, (x + 1) % X), (y, (x - 1) % X), ((y + 1) % Y, x), ((y - 1) % Y, x)):
+                    if mask[yy, xx] and not seen[yy, xx]:
+                        seen[yy, xx] = True
+                        queue.append((yy, xx))
+            comps.append(comp)
+    return comps
+
+
+def component_dE(s_grid, comp, w_right, w_down):
+    """Energy change of flipping the sites of one component, as the
+    difference of the whole-lattice energies (the definition)."""
+    t = np.array(s_grid, dtype=np.int8)
+    e0 = _energy_grid(t, w_right, w_down)
+    for y, x in comp:
+        t[y, x] = -t[y, x]
+    return _energy_grid(t, w_right, w_down) - e0
+
+
+def droplet_targets(spins, reference, w_right, w_down):
+    """Training targets of the cluster form of the learned stage (a reading of
+    the block-flip proposals, not in the paper): with r' = +-r gauge-aligned
+    to s (as flip_targets), the sites where s and r' differ split into
+    connected components on the torus; y_i = 1 iff i lies in a component whose
+    flip alone lowers the energy of s (dE < 0).  Such a component is an exact
+    multi-spin move from s towards the better state.  uint8 [B, n]."""
+    Y, X = w_right.shape
+    d = flip_targets(spins, reference).reshape(-1, Y, X).astype(bool)
+    s = np.asarray(spins, dtype=np.int8).reshape(-1, Y, X)
+    out = np.zeros(d.shape, dtype=np.uint8)
+    for b in range(d.shape[0]):
+        for comp in torus_components(d[b]):
+            if component_dE(s[b], comp, w_right, w_down) < 0:
+                for y, x in comp:
+                    out[b, y, x] = 1
+    return out.reshape(d.shape[0], -1)
+
+
+def propose_clusters(spins, logits, w_right, w_down):
+    """Cluster proposals: every connected component of the sites with logit > 0
+    is flipped iff its flip alone does not raise the energy (dE <= 0).
+    Components are never adjacent, so their flips are independent and the
+    accepted ones can be applied together.  Returns (new spins [B, n],
+    accepted components [B])."""
+    Y, X = w_right.shape
+    s = np.array(spins, dtype=np.int8).reshape(-1, Y, X).copy()
+    z = np.asarray(logits).reshape(-1, Y, X)
+    acc = np.zeros(s.shape[0], dtype=np.int64)
+    for b in range(s.shape[0]):
+        base = s[b].copy()
+        for comp in torus_components(z[b] > 0):
+            if component_dE(base, comp, w_right, w_down) <= 0:
+                for y, x in comp:
+                    s[b, y, x] = -s[b, y, x]
+                acc[b] += 1
+    return s.reshape(s.shape[0], -1), acc

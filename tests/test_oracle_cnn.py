@@ -170,3 +170,78 @@ def test_global_proposal_is_exact():
         take = _energy(inst, cand) <= _energy(inst, s[b])
         np.testing.assert_array_equal(new[b], cand if take else s[b])
         assert acc[b] == int(take)
+
+
+# ---------------------------------------------------------------- clusters
+def _grid_instance(X, Y, seed):
+    inst = synth.torus_instance(X, Y, seed)
+    return inst, inst["w_right"], inst["w_down"]
+
+
+def test_torus_components_hand_built():
+    m = np.zeros((4, 6), dtype=bool)
+    m[0, 0] = m[0, 5] = True          # joined across the left/right wrap
+    m[3, 0] = True                    # joined to (0, 0) across the top/bottom wrap
+    m[2, 2] = m[2, 3] = True          # a separate pair
+    m[1, 4] = True                    # diagonal to nothing, alone
+    comps = sorted(sorted(c) for c in cnn.torus_components(m))
+    assert comps == [[(0, 0), (0, 5), (3, 0)], [(1, 4)], [(2, 2), (2, 3)]]
+
+
+def test_component_energy_changes_add_up_to_the_state_difference():
+    """Components of the disagreement set are never adjacent, so their flip
+    energies add up exactly to E(r') - E(s) (flipping all of them turns s into
+    r'); and the targets are gauge invariant."""
+    X, Y = 12, 8
+    inst, wr, wd = _grid_instance(X, Y, 5)
+    rng = np.random.default_rng(3)
+    for trial in range(6):
+        s = synth.random_spins(1, X * Y, 10 + trial)
+        r = s.copy()
+        flip = rng.random(X * Y) < 0.3
+        r[0, flip] = -r[0, flip]
+        d = cnn.flip_targets(s, r).reshape(Y, X).astype(bool)
+        sg = s.reshape(Y, X)
+        total = sum(cnn.component_dE(sg, c, wr, wd) for c in cnn.torus_components(d))
+        rp = np.where(d, -sg, sg)
+        assert total == cnn._energy_grid(rp, wr, wd) - cnn._energy_grid(sg, wr, wd)
+        # Eq. 2 on the CSR gives the same energies
+        assert cnn._energy_grid(sg, wr, wd) == oracle.energy_csr(inst, s[0])
+        y = cnn.droplet_targets(s, r, wr, wd)
+        np.testing.assert_array_equal(y, cnn.droplet_targets(s, -r, wr, wd))
+        # flipping exactly the target sites lowers the energy by the sum of
+        # the improving components' changes, each negative
+        imp = [cnn.component_dE(sg, c, wr, wd) for c in cnn.torus_components(d)]
+        after = np.where(y.reshape(Y, X).astype(bool), -sg, sg)
+        assert cnn._energy_grid(after, wr, wd) - cnn._energy_grid(sg, wr, wd) == sum(v for v in imp if v < 0)
+    assert (cnn.droplet_targets(s, s, wr, wd) == 0).all() and (cnn.droplet_targets(s, -s, wr, wd) == 0).all()
+
+
+def test_single_site_droplet_is_a_metropolis_move():
+    """A one-site component lowers the energy iff its single-spin flip has
+    dE = -2 s_i sum_j w_ij s_j < 0 (the sweep's own energy change)."""
+    X, Y = 6, 4
+    inst, wr, wd = _grid_instance(X, Y, 9)
+    s = synth.random_spins(1, X * Y, 4)
+    sg = s.reshape(Y, X).astype(np.int64)
+    for i in range(X * Y):
+        y, x = divmod(i, X)
+        f = (wr[y, x] * sg[y, (x + 1) % X] + wr[y, (x - 1) % X] * sg[y, (x - 1) % X]
+             + wd[y, x] * sg[(y + 1) % Y, x] + wd[(y - 1) % Y, x] * sg[(y - 1) % Y, x])
+        assert cnn.component_dE(sg, [(y, x)], wr, wd) == -2 * sg[y, x] * f
+
+
+def test_cluster_proposals_never_raise_the_energy():
+    X, Y = 10, 6
+    inst, wr, wd = _grid_instance(X, Y, 11)
+    s = synth.random_spins(5, X * Y, 21)
+    z = np.random.default_rng(2).normal(size=(5, X * Y))
+    new, acc = cnn.propose_clusters(s, z, wr, wd)
+    for b in range(5):
+        sg, ng = s[b].reshape(Y, X), new[b].reshape(Y, X)
+        comps = cnn.torus_components(z[b].reshape(Y, X) > 0)
+        gains = [cnn.component_dE(sg, c, wr, wd) for c in comps]
+        assert acc[b] == sum(g <= 0 for g in gains)
+        assert cnn._energy_grid(ng, wr, wd) - cnn._energy_grid(sg, wr, wd) == sum(g for g in gains if g <= 0)
+        changed = (sg != ng)
+        assert not (changed & (z[b].reshape(Y, X) <= 0)).any()      # only proposed sites move
