@@ -570,6 +570,39 @@ int ising_propose(const ising_problem* p, int8_t* spins, int32_t B, const float*
                   int32_t* accepted, void* cuda_stream);
 
 /*
+ * ising_propose_clusters -- block flips built from connected components
+ * (this project's learned stage; the paper's own update rule is unpublished,
+ * Section III).  For each configuration, the sites with logit > 0 split into
+ * connected components under 4-neighbour adjacency on the torus (periodic
+ * wrap included); components are never adjacent, so flipping component C
+ * changes Eq. 2's energy by its own boundary terms,
+ * dE_C = -2 sum_{i in C, j ~ i, j not in C} w_ij s_i s_j, and every component
+ * with dE_C <= 0 is flipped.  The energy never rises.
+ * probs    m >= 1 torus problems of one shape (m <= 16); configuration
+ *          q * B + b belongs to probs[q].
+ * spins    device [m * B][n] int8, updated in place.
+ * logits   device [m * B][n] float.
+ * accepted device [m * B] int32 or NULL: components flipped per configuration.
+ * One CTA per configuration with all of its state in shared memory (9 bytes
+ * per site): ISING_ERR_UNSUPPORTED above that (about 25,000 sites) and for
+ * general-graph handles; ISING_ERR_ARG for mixed shapes or bad pointers.
+ */
+int ising_propose_clusters(const ising_problem* const* probs, int32_t m, int8_t* spins, int32_t B,
+                           const float* logits, int32_t* accepted, void* cuda_stream);
+
+/*
+ * ising_droplet_targets -- training targets of the cluster proposals: with
+ * r' = ref or -ref gauge-aligned to s (as ising_flip_targets), the sites
+ * where s and r' differ split into connected components on the torus;
+ * targets_i = 1 iff i lies in a component whose flip alone lowers the energy
+ * of s (dE_C < 0, dE_C as above), an exact energy-lowering move from s
+ * towards r'.  spins, ref: device [B][n] int8; targets: device [B][n] uint8.
+ * Limits and errors as ising_propose_clusters.
+ */
+int ising_droplet_targets(const ising_problem* p, const int8_t* spins, const int8_t* ref, int32_t B,
+                          uint8_t* targets, void* cuda_stream);
+
+/*
  * ising_flip_targets -- training targets for the network: for each of B
  * configurations, y_i = [s_i != r'_i] where r' is ref or -ref, whichever is
  * closer to s in Hamming distance (on a tie, the one that keeps site 0); the

@@ -540,6 +540,44 @@ def propose(prob, spins, logits, tile, accepted=None, stream=None):
     return accepted
 
 
+def propose_clusters(probs, spins, logits, accepted=None, stream=None):
+    """Cluster block flips in place (ising_propose_clusters).  probs: one
+    Problem, or a list of m Problems of one shape whose configurations are
+    stacked in spins [m * B, n]; returns accepted components [m * B]."""
+    torch = _torch()
+    probs = list(probs) if isinstance(probs, (list, tuple)) else [probs]
+    rows = _rows(spins, "spins")
+    m = len(probs)
+    if rows % m:
+        raise ValueError("spins rows must be a multiple of the number of problems")
+    n = probs[0].n
+    spins = _device_tensor(spins, torch.int8, (rows, n), "spins", write=True)
+    logits = _device_tensor(logits, torch.float32, (rows, n), "logits")
+    if accepted is None:
+        accepted = torch.zeros(rows, dtype=torch.int32, device=spins.device)
+    else:
+        accepted = _device_tensor(accepted, torch.int32, (rows,), "accepted", write=True)
+    handles = (ctypes.c_void_p * m)(*[p.handle for p in probs])
+    check(lib().ising_propose_clusters(handles, int(m), _dptr(spins), int(rows // m), _dptr(logits),
+                                       _dptr(accepted), _stream_ptr(stream)), "ising_propose_clusters")
+    return accepted
+
+
+def droplet_targets(prob, spins, ref, out=None, stream=None):
+    """Droplet training targets (ising_droplet_targets): uint8 [B, n]."""
+    torch = _torch()
+    B = _rows(spins, "spins")
+    spins = _device_tensor(spins, torch.int8, (B, prob.n), "spins")
+    ref = _device_tensor(ref, torch.int8, (B, prob.n), "ref")
+    if out is None:
+        out = torch.empty((B, prob.n), dtype=torch.uint8, device=spins.device)
+    else:
+        out = _device_tensor(out, torch.uint8, (B, prob.n), "out", write=True)
+    check(lib().ising_droplet_targets(prob.handle, _dptr(spins), _dptr(ref), int(B), _dptr(out), _stream_ptr(stream)),
+          "ising_droplet_targets")
+    return out
+
+
 def flip_targets(spins, ref, out=None, stream=None):
     """Gauge-aligned flip targets (ising_flip_targets): uint8 [B, n]."""
     torch = _torch()

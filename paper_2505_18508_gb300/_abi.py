@@ -76,6 +76,8 @@ _SIGNATURES = {
                                            ctypes.c_float, _vp]),
     "ising_propose": (ctypes.c_int, [_vp, _vp, _i32, _vp, _i32, _vp, _vp]),
     "ising_flip_targets": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
+    "ising_propose_clusters": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _vp, _vp]),
+    "ising_droplet_targets": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp]),
     "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 

@@ -1,0 +1,118 @@
+"""Cluster moves (ising_propose_clusters, ising_droplet_targets) against the
+CPU oracle, bit for bit: components of the logit > 0 sites flipped iff
+dE <= 0, and droplet targets (improving components of the disagreement with
+a gauge-aligned better state), on ragged and full-size tori, stacked
+problems, and the degenerate masks (empty, everything, a tie in the gauge)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import cnn as ocnn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ia():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2505_18508_gb300 as ia
+    torch.cuda.set_device(0)
+    return ia
+
+
+def _flipped(s, frac, seed):
+    r = s.copy()
+    m = np.random.default_rng(seed).random(s.shape) < frac
+    r[m] = -r[m]
+    return r
+
+
+@pytest.mark.parametrize("X,Y,B", [(12, 8, 4), (20, 10, 3), (34, 6, 2), (50, 50, 2), (200, 100, 1)])
+def test_droplet_targets_match_oracle(ia, X, Y, B):
+    import torch
+    inst = synth.torus_instance(X, Y, 70 + X)
+    prob = ia.Problem.from_instance(inst)
+    s = synth.random_spins(B, X * Y, 3 + X)
+    for frac in (0.05, 0.3, 0.55):
+        r = _flipped(s, frac, int(frac * 100) + X)
+        got = ia.droplet_targets(prob, torch.from_numpy(s).cuda(), torch.from_numpy(r).cuda())
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(got.cpu().numpy(), ocnn.droplet_targets(s, r, inst["w_right"], inst["w_down"]))
+    prob.destroy()
+
+
+def test_droplet_targets_on_annealed_states_and_ties(ia):
+    import torch
+    X, Y, T = 24, 12, 16
+    inst = synth.torus_instance(X, Y, 5)
+    prob = ia.Problem.from_instance(inst)
+    s, c = ia.anneal(prob, T, synth.linear_betas(0.1, 3.0, 300), 9)
+    best = s[int(c.argmax().item())].expand(T, -1).contiguous()
+    got = ia.droplet_targets(prob, s, best)
+    torch.cuda.synchronize()
+    sn, bn = s.cpu().numpy(), best.cpu().numpy()
+    ref = ocnn.droplet_targets(sn, bn, inst["w_right"], inst["w_down"])
+    np.testing.assert_array_equal(got.cpu().numpy(), ref)
+    # an exact gauge tie (n/2 sites differ) with site 0 equal and different
+    n = X * Y
+    s2 = synth.random_spins(2, n, 1)
+    r2 = s2.copy()
+    idx = np.arange(1, n // 2 + 1)
+    r2[0, idx] = -r2[0, idx]                 # site 0 equal
+    r2[1, :n // 2] = -r2[1, :n // 2]         # site 0 different
+    got = ia.droplet_targets(prob, torch.from_numpy(s2).cuda(), torch.from_numpy(r2).cuda())
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(got.cpu().numpy(), ocnn.droplet_targets(s2, r2, inst["w_right"], inst["w_down"]))
+    prob.destroy()
+
+
+@pytest.mark.parametrize("X,Y,B", [(12, 8, 4), (20, 10, 3), (50, 50, 2), (200, 100, 1)])
+def test_cluster_proposals_match_oracle(ia, X, Y, B):
+    import torch
+    inst = synth.torus_instance(X, Y, 90 + X)
+    prob = ia.Problem.from_instance(inst)
+    s = synth.random_spins(B, X * Y, 11 + X)
+    rng = np.random.default_rng(X)
+    for bias in (-1.0, 0.0, 0.6):
+        z = (rng.normal(size=(B, X * Y)) + bias).astype(np.float32)
+        sd = torch.from_numpy(s).cuda()
+        acc = ia.propose_clusters(prob, sd, torch.from_numpy(z).cuda())
+        torch.cuda.synchronize()
+        rs, racc = ocnn.propose_clusters(s, z, inst["w_right"], inst["w_down"])
+        np.testing.assert_array_equal(sd.cpu().numpy(), rs)
+        np.testing.assert_array_equal(acc.cpu().numpy(), racc)
+    prob.destroy()
+
+
+def test_cluster_proposals_stacked_problems_and_degenerate_masks(ia):
+    import torch
+    X, Y, B = 16, 10, 3
+    insts = [synth.torus_instance(X, Y, 200 + q) for q in range(3)]
+    probs = [ia.Problem.from_instance(i) for i in insts]
+    s = synth.random_spins(3 * B, X * Y, 5)
+    z = np.random.default_rng(1).normal(size=(3 * B, X * Y)).astype(np.float32)
+    z[0] = -1.0                              # nothing proposed
+    z[1] = 1.0                               # the whole torus: one component with no boundary, dE = 0
+    sd = torch.from_numpy(s).cuda()
+    acc = ia.propose_clusters(probs, sd, torch.from_numpy(z).cuda())
+    torch.cuda.synchronize()
+    got = sd.cpu().numpy()
+    for q, inst in enumerate(insts):
+        rs, racc = ocnn.propose_clusters(s[q * B:(q + 1) * B], z[q * B:(q + 1) * B], inst["w_right"], inst["w_down"])
+        np.testing.assert_array_equal(got[q * B:(q + 1) * B], rs)
+        np.testing.assert_array_equal(acc.cpu().numpy()[q * B:(q + 1) * B], racc)
+    assert (got[0] == s[0]).all() and (got[1] == -s[1]).all()
+    # limits: mixed shapes and an instance too large for one CTA's shared memory
+    other = ia.Problem.from_instance(synth.torus_instance(X + 2, Y, 1))
+    with pytest.raises(ia.IsingError):
+        ia.propose_clusters([probs[0], other], torch.zeros((2, X * Y), dtype=torch.int8, device="cuda"),
+                            torch.zeros((2, X * Y), device="cuda"))
+    big = ia.Problem.from_instance(synth.torus_instance(200, 200, 1))
+    with pytest.raises(ia.IsingError) as e:
+        ia.propose_clusters(big, torch.zeros((1, 40000), dtype=torch.int8, device="cuda"),
+                            torch.zeros((1, 40000), device="cuda"))
+    assert e.value.code == -8
+    for p in probs + [other, big]:
+        p.destroy()
