@@ -603,6 +603,50 @@ int ising_droplet_targets(const ising_problem* p, const int8_t* spins, const int
                           uint8_t* targets, void* cuda_stream);
 
 /*
+ * ising_learned_create / _launch / _destroy -- the learned form of the
+ * annealer for m torus problems of one shape (this project's extension; the
+ * paper's own update rule is unpublished, Section III), prepared once and
+ * replayed as one CUDA graph: no host round trip between its steps.
+ *   1. sweeps [0, k_first) of the schedule from the Philox start, all
+ *      problems in one persistent batched launch (k_first = 0: the start);
+ *   2. for every chunk [k, k + every) of the rest (the last may be shorter):
+ *      the chunk's sweeps, resumed at global sweep k, in one batched launch;
+ *      the network's logits for each problem's configurations
+ *      (ising_cnn_forward); block flips over all problems
+ *      (ising_propose_clusters), each component accepted iff dE <= 0;
+ *   3. the cut of every configuration (Eq. 1).
+ * With no chunk (k_first = S) this is the plain annealer, bit for bit; with
+ * chunks, the sweeps between proposals are the plain annealer's resumed
+ * exactly, so the proposals are the only difference.
+ * probs    m (1..16) torus problems of one shape, on the current device.
+ * betas    host [S], seeds host [m] (problem q's decision stream).
+ * net      the network; its current weights are read at every launch.
+ * spins    device [m * trials][n] int8: the state, written by every launch
+ *          (problem q's configurations at rows q * trials ...).
+ * cuts     device [m * trials] int32, written at the end of every launch.
+ * accepted device [m * trials] int32 or NULL: components flipped over all
+ *          chunks, per configuration.
+ * logits   device [m * trials][n] float (scratch), ws / ws_bytes: the
+ *          network's workspace for `trials` configurations
+ *          (ising_cnn_workspace_bytes(trials, n, 0)); all owned by the caller
+ *          and used by every launch, so launches of one plan must not
+ *          overlap.
+ * The buffers and arguments are bound into the graph at creation; create
+ * copies the schedule's thresholds to the device and synchronises
+ * cuda_stream.  launch enqueues the graph on cuda_stream.
+ * Errors: ISING_ERR_ARG (bad pointers or sizes, mixed shapes),
+ * ISING_ERR_UNSUPPORTED (a general-graph handle, or an instance the batched
+ * launch or the network cannot take), ISING_ERR_OOM, ISING_ERR_CUDA.
+ */
+typedef struct ising_learned ising_learned;
+int ising_learned_create(ising_problem* const* probs, int32_t m, int32_t trials, const double* betas, int32_t S,
+                         const uint64_t* seeds, int32_t k_first, int32_t every, const ising_cnn* net, int8_t* spins,
+                         int32_t* cuts, int32_t* accepted, float* logits, void* ws, size_t ws_bytes,
+                         void* cuda_stream, ising_learned** out);
+int ising_learned_launch(ising_learned* plan, void* cuda_stream);
+void ising_learned_destroy(ising_learned* plan);
+
+/*
  * ising_flip_targets -- training targets for the network: for each of B
  * configurations, y_i = [s_i != r'_i] where r' is ref or -ref, whichever is
  * closer to s in Hamming distance (on a tie, the one that keeps site 0); the

@@ -540,6 +540,57 @@ def propose(prob, spins, logits, tile, accepted=None, stream=None):
     return accepted
 
 
+class LearnedPlan:
+    """The learned form of the annealer for m same-shape problems, prepared
+    once and replayed as one CUDA graph (ising_learned_create / _launch):
+    sweeps [0, k_first) batched from the Philox start, then for every chunk
+    of `every` sweeps the chunk batched and resumed, the network's logits
+    and cluster block flips; then the cuts.  The state, cuts, accepted counts,
+    logits and the network's workspace are device tensors owned here."""
+
+    def __init__(self, probs, net, trials, betas, seeds, k_first, every=100, stream=None):
+        torch = _torch()
+        self.probs = list(probs)
+        m, n = len(self.probs), self.probs[0].n
+        self.trials = int(trials)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.spins = torch.empty((m * self.trials, n), dtype=torch.int8, device=dev)
+        self.cuts = torch.empty((m * self.trials,), dtype=torch.int32, device=dev)
+        self.accepted = torch.zeros((m * self.trials,), dtype=torch.int32, device=dev)
+        self.logits = torch.empty((m * self.trials, n), dtype=torch.float32, device=dev)
+        need = int(lib().ising_cnn_workspace_bytes(self.trials, int(n), 0))
+        self.ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        self._betas = np.ascontiguousarray(betas, dtype=np.float64)
+        self._seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        assert self._seeds.shape == (m,)
+        handles = (ctypes.c_void_p * m)(*[p.handle for p in self.probs])
+        out = ctypes.c_void_p()
+        self.net = net
+        check(lib().ising_learned_create(handles, int(m), self.trials,
+                                         self._betas.ctypes.data_as(ctypes.c_void_p), int(self._betas.shape[0]),
+                                         self._seeds.ctypes.data_as(ctypes.c_void_p), int(k_first), int(every),
+                                         net.handle, _dptr(self.spins), _dptr(self.cuts), _dptr(self.accepted),
+                                         _dptr(self.logits), _dptr(self.ws), ctypes.c_size_t(self.ws.numel()),
+                                         _stream_ptr(stream), ctypes.byref(out)), "ising_learned_create")
+        self._h = out
+
+    def launch(self, stream=None):
+        """Enqueue one learned anneal; returns (spins, cuts, accepted) views."""
+        check(lib().ising_learned_launch(self._h, _stream_ptr(stream)), "ising_learned_launch")
+        return self.spins, self.cuts, self.accepted
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None:
+            lib().ising_learned_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
 def propose_clusters(probs, spins, logits, accepted=None, stream=None):
     """Cluster block flips in place (ising_propose_clusters).  probs: one
     Problem, or a list of m Problems of one shape whose configurations are

@@ -296,7 +296,8 @@ int batch_schedule(int32_t m, const int32_t* n, const int32_t* H, const int32_t*
 
 int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials, const int32_t* sweeps,
                   const double* const* betas, const uint64_t* seeds, int8_t* const* out_spins,
-                  int32_t* const* out_cuts, int32_t group_trials, int32_t ctas_per_sm, HostBatch& hb) {
+                  int32_t* const* out_cuts, int32_t group_trials, int32_t ctas_per_sm, HostBatch& hb,
+                  const int8_t* const* init_spins = nullptr, uint32_t sweep_offset = 0) {
   if (m < 0 || (m > 0 && (!probs || !trials || !sweeps || !betas || !seeds))) return ISING_ERR_ARG;
   if (group_trials != 0 && (group_trials < 4 || group_trials > 32 || group_trials % 4)) return ISING_ERR_ARG;
   if (ctas_per_sm < 0 || ctas_per_sm > 4) return ISING_ERR_ARG;
@@ -334,6 +335,8 @@ int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials,
     ising::BatchInst& in = hb.inst[q];
     in.flags = p->d_flags;
     in.thr = nullptr;  // patched once the arena address is known
+    in.init = init_spins ? init_spins[q] : nullptr;
+    in.k0 = sweep_offset;
     in.out_spins = out_spins ? out_spins[q] : nullptr;
     in.out_cuts = out_cuts ? out_cuts[q] : nullptr;
     in.X = p->X; in.Y = p->Y; in.H = p->H; in.n = p->n;
@@ -1196,6 +1199,126 @@ int ising_batch_launch(ising_batch* b, void* cuda_stream) {
   cudaError_t e = cudaGraphLaunch(b->exec, st);
   if (e == cudaSuccess) e = cudaEventRecord(b->done, st);
   return map_cuda(e);
+}
+
+// ---------------------------------------------------------------- learned form as one graph
+struct ising_learned {
+  unsigned char* d_arena = nullptr;   // the batch arenas of every annealing launch
+  cudaStream_t capture = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+void ising_learned_destroy(ising_learned* L) {
+  if (!L) return;
+  if (L->exec) cudaGraphExecDestroy(L->exec);
+  if (L->graph) cudaGraphDestroy(L->graph);
+  if (L->capture) cudaStreamDestroy(L->capture);
+  if (L->d_arena) cudaFree(L->d_arena);
+  delete L;
+}
+
+int ising_learned_create(ising_problem* const* probs, int32_t m, int32_t trials, const double* betas, int32_t S,
+                         const uint64_t* seeds, int32_t k_first, int32_t every, const ising_cnn* net, int8_t* spins,
+                         int32_t* cuts, int32_t* accepted, float* logits, void* ws, size_t ws_bytes,
+                         void* cuda_stream, ising_learned** out) {
+  if (!out || !probs || m < 1 || m > 16 || trials < 1 || S < 0 || (S > 0 && !betas) || !seeds || k_first < 0 ||
+      k_first > S || every < 1 || !net || !spins || !cuts || !logits || !ws)
+    return ISING_ERR_ARG;
+  for (int32_t q = 0; q < m; ++q) {
+    if (!probs[q]) return ISING_ERR_ARG;
+    if (probs[q]->graph) return ISING_ERR_UNSUPPORTED;
+    if (probs[q]->X != probs[0]->X || probs[q]->Y != probs[0]->Y || probs[q]->device != probs[0]->device)
+      return ISING_ERR_ARG;
+  }
+  *out = nullptr;
+  const size_t n = static_cast<size_t>(probs[0]->n);
+  // launch 0: sweeps [0, k_first) from the Philox start (k_first = 0 writes
+  // the start state); then one launch per window chunk [k, k + len), resumed
+  // from the state at its global sweep k
+  std::vector<std::pair<int32_t, int32_t>> chunks;
+  for (int32_t k = k_first; k < S; k += every) chunks.emplace_back(k, std::min(every, S - k));
+  std::vector<HostBatch> batches(1 + chunks.size());
+  std::vector<size_t> base(batches.size());
+  size_t total = 0;
+  try {
+    std::vector<int8_t*> outs(m);
+    std::vector<const int8_t*> inits(m);
+    for (int32_t q = 0; q < m; ++q) {
+      outs[q] = spins + static_cast<size_t>(q) * trials * n;
+      inits[q] = outs[q];
+    }
+    const std::vector<int32_t> vt(m, trials);
+    for (size_t c = 0; c < batches.size(); ++c) {
+      const int32_t k = c == 0 ? 0 : chunks[c - 1].first;
+      const int32_t len = c == 0 ? k_first : chunks[c - 1].second;
+      const std::vector<int32_t> vs(m, len);
+      const std::vector<const double*> vb(m, betas ? betas + k : nullptr);
+      const int rc = prepare_batch(probs, m, vt.data(), vs.data(), vb.data(), seeds, outs.data(), nullptr, 0, 0,
+                                   batches[c], c == 0 ? nullptr : inits.data(), static_cast<uint32_t>(k));
+      if (rc != ISING_OK) return rc;
+      base[c] = total;
+      total += align256(batches[c].bytes);
+    }
+  } catch (const std::bad_alloc&) {
+    return ISING_ERR_OOM;
+  }
+  ising_learned* L = new (std::nothrow) ising_learned();
+  if (!L) return ISING_ERR_OOM;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = ising::dev_malloc(reinterpret_cast<void**>(&L->d_arena), total);
+  try {
+    for (size_t c = 0; c < batches.size() && e == cudaSuccess; ++c) {
+      const std::vector<unsigned char> img = arena_image(batches[c], L->d_arena + base[c]);
+      e = cudaMemcpy(L->d_arena + base[c], img.data(), batches[c].bytes, cudaMemcpyHostToDevice);
+    }
+  } catch (const std::bad_alloc&) {
+    ising_learned_destroy(L);
+    return ISING_ERR_OOM;
+  }
+  if (e == cudaSuccess) e = ising::batched_prepare(batches[0].smem);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    ising_learned_destroy(L);
+    return map_cuda(e);
+  }
+  // the whole learned anneal as one graph
+  int rc = ISING_OK;
+  e = cudaStreamCreateWithFlags(&L->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(L->capture, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaStream_t cs = L->capture;
+    cudaError_t ec = accepted ? cudaMemsetAsync(accepted, 0, sizeof(int32_t) * m * trials, cs) : cudaSuccess;
+    for (size_t c = 0; c < batches.size() && ec == cudaSuccess && rc == ISING_OK; ++c) {
+      const ising::BatchArgs a = batch_args(batches[c], L->d_arena + base[c]);
+      ec = cudaMemsetAsync(a.counter, 0, sizeof(uint32_t), cs);
+      if (ec == cudaSuccess)
+        ec = ising::launch_batched(a, batches[c].grid, batches[c].threads, batches[c].smem, cs);
+      if (c == 0 || ec != cudaSuccess) continue;
+      // the network's logits per instance, then the block flips over all
+      for (int32_t q = 0; q < m && rc == ISING_OK; ++q)
+        rc = ising::cnn_forward_ws(net, probs[q], spins + static_cast<size_t>(q) * trials * n, trials,
+                                   logits + static_cast<size_t>(q) * trials * n, ws, ws_bytes, cs);
+      if (rc == ISING_OK) rc = ising::propose_clusters_launch(probs, m, spins, trials, logits, accepted, 1, cs);
+    }
+    for (int32_t q = 0; q < m && ec == cudaSuccess && rc == ISING_OK; ++q)
+      ec = ising::launch_cut(probs[q], spins + static_cast<size_t>(q) * trials * n, trials,
+                             cuts + static_cast<size_t>(q) * trials, cs);
+    e = cudaStreamEndCapture(cs, &L->graph);
+    if (e == cudaSuccess) e = ec;
+  }
+  if (e == cudaSuccess && rc == ISING_OK) e = cudaGraphInstantiate(&L->exec, L->graph, 0);
+  if (e != cudaSuccess || rc != ISING_OK) {
+    ising_learned_destroy(L);
+    return rc != ISING_OK ? rc : map_cuda(e);
+  }
+  *out = L;
+  return ISING_OK;
+}
+
+int ising_learned_launch(ising_learned* L, void* cuda_stream) {
+  if (!L || !L->exec) return ISING_ERR_ARG;
+  return map_cuda(cudaGraphLaunch(L->exec, static_cast<cudaStream_t>(cuda_stream)));
 }
 
 int ising_greedy_colouring(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t* colour,

@@ -5,7 +5,9 @@
 // unit (instance, trial group) from an atomic counter over a list sorted
 // longest-first on the host, anneals it whole in shared memory (the strip
 // body of anneal_core.cuh with a single strip), writes its spins and cuts,
-// and takes the next unit.  Results equal ising_anneal on each instance.
+// and takes the next unit.  Results equal ising_anneal on each instance,
+// including a resumed run (starting spins and the global index of the first
+// sweep).
 #include "anneal_core.cuh"
 
 namespace ising {
@@ -31,12 +33,12 @@ __global__ void __launch_bounds__(1024, 1) batched_kernel(const BatchArgs a) {
     GroupJob job;
     job.flags = in.flags;
     job.thr = in.thr;
-    job.init = nullptr;
+    job.init = in.init;
     job.out_spins = in.out_spins;
     job.out_cuts = in.out_cuts;
     job.X = in.X; job.Y = in.Y; job.H = in.H; job.n = in.n;
     job.T = in.T; job.G = in.G; job.S = in.S;
-    job.k0 = 0;
+    job.k0 = in.k0;
     job.key0 = in.key0; job.key1 = in.key1;
     job.rk = s_rk;
     job.C = 1; job.Rmax = in.Y;

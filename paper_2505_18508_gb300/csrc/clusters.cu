@@ -37,6 +37,7 @@ struct ClusterArgs {
   const int8_t* ref;              // [B][n] (targets) or null
   uint8_t* targets;               // [B][n] (targets) or null
   int32_t* accepted;              // [B] components flipped (proposals) or null
+  int32_t accumulate;             // 1: add to accepted instead of writing it
   const uint8_t* eflags[kMaxClusterProblems];   // per problem: bit 0 right edge w = -1, bit 1 down edge
   int32_t per_problem;            // configurations per problem: image b uses eflags[b / per_problem]
   int32_t X, Y;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterA
       if (tid == 0) {
         int t = 0;
         for (int w = 0; w < kClusterThreads / 32; ++w) t += red[w];
-        a.accepted[b] = t;
+        a.accepted[b] = a.accumulate ? a.accepted[b] + t : t;
       }
     }
   }
@@ -205,10 +206,12 @@ int launch_clusters(const ClusterArgs& a, int32_t images, cudaStream_t st) {
 }  // namespace
 }  // namespace ising
 
-extern "C" int ising_propose_clusters(const ising_problem* const* probs, int32_t m, int8_t* spins, int32_t B,
-                                      const float* logits, int32_t* accepted, void* cuda_stream) {
-  ising::ClusterArgs a{};
-  const int rc = ising::cluster_check(probs, m, B, &a);
+namespace ising {
+
+int propose_clusters_launch(const ising_problem* const* probs, int32_t m, int8_t* spins, int32_t B,
+                            const float* logits, int32_t* accepted, int accumulate, cudaStream_t st) {
+  ClusterArgs a{};
+  const int rc = cluster_check(probs, m, B, &a);
   if (rc != ISING_OK) return rc;
   if (B > 0 && (!spins || !logits)) return ISING_ERR_ARG;
   if (B == 0) return ISING_OK;
@@ -216,7 +219,16 @@ extern "C" int ising_propose_clusters(const ising_problem* const* probs, int32_t
   a.spins = spins;
   a.logits = logits;
   a.accepted = accepted;
-  return ising::launch_clusters<false>(a, m * B, static_cast<cudaStream_t>(cuda_stream));
+  a.accumulate = accumulate;
+  return launch_clusters<false>(a, m * B, st);
+}
+
+}  // namespace ising
+
+extern "C" int ising_propose_clusters(const ising_problem* const* probs, int32_t m, int8_t* spins, int32_t B,
+                                      const float* logits, int32_t* accepted, void* cuda_stream) {
+  return ising::propose_clusters_launch(probs, m, spins, B, logits, accepted, 0,
+                                        static_cast<cudaStream_t>(cuda_stream));
 }
 
 extern "C" int ising_droplet_targets(const ising_problem* p, const int8_t* spins, const int8_t* ref, int32_t B,

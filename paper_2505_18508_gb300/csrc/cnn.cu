@@ -296,6 +296,22 @@ bool tc_supported(const ising_problem* p) {
 
 }  // namespace
 
+namespace ising {
+
+int cnn_forward_ws(const ising_cnn* net, const ising_problem* p, const int8_t* spins, int32_t B, float* logits,
+                   void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (!net || !p || B < 0 || (B > 0 && (!spins || !logits || !ws))) return ISING_ERR_ARG;
+  if (p->graph) return ISING_ERR_UNSUPPORTED;   // the network reads the torus layout
+  if (B == 0) return ISING_OK;
+  if (ws_bytes < ws_layout(B, p->n, 0, nullptr, nullptr)) return ISING_ERR_ARG;
+  if (!tc_supported(p)) return ISING_ERR_UNSUPPORTED;
+  WS w;
+  ws_layout(B, p->n, 0, &w, static_cast<unsigned char*>(ws));
+  return cnn_map(forward_pass(net, p, spins, B, logits, w, st));
+}
+
+}  // namespace ising
+
 extern "C" {
 
 int ising_cnn_create(const float* params, ising_cnn** out) {
@@ -363,14 +379,7 @@ size_t ising_cnn_workspace_bytes(int32_t B, int32_t n, int32_t train) {
 
 int ising_cnn_forward(const ising_cnn* net, const ising_problem* p, const int8_t* spins, int32_t B, float* logits,
                       void* ws, size_t ws_bytes, void* cuda_stream) {
-  if (!net || !p || B < 0 || (B > 0 && (!spins || !logits || !ws))) return ISING_ERR_ARG;
-  if (p->graph) return ISING_ERR_UNSUPPORTED;   // the network reads the torus layout
-  if (B == 0) return ISING_OK;
-  if (ws_bytes < ws_layout(B, p->n, 0, nullptr, nullptr)) return ISING_ERR_ARG;
-  if (!tc_supported(p)) return ISING_ERR_UNSUPPORTED;
-  WS w;
-  ws_layout(B, p->n, 0, &w, static_cast<unsigned char*>(ws));
-  return cnn_map(forward_pass(net, p, spins, B, logits, w, static_cast<cudaStream_t>(cuda_stream)));
+  return ising::cnn_forward_ws(net, p, spins, B, logits, ws, ws_bytes, static_cast<cudaStream_t>(cuda_stream));
 }
 
 int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* spins, const uint8_t* targets,

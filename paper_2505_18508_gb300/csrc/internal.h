@@ -196,7 +196,8 @@ cudaError_t launch_cut(const ising_problem* p, const int8_t* spins, int32_t k, i
 struct BatchInst {                 // one instance of a batch (device-side descriptor)
   const uint8_t* flags;
   const uint32_t* thr;             // [2*S]
-  int8_t* out_spins;               // [T][n] or null
+  const int8_t* init;              // [T][n] starting spins, or null (the Philox start)
+  int8_t* out_spins;               // [T][n] or null (may equal init)
   int32_t* out_cuts;               // [T] or null
   int32_t X, Y, H, n;
   int32_t T, S;
@@ -204,6 +205,7 @@ struct BatchInst {                 // one instance of a batch (device-side descr
   int32_t neg_edges;
   int32_t G;                       // trials per work unit for this instance
   int32_t u16;                     // 1: 16-bit draw mode
+  uint32_t k0;                     // global index of the first sweep (the Philox counter)
 };
 struct BatchUnit {                 // one work item: one trial group of one instance
   int32_t inst;
@@ -238,6 +240,15 @@ cudaError_t launch_graph(const GraphArgs& a, cudaStream_t st);
 cudaError_t launch_graph_measure(const GraphArgs& a, const int8_t* spins, int32_t k, int32_t* cuts,
                                  long long* energies, cudaStream_t st);
 cudaError_t launch_energy_from_cut(const int32_t* cuts, int32_t W, int32_t k, int64_t* out, cudaStream_t st);
+
+// The network's logits for B configurations of one torus problem (cnn.cu;
+// the checks and errors of ising_cnn_forward).
+int cnn_forward_ws(const ising_cnn* net, const ising_problem* p, const int8_t* spins, int32_t B, float* logits,
+                   void* ws, size_t ws_bytes, cudaStream_t st);
+// Cluster proposals (clusters.cu; ising_propose_clusters), adding the
+// accepted counts to `accepted` when accumulate is 1.
+int propose_clusters_launch(const ising_problem* const* probs, int32_t m, int8_t* spins, int32_t B,
+                            const float* logits, int32_t* accepted, int accumulate, cudaStream_t st);
 
 size_t batched_smem_bytes(int32_t H, int32_t Y);
 cudaError_t batched_prepare(size_t smem);

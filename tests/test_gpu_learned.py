@@ -140,3 +140,78 @@ def test_window_and_batched_forms_equal_the_chunked_loop(ia):
     net.destroy()
     for p in probs:
         p.destroy()
+
+
+def _host_loop(ia, probs, net, T, betas, seeds, k_first, every):
+    """The learned form step by step through the single-call ABI: per problem
+    the sweeps before the window, then per chunk each problem's sweeps
+    (resumed), logits, and one cluster-proposal call over all problems."""
+    import torch
+    states = []
+    for p, sd in zip(probs, seeds):
+        s, _ = ia.anneal(p, T, betas[:k_first], sd)
+        states.append(s)
+    s = torch.cat(states, 0).contiguous()
+    logits_seen = []
+    for k0 in range(k_first, len(betas), every):
+        parts, zs = [], []
+        for q, (p, sd) in enumerate(zip(probs, seeds)):
+            sq, _ = ia.anneal(p, T, betas[k0:k0 + every], sd, sweep_offset=k0, init=s[q * T:(q + 1) * T].contiguous())
+            parts.append(sq)
+        s = torch.cat(parts, 0).contiguous()
+        for q, p in enumerate(probs):
+            zs.append(net.forward(p, s[q * T:(q + 1) * T].contiguous()))
+        z = torch.cat(zs, 0).contiguous()
+        logits_seen.append(z.cpu().numpy())
+        ia.propose_clusters(probs, s, z)
+    cuts = torch.cat([ia.cut(p, s[q * T:(q + 1) * T].contiguous()) for q, p in enumerate(probs)])
+    return s, cuts, logits_seen
+
+
+def test_learned_plan_equals_plain_without_chunks_and_the_host_loop_with_them(ia):
+    import torch
+    X, Y, T, S, every = 24, 12, 40, 300, 100
+    insts = [synth.torus_instance(X, Y, 300 + q) for q in range(3)]
+    probs = [ia.Problem.from_instance(i) for i in insts]
+    betas = synth.linear_betas(0.1, 3.0, S)
+    seeds = [901, 902, 903]
+    params = ocnn.init_params(7, scale=0.8)
+    params[ocnn.N_PARAMS - 1] = 0.0
+    net = ia.CNN(params)
+    # no chunk: exactly the plain annealer
+    plan = ia.LearnedPlan(probs, net, T, betas, seeds, k_first=S, every=every)
+    s, c, acc = plan.launch()
+    torch.cuda.synchronize()
+    for q, (p, sd) in enumerate(zip(probs, seeds)):
+        rs, rc = ia.anneal(p, T, betas, sd)
+        assert torch.equal(s[q * T:(q + 1) * T], rs) and torch.equal(c[q * T:(q + 1) * T], rc)
+    assert int(acc.sum().item()) == 0
+    plan.destroy()
+    # chunks from sweep 100: the graph equals the host loop, launch after launch
+    plan = ia.LearnedPlan(probs, net, T, betas, seeds, k_first=100, every=every)
+    hs, hc, logits_seen = _host_loop(ia, probs, net, T, betas, seeds, 100, every)
+    for _ in range(2):
+        s, c, acc = plan.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(s, hs) and torch.equal(c, hc)
+    assert int(acc.sum().item()) > 0
+    # and the host loop equals the oracle fed the same logits
+    for q, inst in enumerate(insts):
+        rs, _ = oracle.anneal(inst, betas[:100], seeds[q], t_count=T)
+        for j, k0 in enumerate(range(100, S, every)):
+            rs, _ = oracle.anneal(inst, betas[k0:k0 + every], seeds[q], t_count=T, sweep_offset=k0, init=rs)
+            rs, _ = ocnn.propose_clusters(rs, logits_seen[j][q * T:(q + 1) * T], inst["w_right"], inst["w_down"])
+        np.testing.assert_array_equal(hs[q * T:(q + 1) * T].cpu().numpy(), rs)
+        np.testing.assert_array_equal(hc[q * T:(q + 1) * T].cpu().numpy(),
+                                      np.array([oracle.cut_csr(inst, r) for r in rs]))
+    plan.destroy()
+    # the window from sweep 0 (every chunk proposes)
+    plan = ia.LearnedPlan(probs, net, T, betas, seeds, k_first=0, every=every)
+    hs, hc, _ = _host_loop(ia, probs, net, T, betas, seeds, 0, every)
+    s, c, _ = plan.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(s, hs) and torch.equal(c, hc)
+    plan.destroy()
+    net.destroy()
+    for p in probs:
+        p.destroy()
