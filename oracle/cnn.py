@@ -283,3 +283,23 @@ def propose_clusters(spins, logits, w_right, w_down):
                     s[b, y, x] = -s[b, y, x]
                 acc[b] += 1
     return s.reshape(s.shape[0], -1), acc
+
+
+def transcribe(spins, shift, w_right, w_down):
+    """Partner cluster moves (a reading of block flips with blocks taken from
+    another trial instead of the network): configuration t of a batch of B
+    takes partner p = (t + shift) mod B; every component of the disagreement
+    between s_t and the gauge-aligned s_p whose flip alone lowers the energy
+    of s_t is flipped (droplet_targets), all partners read before any move.
+    Returns (new spins [B, n], flipped components [B])."""
+    s = np.asarray(spins, dtype=np.int8)
+    B = s.shape[0]
+    partner = s[(np.arange(B) + shift) % B]
+    y = droplet_targets(s, partner, w_right, w_down)
+    Y, X = w_right.shape
+    d = flip_targets(s, partner).reshape(B, Y, X).astype(bool)
+    comps = np.zeros(B, dtype=np.int64)
+    for b in range(B):
+        sg = s[b].reshape(Y, X)
+        comps[b] = sum(component_dE(sg, c, w_right, w_down) < 0 for c in torus_components(d[b]))
+    return np.where(y.astype(bool), -s, s).astype(np.int8), comps

@@ -245,3 +245,21 @@ def test_cluster_proposals_never_raise_the_energy():
         assert cnn._energy_grid(ng, wr, wd) - cnn._energy_grid(sg, wr, wd) == sum(g for g in gains if g <= 0)
         changed = (sg != ng)
         assert not (changed & (z[b].reshape(Y, X) <= 0)).any()      # only proposed sites move
+
+
+def test_transcription_lowers_each_energy_by_its_improving_components():
+    """Each configuration ends exactly lower by the sum of its improving
+    components' changes (never higher), and with a partner identical to it
+    (shift = B) nothing moves."""
+    X, Y, B = 10, 8, 5
+    inst, wr, wd = _grid_instance(X, Y, 13)
+    s = synth.random_spins(B, X * Y, 30)
+    new, comps = cnn.transcribe(s, 2, wr, wd)
+    for b in range(B):
+        sg = s[b].reshape(Y, X)
+        d = cnn.flip_targets(s[b:b + 1], s[(b + 2) % B][None]).reshape(Y, X).astype(bool)
+        gains = [cnn.component_dE(sg, c, wr, wd) for c in cnn.torus_components(d)]
+        assert comps[b] == sum(g < 0 for g in gains)
+        assert cnn._energy_grid(new[b].reshape(Y, X), wr, wd) - cnn._energy_grid(sg, wr, wd) == sum(g for g in gains if g < 0)
+    same, c0 = cnn.transcribe(s, B, wr, wd)
+    assert (same == s).all() and (c0 == 0).all()
