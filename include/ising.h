@@ -603,46 +603,73 @@ int ising_droplet_targets(const ising_problem* p, const int8_t* spins, const int
                           uint8_t* targets, void* cuda_stream);
 
 /*
+ * ising_transcribe -- partner moves: block flips whose blocks come from
+ * another trial of the same instance instead of the network (this project's
+ * extension of the block flips; the paper's own rule is unpublished,
+ * Section III).  Configuration t of problem q takes partner
+ * p = (t + shift) mod B of the same problem; the sites where s_t differs
+ * from the gauge-aligned s_p (as ising_flip_targets) split into connected
+ * components on the torus, and every component whose flip alone lowers the
+ * energy of s_t (dE_C < 0, as ising_propose_clusters) is flipped.  All
+ * configurations read the partners' states before any move: out receives
+ * the new states and must not alias spins.  Each configuration's energy
+ * drops by exactly the sum of its flipped components' changes.
+ * probs    m (1..16) torus problems of one shape; spins / out device
+ *          [m * B][n] int8; accepted device [m * B] int32 or NULL:
+ *          components flipped per configuration.
+ * Limits and errors as ising_propose_clusters; ISING_ERR_ARG also for
+ * shift < 0 or out == spins.
+ */
+int ising_transcribe(const ising_problem* const* probs, int32_t m, const int8_t* spins, int8_t* out, int32_t B,
+                     int32_t shift, int32_t* accepted, void* cuda_stream);
+
+/*
  * ising_learned_create / _launch / _destroy -- the learned form of the
  * annealer for m torus problems of one shape (this project's extension; the
  * paper's own update rule is unpublished, Section III), prepared once and
  * replayed as one CUDA graph: no host round trip between its steps.
  *   1. sweeps [0, k_first) of the schedule from the Philox start, all
  *      problems in one persistent batched launch (k_first = 0: the start);
+ *      with warm = 1 the network's whole-lattice proposal (ising_propose,
+ *      tile 0) is applied to the start state first;
  *   2. for every chunk [k, k + every) of the rest (the last may be shorter):
  *      the chunk's sweeps, resumed at global sweep k, in one batched launch;
- *      the network's logits for each problem's configurations
- *      (ising_cnn_forward); block flips over all problems
- *      (ising_propose_clusters), each component accepted iff dE <= 0;
+ *      then, with a network, its logits for each problem's configurations
+ *      (ising_cnn_forward) and its block flips over all problems
+ *      (ising_propose_clusters); then, with partner_period P > 0, partner
+ *      moves (ising_transcribe) with offset 1 + (j mod P) in chunk j;
  *   3. the cut of every configuration (Eq. 1).
  * With no chunk (k_first = S) this is the plain annealer, bit for bit; with
  * chunks, the sweeps between proposals are the plain annealer's resumed
  * exactly, so the proposals are the only difference.
  * probs    m (1..16) torus problems of one shape, on the current device.
  * betas    host [S], seeds host [m] (problem q's decision stream).
- * net      the network; its current weights are read at every launch.
+ * net      the network or NULL (no network proposals, no warm start); its
+ *          current weights are read at every launch.
  * spins    device [m * trials][n] int8: the state, written by every launch
  *          (problem q's configurations at rows q * trials ...).
  * cuts     device [m * trials] int32, written at the end of every launch.
- * accepted device [m * trials] int32 or NULL: components flipped over all
- *          chunks, per configuration.
+ * accepted device [m * trials] int32 or NULL: block flips and partner
+ *          components taken over all chunks, per configuration.
  * logits   device [m * trials][n] float (scratch), ws / ws_bytes: the
  *          network's workspace for `trials` configurations
- *          (ising_cnn_workspace_bytes(trials, n, 0)); all owned by the caller
- *          and used by every launch, so launches of one plan must not
- *          overlap.
+ *          (ising_cnn_workspace_bytes(trials, n, 0)); needed with a network.
+ *          All owned by the caller and used by every launch, so launches of
+ *          one plan must not overlap.
  * The buffers and arguments are bound into the graph at creation; create
- * copies the schedule's thresholds to the device and synchronises
- * cuda_stream.  launch enqueues the graph on cuda_stream.
- * Errors: ISING_ERR_ARG (bad pointers or sizes, mixed shapes),
- * ISING_ERR_UNSUPPORTED (a general-graph handle, or an instance the batched
- * launch or the network cannot take), ISING_ERR_OOM, ISING_ERR_CUDA.
+ * allocates the plan's own device memory (the thresholds of every launch and,
+ * with partner moves, a second state buffer), copies the thresholds and
+ * synchronises cuda_stream.  launch enqueues the graph on cuda_stream.
+ * Errors: ISING_ERR_ARG (bad pointers or sizes, mixed shapes, warm start
+ * without a network), ISING_ERR_UNSUPPORTED (a general-graph handle, or an
+ * instance the batched launch, the network or the cluster kernel cannot
+ * take), ISING_ERR_OOM, ISING_ERR_CUDA.
  */
 typedef struct ising_learned ising_learned;
 int ising_learned_create(ising_problem* const* probs, int32_t m, int32_t trials, const double* betas, int32_t S,
-                         const uint64_t* seeds, int32_t k_first, int32_t every, const ising_cnn* net, int8_t* spins,
-                         int32_t* cuts, int32_t* accepted, float* logits, void* ws, size_t ws_bytes,
-                         void* cuda_stream, ising_learned** out);
+                         const uint64_t* seeds, int32_t k_first, int32_t every, const ising_cnn* net,
+                         int32_t partner_period, int32_t warm, int8_t* spins, int32_t* cuts, int32_t* accepted,
+                         float* logits, void* ws, size_t ws_bytes, void* cuda_stream, ising_learned** out);
 int ising_learned_launch(ising_learned* plan, void* cuda_stream);
 void ising_learned_destroy(ising_learned* plan);
 

@@ -543,12 +543,15 @@ def propose(prob, spins, logits, tile, accepted=None, stream=None):
 class LearnedPlan:
     """The learned form of the annealer for m same-shape problems, prepared
     once and replayed as one CUDA graph (ising_learned_create / _launch):
-    sweeps [0, k_first) batched from the Philox start, then for every chunk
-    of `every` sweeps the chunk batched and resumed, the network's logits
-    and cluster block flips; then the cuts.  The state, cuts, accepted counts,
-    logits and the network's workspace are device tensors owned here."""
+    sweeps [0, k_first) batched from the Philox start (after the network's
+    warm start with warm=True), then for every chunk of `every` sweeps the
+    chunk batched and resumed, the network's cluster block flips (net not
+    None) and partner moves (partner_period > 0); then the cuts.  The
+    state, cuts, accepted counts, logits and the network's workspace are
+    device tensors owned here."""
 
-    def __init__(self, probs, net, trials, betas, seeds, k_first, every=100, stream=None):
+    def __init__(self, probs, net, trials, betas, seeds, k_first, every=100, partner_period=0, warm=False,
+                 stream=None):
         torch = _torch()
         self.probs = list(probs)
         m, n = len(self.probs), self.probs[0].n
@@ -557,9 +560,11 @@ class LearnedPlan:
         self.spins = torch.empty((m * self.trials, n), dtype=torch.int8, device=dev)
         self.cuts = torch.empty((m * self.trials,), dtype=torch.int32, device=dev)
         self.accepted = torch.zeros((m * self.trials,), dtype=torch.int32, device=dev)
-        self.logits = torch.empty((m * self.trials, n), dtype=torch.float32, device=dev)
-        need = int(lib().ising_cnn_workspace_bytes(self.trials, int(n), 0))
-        self.ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        self.logits = self.ws = None
+        if net is not None:
+            self.logits = torch.empty((m * self.trials, n), dtype=torch.float32, device=dev)
+            need = int(lib().ising_cnn_workspace_bytes(self.trials, int(n), 0))
+            self.ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
         self._betas = np.ascontiguousarray(betas, dtype=np.float64)
         self._seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
         assert self._seeds.shape == (m,)
@@ -569,8 +574,11 @@ class LearnedPlan:
         check(lib().ising_learned_create(handles, int(m), self.trials,
                                          self._betas.ctypes.data_as(ctypes.c_void_p), int(self._betas.shape[0]),
                                          self._seeds.ctypes.data_as(ctypes.c_void_p), int(k_first), int(every),
-                                         net.handle, _dptr(self.spins), _dptr(self.cuts), _dptr(self.accepted),
-                                         _dptr(self.logits), _dptr(self.ws), ctypes.c_size_t(self.ws.numel()),
+                                         net.handle if net is not None else None, int(partner_period), int(bool(warm)),
+                                         _dptr(self.spins), _dptr(self.cuts), _dptr(self.accepted),
+                                         _dptr(self.logits) if self.logits is not None else None,
+                                         _dptr(self.ws) if self.ws is not None else None,
+                                         ctypes.c_size_t(self.ws.numel() if self.ws is not None else 0),
                                          _stream_ptr(stream), ctypes.byref(out)), "ising_learned_create")
         self._h = out
 
@@ -612,6 +620,31 @@ def propose_clusters(probs, spins, logits, accepted=None, stream=None):
     check(lib().ising_propose_clusters(handles, int(m), _dptr(spins), int(rows // m), _dptr(logits),
                                        _dptr(accepted), _stream_ptr(stream)), "ising_propose_clusters")
     return accepted
+
+
+def transcribe(probs, spins, shift, out=None, accepted=None, stream=None):
+    """Partner moves (ising_transcribe): returns (new spins [m * B, n],
+    flipped components [m * B]); probs as in propose_clusters."""
+    torch = _torch()
+    probs = list(probs) if isinstance(probs, (list, tuple)) else [probs]
+    rows = _rows(spins, "spins")
+    m = len(probs)
+    if rows % m:
+        raise ValueError("spins rows must be a multiple of the number of problems")
+    n = probs[0].n
+    spins = _device_tensor(spins, torch.int8, (rows, n), "spins")
+    if out is None:
+        out = torch.empty_like(spins)
+    else:
+        out = _device_tensor(out, torch.int8, (rows, n), "out", write=True)
+    if accepted is None:
+        accepted = torch.zeros(rows, dtype=torch.int32, device=spins.device)
+    else:
+        accepted = _device_tensor(accepted, torch.int32, (rows,), "accepted", write=True)
+    handles = (ctypes.c_void_p * m)(*[p.handle for p in probs])
+    check(lib().ising_transcribe(handles, int(m), _dptr(spins), _dptr(out), int(rows // m), int(shift),
+                                 _dptr(accepted), _stream_ptr(stream)), "ising_transcribe")
+    return out, accepted
 
 
 def droplet_targets(prob, spins, ref, out=None, stream=None):

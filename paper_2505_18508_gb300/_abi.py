@@ -78,8 +78,9 @@ _SIGNATURES = {
     "ising_flip_targets": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
     "ising_propose_clusters": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _vp, _vp]),
     "ising_droplet_targets": (ctypes.c_int, [_vp, _vp, _vp, _i32, _vp, _vp]),
-    "ising_learned_create": (ctypes.c_int, [_vp, _i32, _i32, _vp, _i32, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp,
-                                            _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
+    "ising_transcribe": (ctypes.c_int, [_vp, _i32, _vp, _vp, _i32, _i32, _vp, _vp]),
+    "ising_learned_create": (ctypes.c_int, [_vp, _i32, _i32, _vp, _i32, _vp, _i32, _i32, _vp, _i32, _i32, _vp, _vp,
+                                            _vp, _vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
     "ising_learned_launch": (ctypes.c_int, [_vp, _vp]),
     "ising_learned_destroy": (None, [_vp]),
     "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),

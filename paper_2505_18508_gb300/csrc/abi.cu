@@ -1204,6 +1204,7 @@ int ising_batch_launch(ising_batch* b, void* cuda_stream) {
 // ---------------------------------------------------------------- learned form as one graph
 struct ising_learned {
   unsigned char* d_arena = nullptr;   // the batch arenas of every annealing launch
+  int8_t* d_other = nullptr;          // second state buffer of the partner moves
   cudaStream_t capture = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1215,15 +1216,17 @@ void ising_learned_destroy(ising_learned* L) {
   if (L->graph) cudaGraphDestroy(L->graph);
   if (L->capture) cudaStreamDestroy(L->capture);
   if (L->d_arena) cudaFree(L->d_arena);
+  if (L->d_other) cudaFree(L->d_other);
   delete L;
 }
 
 int ising_learned_create(ising_problem* const* probs, int32_t m, int32_t trials, const double* betas, int32_t S,
-                         const uint64_t* seeds, int32_t k_first, int32_t every, const ising_cnn* net, int8_t* spins,
-                         int32_t* cuts, int32_t* accepted, float* logits, void* ws, size_t ws_bytes,
-                         void* cuda_stream, ising_learned** out) {
+                         const uint64_t* seeds, int32_t k_first, int32_t every, const ising_cnn* net,
+                         int32_t partner_period, int32_t warm, int8_t* spins, int32_t* cuts, int32_t* accepted,
+                         float* logits, void* ws, size_t ws_bytes, void* cuda_stream, ising_learned** out) {
   if (!out || !probs || m < 1 || m > 16 || trials < 1 || S < 0 || (S > 0 && !betas) || !seeds || k_first < 0 ||
-      k_first > S || every < 1 || !net || !spins || !cuts || !logits || !ws)
+      k_first > S || every < 1 || partner_period < 0 || warm < 0 || warm > 1 || (warm && !net) || !spins || !cuts ||
+      (net && (!logits || !ws)))
     return ISING_ERR_ARG;
   for (int32_t q = 0; q < m; ++q) {
     if (!probs[q]) return ISING_ERR_ARG;
@@ -1233,40 +1236,68 @@ int ising_learned_create(ising_problem* const* probs, int32_t m, int32_t trials,
   }
   *out = nullptr;
   const size_t n = static_cast<size_t>(probs[0]->n);
-  // launch 0: sweeps [0, k_first) from the Philox start (k_first = 0 writes
-  // the start state); then one launch per window chunk [k, k + len), resumed
-  // from the state at its global sweep k
-  std::vector<std::pair<int32_t, int32_t>> chunks;
-  for (int32_t k = k_first; k < S; k += every) chunks.emplace_back(k, std::min(every, S - k));
-  std::vector<HostBatch> batches(1 + chunks.size());
-  std::vector<size_t> base(batches.size());
+  const size_t state_bytes = static_cast<size_t>(m) * trials * n;
+  ising_learned* L = new (std::nothrow) ising_learned();
+  if (!L) return ISING_ERR_OOM;
+  cudaError_t e = cudaSuccess;
+  if (partner_period > 0) e = ising::dev_malloc(reinterpret_cast<void**>(&L->d_other), state_bytes);
+  if (e != cudaSuccess) {
+    ising_learned_destroy(L);
+    return map_cuda(e);
+  }
+  int8_t* A = spins;
+  int8_t* B2 = L->d_other;
+  // the annealing launches: the start (warm: its sweeps follow the warm
+  // start as a second launch), then one per window chunk [k, k + len),
+  // resumed at global sweep k from the state of the previous step (after a
+  // partner move that is the second buffer)
+  struct Step {
+    int32_t k0, len;
+    const int8_t* init;   // null: the Philox start
+    bool chunk;           // a window chunk: proposals follow
+  };
+  std::vector<Step> steps;
+  if (warm) {
+    steps.push_back({0, 0, nullptr, false});
+    if (k_first > 0) steps.push_back({0, k_first, A, false});
+  } else {
+    steps.push_back({0, k_first, nullptr, false});
+  }
+  {
+    int32_t j = 0;
+    for (int32_t k = k_first; k < S; k += every, ++j)
+      steps.push_back({k, std::min(every, S - k), (partner_period > 0 && j > 0) ? B2 : A, true});
+  }
+  std::vector<HostBatch> batches(steps.size());
+  std::vector<size_t> base(steps.size());
   size_t total = 0;
   try {
     std::vector<int8_t*> outs(m);
     std::vector<const int8_t*> inits(m);
-    for (int32_t q = 0; q < m; ++q) {
-      outs[q] = spins + static_cast<size_t>(q) * trials * n;
-      inits[q] = outs[q];
-    }
     const std::vector<int32_t> vt(m, trials);
-    for (size_t c = 0; c < batches.size(); ++c) {
-      const int32_t k = c == 0 ? 0 : chunks[c - 1].first;
-      const int32_t len = c == 0 ? k_first : chunks[c - 1].second;
-      const std::vector<int32_t> vs(m, len);
-      const std::vector<const double*> vb(m, betas ? betas + k : nullptr);
+    for (size_t c = 0; c < steps.size(); ++c) {
+      for (int32_t q = 0; q < m; ++q) {
+        outs[q] = A + static_cast<size_t>(q) * trials * n;
+        inits[q] = steps[c].init ? steps[c].init + static_cast<size_t>(q) * trials * n : nullptr;
+      }
+      const std::vector<int32_t> vs(m, steps[c].len);
+      const std::vector<const double*> vb(m, betas ? betas + steps[c].k0 : nullptr);
       const int rc = prepare_batch(probs, m, vt.data(), vs.data(), vb.data(), seeds, outs.data(), nullptr, 0, 0,
-                                   batches[c], c == 0 ? nullptr : inits.data(), static_cast<uint32_t>(k));
-      if (rc != ISING_OK) return rc;
+                                   batches[c], steps[c].init ? inits.data() : nullptr,
+                                   static_cast<uint32_t>(steps[c].k0));
+      if (rc != ISING_OK) {
+        ising_learned_destroy(L);
+        return rc;
+      }
       base[c] = total;
       total += align256(batches[c].bytes);
     }
   } catch (const std::bad_alloc&) {
+    ising_learned_destroy(L);
     return ISING_ERR_OOM;
   }
-  ising_learned* L = new (std::nothrow) ising_learned();
-  if (!L) return ISING_ERR_OOM;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  cudaError_t e = ising::dev_malloc(reinterpret_cast<void**>(&L->d_arena), total);
+  e = ising::dev_malloc(reinterpret_cast<void**>(&L->d_arena), total);
   try {
     for (size_t c = 0; c < batches.size() && e == cudaSuccess; ++c) {
       const std::vector<unsigned char> img = arena_image(batches[c], L->d_arena + base[c]);
@@ -1289,20 +1320,40 @@ int ising_learned_create(ising_problem* const* probs, int32_t m, int32_t trials,
   if (e == cudaSuccess) {
     cudaStream_t cs = L->capture;
     cudaError_t ec = accepted ? cudaMemsetAsync(accepted, 0, sizeof(int32_t) * m * trials, cs) : cudaSuccess;
-    for (size_t c = 0; c < batches.size() && ec == cudaSuccess && rc == ISING_OK; ++c) {
+    auto logits_of = [&](int32_t q) {
+      for (int32_t r = q; r < q + 1 && rc == ISING_OK; ++r)
+        rc = ising::cnn_forward_ws(net, probs[r], A + static_cast<size_t>(r) * trials * n, trials,
+                                   logits + static_cast<size_t>(r) * trials * n, ws, ws_bytes, cs);
+    };
+    int32_t j = 0;
+    for (size_t c = 0; c < steps.size() && ec == cudaSuccess && rc == ISING_OK; ++c) {
       const ising::BatchArgs a = batch_args(batches[c], L->d_arena + base[c]);
       ec = cudaMemsetAsync(a.counter, 0, sizeof(uint32_t), cs);
       if (ec == cudaSuccess)
         ec = ising::launch_batched(a, batches[c].grid, batches[c].threads, batches[c].smem, cs);
-      if (c == 0 || ec != cudaSuccess) continue;
-      // the network's logits per instance, then the block flips over all
-      for (int32_t q = 0; q < m && rc == ISING_OK; ++q)
-        rc = ising::cnn_forward_ws(net, probs[q], spins + static_cast<size_t>(q) * trials * n, trials,
-                                   logits + static_cast<size_t>(q) * trials * n, ws, ws_bytes, cs);
-      if (rc == ISING_OK) rc = ising::propose_clusters_launch(probs, m, spins, trials, logits, accepted, 1, cs);
+      if (ec != cudaSuccess) break;
+      if (warm && c == 0) {   // warm start: the network's whole-lattice proposal on the start state
+        for (int32_t q = 0; q < m && rc == ISING_OK; ++q) {
+          logits_of(q);
+          if (rc == ISING_OK)
+            rc = ising_propose(probs[q], A + static_cast<size_t>(q) * trials * n, trials,
+                               logits + static_cast<size_t>(q) * trials * n, 0, nullptr, cs);
+        }
+        continue;
+      }
+      if (!steps[c].chunk) continue;
+      if (net) {   // the network's logits per instance, then its block flips over all
+        for (int32_t q = 0; q < m && rc == ISING_OK; ++q) logits_of(q);
+        if (rc == ISING_OK) rc = ising::propose_clusters_launch(probs, m, A, trials, logits, accepted, 1, cs);
+      }
+      if (partner_period > 0 && rc == ISING_OK)   // partner moves into the second buffer
+        rc = ising::transcribe_launch(probs, m, A, B2, trials, 1 + j % partner_period, accepted, 1, cs);
+      ++j;
     }
+    if (ec == cudaSuccess && rc == ISING_OK && partner_period > 0 && j > 0)
+      ec = cudaMemcpyAsync(A, B2, state_bytes, cudaMemcpyDeviceToDevice, cs);
     for (int32_t q = 0; q < m && ec == cudaSuccess && rc == ISING_OK; ++q)
-      ec = ising::launch_cut(probs[q], spins + static_cast<size_t>(q) * trials * n, trials,
+      ec = ising::launch_cut(probs[q], A + static_cast<size_t>(q) * trials * n, trials,
                              cuts + static_cast<size_t>(q) * trials, cs);
     e = cudaStreamEndCapture(cs, &L->graph);
     if (e == cudaSuccess) e = ec;

@@ -13,6 +13,10 @@
 //   the gauge-aligned better state r' (r or -r, whichever is closer to s; a
 //   tie keeps site 0); y_i = 1 iff i lies in a component with dE_C < 0, an
 //   exact energy-lowering move from s towards r'.
+// * Partner moves: the same components with r = another configuration of the
+//   same problem (partner (t + shift) mod B), every component with dE_C < 0
+//   flipped; all configurations read their partners' states before any move
+//   (input and output buffers differ).
 //
 // One CTA per configuration, everything in shared memory: the spins, a label
 // per site (the smallest site index of its component once converged) and a
@@ -32,7 +36,9 @@ constexpr int kClusterThreads = 1024;
 constexpr int kMaxClusterProblems = 16;
 
 struct ClusterArgs {
-  int8_t* spins;                  // [B][n] (proposals: updated in place)
+  int8_t* spins;                  // [B][n] (proposals: updated in place; partner moves: read only)
+  int8_t* out;                    // [B][n] new states (partner moves)
+  int32_t shift;                  // partner offset within a problem's configurations (partner moves)
   const float* logits;            // [B][n] (proposals) or null
   const int8_t* ref;              // [B][n] (targets) or null
   uint8_t* targets;               // [B][n] (targets) or null
@@ -45,8 +51,10 @@ struct ClusterArgs {
 
 __device__ __forceinline__ int wrapc(int v, int m) { return v < 0 ? v + m : (v >= m ? v - m : v); }
 
-template <bool kTargets>
+// kMode: 0 = proposals from logits, 1 = droplet targets, 2 = partner moves
+template <int kMode>
 __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterArgs a) {
+  constexpr bool kTargets = kMode != 0;   // the mask is the disagreement with a reference
   extern __shared__ __align__(16) unsigned char smem[];
   const int X = a.X, Y = a.Y, n = X * Y;
   int32_t* lab = reinterpret_cast<int32_t*>(smem);            // [n]
@@ -58,11 +66,16 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterA
   const uint8_t* ef = a.eflags[b / a.per_problem];
   int8_t* s = a.spins + static_cast<size_t>(b) * n;
 
-  // gauge of the reference (targets only): r' = -r when more than half of the
+  // gauge of the reference (targets and partner moves): r' = -r when more than half of the
   // sites differ, or exactly half and site 0 differs
+  const int8_t* r = nullptr;
+  if constexpr (kMode == 1) r = a.ref + static_cast<size_t>(b) * n;
+  if constexpr (kMode == 2) {
+    const int q = b / a.per_problem, t = b - q * a.per_problem;
+    r = a.spins + (static_cast<size_t>(q) * a.per_problem + (t + a.shift) % a.per_problem) * n;
+  }
   int flip_ref = 0;
   if constexpr (kTargets) {
-    const int8_t* r = a.ref + static_cast<size_t>(b) * n;
     int d = 0;
     for (int i = tid; i < n; i += kClusterThreads) d += (s[i] > 0) != (r[i] > 0);
     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xFFFFFFFFu, d, o);
@@ -80,7 +93,6 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterA
     const int8_t si = s[i] > 0 ? int8_t(1) : int8_t(-1);
     bool in;
     if constexpr (kTargets) {
-      const int8_t* r = a.ref + static_cast<size_t>(b) * n;
       in = (((s[i] > 0) != (r[i] > 0)) ? 1 : 0) ^ flip_ref;
     } else {
       in = a.logits[static_cast<size_t>(b) * n + i] > 0.f;
@@ -148,8 +160,12 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterA
   int cnt = 0;
   for (int i = tid; i < n; i += kClusterThreads) {
     const int l = lab[i];
-    if constexpr (kTargets) {
+    if constexpr (kMode == 1) {
       a.targets[static_cast<size_t>(b) * n + i] = static_cast<uint8_t>(l != INT_MAX && dE[l] < 0);
+    } else if constexpr (kMode == 2) {
+      const bool f = l != INT_MAX && dE[l] < 0;
+      a.out[static_cast<size_t>(b) * n + i] = f ? static_cast<int8_t>(-sv[i]) : sv[i];
+      cnt += f && l == i;
     } else {
       if (l != INT_MAX && dE[l] <= 0) {
         s[i] = static_cast<int8_t>(-sv[i]);
@@ -157,7 +173,7 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterA
       }
     }
   }
-  if constexpr (!kTargets) {
+  if constexpr (kMode != 1) {
     if (a.accepted) {
       for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
       __syncthreads();
@@ -193,13 +209,13 @@ int cluster_check(const ising_problem* const* probs, int32_t m, int32_t B, Clust
   return ISING_OK;
 }
 
-template <bool kTargets>
+template <int kMode>
 int launch_clusters(const ClusterArgs& a, int32_t images, cudaStream_t st) {
   const size_t sm = cluster_smem(a.X * a.Y);
-  if (cudaFuncSetAttribute(cluster_kernel<kTargets>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(cluster_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(sm)) != cudaSuccess)
     return ISING_ERR_CUDA;
-  cluster_kernel<kTargets><<<images, kClusterThreads, sm, st>>>(a);
+  cluster_kernel<kMode><<<images, kClusterThreads, sm, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? ISING_OK : ISING_ERR_CUDA;
 }
 
@@ -220,7 +236,23 @@ int propose_clusters_launch(const ising_problem* const* probs, int32_t m, int8_t
   a.logits = logits;
   a.accepted = accepted;
   a.accumulate = accumulate;
-  return launch_clusters<false>(a, m * B, st);
+  return launch_clusters<0>(a, m * B, st);
+}
+
+int transcribe_launch(const ising_problem* const* probs, int32_t m, const int8_t* spins, int8_t* out, int32_t B,
+                      int32_t shift, int32_t* accepted, int accumulate, cudaStream_t st) {
+  ClusterArgs a{};
+  const int rc = cluster_check(probs, m, B, &a);
+  if (rc != ISING_OK) return rc;
+  if (shift < 0 || (B > 0 && (!spins || !out || spins == out))) return ISING_ERR_ARG;
+  if (B == 0) return ISING_OK;
+  if (static_cast<long long>(m) * B > 0x7FFFFFFFLL) return ISING_ERR_UNSUPPORTED;
+  a.spins = const_cast<int8_t*>(spins);   // read only in this mode
+  a.out = out;
+  a.shift = shift % B;
+  a.accepted = accepted;
+  a.accumulate = accumulate;
+  return launch_clusters<2>(a, m * B, st);
 }
 
 }  // namespace ising
@@ -241,5 +273,10 @@ extern "C" int ising_droplet_targets(const ising_problem* p, const int8_t* spins
   a.spins = const_cast<int8_t*>(spins);   // read only in this mode
   a.ref = ref;
   a.targets = targets;
-  return ising::launch_clusters<true>(a, B, static_cast<cudaStream_t>(cuda_stream));
+  return ising::launch_clusters<1>(a, B, static_cast<cudaStream_t>(cuda_stream));
+}
+
+extern "C" int ising_transcribe(const ising_problem* const* probs, int32_t m, const int8_t* spins, int8_t* out,
+                                int32_t B, int32_t shift, int32_t* accepted, void* cuda_stream) {
+  return ising::transcribe_launch(probs, m, spins, out, B, shift, accepted, 0, static_cast<cudaStream_t>(cuda_stream));
 }

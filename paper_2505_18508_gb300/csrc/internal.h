@@ -250,6 +250,11 @@ int cnn_forward_ws(const ising_cnn* net, const ising_problem* p, const int8_t* s
 int propose_clusters_launch(const ising_problem* const* probs, int32_t m, int8_t* spins, int32_t B,
                             const float* logits, int32_t* accepted, int accumulate, cudaStream_t st);
 
+// Partner moves (clusters.cu; ising_transcribe), adding to `accepted` when
+// accumulate is 1.
+int transcribe_launch(const ising_problem* const* probs, int32_t m, const int8_t* spins, int8_t* out, int32_t B,
+                      int32_t shift, int32_t* accepted, int accumulate, cudaStream_t st);
+
 size_t batched_smem_bytes(int32_t H, int32_t Y);
 cudaError_t batched_prepare(size_t smem);
 cudaError_t launch_batched(const BatchArgs& a, int grid, int threads, size_t smem, cudaStream_t stream);

@@ -116,3 +116,39 @@ def test_cluster_proposals_stacked_problems_and_degenerate_masks(ia):
     assert e.value.code == -8
     for p in probs + [other, big]:
         p.destroy()
+
+
+@pytest.mark.parametrize("X,Y,B,shift", [(12, 8, 5, 1), (12, 8, 5, 2), (50, 50, 3, 1), (200, 100, 2, 1), (16, 10, 4, 4)])
+def test_partner_moves_match_oracle(ia, X, Y, B, shift):
+    import torch
+    inst = synth.torus_instance(X, Y, 400 + X)
+    prob = ia.Problem.from_instance(inst)
+    s = synth.random_spins(B, X * Y, 40 + X)
+    sd = torch.from_numpy(s).cuda()
+    out, acc = ia.transcribe(prob, sd, shift)
+    torch.cuda.synchronize()
+    rs, racc = ocnn.transcribe(s, shift, inst["w_right"], inst["w_down"])
+    np.testing.assert_array_equal(out.cpu().numpy(), rs)
+    np.testing.assert_array_equal(acc.cpu().numpy(), racc)
+    assert (sd.cpu().numpy() == s).all()                      # the input is not modified
+    prob.destroy()
+
+
+def test_partner_moves_on_annealed_states_of_stacked_problems(ia):
+    import torch
+    X, Y, T = 24, 12, 8
+    insts = [synth.torus_instance(X, Y, 500 + q) for q in range(2)]
+    probs = [ia.Problem.from_instance(i) for i in insts]
+    betas = synth.linear_betas(0.1, 3.0, 200)
+    s = torch.cat([ia.anneal(p, T, betas, 31 + q)[0] for q, p in enumerate(probs)]).contiguous()
+    out, acc = ia.transcribe(probs, s, 3)
+    torch.cuda.synchronize()
+    sn = s.cpu().numpy()
+    for q, inst in enumerate(insts):
+        rs, racc = ocnn.transcribe(sn[q * T:(q + 1) * T], 3, inst["w_right"], inst["w_down"])
+        np.testing.assert_array_equal(out.cpu().numpy()[q * T:(q + 1) * T], rs)
+        np.testing.assert_array_equal(acc.cpu().numpy()[q * T:(q + 1) * T], racc)
+    with pytest.raises(ia.IsingError):
+        ia.transcribe(probs, s, 1, out=s)                      # out may not alias the input
+    for p in probs:
+        p.destroy()

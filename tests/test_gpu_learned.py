@@ -142,28 +142,35 @@ def test_window_and_batched_forms_equal_the_chunked_loop(ia):
         p.destroy()
 
 
-def _host_loop(ia, probs, net, T, betas, seeds, k_first, every):
+def _host_loop(ia, probs, net, T, betas, seeds, k_first, every, partner_period=0, warm=False):
     """The learned form step by step through the single-call ABI: per problem
-    the sweeps before the window, then per chunk each problem's sweeps
-    (resumed), logits, and one cluster-proposal call over all problems."""
+    the sweeps before the window (after the warm start), then per chunk each
+    problem's sweeps (resumed), the network's logits and one cluster-proposal
+    call over all problems, then the partner moves."""
     import torch
     states = []
     for p, sd in zip(probs, seeds):
-        s, _ = ia.anneal(p, T, betas[:k_first], sd)
+        if warm:
+            s0, _ = ia.anneal(p, T, np.zeros(0), sd)
+            ia.propose(p, s0, net.forward(p, s0), 0)
+            s, _ = ia.anneal(p, T, betas[:k_first], sd, init=s0)
+        else:
+            s, _ = ia.anneal(p, T, betas[:k_first], sd)
         states.append(s)
     s = torch.cat(states, 0).contiguous()
     logits_seen = []
-    for k0 in range(k_first, len(betas), every):
-        parts, zs = [], []
+    for j, k0 in enumerate(range(k_first, len(betas), every)):
+        parts = []
         for q, (p, sd) in enumerate(zip(probs, seeds)):
             sq, _ = ia.anneal(p, T, betas[k0:k0 + every], sd, sweep_offset=k0, init=s[q * T:(q + 1) * T].contiguous())
             parts.append(sq)
         s = torch.cat(parts, 0).contiguous()
-        for q, p in enumerate(probs):
-            zs.append(net.forward(p, s[q * T:(q + 1) * T].contiguous()))
-        z = torch.cat(zs, 0).contiguous()
-        logits_seen.append(z.cpu().numpy())
-        ia.propose_clusters(probs, s, z)
+        if net is not None:
+            z = torch.cat([net.forward(p, s[q * T:(q + 1) * T].contiguous()) for q, p in enumerate(probs)]).contiguous()
+            logits_seen.append(z.cpu().numpy())
+            ia.propose_clusters(probs, s, z)
+        if partner_period:
+            s, _ = ia.transcribe(probs, s, 1 + j % partner_period)
     cuts = torch.cat([ia.cut(p, s[q * T:(q + 1) * T].contiguous()) for q, p in enumerate(probs)])
     return s, cuts, logits_seen
 
@@ -212,6 +219,52 @@ def test_learned_plan_equals_plain_without_chunks_and_the_host_loop_with_them(ia
     torch.cuda.synchronize()
     assert torch.equal(s, hs) and torch.equal(c, hc)
     plan.destroy()
+    net.destroy()
+    for p in probs:
+        p.destroy()
+
+
+def test_learned_plan_partner_moves_and_warm_start(ia):
+    import torch
+    X, Y, T, S, every = 20, 10, 24, 400, 100
+    insts = [synth.torus_instance(X, Y, 320 + q) for q in range(2)]
+    probs = [ia.Problem.from_instance(i) for i in insts]
+    betas = synth.linear_betas(0.1, 3.0, S)
+    seeds = [77, 78]
+    params = ocnn.init_params(9, scale=0.8)
+    params[ocnn.N_PARAMS - 1] = -0.5
+    net = ia.CNN(params)
+    cases = [dict(net=None, partner_period=3, warm=False, k_first=100),
+             dict(net=net, partner_period=2, warm=False, k_first=200),
+             dict(net=net, partner_period=0, warm=True, k_first=100),
+             dict(net=net, partner_period=1, warm=True, k_first=0)]
+    for cs in cases:
+        plan = ia.LearnedPlan(probs, cs["net"], T, betas, seeds, k_first=cs["k_first"], every=every,
+                              partner_period=cs["partner_period"], warm=cs["warm"])
+        hs, hc, logits_seen = _host_loop(ia, probs, cs["net"], T, betas, seeds, cs["k_first"], every,
+                                         cs["partner_period"], cs["warm"])
+        for _ in range(2):
+            s, c, acc = plan.launch()
+            torch.cuda.synchronize()
+            assert torch.equal(s, hs) and torch.equal(c, hc), cs
+        plan.destroy()
+        if cs["warm"]:
+            continue
+        # the oracle fed the same logits: chunks, network block flips, partner moves
+        rs_all = [oracle.anneal(inst, betas[:cs["k_first"]], seeds[q], t_count=T)[0] for q, inst in enumerate(insts)]
+        for j, k0 in enumerate(range(cs["k_first"], S, every)):
+            rs_all = [oracle.anneal(inst, betas[k0:k0 + every], seeds[q], t_count=T, sweep_offset=k0,
+                                    init=rs_all[q])[0] for q, inst in enumerate(insts)]
+            if cs["net"] is not None:
+                rs_all = [ocnn.propose_clusters(rs_all[q], logits_seen[j][q * T:(q + 1) * T], inst["w_right"],
+                                                inst["w_down"])[0] for q, inst in enumerate(insts)]
+            if cs["partner_period"]:
+                rs_all = [ocnn.transcribe(rs_all[q], 1 + j % cs["partner_period"], inst["w_right"], inst["w_down"])[0]
+                          for q, inst in enumerate(insts)]
+        for q, inst in enumerate(insts):
+            np.testing.assert_array_equal(hs[q * T:(q + 1) * T].cpu().numpy(), rs_all[q])
+            np.testing.assert_array_equal(hc[q * T:(q + 1) * T].cpu().numpy(),
+                                          np.array([oracle.cut_csr(inst, r) for r in rs_all[q]]))
     net.destroy()
     for p in probs:
         p.destroy()
