@@ -56,7 +56,7 @@ IMAD_OPS_PER_UPDATE = 10
 # configuration: 427,008 + 360,704 bytes
 FLOW_TRAFFIC_BYTES = 427008 + 360704
 # the headline line stays well inside what a log tail keeps
-HEADLINE_MAX_BYTES = 4096
+HEADLINE_MAX_BYTES = 6144
 HEADLINE_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                  "scaling", "vs_baseline", "dtype", "data", "config", "e2e", "gpu_launches", "roofline",
                  "cpu_baseline", "clocks")
@@ -448,151 +448,183 @@ def campaign_leg(args):
     return out
 
 
-def learned_leg(args, budgets=(1000, 3000, 10000, 30000), every=100, tile=10, n_train=256, train_sweeps=1000,
-                steps=800, end_window=500):
-    """Config 5 of the workload set: 200x100 tori, 8 seeds x 512 trials, the
-    plain annealer against the learned form (network trained on 20,000-spin
-    snapshots of the plain annealer on held-out seeds), on the sweep-budget
-    ladder.  Per seed: best = the highest cut either form found at any budget,
-    target = ceil(0.999 best); per (form, budget): P_s, r and
-    TTT = (batch wall time / trials) * r (Eq. 3, 5)."""
+def _train_droplet_net(X, Y, seeds, trials, S_train, steps, init_seed=3):
+    """The network trained on droplet targets: `trials` plain anneals of each
+    held-out instance (seeds), targets = the improving components of each
+    final state's disagreement with the instance's best state."""
     import torch
     import paper_2505_18508_gb300 as ia
-    from paper_2505_18508_gb300 import learned, stats
+    from paper_2505_18508_gb300 import learned
     t0 = time.perf_counter()
-    tb = synth.linear_betas(0.1, 3.0, train_sweeps)
-    train = [synth.torus_instance(200, 100, 40000 + k) for k in range(n_train)]
-    data = learned.make_dataset(train, tb, every, snap_trials=4, target="future")
-    net = ia.CNN(synth.cnn_init_params(3, scale=0.7))
-    losses = learned.train(net, data, steps, batch=16, lr=2e-3, log_every=steps // 4)
+    probs = [ia.Problem.from_instance(synth.torus_instance(X, Y, sd)) for sd in seeds]
+    data = learned.droplet_dataset(probs, trials, synth.linear_betas(0.1, 3.0, S_train))
+    pos = float(np.mean([float(y.float().mean().item()) for _, _, y, _ in data]))
+    net = ia.CNN(synth.cnn_init_params(init_seed, scale=0.7))
+    losses = learned.train(net, data, steps, batch=16, lr=2e-3, log_every=max(1, steps // 4))
     torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    for d in data:
-        d[0].destroy()
-    T = 512
-    # the network's forward pass on this workload (one proposal round's logits)
-    prob = ia.Problem.from_instance(synth.torus_instance(200, 100, 30000))
-    s0 = torch.from_numpy(synth.random_spins(T, prob.n, 1)).cuda()
-    z = torch.empty((T, prob.n), dtype=torch.float32, device="cuda")
-    for _ in range(3):
-        net.forward(prob, s0, out=z)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(10):
-        net.forward(prob, s0, out=z)
-    e1.record()
-    torch.cuda.synchronize()
-    fwd_ms = e0.elapsed_time(e1) / 10
-    sites = T * prob.n
-    fwd_gbs = CNN_BYTES_PER_SITE * sites / (fwd_ms * 1e-3) / 1e9
-    cnn = {"forward_ms": fwd_ms, "sites": sites,
-           "useful_tflops": CNN_FLOP_PER_SITE * sites / (fwd_ms * 1e-3) / 1e12,
-           "algorithmic_gbs": fwd_gbs, "hbm_frac": fwd_gbs / PEAK_HBM_GBS,
-           "note": "forward = 4 tcgen05 convolution launches; 389 algorithmic HBM bytes per site; "
-                   "hbm_frac of measured copy bandwidth"}
-    prob.destroy()
-    # forms, instance by instance: the plain annealer; the learned form with
-    # proposals every `every` sweeps over the whole schedule (config 5 as
-    # stated); and the same with proposals only in the last `end_window`
-    # sweeps, where the annealer has cooled and only coordinated block flips
-    # can still lower the energy.  Batched forms, all 8 instances at once: the
-    # plain annealer in one persistent launch, and learned_end with the sweeps
-    # before its window in one persistent launch.  A batched form's results
-    # equal its per-instance form's (checked below); only the wall time, shared
-    # by the 8 x T trials, differs.
-    forms = ("plain", "learned", "learned_end")
-    bforms = {"plain_batched": "plain", "learned_end_batched": "learned_end"}
-    probs = [ia.Problem.from_instance(synth.torus_instance(200, 100, 30000 + q)) for q in range(8)]
-    seeds = [70000 + q for q in range(8)]
-    runs = [{S: {} for S in budgets} for _ in probs]
-    batched_same = True
-    for S in budgets:
-        betas = synth.linear_betas(0.1, 3.0, S)
-        end_start = max(0, S - end_window)
-        for q, (prob, seed) in enumerate(zip(probs, seeds)):
-            for name in forms:
-                st = {}
-                torch.cuda.synchronize(); a = time.perf_counter()
-                if name == "plain":
-                    _, c = ia.anneal(prob, T, betas, seed)
-                else:
-                    start = 0 if name == "learned" else end_start
-                    _, c = learned.anneal_learned(prob, net, T, betas, seed, every=every, tile=tile, stats=st,
-                                                  start=start)
-                torch.cuda.synchronize(); b = time.perf_counter()
-                runs[q][S][name] = (c.cpu().numpy(), b - a, st.get("accepted_per_trial"))
-        for name, base in bforms.items():
-            torch.cuda.synchronize(); a = time.perf_counter()
-            if name == "plain_batched":
-                _, cs = ia.anneal_batched(probs, [T] * 8, [S] * 8, [betas] * 8, seeds)
-            else:
-                _, cs = learned.anneal_learned_batched(probs, net, T, betas, seeds, every=every, tile=tile,
-                                                       start=end_start)
-            torch.cuda.synchronize(); b = time.perf_counter()
-            for q in range(8):
-                c = cs[q].cpu().numpy()
-                batched_same = batched_same and bool(np.array_equal(c, runs[q][S][base][0]))
-                runs[q][S][name] = (c, (b - a) / 8, None)   # the batch's wall time per instance
-    rows = []
-    allforms = forms + tuple(bforms)
-    for q in range(8):
-        best = int(max(max(v[f][0].max() for f in forms) for v in runs[q].values()))
-        tgt = stats.target_cut(best)
-        row = {"seed": 30000 + q, "best": best, "target": tgt}
+    for p in probs:
+        p.destroy()
+    p_hat = min(max(pos, 1e-9), 1 - 1e-9)
+    return net, {"instances": len(seeds), "trials": trials, "sweeps": S_train, "steps": steps,
+                 "target_positive_fraction": pos, "loss": losses,
+                 "base_rate_entropy": -(p_hat * math.log(p_hat) + (1 - p_hat) * math.log(1 - p_hat)),
+                 "seconds": time.perf_counter() - t0}
+
+
+def _run_forms(X, Y, eval_seeds, seed0, T, budgets, window, every, forms, warm=False):
+    """Every form on every evaluation instance and budget, 8 instances per
+    launch (one CUDA graph per form and budget).  forms: name -> (net or
+    None, partner period) or None for the plain annealer.  Returns
+    {(S, instance seed): {form: (cuts, wall ms per instance, accepted)}}."""
+    import torch
+    import paper_2505_18508_gb300 as ia
+    res = {}
+    for g0 in range(0, len(eval_seeds), 8):
+        group = eval_seeds[g0:g0 + 8]
+        probs = [ia.Problem.from_instance(synth.torus_instance(X, Y, sd)) for sd in group]
+        seeds = [seed0 + sd for sd in group]
+        m = len(group)
         for S in budgets:
-            for name in allforms:
-                cuts, wall, acc = runs[q][S][name]
-                Ps = stats.success_probability(cuts, tgt)
-                r = stats.repetitions(Ps)
-                e = {"P_s": Ps, "mean_cut": float(cuts.mean()), "wall_s": wall,
-                     "TTT_s": (wall / T) * r if math.isfinite(r) else None}
-                if acc is not None:
-                    e["accepted_per_trial"] = acc
-                row[f"{name}@{S}"] = e
-        rows.append(row)
-    for prob in probs:
-        prob.destroy()
+            betas = synth.linear_betas(0.1, 3.0, S)
+            kf = max(0, S - window)
+            for name, spec in forms.items():
+                if spec is None:
+                    plan = ia.BatchPlan(probs, [T] * m, [S] * m, [betas] * m, seeds, want_spins=False)
+                else:
+                    net, period = spec
+                    plan = ia.LearnedPlan(probs, net, T, betas, seeds, k_first=kf, every=every, partner_period=period,
+                                          warm=warm and net is not None)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                out = plan.launch()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                if spec is None:
+                    cuts, acc = torch.cat(out[1]).cpu().numpy().reshape(m, T), None
+                else:
+                    cuts = out[1].cpu().numpy().reshape(m, T)
+                    acc = out[2].double().reshape(m, T).mean(dim=1).cpu().numpy()
+                for q, sd in enumerate(group):
+                    res.setdefault((S, sd), {})[name] = (cuts[q], ms / m, None if acc is None else float(acc[q]))
+                plan.destroy()
+        for p in probs:
+            p.destroy()
+    return res
+
+
+def _form_stats(res, names, T):
+    """Per instance: target = ceil(0.999 best) over the forms `names` and every
+    budget (Eq. 3-5 with the paper's 99.9 % style); per form and budget the
+    mean and standard error over instances of P_s, and per instance the
+    form's best time-to-target over the budgets (TTT = wall per trial x r)."""
+    from paper_2505_18508_gb300 import stats
+    budgets = sorted({S for S, _ in res})
+    insts = sorted({sd for _, sd in res})
+    ps = {(f, S): [] for f in names for S in budgets}
+    ttt = {f: [] for f in names}
+    for sd in insts:
+        best = max(int(res[(S, sd)][f][0].max()) for S in budgets for f in names)
+        tgt = stats.target_cut(best)
+        best_t = {f: math.inf for f in names}
+        for S in budgets:
+            for f in names:
+                cuts, ms, _ = res[(S, sd)][f]
+                P = stats.success_probability(cuts, tgt)
+                ps[(f, S)].append(P)
+                r = stats.repetitions(P)
+                if math.isfinite(r):
+                    best_t[f] = min(best_t[f], ms / 1e3 / T * r)
+        for f in names:
+            ttt[f].append(best_t[f])
+    k = len(insts)
+    out = {"P_s": {f"{f}@{S}": [float(np.mean(v)), float(np.std(v, ddof=1) / math.sqrt(k)) if k > 1 else 0.0]
+                   for (f, S), v in ps.items()}}
+    out["TTT_s"] = {}
+    for f, v in ttt.items():
+        fin = [x for x in v if math.isfinite(x)]
+        out["TTT_s"][f] = {"median": float(np.median(v)) if len(fin) * 2 > k else None, "reached": len(fin),
+                           "mean_reached": float(np.mean(fin)) if fin else None,
+                           "se_reached": float(np.std(fin, ddof=1) / math.sqrt(len(fin))) if len(fin) > 1 else None}
+    return out
+
+
+def _cut_stats(res, names):
+    budgets = sorted({S for S, _ in res})
+    return {f"{f}@{S}": {"mean_cut": float(np.mean([res[k][f][0].mean() for k in res if k[0] == S])),
+                         "best_cut_mean": float(np.mean([res[k][f][0].max() for k in res if k[0] == S])),
+                         "wall_ms_per_instance": float(np.mean([res[k][f][1] for k in res if k[0] == S])),
+                         "accepted_per_trial": (float(np.mean([res[k][f][2] for k in res if k[0] == S]))
+                                                if res[next(iter(res))][f][2] is not None else None)}
+            for f in names for S in budgets}
+
+
+def learned_leg(args):
+    """Config 5 of the workload set: 200x100 tori, 16 evaluation instances
+    (seeds 30000-30015) x 512 trials, beta 0.1 -> 3.0 over S sweeps on a
+    budget ladder; the network trained on droplet targets of 20,000-spin
+    instances (seeds 40000-40255).  Forms, each one CUDA graph over 8
+    instances: the plain annealer; the network's cluster block flips after
+    every 100-sweep chunk of the last `window` sweeps (trained, and untrained
+    for what training adds); partner moves in the same window; both.
+    Statistics per instance against 99.9 % of the best cut any form found."""
+    X, Y, T = 200, 100, 512
+    net, train = _train_droplet_net(X, Y, list(range(40000, 40000 + args.learned_train)), 16, 10000, 800)
+    import paper_2505_18508_gb300 as ia
+    untrained = ia.CNN(synth.cnn_init_params(3, scale=0.7))
+    budgets = [int(b) for b in args.learned_budgets.split(",")]
+    forms = {"plain": None, "learned": (net, 0), "untrained": (untrained, 0), "partner": (None, 7),
+             "learned_partner": (net, 7)}
+    res = _run_forms(X, Y, list(range(30000, 30000 + args.learned_seeds)), 40000, T, budgets, 1000, 100, forms)
     net.destroy()
+    untrained.destroy()
+    names = list(forms)
+    all_forms = _form_stats(res, names, T)
+    net_only = _form_stats(res, ["plain", "learned", "untrained"], T)
+    top = str(max(budgets))
+    return {"summary": {"P_s@" + top: {f: all_forms["P_s"][f"{f}@{top}"] for f in names},
+                        "median_TTT_s": {f: all_forms["TTT_s"][f]["median"] for f in names},
+                        "TTT_reached": {f: all_forms["TTT_s"][f]["reached"] for f in names},
+                        "network_only_P_s@" + top: {f: net_only["P_s"][f"{f}@{top}"]
+                                                    for f in ("plain", "learned", "untrained")},
+                        "instances": len({sd for _, sd in res})},
+            "workload": f"200x100 tori, instance seeds 30000-{30000 + args.learned_seeds - 1}, 512 trials each, "
+                        f"beta 0.1->3.0 over S sweeps, S in {budgets}; proposals after every 100-sweep chunk of the "
+                        "last 1,000 sweeps; each form one CUDA graph over 8 instances (wall time shared by 8 x 512 "
+                        "trials)",
+            "train": train, "targets_all_forms": all_forms, "targets_plain_and_network": net_only,
+            "cuts": _cut_stats(res, names)}
 
-    def med(key):
-        v = [r[key]["TTT_s"] for r in rows if r[key]["TTT_s"] is not None]
-        return float(np.median(v)) if len(v) == len(rows) else None
-    ladder = {f"{name}@{S}": {"median_TTT_s": med(f"{name}@{S}"),
-                              "reached": sum(r[f"{name}@{S}"]["TTT_s"] is not None for r in rows),
-                              "mean_P_s": float(np.mean([r[f"{name}@{S}"]["P_s"] for r in rows]))}
-              for S in budgets for name in allforms}
 
-    def best_budget(prefix):
-        c = [(v["median_TTT_s"], k) for k, v in ladder.items() if k.startswith(prefix) and v["median_TTT_s"]]
-        return min(c) if c else (None, None)
-    bp, bl, be = best_budget("plain@"), best_budget("learned@"), best_budget("learned_end@")
-    bpb, beb = best_budget("plain_batched@"), best_budget("learned_end_batched@")
-    best_med = {"plain": bp[0], "learned": bl[0], "learned_end": be[0], "plain_batched": bpb[0],
-                "learned_end_batched": beb[0]}
-    best_med_full = {"plain": bp, "learned": bl, "learned_end": be, "plain_batched": bpb, "learned_end_batched": beb}
-    summary = {"median_TTT_s": {k: best_med[k] for k in ("plain", "plain_batched", "learned_end",
-                                                          "learned_end_batched", "learned")},
-               "mean_P_s@30000": {f: ladder[f"{f}@30000"]["mean_P_s"] for f in allforms if f"{f}@30000" in ladder},
-               "seeds": len(rows)}
-    return {"summary": summary,
-            "workload": "200x100 tori, seeds 30000-30007, 512 trials each, beta 0.1->3.0 over S sweeps, "
-                        f"S in {list(budgets)}; proposals every {every} sweeps, tiles {tile}x{tile} "
-                        f"(learned: whole schedule; learned_end: last {end_window} sweeps); *_batched: the 8 "
-                        "instances in one persistent launch (learned_end_batched: up to its window), wall time "
-                        "shared by all 8 x 512 trials",
-            "batched_results_equal_per_instance": batched_same,
-            "train": {"instances": n_train, "snapshot_sweeps": train_sweeps, "steps": steps, "loss": losses,
-                      "seconds": t_train},
-            "cnn_forward": cnn,
-            "ladder": ladder,
-            "best_median_TTT_s": best_med_full,
-            "per_seed": rows}
+def learned100_leg(args):
+    """Config 4 of the workload set: 100x100 tori, 8 evaluation instances
+    (seeds 20000-20007) x 512 trials; the network trained on droplet targets
+    of 256 held-out instances (seeds 10000-10255); the learned form with a
+    warm start (the network's whole-lattice proposal on the start state) and
+    cluster block flips after every 100-sweep chunk of the last 1,000 sweeps,
+    against the plain annealer and partner moves."""
+    X, Y, T = 100, 100, 512
+    net, train = _train_droplet_net(X, Y, list(range(10000, 10256)), 8, 3000, 600, init_seed=5)
+    budgets = [1000, 3000, 10000]
+    forms = {"plain": None, "learned": (net, 0), "partner": (None, 7), "learned_partner": (net, 7)}
+    res = _run_forms(X, Y, list(range(20000, 20008)), 20000, T, budgets, 1000, 100, forms, warm=True)
+    net.destroy()
+    names = list(forms)
+    st = _form_stats(res, names, T)
+    return {"summary": {"P_s@10000": {f: st["P_s"][f"{f}@10000"] for f in names},
+                        "median_TTT_s": {f: st["TTT_s"][f]["median"] for f in names},
+                        "TTT_reached": {f: st["TTT_s"][f]["reached"] for f in names}},
+            "workload": "100x100 tori, instance seeds 20000-20007, 512 trials each, beta 0.1->3.0 over S sweeps, "
+                        f"S in {budgets}; warm start plus cluster block flips after every 100-sweep chunk of the last "
+                        "1,000 sweeps",
+            "train": train, "stats": st, "cuts": _cut_stats(res, names)}
 
 
 LEGS = {"draw16": draw16_leg, "batched": batched_leg, "graph": graph_leg, "pt": pt_leg, "trace": trace_leg,
-        "cnn": cnn_leg, "campaign": campaign_leg, "learned": learned_leg}
+        "cnn": cnn_leg, "campaign": campaign_leg, "learned": learned_leg, "learned100": learned100_leg}
 # legs the default run adds after the headline's timed region
-DEFAULT_LEGS = ("draw16", "batched", "graph", "pt", "campaign", "learned")
+DEFAULT_LEGS = ("draw16", "batched", "graph", "pt", "campaign", "learned", "learned100")
 
 
 def leg_summary(name, d):
@@ -611,7 +643,7 @@ def leg_summary(name, d):
         return {k: v["value"] for k, v in d.items()}
     if name == "campaign":
         return {"sweeps": [b["sweeps"] for b in d["budgets"]], "highest": [b["highest"] for b in d["budgets"]]}
-    if name == "learned":
+    if name in ("learned", "learned100"):
         return d.get("summary")
     if name == "cnn":
         return {"forward_ms": d["forward_ms"], "forward_hbm_frac": d["forward_hbm_frac"]}
@@ -620,8 +652,9 @@ def leg_summary(name, d):
 
 def headline_line(base, legs):
     """The last stdout line: the contract's keys, with every number rounded,
-    and a one-number summary per leg.  Raises if a key is missing or the line
-    outgrows HEADLINE_MAX_BYTES."""
+    and a one-number summary per leg.  Leg summaries are dropped, largest
+    first, while the line is longer than HEADLINE_MAX_BYTES; a line whose
+    contract keys alone are too long raises, as does a missing key."""
     line = {k: base[k] for k in HEADLINE_KEYS}
     for k in ("ttt_99_9",):
         if k in base:
@@ -629,6 +662,12 @@ def headline_line(base, legs):
     line["legs"] = {name: leg_summary(name, d) for name, d in legs.items()}
     line = _round(line)
     text = json.dumps(line, separators=(",", ":"))
+    while len(text) > HEADLINE_MAX_BYTES and any(v is not None and v != "on its own line"
+                                                 for v in line["legs"].values()):
+        big = max((k for k, v in line["legs"].items() if v is not None and v != "on its own line"),
+                  key=lambda k: len(json.dumps(line["legs"][k])))
+        line["legs"][big] = "on its own line"
+        text = json.dumps(line, separators=(",", ":"))
     if len(text) > HEADLINE_MAX_BYTES:
         raise ValueError(f"headline line is {len(text)} bytes (limit {HEADLINE_MAX_BYTES})")
     return text
@@ -713,6 +752,8 @@ def _parser():
     ap.add_argument("--budgets", default="1000,3000,10000,30000,100000,300000")
     ap.add_argument("--campaign-trials", type=int, default=512)
     ap.add_argument("--learned-seeds", type=int, default=16)
+    ap.add_argument("--learned-train", type=int, default=256)
+    ap.add_argument("--learned-budgets", default="3000,10000,30000")
     return ap
 
 

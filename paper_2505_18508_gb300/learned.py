@@ -24,12 +24,18 @@ Training data (held-out instances): the plain annealer's best state r of each
 instance (best cut over `ref_trials` trials of the full schedule) and
 snapshots s of other trials at the end of each chunk; targets are the
 gauge-aligned flip targets [s != +-r].
+
+The cluster form (LearnedPlan, one CUDA graph over several instances) uses
+connected-component block flips instead of tiles, trained on droplet
+targets (droplet_dataset): the improving components of each final state's
+disagreement with its instance's best state.  Its proposals can also take
+their blocks from a partner trial instead of the network (partner moves).
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import CNN, Problem, anneal, anneal_batched, cut, flip_targets, propose  # noqa: F401
+from . import CNN, Problem, anneal, anneal_batched, cut, droplet_targets, flip_targets, propose  # noqa: F401
 
 
 def _torch():
@@ -164,3 +170,20 @@ def anneal_learned_batched(probs, net, trials, betas, seeds, every=100, tile=10,
         spins.append(s)
         cuts.append(cut(p, s))
     return spins, cuts
+
+
+def droplet_dataset(probs, trials, betas, seed=50000):
+    """[(Problem, final states int8 [trials, n], droplet targets uint8
+    [trials, n], best cut)] for each problem: `trials` plain anneals of the
+    full schedule (all problems in batched launches of up to 8), targets
+    against the best final state of the problem (ising_droplet_targets)."""
+    data = []
+    for g0 in range(0, len(probs), 8):
+        group = probs[g0:g0 + 8]
+        spins, cuts = anneal_batched(group, [trials] * len(group), [len(betas)] * len(group), [betas] * len(group),
+                                     [seed + g0 + q for q in range(len(group))])
+        for p, s, c in zip(group, spins, cuts):
+            best = s[int(c.argmax().item())]
+            y = droplet_targets(p, s, best.expand(s.shape[0], -1).contiguous())
+            data.append((p, s, y, int(c.max().item())))
+    return data

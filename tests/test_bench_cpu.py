@@ -65,13 +65,21 @@ def test_headline_has_the_contract_keys_and_is_compact():
     assert len(line["legs"]["trace"]["error"]) <= 200
 
 
+def test_oversized_leg_summaries_are_moved_off_the_headline():
+    legs = _legs()
+    legs["learned"]["summary"]["padding"] = ["x" * 50] * 200
+    line = json.loads(bench.headline_line(_base(), legs))
+    assert line["legs"]["learned"] == "on its own line"
+    assert line["legs"]["campaign"]["highest"][0] == 13800      # the others stay
+
+
 def test_headline_rejects_missing_keys_and_oversize():
     base = _base()
     del base["roofline"]
     with pytest.raises(KeyError):
         bench.headline_line(base, {})
     base = _base()
-    base["config"]["padding"] = "x" * 5000
+    base["config"]["padding"] = "x" * 7000
     with pytest.raises(ValueError):
         bench.headline_line(base, {})
 
