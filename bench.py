@@ -51,10 +51,10 @@ IMAD_LANES_PER_SM = 64
 # Philox4x32-10 multiplies per spin update: 10 rounds x 2 products x 2 halves / 4 draws
 IMAD_OPS_PER_UPDATE = 10
 # DRAM bytes (read + write) of one launch of the persistent annealing kernel
-# on this workload, from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, --clock-control none) of the same launch
-# configuration: 427,008 + 360,704 bytes
-FLOW_TRAFFIC_BYTES = 427008 + 360704
+# on this workload (the timed launch, after the L2 flush), from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, --clock-control none) of the
+# same launch configuration: 3,460,352 + 132,864 bytes
+FLOW_TRAFFIC_BYTES = 3460352 + 132864
 # the headline line stays well inside what a log tail keeps
 HEADLINE_MAX_BYTES = 6144
 HEADLINE_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
