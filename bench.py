@@ -597,6 +597,41 @@ def learned_leg(args):
             "cuts": _cut_stats(res, names)}
 
 
+def partner_leg(args):
+    """The cost of the partner moves inside the plan: 8 tori 200x100 x 512
+    trials, beta 0.1 -> 3.0 over --leg-sweeps sweeps, the plain annealer
+    (one batched graph) against the same with partner moves after every
+    100-sweep chunk of the last 1,000 sweeps (one learned-plan graph), each
+    replayed --reps times after one warm-up replay (CUDA events)."""
+    import torch
+    import paper_2505_18508_gb300 as ia
+    X, Y, T, S = 200, 100, 512, args.leg_sweeps
+    probs = [ia.Problem.from_instance(synth.torus_instance(X, Y, 30000 + q)) for q in range(8)]
+    seeds = [70000 + q for q in range(8)]
+    betas = synth.linear_betas(0.1, 3.0, S)
+    plans = {"plain": ia.BatchPlan(probs, [T] * 8, [S] * 8, [betas] * 8, seeds, want_spins=False),
+             "partner": ia.LearnedPlan(probs, None, T, betas, seeds, k_first=max(0, S - 1000), every=100,
+                                       partner_period=7)}
+    out = {"workload": f"8 tori 200x100, 512 trials, {S} sweeps; partner moves after every 100-sweep chunk of the "
+                       "last 1,000 sweeps"}
+    for name, plan in plans.items():
+        plan.launch()
+        torch.cuda.synchronize()
+        ms = _cuda_time(plan.launch, args.reps)
+        res = plan.launch()
+        torch.cuda.synchronize()
+        cuts = torch.cat(res[1]) if name == "plain" else res[1]
+        out[name] = {"ms_per_replay": ms, "mean_cut": float(cuts.double().mean().item()),
+                     "best_cut_mean": float(cuts.reshape(8, T).max(dim=1).values.double().mean().item())}
+        if name == "partner":
+            out[name]["components_per_trial"] = float(res[2].double().mean().item())
+        plan.destroy()
+    out["overhead"] = out["partner"]["ms_per_replay"] / out["plain"]["ms_per_replay"] - 1.0
+    for p in probs:
+        p.destroy()
+    return out
+
+
 def learned100_leg(args):
     """Config 4 of the workload set: 100x100 tori, 8 evaluation instances
     (seeds 20000-20007) x 512 trials; the network trained on droplet targets
@@ -622,7 +657,8 @@ def learned100_leg(args):
 
 
 LEGS = {"draw16": draw16_leg, "batched": batched_leg, "graph": graph_leg, "pt": pt_leg, "trace": trace_leg,
-        "cnn": cnn_leg, "campaign": campaign_leg, "learned": learned_leg, "learned100": learned100_leg}
+        "cnn": cnn_leg, "campaign": campaign_leg, "learned": learned_leg, "learned100": learned100_leg,
+        "partner": partner_leg}
 # legs the default run adds after the headline's timed region
 DEFAULT_LEGS = ("draw16", "batched", "graph", "pt", "campaign", "learned", "learned100")
 
@@ -637,6 +673,8 @@ def leg_summary(name, d):
         return {"value": d["value"], "frac": d["roofline"]["frac"]}
     if name in ("batched", "trace"):
         return {"value": d["value"]}
+    if name == "partner":
+        return {"overhead": d["overhead"]}
     if name == "pt":
         return {"value": d["value"], "coldest_best_cut": d["coldest"]["best_cut"]}
     if name == "graph":
