@@ -218,12 +218,14 @@ __device__ __forceinline__ uint32_t update_word_m(uint32_t s, uint32_t nl, uint3
                                                  uint32_t mL, uint32_t mR, uint32_t mU, uint32_t mD, uint32_t i,
                                                  const Heads& heads, int nq, uint32_t T4, uint32_t T8,
                                                  const uint32_t* __restrict__ rk) {
+  // per trial: eX set where the edge to neighbour X is unsatisfied
+  // (w s s' = +1, it adds to the energy); ge2: two or more (dE <= 0, always
+  // flip), any: at least one (dE = 4 when not ge2, else dE = 8)
   const uint32_t eL = ~(s ^ nl ^ mL), eR = ~(s ^ nr ^ mR);
   const uint32_t eU = ~(s ^ nu ^ mU), eD = ~(s ^ nd ^ mD);
-  const uint32_t any = eL | eR | eU | eD;
-  const uint32_t eq1 = ((eL ^ eR) ^ (eU ^ eD)) & ~((eL & eR) | (eU & eD));
-  const uint32_t eq0 = ~any;
-  const uint32_t ge2 = any & ~eq1;
+  const uint32_t abc = eL | eR | eU;
+  const uint32_t any = abc | eD;
+  const uint32_t ge2 = (eL & eR) | (eU & (eL | eR)) | (eD & abc);
   // site-dependent products of rounds 1 and 2
   uint32_t hi0, lo0, hi1, lo1;
   mulhilo(kPhiloxM0, i, hi0, lo0);
@@ -244,7 +246,8 @@ __device__ __forceinline__ uint32_t update_word_m(uint32_t s, uint32_t nl, uint3
       for (int j = nq - 1; j >= 0; --j) quad_step(rej4, rej8, heads(j), hi1, lo1, lo0, T4, T8, rk);
     }
   }
-  return s ^ (ge2 | (eq1 & ~rej4) | (eq0 & ~rej8));
+  // ge2 trials flip whatever their draws; the others by their class's compare
+  return s ^ (ge2 | (any & ~rej4) | (~any & ~rej8));
 }
 
 // The same with the edge signs as the flag byte f (bit 0: left edge has

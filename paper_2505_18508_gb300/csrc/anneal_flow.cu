@@ -389,7 +389,8 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   //         the own row's colour-c counter << 16},
   // where run is the item's increment of that counter (see the item table)
   // and mirror marks rows that exchange words with another CTA through the
-  // global mirror (their chunks take the general path).  Per colour and
+  // global mirror; it is then set on every item of the chunks that take the
+  // general path (a mirror row, or more than 32 counters).  Per colour and
   // chunk, 32 counter addresses: the colour-(1-c) counters of every row the
   // chunk's items read (own, above, below), then the idle row's saturated
   // counter; ~0 when they are more than 32 (the chunk then takes the general
@@ -446,11 +447,22 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       for (int l = 0; l < 32; ++l)
         out[l] = (over && l == 31) ? 0xFFFFFFFFu : cnt32 + 4u * (l < nl ? list[l] : base + static_cast<uint32_t>(nloc));
     }
+    __syncthreads();
+    // a chunk with a mirror row or too many counters takes the general path
+    // as a whole: the mirror bit of every item of it is set, so that the
+    // loop branches on one record field, the same in every lane
+    for (int idx = tid; idx < 2 * NC; idx += kFlowThreads) {
+      const int c = idx / NC, kc = idx - c * NC;
+      uint4* r1 = sm.rec + 2 * cap + static_cast<uint32_t>(c) * cap + 32u * static_cast<uint32_t>(kc);
+      bool gen = sm.ccnt[(static_cast<size_t>(c) * (cap >> 5) + kc) * 32 + 31] == 0xFFFFFFFFu;
+      for (int l = 0; l < 32; ++l) gen = gen || ((r1[l].w >> 8) & 1u) != 0u;
+      if (gen)
+        for (int l = 0; l < 32; ++l) r1[l].w |= 1u << 8;
+    }
   }
   __syncthreads();
 
   // ---- the half-sweeps, chunk by chunk
-  const long long M = 2LL * a.S * NC;
   uint4* wh = sm.whead + warp * (kMaxSeg * 8);
   uint2* wt = sm.wthr + warp * kMaxSeg;
   const uint32_t fl32 = smem_addr(sm.fl);
@@ -459,9 +471,10 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   const uint32_t cc32 = smem_addr(sm.ccnt) + 4u * lane;
   int head_kk = -1;
   uint32_t T4 = 0, T8 = 0;
-  int hs = 0, k = warp;
+  int hs = 0, k = warp;   // this warp's chunk: half-sweep hs, chunk k of it
   while (k >= NC && NC > 0) { k -= NC; ++hs; }
-  for (long long m = warp; m < M; m += kFlowWarps) {
+  const int HS = NC > 0 ? 2 * a.S : 0;
+  while (hs < HS) {
     const int kk = hs >> 1, c = hs & 1;
     if (kk != head_kk) {   // Philox heads and thresholds of this sweep
       __syncwarp();
@@ -485,20 +498,19 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
     const uint32_t ck = static_cast<uint32_t>(c) * (cap >> 5) + static_cast<uint32_t>(k);
     bool fast = false;
     uint4 R1;
-    uint32_t caddr = 0;
     if (a.use_rec) {
       R1 = lds_v4u(rec32 + rstride + 512u * ck);
-      caddr = lds_u32(cc32 + 128u * ck);
-      fast = !__any_sync(0xFFFFFFFFu, ((R1.w >> 8) & 1u) || caddr == 0xFFFFFFFFu);
+      fast = ((R1.w >> 8) & 1u) == 0u;   // the same in every lane of the chunk
     }
     if (fast) {
       // ---- fast path: the chunk reads and writes this CTA's shared memory
       // only; each lane acquires one of the counters the chunk waits for
+      const uint32_t caddr = lds_u32(cc32 + 128u * ck);
       const uint4 R0 = lds_v4u(rec32 + 512u * ck);
       const uint32_t v = ld_acquire_cta(caddr);
       if (!__all_sync(0xFFFFFFFFu, v >= need) || a.stall_test) {
         bool lane_ok = v >= need || wait_count<false>(nullptr, caddr, need, a);
-        if (a.stall_test && j == 0 && m == 0) lane_ok = lane_ok && wait_count<false>(nullptr, caddr, 0xFFFFFFFFu, a);
+        if (a.stall_test && j == 0 && hs == 0 && k == 0) lane_ok = lane_ok && wait_count<false>(nullptr, caddr, 0xFFFFFFFFu, a);
         if (!__all_sync(0xFFFFFFFFu, lane_ok)) break;
       }
       __syncwarp();   // every lane's reads after all lanes' acquires
@@ -545,7 +557,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
           lane_ok = gu ? wait_count<true>(a.gcnt + B.x, 0u, need, a) : wait_count<false>(nullptr, c_up, need, a);
         if (lane_ok && v2 < need)
           lane_ok = gd ? wait_count<true>(a.gcnt + B.y, 0u, need, a) : wait_count<false>(nullptr, c_dn, need, a);
-        if (a.stall_test && j == 0 && m == 0) lane_ok = lane_ok && wait_count<false>(nullptr, c_self, 0xFFFFFFFFu, a);
+        if (a.stall_test && j == 0 && hs == 0 && k == 0) lane_ok = lane_ok && wait_count<false>(nullptr, c_self, 0xFFFFFFFFu, a);
         if (!__all_sync(0xFFFFFFFFu, lane_ok)) break;
       }
       // the word, its left and right neighbours (the row's wrap at h = 0 / H - 1)
