@@ -474,8 +474,13 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   int hs = 0, k = warp;   // this warp's chunk: half-sweep hs, chunk k of it
   while (k >= NC && NC > 0) { k -= NC; ++hs; }
   const int HS = NC > 0 ? 2 * a.S : 0;
+  // sweep kk, colour c, the counter value the chunk's rows must have reached
+  // and the chunk's index in the records; they change only when the warp
+  // moves on to the next half-sweep
+  int kk = hs >> 1, c = hs & 1;
+  uint32_t need = static_cast<uint32_t>(H) * static_cast<uint32_t>(kk + c);
+  uint32_t ck = static_cast<uint32_t>(c) * (cap >> 5) + static_cast<uint32_t>(k);
   while (hs < HS) {
-    const int kk = hs >> 1, c = hs & 1;
     if (kk != head_kk) {   // Philox heads and thresholds of this sweep
       __syncwarp();
       if (lane < nseg * 8) {
@@ -494,8 +499,6 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       T8 = __ldg(a.thr + 2 * kk + 1);
       head_kk = kk;
     }
-    const uint32_t need = static_cast<uint32_t>(H) * static_cast<uint32_t>(kk + c);
-    const uint32_t ck = static_cast<uint32_t>(c) * (cap >> 5) + static_cast<uint32_t>(k);
     bool fast = false;
     uint4 R1;
     if (a.use_rec) {
@@ -591,7 +594,14 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       }
     }
     k += kFlowWarps;
-    while (k >= NC) { k -= NC; ++hs; }
+    ck += kFlowWarps;
+    if (k >= NC) {
+      do { k -= NC; ++hs; } while (k >= NC);
+      kk = hs >> 1;
+      c = hs & 1;
+      need = static_cast<uint32_t>(H) * static_cast<uint32_t>(kk + c);
+      ck = static_cast<uint32_t>(c) * (cap >> 5) + static_cast<uint32_t>(k);
+    }
   }
   __shared__ int s_stop;
   __syncthreads();
