@@ -514,7 +514,7 @@ size_t ising_cnn_workspace_bytes(int32_t B, int32_t n, int32_t train);
  * The convolutions run on the tensor cores; a device-side wait on them that
  * runs out (after about two seconds) leaves ISING_ERR_TIMEOUT in the
  * handle's status word (ising_get_status).
- * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (torus width above 640, or a
+ * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (torus width above 512, or a
  * general-graph handle), ISING_ERR_CUDA.
  */
 int ising_cnn_forward(const ising_cnn* net, const ising_problem* p, const int8_t* spins, int32_t B,
@@ -528,7 +528,7 @@ int ising_cnn_forward(const ising_cnn* net, const ising_problem* p, const int8_t
  * loss     device float (overwritten).
  * ws       device workspace of at least ising_cnn_workspace_bytes(B, n, 1).
  * Device-side timeouts as in ising_cnn_forward.  Errors: ISING_ERR_ARG,
- * ISING_ERR_UNSUPPORTED (torus width above 592, or a general-graph handle),
+ * ISING_ERR_UNSUPPORTED (torus width above 512, or a general-graph handle),
  * ISING_ERR_CUDA.
  */
 int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* spins, const uint8_t* targets,

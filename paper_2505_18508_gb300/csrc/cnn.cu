@@ -291,7 +291,8 @@ cudaError_t forward_pass(const ising_cnn* net, const ising_problem* p, const int
 }
 
 bool tc_supported(const ising_problem* p) {
-  return p->X <= 1024 && conv_tc_smem(1, p->X) <= 227 * 1024;
+  // four 32-column accumulators per 128-pixel tile within 512 tensor-memory columns
+  return p->X <= 512 && conv_tc_smem(1, p->X) <= 227 * 1024;
 }
 
 }  // namespace

@@ -17,16 +17,20 @@
 // Descriptor (SM100 shared-memory matrix descriptor, no swizzle): start >> 4,
 // leading byte offset (next 8-channel chunk) >> 4, stride byte offset (next
 // 8 pixels = 128 bytes) >> 4, version 1.  Instruction: kind::f16, BF16 A and
-// B, FP32 D, both K-major, M = 128, N = 16 or 32.
+// B, FP32 D, both K-major, M = 128, N = 16 to 96.
 //
-// Persistent CTAs of 256 threads (two warpgroups) walk consecutive output
-// rows, keeping a ring of five staged input rows (each new output row stages
-// one input row, three iterations ahead) and two TMEM accumulator buffers.
-// Per row: one thread issues the MMAs of every 128-pixel tile of the row
-// (9 taps x K/16 each) and commits to the buffer's mbarrier; meanwhile all
-// threads wait (bounded) for the previous row's MMAs, tcgen05.ld its
-// accumulator and run the fused epilogue.  The weight-gradient kernel below
-// uses 128 threads.
+// Persistent CTAs of 256 threads (two warpgroups) walk consecutive staged
+// input rows, keeping a ring of five of them (each iteration stages one,
+// three iterations ahead) and a ring of four TMEM accumulators (output rows)
+// per tile.  Per staged row: one thread issues, per 128-pixel tile, kx and K
+// step, one MMA into the accumulators of the up to three output rows the row
+// feeds (N = 32 per row, the ky weights side by side; measured on GB300, an
+// M = 128, K = 16 MMA takes about as long with N = 32 as with N = 96, so this
+// needs a third of the MMAs of one per output row and tap) and commits to an
+// mbarrier; meanwhile all threads wait (bounded) for the previous row's MMAs,
+// drain the output row they completed (tcgen05.ld, fused epilogue, zero the
+// accumulator for its next row).  The weight-gradient kernel below uses 128
+// threads.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -40,6 +44,7 @@ namespace {
 constexpr int kTcThreads = 128;        // weight-gradient kernel
 constexpr int kConvThreads = 256;      // convolution kernel: two warpgroups
 constexpr int kRing = 5;               // staged input rows per convolution CTA
+constexpr int kAcc = 4;                // output-row accumulators per tile (a power of two)
 constexpr long long kWaitCycles = 4000000000LL;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -103,6 +108,14 @@ __device__ __forceinline__ void tmem_ld<1>(uint32_t taddr, float* v) {
   v[0] = __uint_as_float(r);
 }
 
+// Zero 16 consecutive 32-bit columns of the calling warp's 32 lanes
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(
+                   taddr),
+               "r"(0u)
+               : "memory");
+}
+
 __device__ __forceinline__ int wrapi(int v, int m) { return v < 0 ? v + m : (v >= m ? v - m : v); }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
@@ -112,7 +125,7 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_group2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 
 // Bounded wait on an mbarrier phase by the calling thread: false when `limit`
 // cycles pass first.
@@ -135,16 +148,22 @@ __device__ __forceinline__ bool wait_mbar(uint32_t mbar, uint32_t phase, long lo
 // kOut: 0 = BF16 [P][32] relu(acc + bias); 1 = BF16 [P][32] acc * [mask > 0];
 //       2 = FP32 [P] acc(channel 0) + bias[0].
 //
-// Pipeline over the output rows y of one image (a CTA's rows split at image
-// boundaries into segments): input rows live in a ring of five slots (slot =
-// unwrapped row mod 5) and accumulators in two TMEM buffers (row mod 2).  In
-// iteration y: barrier (row y+1 staged, buffer y mod 2 drained) -> MMAs of row
-// y -> wait for the MMAs of row y-1 (frees slot y-2 and buffer y-1) -> start
-// copying row y+3 into slot y+3 = y-2 (cp.async) -> epilogue of row y-1 ->
-// wait for the copies of row y+2 (issued one iteration earlier).  Row y's
-// MMAs overlap row y-1's epilogue, and each row's loads have a whole
-// iteration to land.  256 threads: warp w drains TMEM lanes 32 (w mod 4) ..
-// and columns 16 (w / 4) .. of the accumulator.
+// Pipeline over the staged input rows r = ya-1 .. yb+1 of one image segment
+// ya..yb (a CTA's rows split at image boundaries): input rows live in a ring
+// of five slots (slot = unwrapped row mod 5), output rows in a ring of kAcc
+// = 4 accumulators per 128-pixel tile (row y in slot y mod 4).  Along the
+// columns the slots run in descending row order, so the rows r + 1, r, r - 1
+// that staged row r feeds (ky = 0, 1, 2) sit side by side: per tile, kx and K
+// step one MMA with N = 32 x (the valid ky) and B = those ky's weights side by
+// side, instead of one MMA per output row and tap with N = 32 (an MMA costs
+// about the same whether N is 32 or 96).  A window that wraps around the ring
+// takes two MMAs.  Accumulators start at zero and the epilogue zeroes each
+// one it drains, so every MMA accumulates.  Iteration r: barrier (row r
+// staged, row r + 1's accumulator drained) -> the MMAs of row r -> wait for
+// the MMAs of row r - 1 (frees slot r - 1; row r - 2 is complete) -> start
+// copying row r + 3 into slot r + 3 = r - 2 (cp.async) -> epilogue of row
+// r - 2 -> wait for the copies of row r + 1.  256 threads: warp w drains TMEM
+// lanes 32 (w mod 4) .. and columns 16 (w / 4) .. of an accumulator.
 template <int kIn, int kOut>
 __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) {
   constexpr int KC = kIn == 0 ? 2 : 4;          // 8-channel chunks of the input
@@ -164,13 +183,20 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  for (int i = tid; i < static_cast<int>(wbytes / 16); i += kConvThreads)
-    reinterpret_cast<uint4*>(sw)[i] = reinterpret_cast<const uint4*>(a.wt)[i];
+  // weights: the canonical [tap][chunk][N group][128 B] blocks reordered to
+  // [kx][chunk][ky][N group], so that the three ky of one (kx, chunk) form one
+  // B operand of N = 3 x 32 rows
+  for (int i = tid; i < static_cast<int>(wbytes / 16); i += kConvThreads) {
+    const int blk = i >> 3, tap = blk / (KC * NG), rem = blk - tap * (KC * NG), kc = rem / NG, ng = rem - kc * NG;
+    const int ky = tap / 3, kx = tap - 3 * ky;
+    const int dst = ((kx * KC + kc) * 3 + ky) * NG + ng;
+    reinterpret_cast<uint4*>(sw)[dst * 8 + (i & 7)] = reinterpret_cast<const uint4*>(a.wt)[i];
+  }
   for (int i = tid; i < static_cast<int>(kRing * slot_bytes / 16); i += kConvThreads)
     reinterpret_cast<uint4*>(srow)[i] = make_uint4(0, 0, 0, 0);   // padding: never rewritten
   const uint32_t bufcols = static_cast<uint32_t>(ntile * N);
   uint32_t tcols = 32;
-  while (tcols < 2 * bufcols) tcols <<= 1;
+  while (tcols < kAcc * bufcols) tcols <<= 1;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
                  "r"(tcols));
@@ -191,6 +217,16 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
 #pragma unroll
   for (int c = 0; c < 16; ++c) bias_r[c] = kOut == 0 ? __ldg(a.bias + half * 16 + c) : 0.f;
   const float bias0 = kOut == 2 ? __ldg(a.bias) : 0.f;
+  // accumulator of output row y, tile t: columns t * kAcc * N + N * (kAcc - 1 - y mod kAcc)
+  auto acc_col = [&](int t, int y) {
+    return static_cast<uint32_t>(t * kAcc * N + N * (kAcc - 1 - (y & (kAcc - 1))));
+  };
+  // every accumulator starts at zero (each warp clears its lanes and columns)
+  if (half * 16 < N) {
+    for (int t = 0; t < ntile; ++t)
+      for (int s = 0; s < kAcc; ++s) tmem_zero16(tmem + lane_off + static_cast<uint32_t>((t * kAcc + s) * N + half * 16));
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
 
   // stage unwrapped input row yu of image b into its ring slot
   auto stage = [&](int b, int yu) {
@@ -222,27 +258,37 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
   // and shared addresses stay below 256 KB, so offsets add without carries.
   const uint32_t lbo_a = static_cast<uint32_t>(RP) * 16;
   const uint64_t adesc0 = smem_desc(saddr(srow), lbo_a, 128);
-  const uint64_t bdesc0 = smem_desc(saddr(sw), NG * 128, 128);
   const uint32_t slot16 = static_cast<uint32_t>(slot_bytes >> 4);
-  auto issue_mmas = [&](int y, uint32_t buf) {
-    constexpr uint32_t idesc = idesc_bf16(128, N);
-    uint64_t arow[3];
+  const uint64_t bdesc3 = smem_desc(saddr(sw), 3 * NG * 128, 128);   // K step: next chunk of the reordered weights
+  // the MMAs of staged row r (unwrapped, segment ya..yb), committed to mbar[cb]
+  auto issue_window = [&](int r, int ya, int yb, int cb) {
+    const int kmin = r + 1 - yb > 0 ? r + 1 - yb : 0;
+    const int kmax = r + 1 - ya < 2 ? r + 1 - ya : 2;
+    const uint64_t ad0 = adesc0 + static_cast<uint64_t>(((r + kRing) % kRing) * slot16);
+    const int qhi = (r + 1 - kmin) & (kAcc - 1);   // slot of the highest row (ky = kmin)
+    const int len = kmax - kmin + 1;
+    const int len0 = len < qhi + 1 ? len : qhi + 1;
+    for (int run = 0; run < 2; ++run) {
+      const int k0 = run == 0 ? kmin : kmin + len0;
+      const int L = run == 0 ? len0 : len - len0;
+      if (L <= 0) continue;
+      const int y0 = r + 1 - k0;   // the run's highest row
+      const uint32_t idesc = idesc_bf16(128, N * L);
+      for (int t = 0; t < ntile; ++t) {
+        const uint32_t d = tmem + acc_col(t, y0);
 #pragma unroll
-    for (int ky = 0; ky < 3; ++ky) arow[ky] = adesc0 + static_cast<uint64_t>(((y + ky - 1 + kRing) % kRing) * slot16);
-    for (int t = 0; t < ntile; ++t) {
-      const uint32_t d = tmem + buf * bufcols + static_cast<uint32_t>(t * N);
+        for (int kx = 0; kx < 3; ++kx) {
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-#pragma unroll
-        for (int ks = 0; ks < KC / 2; ++ks) {
-          const uint64_t ad = arow[tap / 3] + static_cast<uint64_t>((2 * ks * lbo_a + (t * 128 + tap % 3) * 16) >> 4);
-          const uint64_t bd = bdesc0 + static_cast<uint64_t>(((tap * KC + 2 * ks) * NG * 128) >> 4);
-          mma_tc(d, ad, bd, idesc, (tap | ks) != 0);
+          for (int ks = 0; ks < KC / 2; ++ks) {
+            const uint64_t ad = ad0 + static_cast<uint64_t>((2 * ks * lbo_a + (t * 128 + kx) * 16) >> 4);
+            const uint64_t bd = bdesc3 + static_cast<uint64_t>((((kx * KC + 2 * ks) * 3 + k0) * NG * 128) >> 4);
+            mma_tc(d, ad, bd, idesc, 1u);
+          }
         }
       }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     saddr(mbar + buf))
+                     saddr(mbar + cb))
                  : "memory");
   };
 
@@ -266,20 +312,22 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
     }
   };
 
-  auto epilogue = [&](int b, int y, uint32_t buf) {
+  auto epilogue = [&](int b, int y) {
     if (kOut == 2 && half) return;               // one logit channel: the first warpgroup alone
     for (int t = 0; t < ntile; ++t) {
       const int x = t * 128 + (warp & 3) * 32 + lane;
       const size_t p = static_cast<size_t>(b) * n + static_cast<size_t>(y) * X + x;
-      const uint32_t col = tmem + lane_off + buf * bufcols + static_cast<uint32_t>(t * N);
+      const uint32_t col = tmem + lane_off + acc_col(t, y);
       if (kOut == 2) {
         float v[1];
         tmem_ld<1>(col, v);
+        tmem_zero16(col);
         if (x < X) a.out_f32[p] = v[0] + bias0;
         continue;
       }
       float v[16];
       tmem_ld<16>(col + static_cast<uint32_t>(half * 16), v);
+      tmem_zero16(col + static_cast<uint32_t>(half * 16));
       if (x >= X) continue;
       __align__(16) __nv_bfloat16 o[16];
       if (kOut == 0) {
@@ -300,6 +348,7 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
       dst[0] = reinterpret_cast<const uint4*>(o)[0];
       dst[1] = reinterpret_cast<const uint4*>(o)[1];
     }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");   // the zeroed accumulator
   };
 
   const long long R = static_cast<long long>(a.B) * Y;
@@ -319,26 +368,27 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
     stage(b, ya);
     stage(b, ya + 1);
     if (kIn != 0) cp_async_commit_wait_all();
-    if (ya + 2 <= yb + 1) stage(b, ya + 2);
-    if (kIn != 0) cp_async_commit();
-    for (int y = ya; y <= yb; ++y) {
-      // row y+1 staged by every thread, buffer y mod 2 drained by every thread;
-      // a wait that ran out anywhere ends the CTA's work here
+    for (int r = ya - 1; r <= yb + 1; ++r) {
+      const uint32_t cb = static_cast<uint32_t>(r - ya + 1) & 1u;   // MMA barrier of staged row r
+      // row r staged by every thread, row r + 1's accumulator drained and
+      // zeroed by every thread; a wait that ran out anywhere ends the CTA's
+      // work here
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       ok = __syncthreads_and(ok) != 0;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!ok) break;
-      if (tid == 0) issue_mmas(y, static_cast<uint32_t>(y & 1));
-      pending |= 1u << (y & 1);
+      if (tid == 0) issue_window(r, ya, yb, static_cast<int>(cb));
+      pending |= 1u << cb;
       if (stall) {   // test switch: a bounded wait on the barrier nothing arrives at
         stall = false;
         if (!wait_mbar(saddr(mbar + 2), 0u, limit)) ok = false;
       }
-      if (y > ya) prefetch_mask(b, y - 1);
+      const bool out_row = r - 2 >= ya;   // row r - 2 is complete once row r - 1's MMAs are
+      if (out_row) prefetch_mask(b, r - 2);
       bool prev = false;
-      if (ok && y > ya) {
-        const uint32_t pb = static_cast<uint32_t>((y - 1) & 1);
+      if (ok && r >= ya) {
+        const uint32_t pb = cb ^ 1u;
         prev = wait_mbar(saddr(mbar + pb), (phases >> pb) & 1u, limit);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (prev) {
@@ -348,20 +398,21 @@ __global__ void __launch_bounds__(kConvThreads, 3) conv_tc_kernel(TcConvArgs a) 
           ok = false;
         }
       }
-      if (ok && y + 3 <= yb + 1) stage(b, y + 3);
-      if (kIn != 0) cp_async_commit();       // (possibly empty) group of row y+3
-      if (prev) epilogue(b, y - 1, static_cast<uint32_t>((y - 1) & 1));
-      if (kIn != 0) cp_async_wait_all_but_one();   // row y+2 has landed
+      if (ok && r + 3 <= yb + 1) stage(b, r + 3);
+      if (kIn != 0) cp_async_commit();           // (possibly empty) group of row r + 3
+      if (prev && out_row) epilogue(b, r - 2);
+      if (kIn != 0) cp_async_wait_group2();      // row r + 1 has landed
     }
     if (ok) {
+      // row yb: its last contributions are staged row yb + 1's MMAs
       prefetch_mask(b, yb);
-      const uint32_t lb = static_cast<uint32_t>(yb & 1);
+      const uint32_t lb = static_cast<uint32_t>(yb - ya + 2) & 1u;
       const bool last = wait_mbar(saddr(mbar + lb), (phases >> lb) & 1u, limit);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (last) {
         phases ^= 1u << lb;
         pending &= ~(1u << lb);
-        epilogue(b, yb, lb);
+        epilogue(b, yb);
       } else {
         ok = false;
       }
@@ -418,7 +469,7 @@ cudaError_t launch_one(const TcConvArgs& a, int sms, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   int per_sm = static_cast<int>(static_cast<size_t>(smem_sm) / (sm + static_cast<size_t>(reserved)));
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int cols = 2 * ((a.X + 127) / 128) * (kOut == 2 ? 16 : 32);
+  const int cols = kAcc * ((a.X + 127) / 128) * (kOut == 2 ? 16 : 32);
   int tc = 32;
   while (tc < cols) tc <<= 1;
   if (tc > 512) return cudaErrorInvalidConfiguration;
