@@ -511,8 +511,8 @@ int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp, bool weighted = t
 }  // namespace
 
 // A flow-kernel run prepared once for repeated launches: its plan and a
-// device arena of (optional) thresholds | split | mirror | zeroed: counters,
-// cut sums, done, abort.
+// device arena of (optional) thresholds | split | zeroed before every launch:
+// the tagged mirror, cut sums, done, abort.
 struct FlowRun {
   ising_problem* p = nullptr;
   FlowPlan fp;
@@ -545,9 +545,9 @@ int flow_run_create(ising_problem* p, int32_t trials, size_t thr_words, FlowRun*
   r->p = p;
   r->trials = trials;
   r->o_split = align256(thr_words * sizeof(uint32_t));
-  r->o_gm = r->o_split + align256(fp.split.size() * sizeof(int32_t));
-  r->o_zero = r->o_gm + align256(static_cast<size_t>(fp.RT) * 2 * p->H * sizeof(uint32_t));
-  r->o_acc = r->o_zero + align256(static_cast<size_t>(fp.RT) * 2 * sizeof(uint32_t));
+  r->o_zero = r->o_split + align256(fp.split.size() * sizeof(int32_t));
+  r->o_gm = r->o_zero;   // the tagged mirror is zeroed before every launch
+  r->o_acc = r->o_gm + align256(static_cast<size_t>(fp.RT) * 2 * p->H * sizeof(unsigned long long));
   r->o_done = r->o_acc + align256(static_cast<size_t>(trials) * sizeof(int32_t));
   r->o_abort = r->o_done + 256;
   r->bytes = r->o_abort + 256;
@@ -593,8 +593,7 @@ int flow_run_launch(FlowRun* r, const uint32_t* d_thr, int32_t thr_group_stride,
     a.LRmax = fp.LRmax;
     a.neg_edges = p->neg_edges;
     a.split = reinterpret_cast<const int32_t*>(r->d + r->o_split);
-    a.gm = reinterpret_cast<uint32_t*>(r->d + r->o_gm);
-    a.gcnt = reinterpret_cast<uint32_t*>(r->d + r->o_zero);
+    a.gm = reinterpret_cast<unsigned long long*>(r->d + r->o_gm);
     a.acc = reinterpret_cast<int32_t*>(r->d + r->o_acc);
     a.done = reinterpret_cast<uint32_t*>(r->d + r->o_done);
     a.abort_flag = reinterpret_cast<uint32_t*>(r->d + r->o_abort);

@@ -17,11 +17,13 @@
 //   waits for exactly its neighbours and never for the whole CTA.
 // * Rows that another CTA reads ("published" rows: shared rows and the rows
 //   next to a shared or another CTA's row) are also written to a global
-//   mirror, with a per-row completion counter in global memory that all of
-//   the row's owners count into; a reader acquires that counter before it
-//   reads the row from the mirror.  Published rows come first in each
-//   half-sweep, so the counters are usually complete long before anyone
-//   waits on them.
+//   mirror as tagged words: the word and its half-sweep + 1 in one 8-byte
+//   store.  A reader loads the 8 bytes of each word it needs and uses them
+//   once the tag is the half-sweep it waits for; no fence and no counter is
+//   needed on either side (a writer cannot get a half-sweep ahead of a
+//   reader of the same word, since its next update needs the reader's).
+//   Published rows come first in each half-sweep, so their words are usually
+//   there long before anyone reads them.
 //
 // * Fast path: when its records fit in shared memory, every item has two
 //   16-byte records with the shared addresses of its word and neighbours,
@@ -29,8 +31,7 @@
 //   the completion counters it waits for (one per lane).  Chunks that touch
 //   no mirror row then cost two record loads, one acquire per lane and the
 //   word update; the others take the general path, which decodes the row
-//   and item tables.  A published row's mirror counter is released once per
-//   run of its items in a chunk, after a warp barrier.
+//   and item tables and reads and writes the mirror.
 //
 // Every wait is bounded by a cycle limit.  A wait that runs out writes
 // ISING_ERR_TIMEOUT to the problem's status word and raises an abort flag that
@@ -119,11 +120,6 @@ __device__ __forceinline__ FlowSmem flow_carve(unsigned char* smem, int32_t LR, 
   return s;
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 // acquire / release on the completion counters: a counter read with acquire
 // orders the reader's later loads after it, and a release increment orders
@@ -139,27 +135,33 @@ __device__ __forceinline__ void red_release_cta(uint32_t addr, uint32_t v) {
   asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void red_release_gpu(uint32_t* p, uint32_t v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// Tagged mirror words: the word in the low half and (half-sweep + 1) in the
+// high half, written and read as one 8-byte access (single-copy atomic), so
+// a reader that sees the tag it waits for also sees that half-sweep's word;
+// no fence is needed on either side.  A writer cannot overwrite a word before
+// its readers took it: its next update of that word needs theirs, which need
+// this one.
+__device__ __forceinline__ unsigned long long ld_tagged(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
-
-// Bounded wait until a completion counter reaches `need`: the shared counter
-// at shared address `saddr`, or with kGlobal the global counter `gp`, read
-// with acquire semantics.  Returns false if the wait was abandoned (limit
-// reached, or another wait raised the abort flag).
-template <bool kGlobal>
-__device__ __forceinline__ uint32_t load_count(const uint32_t* gp, uint32_t saddr) {
-  return kGlobal ? ld_acquire_gpu(gp) : ld_acquire_cta(saddr);
+__device__ __forceinline__ void st_tagged(unsigned long long* p, uint32_t word, uint32_t tag) {
+  const unsigned long long v = (static_cast<unsigned long long>(tag) << 32) | word;
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ uint32_t tag_of(unsigned long long v) { return static_cast<uint32_t>(v >> 32); }
 
-template <bool kGlobal>
-__device__ __noinline__ bool wait_count(const uint32_t* gp, uint32_t saddr, uint32_t need, const FlowArgs& a) {
-  uint32_t v = load_count<kGlobal>(gp, saddr);
+// Bounded wait until the shared completion counter at shared address `saddr`
+// reaches `need` (read with acquire semantics).  Returns false if the wait was
+// abandoned (limit reached, or another wait raised the abort flag).
+__device__ __noinline__ bool wait_count(uint32_t saddr, uint32_t need, const FlowArgs& a) {
+  uint32_t v = ld_acquire_cta(saddr);
   if (v >= need) return true;
   const long long t0 = clock64();
   for (uint32_t it = 0;; ++it) {
-    __nanosleep(64);   // keep the issue slots for the warps that have work
-    v = load_count<kGlobal>(gp, saddr);
+    if (it >= 8) __nanosleep(32);   // after a short spin, keep the issue slots for the warps that have work
+    v = ld_acquire_cta(saddr);
     if (v >= need) return true;
     if ((it & 15u) == 15u) {
       if (*reinterpret_cast<const volatile uint32_t*>(a.abort_flag) != 0u) return false;
@@ -170,6 +172,27 @@ __device__ __noinline__ bool wait_count(const uint32_t* gp, uint32_t saddr, uint
       }
     }
   }
+}
+
+// The same for a tagged mirror word: waits until its tag is `tag` and
+// returns the tagged word (whose tag differs from `tag` if the wait was
+// abandoned).
+__device__ __noinline__ unsigned long long wait_tag(const unsigned long long* p, uint32_t tag, const FlowArgs& a) {
+  unsigned long long v = ld_tagged(p);
+  const long long t0 = clock64();
+  for (uint32_t it = 0; tag_of(v) != tag; ++it) {
+    if (it >= 8) __nanosleep(32);
+    v = ld_tagged(p);
+    if ((it & 15u) == 15u && tag_of(v) != tag) {
+      if (*reinterpret_cast<const volatile uint32_t*>(a.abort_flag) != 0u) return v;
+      if (clock64() - t0 > a.spin_limit) {
+        atomicExch(a.status, ISING_ERR_TIMEOUT);
+        atomicExch(a.abort_flag, 1u);
+        return v;
+      }
+    }
+  }
+  return v;
 }
 
 // kGroupThr: every trial group has its own threshold table (a.thr_group_stride)
@@ -512,8 +535,8 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       const uint4 R0 = lds_v4u(rec32 + 512u * ck);
       const uint32_t v = ld_acquire_cta(caddr);
       if (!__all_sync(0xFFFFFFFFu, v >= need) || a.stall_test) {
-        bool lane_ok = v >= need || wait_count<false>(nullptr, caddr, need, a);
-        if (a.stall_test && j == 0 && hs == 0 && k == 0) lane_ok = lane_ok && wait_count<false>(nullptr, caddr, 0xFFFFFFFFu, a);
+        bool lane_ok = v >= need || wait_count(caddr, need, a);
+        if (a.stall_test && j == 0 && hs == 0 && k == 0) lane_ok = lane_ok && wait_count(caddr, 0xFFFFFFFFu, a);
         if (!__all_sync(0xFFFFFFFFu, lane_ok)) break;
       }
       __syncwarp();   // every lane's reads after all lanes' acquires
@@ -541,41 +564,71 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
       const uint32_t c_self = rc + 4u * lr, c_up = rc + 4u * (static_cast<uint32_t>(A.w) & 0xFFFFu),
                      c_dn = rc + 4u * (static_cast<uint32_t>(A.w) >> 16);
       // the three colour-(1-c) rows this item reads must have finished the
-      // previous half-sweep.  Rows of another CTA are read from the mirror
-      // (except in the very first half-sweep, which reads the halo slots),
-      // and this CTA's rows that another CTA reads are published to it.
+      // previous half-sweep.  Rows of another CTA (and a row split between
+      // two CTAs) are read from the tagged mirror, whose words carry their
+      // half-sweep (except in the very first half-sweep, which reads the halo
+      // slots); this CTA's own rows by the completion counters.  This CTA's
+      // rows that another CTA reads are published to the mirror.
       const bool gu = B.x >= 0 && need > 0, gd = B.y >= 0 && need > 0;
       const bool gs = ((A.z >> 17) & 1) && need > 0;
-      const uint32_t v0 = gs ? ld_acquire_gpu(a.gcnt + (B.z ^ 1)) : ld_acquire_cta(c_self);
-      const uint32_t v1 = gu ? ld_acquire_gpu(a.gcnt + B.x) : ld_acquire_cta(c_up);
-      const uint32_t v2 = gd ? ld_acquire_gpu(a.gcnt + B.y) : ld_acquire_cta(c_dn);
-      const bool ready = v0 >= need && v1 >= need && v2 >= need;
-      // one vote for the chunk: the bounded per-lane waits run only when some
-      // lane is not ready yet (the usual case needs none)
-      if (!__all_sync(0xFFFFFFFFu, ready) || a.stall_test) {
-        bool lane_ok = true;
-        if (v0 < need)
-          lane_ok = gs ? wait_count<true>(a.gcnt + (B.z ^ 1), 0u, need, a) : wait_count<false>(nullptr, c_self, need, a);
-        if (lane_ok && v1 < need)
-          lane_ok = gu ? wait_count<true>(a.gcnt + B.x, 0u, need, a) : wait_count<false>(nullptr, c_up, need, a);
-        if (lane_ok && v2 < need)
-          lane_ok = gd ? wait_count<true>(a.gcnt + B.y, 0u, need, a) : wait_count<false>(nullptr, c_dn, need, a);
-        if (a.stall_test && j == 0 && hs == 0 && k == 0) lane_ok = lane_ok && wait_count<false>(nullptr, c_self, 0xFFFFFFFFu, a);
-        if (!__all_sync(0xFFFFFFFFu, lane_ok)) break;
-      }
+      const uint32_t tag = static_cast<uint32_t>(hs);   // (half-sweep hs - 1) + 1
       // the word, its left and right neighbours (the row's wrap at h = 0 / H - 1)
       const uint32_t par = (static_cast<uint32_t>(A.z) >> 16) & 1u;
       const uint32_t own = (static_cast<uint32_t>(B.w) & 0xFFFFu) + h;
       const uint32_t nbr = static_cast<uint32_t>(B.w) >> 16;
       const uint32_t hl = h + par == 0u ? static_cast<uint32_t>(H) - 1u : h + par - 1u;
       const uint32_t hr = h + par == static_cast<uint32_t>(H) ? 0u : h + par;
-      const uint32_t* gself = a.gm + static_cast<size_t>(B.z ^ 1) * H;
-      const uint32_t nl = gs ? __ldcg(gself + hl) : lds_u32(sp32 + 4u * (nbr + hl));
-      const uint32_t nr = gs ? __ldcg(gself + hr) : lds_u32(sp32 + 4u * (nbr + hr));
-      const uint32_t nu = gu ? __ldcg(a.gm + static_cast<size_t>(B.x) * H + h)
-                             : lds_u32(sp32 + 4u * ((static_cast<uint32_t>(A.x) & 0xFFFFu) + h));
-      const uint32_t nd = gd ? __ldcg(a.gm + static_cast<size_t>(B.y) * H + h)
-                             : lds_u32(sp32 + 4u * ((static_cast<uint32_t>(A.x) >> 16) + h));
+      const unsigned long long* gself = a.gm + (gs ? static_cast<size_t>(B.z ^ 1) * H : 0);
+      const unsigned long long* gup = a.gm + (gu ? static_cast<size_t>(B.x) * H + h : 0);
+      const unsigned long long* gdn = a.gm + (gd ? static_cast<size_t>(B.y) * H + h : 0);
+      const unsigned long long ml = gs ? ld_tagged(gself + hl) : 0ull, mr = gs ? ld_tagged(gself + hr) : 0ull;
+      const unsigned long long mu = gu ? ld_tagged(gup) : 0ull, md = gd ? ld_tagged(gdn) : 0ull;
+      const uint32_t v0 = gs ? need : ld_acquire_cta(c_self);
+      const uint32_t v1 = gu ? need : ld_acquire_cta(c_up);
+      const uint32_t v2 = gd ? need : ld_acquire_cta(c_dn);
+      uint32_t nl = static_cast<uint32_t>(ml), nr = static_cast<uint32_t>(mr);
+      uint32_t nu = static_cast<uint32_t>(mu), nd = static_cast<uint32_t>(md);
+      const bool ready = v0 >= need && v1 >= need && v2 >= need && (!gs || (tag_of(ml) == tag && tag_of(mr) == tag)) &&
+                         (!gu || tag_of(mu) == tag) && (!gd || tag_of(md) == tag);
+      // one vote for the chunk: the bounded per-lane waits run only when some
+      // lane is not ready yet (the usual case needs none)
+      if (!__all_sync(0xFFFFFFFFu, ready) || a.stall_test) {
+        bool lane_ok = true;
+        if (gs) {
+          if (tag_of(ml) != tag) {
+            const unsigned long long w = wait_tag(gself + hl, tag, a);
+            nl = static_cast<uint32_t>(w);
+            lane_ok = tag_of(w) == tag;
+          }
+          if (lane_ok && tag_of(mr) != tag) {
+            const unsigned long long w = wait_tag(gself + hr, tag, a);
+            nr = static_cast<uint32_t>(w);
+            lane_ok = tag_of(w) == tag;
+          }
+        } else if (v0 < need) {
+          lane_ok = wait_count(c_self, need, a);
+        }
+        if (lane_ok && gu && tag_of(mu) != tag) {
+          const unsigned long long w = wait_tag(gup, tag, a);
+          nu = static_cast<uint32_t>(w);
+          lane_ok = tag_of(w) == tag;
+        }
+        if (lane_ok && !gu && v1 < need) lane_ok = wait_count(c_up, need, a);
+        if (lane_ok && gd && tag_of(md) != tag) {
+          const unsigned long long w = wait_tag(gdn, tag, a);
+          nd = static_cast<uint32_t>(w);
+          lane_ok = tag_of(w) == tag;
+        }
+        if (lane_ok && !gd && v2 < need) lane_ok = wait_count(c_dn, need, a);
+        if (a.stall_test && j == 0 && hs == 0 && k == 0) lane_ok = lane_ok && wait_count(c_self, 0xFFFFFFFFu, a);
+        if (!__all_sync(0xFFFFFFFFu, lane_ok)) break;
+      }
+      if (!gs) {
+        nl = lds_u32(sp32 + 4u * (nbr + hl));
+        nr = lds_u32(sp32 + 4u * (nbr + hr));
+      }
+      if (!gu) nu = lds_u32(sp32 + 4u * ((static_cast<uint32_t>(A.x) & 0xFFFFu) + h));
+      if (!gd) nd = lds_u32(sp32 + 4u * ((static_cast<uint32_t>(A.x) >> 16) + h));
       uint2 tq = make_uint2(T4, T8);
       if constexpr (kGroupThr) tq = wt[(A.z & 0xFF) >> 3];
       const uint32_t ns = update_word_h<kU16>(lds_u32(sp32 + 4u * own), nl, nr, nu, nd, lds_u8(fl32 + own),
@@ -583,15 +636,12 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
                                               HeadsShared{wh32 + 16u * (static_cast<uint32_t>(A.z) & 0xFFu)},
                                               (A.z >> 8) & 0xFF, tq.x, tq.y, a.rk);
       sts_u32(sp32 + 4u * own, ns);
-      if (B.z >= 0) __stcg(a.gm + static_cast<size_t>(B.z) * H + h, ns);   // published row: its mirror word
+      if (B.z >= 0) st_tagged(a.gm + static_cast<size_t>(B.z) * H + h, ns, static_cast<uint32_t>(hs) + 1u);   // published row
       __syncwarp();
-      // the last lane of each run of one row's items counts the run, in the
-      // CTA's counter and, for a published row, at GPU scope in the mirror's
-      // (the warp barrier orders the other lanes' stores before the release)
-      if (it.y) {
-        red_release_cta(cnt32 + 4u * (static_cast<uint32_t>(c * NR) + lr), static_cast<uint32_t>(it.y));
-        if (B.z >= 0) red_release_gpu(a.gcnt + B.z, static_cast<uint32_t>(it.y));
-      }
+      // the last lane of each run of one row's items counts the run in the
+      // CTA's counter (the warp barrier orders the other lanes' stores before
+      // the release)
+      if (it.y) red_release_cta(cnt32 + 4u * (static_cast<uint32_t>(c * NR) + lr), static_cast<uint32_t>(it.y));
     }
     k += kFlowWarps;
     ck += kFlowWarps;
@@ -630,7 +680,8 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
   // ---- cut partials per trial: own right and down edges, summed over lanes
   // with ballots, per segment (all lanes of a pass share the segment's group)
   if (a.out_cuts) {
-    const uint32_t fin = static_cast<uint32_t>(H) * a.S;
+    // tag of the last half-sweep of a colour-0 word (a colour-1 word's is one more)
+    const uint32_t fin = 2u * static_cast<uint32_t>(a.S) - 1u;
     bool cut_ok = true;
     for (int s = 0; s < nseg && cut_ok; ++s) {
       const int g = sm.seg_g[s];
@@ -663,16 +714,18 @@ __global__ void __launch_bounds__(kFlowThreads, 1) anneal_flow_kernel(const __gr
           uint32_t sr;
           const int xs = sm.r_xself[lr];
           if (xs >= 0 && a.S > 0) {   // a shared row: its final words are in the mirror
-            lok = wait_count<true>(a.gcnt + 2 * xs + (1 - c), 0u, fin, a);
-            sr = lok ? __ldcg(a.gm + (static_cast<size_t>(2) * xs + (1 - c)) * H + hr) : 0u;
+            const unsigned long long w = wait_tag(a.gm + (static_cast<size_t>(2) * xs + (1 - c)) * H + hr, fin + (1u - c), a);
+            lok = tag_of(w) == fin + (1u - c);
+            sr = static_cast<uint32_t>(w);
           } else {
             sr = nb[lr * H + hr];
           }
           uint32_t sd;
           const int xdn = sm.r_xdn[lr];
           if (lok && xdn >= 0 && a.S > 0) {
-            lok = wait_count<true>(a.gcnt + 2 * xdn + (1 - c), 0u, fin, a);
-            sd = lok ? __ldcg(a.gm + (static_cast<size_t>(2) * xdn + (1 - c)) * H + h) : 0u;
+            const unsigned long long w = wait_tag(a.gm + (static_cast<size_t>(2) * xdn + (1 - c)) * H + h, fin + (1u - c), a);
+            lok = tag_of(w) == fin + (1u - c);
+            sd = static_cast<uint32_t>(w);
           } else {
             sd = nb[sm.r_dn[lr] * H + h];
           }

@@ -89,8 +89,7 @@ struct FlowArgs {
   int32_t LRmax;            // local rows (own rows and halo slots) of the largest CTA
   int32_t neg_edges;
   const int32_t* split;     // [P+1] first stacked site word (row * H + h) of each CTA
-  uint32_t* gm;             // [RT][2][H] mirror of rows read by another CTA
-  uint32_t* gcnt;           // [RT][2] completed items of those rows (zeroed)
+  unsigned long long* gm;   // [RT][2][H] mirror of rows read by another CTA: word | (half-sweep + 1) << 32 (zeroed)
   int32_t* acc;             // [T] per-trial cut partial sums (zeroed)
   uint32_t* done;           // CTAs finished (zeroed)
   uint32_t* abort_flag;     // set by a wait that ran out (zeroed)
