@@ -104,8 +104,13 @@ void ising_destroy(ising_problem* p);
  * out_cuts      device [T] final Eq. 1 cuts, or NULL.
  * cuda_stream   stream to queue on.
  *
- * Scratch: the per-sweep threshold table (8*S bytes) is allocated and freed
- * in stream order with cudaMallocAsync / cudaFreeAsync.
+ * Scratch: the per-sweep threshold table (8*S bytes) and, on the persistent
+ * kernel, its row tables and the mirror of the rows two CTAs share (8 bytes
+ * per word of those rows) are allocated and freed in stream order
+ * (cudaMallocFromPoolAsync / cudaFreeAsync) from a memory pool of the
+ * library's own per device, which keeps the memory it has held until the
+ * process exits, so that a call after a synchronisation does not map its
+ * scratch again.
  * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (no launch shape fits),
  * ISING_ERR_OOM, ISING_ERR_CUDA.
  */
@@ -139,7 +144,8 @@ int ising_cut(const ising_problem* p, const int8_t* spins, int32_t k,
  *            (the array itself or any entry).
  * out_cuts   host array of m device pointers ([trials[q]] int32) or NULL.
  * Scratch: descriptors, work list and thresholds in one stream-ordered
- * allocation, freed in stream order.
+ * allocation from the library's pool (as ising_anneal), freed in stream
+ * order.
  */
 int ising_anneal_batched(ising_problem* const* probs, int32_t m, const int32_t* trials,
                          const int32_t* sweeps, const double* const* betas,

@@ -2,6 +2,7 @@
 // a test hook that makes allocations fail (fault injection on the host, never
 // on the GPU), the log level, hex import/export of configurations, and the
 // decision-stream generator as an entry point.
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -50,9 +51,44 @@ cudaError_t dev_malloc(void** p, size_t bytes) {
   return cudaMalloc(p, bytes);
 }
 
+// The library's stream-ordered allocations come from a pool of its own per
+// device that keeps the memory it has held (release threshold: all of it).
+// The default pool returns freed memory at every synchronisation, and mapping
+// it again made the first call after one several milliseconds slower.
+static cudaError_t library_pool(cudaMemPool_t* pool) {
+  static std::mutex m;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaDeviceGetDefaultMemPool(pool, dev);
+  std::lock_guard<std::mutex> lock(m);
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t created = nullptr;
+    e = cudaMemPoolCreate(&created, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = ~0ull;
+    e = cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(created);
+      return e;
+    }
+    pools[dev] = created;
+  }
+  *pool = pools[dev];
+  return cudaSuccess;
+}
+
 cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
   if (take_failure()) return cudaErrorMemoryAllocation;
-  return cudaMallocAsync(p, bytes, st);
+  cudaMemPool_t pool = nullptr;
+  const cudaError_t e = library_pool(&pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
 }
 
 int log_level() {
