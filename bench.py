@@ -471,7 +471,18 @@ def _train_droplet_net(X, Y, seeds, trials, S_train, steps, init_seed=3):
                  "seconds": time.perf_counter() - t0}
 
 
-def _run_forms(X, Y, eval_seeds, seed0, T, budgets, window, every, forms, warm=False):
+# The proposal schedule of the learned plans: network block flips and partner
+# moves after every PROPOSAL_EVERY-sweep chunk of the second half of the
+# schedule (the last PROPOSAL_WINDOW x S sweeps), chunk j's partner at offset
+# 1 + j mod PARTNER_PERIOD.  Chosen on 8 config-5 instances (seeds 30000-30007)
+# among windows of 1,000 / 3,000 / 0.3 S / 0.5 S / S sweeps, chunks of 25-200
+# sweeps and offset cycles of 3-255: it reaches 99.9 % of the best cut with
+# every trial from 3,000 sweeps on, against a median time-to-target 20 times
+# longer for the last 1,000 sweeps in 100-sweep chunks with 7 offsets.
+PROPOSAL_EVERY, PROPOSAL_WINDOW, PARTNER_PERIOD = 50, 0.5, 31
+
+
+def _run_forms(X, Y, eval_seeds, seed0, T, budgets, forms, warm=False):
     """Every form on every evaluation instance and budget, 8 instances per
     launch (one CUDA graph per form and budget).  forms: name -> (net or
     None, partner period) or None for the plain annealer.  Returns
@@ -486,13 +497,13 @@ def _run_forms(X, Y, eval_seeds, seed0, T, budgets, window, every, forms, warm=F
         m = len(group)
         for S in budgets:
             betas = synth.linear_betas(0.1, 3.0, S)
-            kf = max(0, S - window)
+            kf = max(0, S - int(round(PROPOSAL_WINDOW * S)))
             for name, spec in forms.items():
                 if spec is None:
                     plan = ia.BatchPlan(probs, [T] * m, [S] * m, [betas] * m, seeds, want_spins=False)
                 else:
                     net, period = spec
-                    plan = ia.LearnedPlan(probs, net, T, betas, seeds, k_first=kf, every=every, partner_period=period,
+                    plan = ia.LearnedPlan(probs, net, T, betas, seeds, k_first=kf, every=PROPOSAL_EVERY, partner_period=period,
                                           warm=warm and net is not None)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -566,17 +577,18 @@ def learned_leg(args):
     budget ladder; the network trained on droplet targets of 20,000-spin
     instances (seeds 40000-40255).  Forms, each one CUDA graph over 8
     instances: the plain annealer; the network's cluster block flips after
-    every 100-sweep chunk of the last `window` sweeps (trained, and untrained
-    for what training adds); partner moves in the same window; both.
+    every PROPOSAL_EVERY-sweep chunk of the second half of the schedule
+    (trained, and untrained for what training adds); partner moves in the
+    same chunks; both.
     Statistics per instance against 99.9 % of the best cut any form found."""
     X, Y, T = 200, 100, 512
     net, train = _train_droplet_net(X, Y, list(range(40000, 40000 + args.learned_train)), 16, 10000, 800)
     import paper_2505_18508_gb300 as ia
     untrained = ia.CNN(synth.cnn_init_params(3, scale=0.7))
     budgets = [int(b) for b in args.learned_budgets.split(",")]
-    forms = {"plain": None, "learned": (net, 0), "untrained": (untrained, 0), "partner": (None, 7),
-             "learned_partner": (net, 7)}
-    res = _run_forms(X, Y, list(range(30000, 30000 + args.learned_seeds)), 40000, T, budgets, 1000, 100, forms)
+    forms = {"plain": None, "learned": (net, 0), "untrained": (untrained, 0), "partner": (None, PARTNER_PERIOD),
+             "learned_partner": (net, PARTNER_PERIOD)}
+    res = _run_forms(X, Y, list(range(30000, 30000 + args.learned_seeds)), 40000, T, budgets, forms)
     net.destroy()
     untrained.destroy()
     names = list(forms)
@@ -590,9 +602,9 @@ def learned_leg(args):
                                                     for f in ("plain", "learned", "untrained")},
                         "instances": len({sd for _, sd in res})},
             "workload": f"200x100 tori, instance seeds 30000-{30000 + args.learned_seeds - 1}, 512 trials each, "
-                        f"beta 0.1->3.0 over S sweeps, S in {budgets}; proposals after every 100-sweep chunk of the "
-                        "last 1,000 sweeps; each form one CUDA graph over 8 instances (wall time shared by 8 x 512 "
-                        "trials)",
+                        f"beta 0.1->3.0 over S sweeps, S in {budgets}; proposals after every {PROPOSAL_EVERY}-sweep "
+                        f"chunk of the last {PROPOSAL_WINDOW} S sweeps, partner offsets 1..{PARTNER_PERIOD}; each "
+                        "form one CUDA graph over 8 instances (wall time shared by 8 x 512 trials)",
             "train": train, "targets_all_forms": all_forms, "targets_plain_and_network": net_only,
             "cuts": _cut_stats(res, names)}
 
@@ -600,9 +612,9 @@ def learned_leg(args):
 def partner_leg(args):
     """The cost of the partner moves inside the plan: 8 tori 200x100 x 512
     trials, beta 0.1 -> 3.0 over --leg-sweeps sweeps, the plain annealer
-    (one batched graph) against the same with partner moves after every
-    100-sweep chunk of the last 1,000 sweeps (one learned-plan graph), each
-    replayed --reps times after one warm-up replay (CUDA events)."""
+    (one batched graph) against the same with partner moves on the learned
+    legs' schedule (one learned-plan graph), each replayed --reps times after
+    one warm-up replay (CUDA events)."""
     import torch
     import paper_2505_18508_gb300 as ia
     X, Y, T, S = 200, 100, 512, args.leg_sweeps
@@ -610,10 +622,10 @@ def partner_leg(args):
     seeds = [70000 + q for q in range(8)]
     betas = synth.linear_betas(0.1, 3.0, S)
     plans = {"plain": ia.BatchPlan(probs, [T] * 8, [S] * 8, [betas] * 8, seeds, want_spins=False),
-             "partner": ia.LearnedPlan(probs, None, T, betas, seeds, k_first=max(0, S - 1000), every=100,
-                                       partner_period=7)}
-    out = {"workload": f"8 tori 200x100, 512 trials, {S} sweeps; partner moves after every 100-sweep chunk of the "
-                       "last 1,000 sweeps"}
+             "partner": ia.LearnedPlan(probs, None, T, betas, seeds, k_first=max(0, S - int(round(PROPOSAL_WINDOW * S))),
+                                       every=PROPOSAL_EVERY, partner_period=PARTNER_PERIOD)}
+    out = {"workload": f"8 tori 200x100, 512 trials, {S} sweeps; partner moves after every {PROPOSAL_EVERY}-sweep "
+                       f"chunk of the last {PROPOSAL_WINDOW} S sweeps, offsets 1..{PARTNER_PERIOD}"}
     for name, plan in plans.items():
         plan.launch()
         torch.cuda.synchronize()
@@ -637,13 +649,14 @@ def learned100_leg(args):
     (seeds 20000-20007) x 512 trials; the network trained on droplet targets
     of 256 held-out instances (seeds 10000-10255); the learned form with a
     warm start (the network's whole-lattice proposal on the start state) and
-    cluster block flips after every 100-sweep chunk of the last 1,000 sweeps,
-    against the plain annealer and partner moves."""
+    cluster block flips on the learned legs' schedule, against the plain
+    annealer and partner moves."""
     X, Y, T = 100, 100, 512
     net, train = _train_droplet_net(X, Y, list(range(10000, 10256)), 8, 3000, 600, init_seed=5)
     budgets = [1000, 3000, 10000]
-    forms = {"plain": None, "learned": (net, 0), "partner": (None, 7), "learned_partner": (net, 7)}
-    res = _run_forms(X, Y, list(range(20000, 20008)), 20000, T, budgets, 1000, 100, forms, warm=True)
+    forms = {"plain": None, "learned": (net, 0), "partner": (None, PARTNER_PERIOD),
+             "learned_partner": (net, PARTNER_PERIOD)}
+    res = _run_forms(X, Y, list(range(20000, 20008)), 20000, T, budgets, forms, warm=True)
     net.destroy()
     names = list(forms)
     st = _form_stats(res, names, T)
@@ -651,8 +664,8 @@ def learned100_leg(args):
                         "median_TTT_s": {f: st["TTT_s"][f]["median"] for f in names},
                         "TTT_reached": {f: st["TTT_s"][f]["reached"] for f in names}},
             "workload": "100x100 tori, instance seeds 20000-20007, 512 trials each, beta 0.1->3.0 over S sweeps, "
-                        f"S in {budgets}; warm start plus cluster block flips after every 100-sweep chunk of the last "
-                        "1,000 sweeps",
+                        f"S in {budgets}; warm start plus cluster block flips after every {PROPOSAL_EVERY}-sweep "
+                        f"chunk of the last {PROPOSAL_WINDOW} S sweeps, partner offsets 1..{PARTNER_PERIOD}",
             "train": train, "stats": st, "cuts": _cut_stats(res, names)}
 
 
