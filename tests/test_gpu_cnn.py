@@ -35,7 +35,10 @@ def _params(seed, scale=0.7):
     return p
 
 
-@pytest.mark.parametrize("X,Y,B", [(20, 10, 3), (24, 8, 2), (100, 100, 2), (200, 100, 1), (6, 4, 4)])
+# widths up to 512: three and four 128-pixel tiles per row (the accumulator
+# ring of the convolution then fills all 512 tensor-memory columns)
+@pytest.mark.parametrize("X,Y,B", [(20, 10, 3), (24, 8, 2), (100, 100, 2), (200, 100, 1), (6, 4, 4), (300, 6, 2),
+                                   (512, 4, 1)])
 def test_forward_against_fp64(ia, X, Y, B):
     import torch
     inst = synth.torus_instance(X, Y, 5)
@@ -48,6 +51,17 @@ def test_forward_against_fp64(ia, X, Y, B):
     ref = ocnn.forward(params, s, inst["w_right"], inst["w_down"]).reshape(B, -1)
     err = np.abs(z.cpu().numpy() - ref).max()
     assert err <= 2e-2, (err, np.abs(ref).max())
+    net.destroy(); prob.destroy()
+
+
+def test_forward_refuses_widths_above_512(ia):
+    import torch
+    inst = synth.torus_instance(520, 4, 5)
+    prob = ia.Problem.from_instance(inst)
+    net = ia.CNN(_params(1))
+    with pytest.raises(ia.IsingError) as ei:
+        net.forward(prob, torch.from_numpy(synth.random_spins(1, 520 * 4, 7)).cuda())
+    assert ei.value.code == -8          # ISING_ERR_UNSUPPORTED
     net.destroy(); prob.destroy()
 
 
