@@ -104,14 +104,22 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterA
   __syncthreads();
 
   // ---- labels: minimum over the masked neighbours, then one pointer jump
+  // site i = tid + m * kClusterThreads at row y, column x, advanced without
+  // a division
+  const int dq = kClusterThreads / X, dr = kClusterThreads - dq * X;
+  const int y_first = tid / X, x_first = tid - y_first * X;
   for (int pass = 0; pass <= n; ++pass) {
     if (tid == 0) s_flag = 0;
     __syncthreads();
     int changed = 0;
-    for (int i = tid; i < n; i += kClusterThreads) {
+    int y = y_first, x = x_first;
+    for (int i = tid; i < n; i += kClusterThreads, y += dq, x += dr) {
+      if (x >= X) {
+        x -= X;
+        ++y;
+      }
       const int l = lab[i];
       if (l == INT_MAX) continue;
-      const int y = i / X, x = i - y * X;
       int mn = l;
       const int j0 = y * X + wrapc(x + 1, X), j1 = y * X + wrapc(x - 1, X);
       const int j2 = wrapc(y + 1, Y) * X + x, j3 = wrapc(y - 1, Y) * X + x;
@@ -135,12 +143,16 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterA
 
   // ---- dE per component: boundary terms, summed per label within a warp first
   const int span = (n + kClusterThreads - 1) / kClusterThreads * kClusterThreads;
-  for (int i = tid; i < span; i += kClusterThreads) {
+  int y = y_first, x = x_first;
+  for (int i = tid; i < span; i += kClusterThreads, y += dq, x += dr) {
+    if (x >= X) {
+      x -= X;
+      ++y;
+    }
     int l = INT_MAX, c = 0;
     if (i < n) {
       l = lab[i];
       if (l != INT_MAX) {
-        const int y = i / X, x = i - y * X;
         const int xl = wrapc(x - 1, X), xr = wrapc(x + 1, X), yu = wrapc(y - 1, Y), yd = wrapc(y + 1, Y);
         const int j[4] = {y * X + xr, y * X + xl, yd * X + x, yu * X + x};
         const int w[4] = {(ef[i] & 1u) ? -1 : 1, (ef[y * X + xl] & 1u) ? -1 : 1, (ef[i] & 2u) ? -1 : 1,
@@ -150,6 +162,8 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterA
           if (lab[j[d]] == INT_MAX) c += -2 * w[d] * sv[i] * sv[j[d]];
       }
     }
+    // only lanes with a boundary term take part (most warps have none)
+    if (__ballot_sync(0xFFFFFFFFu, c != 0) == 0u) continue;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, l);
     const int sum = __reduce_add_sync(peers, c);
     if (l != INT_MAX && lane == __ffs(peers) - 1 && sum != 0) atomicAdd(&dE[l], sum);
