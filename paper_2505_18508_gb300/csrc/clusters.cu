@@ -47,6 +47,8 @@ struct ClusterArgs {
   const uint8_t* eflags[kMaxClusterProblems];   // per problem: bit 0 right edge w = -1, bit 1 down edge
   int32_t per_problem;            // configurations per problem: image b uses eflags[b / per_problem]
   int32_t X, Y;
+  int32_t use_list;               // 1: the masked sites are listed in shared memory at byte offset list_off
+  uint32_t list_off;
 };
 
 __device__ __forceinline__ int wrapc(int v, int m) { return v < 0 ? v + m : (v >= m ? v - m : v); }
@@ -103,35 +105,88 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterA
   }
   __syncthreads();
 
+  // ---- the masked sites as a list (when it fits in shared memory): the
+  // label passes and the energy sums then visit only them
+  const bool use_list = a.use_list != 0;
+  uint16_t* list = reinterpret_cast<uint16_t*>(smem + a.list_off);
+  __shared__ int s_cnt;
+  int nlist = n;
+  if (use_list) {
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    for (int i0 = 0; i0 < n; i0 += kClusterThreads) {   // the same count of iterations in every thread
+      const int i = i0 + tid;
+      const bool m = i < n && lab[i] != INT_MAX;
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, m);
+      int base = 0;
+      if (lane == 0 && bal != 0u) base = atomicAdd(&s_cnt, __popc(bal));
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      if (m) list[base + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(i);
+    }
+    __syncthreads();
+    nlist = s_cnt;
+  }
+  // row of a listed site without a division: floor(i * ceil(2^32 / X) / 2^32)
+  // is exact for i, X < 2^16
+  const uint32_t mX = X > 1 ? 0xFFFFFFFFu / static_cast<uint32_t>(X) + 1u : 0u;
+  auto row_of = [&](int i) { return X > 1 ? static_cast<int>(__umulhi(static_cast<uint32_t>(i), mX)) : i; };
+
+  // one relaxation of masked site i at (y, x): the minimum over its masked
+  // neighbours and one pointer jump; true if its label fell
+  auto relax = [&](int i, int y, int x) {
+    const int l = lab[i];
+    int mn = l;
+    const int j0 = y * X + wrapc(x + 1, X), j1 = y * X + wrapc(x - 1, X);
+    const int j2 = wrapc(y + 1, Y) * X + x, j3 = wrapc(y - 1, Y) * X + x;
+    mn = min(mn, lab[j0]);
+    mn = min(mn, lab[j1]);
+    mn = min(mn, lab[j2]);
+    mn = min(mn, lab[j3]);
+    mn = min(mn, lab[mn]);
+    if (mn < l) {
+      atomicMin(&lab[i], mn);
+      atomicMin(&lab[l], mn);   // lower the old label's site too: joins the trees faster
+      return true;
+    }
+    return false;
+  };
+  // the boundary terms of masked site i at (y, x)
+  auto boundary = [&](int i, int y, int x) {
+    const int xl = wrapc(x - 1, X), xr = wrapc(x + 1, X), yu = wrapc(y - 1, Y), yd = wrapc(y + 1, Y);
+    const int j[4] = {y * X + xr, y * X + xl, yd * X + x, yu * X + x};
+    const int w[4] = {(ef[i] & 1u) ? -1 : 1, (ef[y * X + xl] & 1u) ? -1 : 1, (ef[i] & 2u) ? -1 : 1,
+                      (ef[yu * X + x] & 2u) ? -1 : 1};
+    int c = 0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if (lab[j[d]] == INT_MAX) c += -2 * w[d] * sv[i] * sv[j[d]];
+    return c;
+  };
+
   // ---- labels: minimum over the masked neighbours, then one pointer jump
-  // site i = tid + m * kClusterThreads at row y, column x, advanced without
-  // a division
+  // (without the list: site i = tid + m * kClusterThreads at row y, column x,
+  // advanced without a division)
   const int dq = kClusterThreads / X, dr = kClusterThreads - dq * X;
   const int y_first = tid / X, x_first = tid - y_first * X;
   for (int pass = 0; pass <= n; ++pass) {
     if (tid == 0) s_flag = 0;
     __syncthreads();
     int changed = 0;
-    int y = y_first, x = x_first;
-    for (int i = tid; i < n; i += kClusterThreads, y += dq, x += dr) {
-      if (x >= X) {
-        x -= X;
-        ++y;
+    if (use_list) {
+      for (int q = tid; q < nlist; q += kClusterThreads) {
+        const int i = list[q];
+        const int y = row_of(i);
+        if (relax(i, y, i - y * X)) changed = 1;
       }
-      const int l = lab[i];
-      if (l == INT_MAX) continue;
-      int mn = l;
-      const int j0 = y * X + wrapc(x + 1, X), j1 = y * X + wrapc(x - 1, X);
-      const int j2 = wrapc(y + 1, Y) * X + x, j3 = wrapc(y - 1, Y) * X + x;
-      mn = min(mn, lab[j0]);
-      mn = min(mn, lab[j1]);
-      mn = min(mn, lab[j2]);
-      mn = min(mn, lab[j3]);
-      mn = min(mn, lab[mn]);
-      if (mn < l) {
-        atomicMin(&lab[i], mn);
-        atomicMin(&lab[l], mn);   // lower the old label's site too: joins the trees faster
-        changed = 1;
+    } else {
+      int y = y_first, x = x_first;
+      for (int i = tid; i < n; i += kClusterThreads, y += dq, x += dr) {
+        if (x >= X) {
+          x -= X;
+          ++y;
+        }
+        if (lab[i] == INT_MAX) continue;
+        if (relax(i, y, x)) changed = 1;
       }
     }
     if (changed) s_flag = 1;
@@ -142,24 +197,23 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterA
   }
 
   // ---- dE per component: boundary terms, summed per label within a warp first
-  const int span = (n + kClusterThreads - 1) / kClusterThreads * kClusterThreads;
+  const int span = (nlist + kClusterThreads - 1) / kClusterThreads * kClusterThreads;
   int y = y_first, x = x_first;
-  for (int i = tid; i < span; i += kClusterThreads, y += dq, x += dr) {
+  for (int q = tid; q < span; q += kClusterThreads, y += dq, x += dr) {
     if (x >= X) {
       x -= X;
       ++y;
     }
     int l = INT_MAX, c = 0;
-    if (i < n) {
-      l = lab[i];
-      if (l != INT_MAX) {
-        const int xl = wrapc(x - 1, X), xr = wrapc(x + 1, X), yu = wrapc(y - 1, Y), yd = wrapc(y + 1, Y);
-        const int j[4] = {y * X + xr, y * X + xl, yd * X + x, yu * X + x};
-        const int w[4] = {(ef[i] & 1u) ? -1 : 1, (ef[y * X + xl] & 1u) ? -1 : 1, (ef[i] & 2u) ? -1 : 1,
-                          (ef[yu * X + x] & 2u) ? -1 : 1};
-#pragma unroll
-        for (int d = 0; d < 4; ++d)
-          if (lab[j[d]] == INT_MAX) c += -2 * w[d] * sv[i] * sv[j[d]];
+    if (q < nlist) {
+      if (use_list) {
+        const int i = list[q];
+        const int yi = row_of(i);
+        l = lab[i];
+        c = boundary(i, yi, i - yi * X);
+      } else {
+        l = lab[q];
+        if (l != INT_MAX) c = boundary(q, y, x);
       }
     }
     // only lanes with a boundary term take part (most warps have none)
@@ -203,6 +257,9 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(const ClusterA
 }
 
 size_t cluster_smem(int n) { return static_cast<size_t>(n) * 9; }
+// with the list of masked sites (16-bit indices) after the other arrays
+size_t cluster_list_off(int n) { return (cluster_smem(n) + 15) & ~static_cast<size_t>(15); }
+size_t cluster_smem_list(int n) { return cluster_list_off(n) + static_cast<size_t>(n) * 2; }
 
 int cluster_check(const ising_problem* const* probs, int32_t m, int32_t B, ClusterArgs* a) {
   if (!probs || m < 1 || m > kMaxClusterProblems || B < 0) return ISING_ERR_ARG;
@@ -224,8 +281,15 @@ int cluster_check(const ising_problem* const* probs, int32_t m, int32_t B, Clust
 }
 
 template <int kMode>
-int launch_clusters(const ClusterArgs& a, int32_t images, cudaStream_t st) {
-  const size_t sm = cluster_smem(a.X * a.Y);
+int launch_clusters(ClusterArgs a, int32_t images, cudaStream_t st) {
+  const int n = a.X * a.Y;
+  int dev = 0, smem_max = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return ISING_ERR_CUDA;
+  a.use_list = n < 65536 && cluster_smem_list(n) <= static_cast<size_t>(smem_max) ? 1 : 0;
+  a.list_off = static_cast<uint32_t>(cluster_list_off(n));
+  const size_t sm = a.use_list ? cluster_smem_list(n) : cluster_smem(n);
   if (cudaFuncSetAttribute(cluster_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(sm)) != cudaSuccess)
     return ISING_ERR_CUDA;
