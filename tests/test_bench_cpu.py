@@ -93,3 +93,36 @@ def test_reference_sample_is_stratified_over_the_schedule():
     full = bench.synth.linear_betas(0.1, 3.0, 10000)
     for j in jobs:                                                       # each a slice of the full schedule
         assert len(j[1]) == 1000 and (j[1] == full[j[5]:j[5] + 1000]).all()
+
+
+def test_form_stats_targets_success_and_time_to_target():
+    """bench's per-instance statistics on hand-made cuts: target = ceil(0.999
+    x the best cut of any listed form at any budget); P_s per form and budget;
+    TTT per instance = min over budgets of (wall per trial) x r(P_s), Eq. 3-5."""
+    np = pytest.importorskip("numpy")
+    T = 2
+    res = {
+        # instance 1: best cut 1000 -> target 999
+        (10, 1): {"a": (np.array([999, 990]), 2.0, None), "b": (np.array([900, 900]), 1.0, None)},
+        (20, 1): {"a": (np.array([1000, 1000]), 4.0, None), "b": (np.array([998, 997]), 2.0, None)},
+        # instance 2: best cut 2001 (form b) -> target ceil(1998.999) = 1999
+        (10, 2): {"a": (np.array([1998, 1990]), 2.0, None), "b": (np.array([2001, 1000]), 1.0, None)},
+        (20, 2): {"a": (np.array([1999, 1000]), 4.0, None), "b": (np.array([1999, 1999]), 2.0, None)},
+    }
+    out = bench._form_stats(res, ["a", "b"], T)
+    ps = out["P_s"]
+    assert ps["a@10"][0] == pytest.approx(0.25) and ps["a@20"][0] == pytest.approx(0.75)
+    assert ps["b@10"][0] == pytest.approx(0.25) and ps["b@20"][0] == pytest.approx(0.5)
+    # standard error over the two instances: std(ddof=1) / sqrt(2)
+    assert ps["a@20"][1] == pytest.approx(np.std([1.0, 0.5], ddof=1) / math.sqrt(2))
+    r_half = math.log(0.01) / math.log(0.5)
+    # a: instance 1 best at S=20 (P=1, 2 ms/trial); instance 2 at S=20 (P=0.5, 2 ms/trial)
+    # b: instance 1 never reaches 999; instance 2: S=20 (P=1, 1 ms/trial) beats S=10 (P=0.5, 0.5 ms x r)
+    ta, tb = out["TTT_s"]["a"], out["TTT_s"]["b"]
+    assert ta["reached"] == 2 and tb["reached"] == 1
+    assert ta["median"] == pytest.approx(np.median([2e-3, 2e-3 * r_half]))
+    assert tb["median"] is None                       # half or fewer reached: no median
+    assert tb["mean_reached"] == pytest.approx(min(0.5e-3 * r_half, 1e-3))
+    # restricting the forms lowers instance 2's best cut to 1999 -> target 1998
+    only_a = bench._form_stats(res, ["a"], T)
+    assert only_a["P_s"]["a@10"][0] == pytest.approx((0.5 + 0.5) / 2)
