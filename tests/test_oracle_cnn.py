@@ -4,7 +4,8 @@
 * gradient: central finite differences in FP64;
 * loss: exact values (zero logits give ln 2);
 * targets: gauge invariance;
-* proposals: acceptance re-derived from whole-lattice energy differences.
+* proposals: acceptance re-derived from whole-lattice energy differences;
+* torus components: networkx's periodic grid graph on random masks.
 """
 import math
 
@@ -186,6 +187,20 @@ def test_torus_components_hand_built():
     m[1, 4] = True                    # diagonal to nothing, alone
     comps = sorted(sorted(c) for c in cnn.torus_components(m))
     assert comps == [[(0, 0), (0, 5), (3, 0)], [(1, 4)], [(2, 2), (2, 3)]]
+
+
+@pytest.mark.parametrize("Y, X, p", [(4, 4, 0.5), (6, 10, 0.3), (8, 6, 0.55), (10, 12, 0.45)])
+def test_torus_components_equal_periodic_grid_graph_components(Y, X, p):
+    """On random masks, the components are those of the masked sites' subgraph
+    of networkx's periodic 2-D grid (a library routine, not the search)."""
+    nx = pytest.importorskip("networkx")
+    grid = nx.grid_2d_graph(Y, X, periodic=True)
+    rng = np.random.default_rng(Y * 100 + X)
+    for _ in range(20):
+        m = rng.random((Y, X)) < p
+        ours = sorted(sorted(c) for c in cnn.torus_components(m))
+        lib = sorted(sorted(c) for c in nx.connected_components(grid.subgraph(zip(*np.nonzero(m)))))
+        assert ours == [[(int(y), int(x)) for y, x in c] for c in lib]
 
 
 def test_component_energy_changes_add_up_to_the_state_difference():
