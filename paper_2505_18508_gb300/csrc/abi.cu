@@ -325,7 +325,8 @@ int prepare_batch(ising_problem* const* probs, int32_t m, const int32_t* trials,
   }
   BatchSchedule bs;
   const int rc = batch_schedule(m, vn.data(), vH.data(), vY.data(), trials, sweeps, vblk.data(), group_trials,
-                                ctas_per_sm, num_sms_of(device), max_smem_of(device), &bs);
+                                ctas_per_sm, num_sms_of(device),
+                                max_smem_of(device) - static_cast<int>(ising::batched_static_smem()), &bs);
   if (rc != ISING_OK) return rc;
   hb.grid = num_sms_of(device) * bs.per_sm;
   hb.threads = bs.threads;
@@ -469,7 +470,7 @@ int flow_split(int32_t Y, int32_t H, int32_t T, int32_t G, int32_t blk, int32_t 
 // groups than the kernel tracks or its rows would not fit in shared memory.
 int plan_flow(const ising_problem* p, int32_t T, FlowPlan* fp, bool weighted = true) {
   const int sms = num_sms_of(p->device);
-  const int smem_max = max_smem_of(p->device);
+  const int smem_max = max_smem_of(p->device) - static_cast<int>(ising::flow_static_smem());
   int G = p->cfg_group;
   if (G == 0) G = default_group(p, T);
   const int blk = p->draw_bits == 16 ? 8 : 4;

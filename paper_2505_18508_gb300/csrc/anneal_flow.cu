@@ -797,6 +797,19 @@ cudaError_t launch_flow(const FlowArgs& a, cudaStream_t stream) {
   return a.u16 ? launch_flow_mode<true, false>(a, stream) : launch_flow_mode<false, false>(a, stream);
 }
 
+size_t flow_static_smem() {
+  const void* fns[4] = {reinterpret_cast<const void*>(anneal_flow_kernel<false, false>),
+                        reinterpret_cast<const void*>(anneal_flow_kernel<true, false>),
+                        reinterpret_cast<const void*>(anneal_flow_kernel<false, true>),
+                        reinterpret_cast<const void*>(anneal_flow_kernel<true, true>)};
+  size_t v = 0;
+  for (const void* fn : fns) {
+    const size_t b = static_smem_of(fn);
+    if (b > v) v = b;
+  }
+  return v;
+}
+
 cudaError_t flow_max_ctas(size_t smem, int* per_sm) {
   const void* fns[4] = {reinterpret_cast<const void*>(anneal_flow_kernel<false, false>),
                         reinterpret_cast<const void*>(anneal_flow_kernel<true, false>),

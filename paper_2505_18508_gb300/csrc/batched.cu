@@ -52,6 +52,8 @@ __global__ void __launch_bounds__(1024, 1) batched_kernel(const BatchArgs a) {
 
 size_t batched_smem_bytes(int32_t H, int32_t Y) { return core_smem_bytes(H, Y); }
 
+size_t batched_static_smem() { return static_smem_of(reinterpret_cast<const void*>(batched_kernel)); }
+
 cudaError_t batched_prepare(size_t smem) {
   return cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
 }

@@ -261,6 +261,25 @@ size_t cluster_smem(int n) { return static_cast<size_t>(n) * 9; }
 size_t cluster_list_off(int n) { return (cluster_smem(n) + 15) & ~static_cast<size_t>(15); }
 size_t cluster_smem_list(int n) { return cluster_list_off(n) + static_cast<size_t>(n) * 2; }
 
+// the dynamic shared memory a launch may ask for: the per-block opt-in limit
+// less the kernel's own static arrays (the same in every mode)
+int cluster_dyn_max(int* out) {
+  int dev = 0, smem_max = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return ISING_ERR_CUDA;
+  size_t st = 0;
+  const void* fns[3] = {reinterpret_cast<const void*>(cluster_kernel<0>),
+                        reinterpret_cast<const void*>(cluster_kernel<1>),
+                        reinterpret_cast<const void*>(cluster_kernel<2>)};
+  for (const void* fn : fns) {
+    const size_t b = static_smem_of(fn);
+    if (b > st) st = b;
+  }
+  *out = smem_max - static_cast<int>(st);
+  return ISING_OK;
+}
+
 int cluster_check(const ising_problem* const* probs, int32_t m, int32_t B, ClusterArgs* a) {
   if (!probs || m < 1 || m > kMaxClusterProblems || B < 0) return ISING_ERR_ARG;
   for (int q = 0; q < m; ++q) {
@@ -268,11 +287,10 @@ int cluster_check(const ising_problem* const* probs, int32_t m, int32_t B, Clust
     if (probs[q]->graph) return ISING_ERR_UNSUPPORTED;
     if (probs[q]->X != probs[0]->X || probs[q]->Y != probs[0]->Y) return ISING_ERR_ARG;
   }
-  int dev = 0, smem_max = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-    return ISING_ERR_CUDA;
-  if (cluster_smem(probs[0]->n) > static_cast<size_t>(smem_max)) return ISING_ERR_UNSUPPORTED;
+  int dyn_max = 0;
+  const int rc = cluster_dyn_max(&dyn_max);
+  if (rc != ISING_OK) return rc;
+  if (dyn_max < 0 || cluster_smem(probs[0]->n) > static_cast<size_t>(dyn_max)) return ISING_ERR_UNSUPPORTED;
   for (int q = 0; q < m; ++q) a->eflags[q] = probs[q]->d_eflags;
   a->per_problem = B > 0 ? B : 1;
   a->X = probs[0]->X;
@@ -283,11 +301,10 @@ int cluster_check(const ising_problem* const* probs, int32_t m, int32_t B, Clust
 template <int kMode>
 int launch_clusters(ClusterArgs a, int32_t images, cudaStream_t st) {
   const int n = a.X * a.Y;
-  int dev = 0, smem_max = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-    return ISING_ERR_CUDA;
-  a.use_list = n < 65536 && cluster_smem_list(n) <= static_cast<size_t>(smem_max) ? 1 : 0;
+  int dyn_max = 0;
+  const int rc = cluster_dyn_max(&dyn_max);
+  if (rc != ISING_OK) return rc;
+  a.use_list = n < 65536 && dyn_max >= 0 && cluster_smem_list(n) <= static_cast<size_t>(dyn_max) ? 1 : 0;
   a.list_off = static_cast<uint32_t>(cluster_list_off(n));
   const size_t sm = a.use_list ? cluster_smem_list(n) : cluster_smem(n);
   if (cudaFuncSetAttribute(cluster_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,

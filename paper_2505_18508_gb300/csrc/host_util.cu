@@ -91,6 +91,15 @@ cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
   return cudaMallocFromPoolAsync(p, bytes, pool, st);
 }
 
+size_t static_smem_of(const void* kernel) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+    (void)cudaGetLastError();   // leave no error for the next launch check to find
+    return 1024;
+  }
+  return fa.sharedSizeBytes;
+}
+
 int log_level() {
   static const int level = [] {
     const char* v = std::getenv("ISING_LOG");

@@ -52,6 +52,10 @@ inline cudaError_t dev_malloc_async(T** p, size_t bytes, cudaStream_t st) {
   return dev_malloc_async(reinterpret_cast<void**>(p), bytes, st);
 }
 int log_level();
+// Static shared memory of a kernel (cudaFuncGetAttributes), which counts
+// against the per-block opt-in limit together with the dynamic size; 1 KiB
+// when the attributes cannot be read.
+size_t static_smem_of(const void* kernel);
 
 // Everything the strip kernel reads; passed by value as the kernel parameter.
 struct AnnealArgs {
@@ -106,6 +110,7 @@ int flow_threads();
 int flow_max_segments();
 cudaError_t launch_flow(const FlowArgs& a, cudaStream_t stream);
 cudaError_t flow_max_ctas(size_t smem, int* per_sm);
+size_t flow_static_smem();   // the largest over the kernel's instantiations
 
 }  // namespace ising
 
@@ -256,6 +261,7 @@ int transcribe_launch(const ising_problem* const* probs, int32_t m, const int8_t
 
 size_t batched_smem_bytes(int32_t H, int32_t Y);
 cudaError_t batched_prepare(size_t smem);
+size_t batched_static_smem();
 cudaError_t launch_batched(const BatchArgs& a, int grid, int threads, size_t smem, cudaStream_t stream);
 
 }  // namespace ising

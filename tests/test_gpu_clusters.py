@@ -152,3 +152,41 @@ def test_partner_moves_on_annealed_states_of_stacked_problems(ia):
         ia.transcribe(probs, s, 1, out=s)                      # out may not alias the input
     for p in probs:
         p.destroy()
+
+
+@pytest.mark.parametrize("X,Y", [(160, 132), (4, 6452)])
+def test_cluster_moves_at_the_shared_memory_limit(ia, X, Y):
+    """Sizes at the per-block shared-memory limit (227 KiB), which the kernel's
+    static arrays share with its 9 bytes per site (and the 2-byte list of
+    masked sites when that fits): 160x132 (21,120 sites) has room for the
+    per-site arrays but not for the list beside the static arrays; 4x6452
+    (25,808 sites) is the largest size that fits at all.  Proposals and
+    partner moves equal the oracle's; 4x6454 is refused as unsupported and
+    the next call is exact."""
+    import torch
+    inst = synth.torus_instance(X, Y, 600 + X)
+    prob = ia.Problem.from_instance(inst)
+    n, B = X * Y, 2
+    s = synth.random_spins(B, n, 60 + X)
+    z = (np.random.default_rng(X).normal(size=(B, n)) + 0.3).astype(np.float32)
+    sd = torch.from_numpy(s).cuda()
+    acc = ia.propose_clusters(prob, sd, torch.from_numpy(z).cuda())
+    torch.cuda.synchronize()
+    rs, racc = ocnn.propose_clusters(s, z, inst["w_right"], inst["w_down"])
+    np.testing.assert_array_equal(sd.cpu().numpy(), rs)
+    np.testing.assert_array_equal(acc.cpu().numpy(), racc)
+    out, acc = ia.transcribe(prob, torch.from_numpy(s).cuda(), 1)
+    torch.cuda.synchronize()
+    rs, racc = ocnn.transcribe(s, 1, inst["w_right"], inst["w_down"])
+    np.testing.assert_array_equal(out.cpu().numpy(), rs)
+    np.testing.assert_array_equal(acc.cpu().numpy(), racc)
+    if X == 4:
+        big = ia.Problem.from_instance(synth.torus_instance(4, Y + 2, 1))
+        with pytest.raises(ia.IsingError) as e:
+            ia.transcribe(big, torch.zeros((B, 4 * (Y + 2)), dtype=torch.int8, device="cuda"), 1)
+        assert e.value.code == -8
+        big.destroy()
+        out2, _ = ia.transcribe(prob, torch.from_numpy(s).cuda(), 1)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out2.cpu().numpy(), rs)
+    prob.destroy()
