@@ -261,25 +261,18 @@ size_t cluster_smem(int n) { return static_cast<size_t>(n) * 9; }
 size_t cluster_list_off(int n) { return (cluster_smem(n) + 15) & ~static_cast<size_t>(15); }
 size_t cluster_smem_list(int n) { return cluster_list_off(n) + static_cast<size_t>(n) * 2; }
 
-// the dynamic shared memory a launch may ask for: the per-block opt-in limit
-// less the kernel's own static arrays (the same in every mode)
-int cluster_dyn_max(int* out) {
+// the dynamic shared memory a launch of `kernel` may ask for: the per-block
+// opt-in limit less the kernel's own static arrays
+int cluster_dyn_max(const void* kernel, int* out) {
   int dev = 0, smem_max = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return ISING_ERR_CUDA;
-  size_t st = 0;
-  const void* fns[3] = {reinterpret_cast<const void*>(cluster_kernel<0>),
-                        reinterpret_cast<const void*>(cluster_kernel<1>),
-                        reinterpret_cast<const void*>(cluster_kernel<2>)};
-  for (const void* fn : fns) {
-    const size_t b = static_smem_of(fn);
-    if (b > st) st = b;
-  }
-  *out = smem_max - static_cast<int>(st);
+  *out = smem_max - static_cast<int>(static_smem_of(kernel));
   return ISING_OK;
 }
 
+template <int kMode>
 int cluster_check(const ising_problem* const* probs, int32_t m, int32_t B, ClusterArgs* a) {
   if (!probs || m < 1 || m > kMaxClusterProblems || B < 0) return ISING_ERR_ARG;
   for (int q = 0; q < m; ++q) {
@@ -288,7 +281,7 @@ int cluster_check(const ising_problem* const* probs, int32_t m, int32_t B, Clust
     if (probs[q]->X != probs[0]->X || probs[q]->Y != probs[0]->Y) return ISING_ERR_ARG;
   }
   int dyn_max = 0;
-  const int rc = cluster_dyn_max(&dyn_max);
+  const int rc = cluster_dyn_max(reinterpret_cast<const void*>(cluster_kernel<kMode>), &dyn_max);
   if (rc != ISING_OK) return rc;
   if (dyn_max < 0 || cluster_smem(probs[0]->n) > static_cast<size_t>(dyn_max)) return ISING_ERR_UNSUPPORTED;
   for (int q = 0; q < m; ++q) a->eflags[q] = probs[q]->d_eflags;
@@ -302,7 +295,7 @@ template <int kMode>
 int launch_clusters(ClusterArgs a, int32_t images, cudaStream_t st) {
   const int n = a.X * a.Y;
   int dyn_max = 0;
-  const int rc = cluster_dyn_max(&dyn_max);
+  const int rc = cluster_dyn_max(reinterpret_cast<const void*>(cluster_kernel<kMode>), &dyn_max);
   if (rc != ISING_OK) return rc;
   a.use_list = n < 65536 && dyn_max >= 0 && cluster_smem_list(n) <= static_cast<size_t>(dyn_max) ? 1 : 0;
   a.list_off = static_cast<uint32_t>(cluster_list_off(n));
@@ -322,7 +315,7 @@ namespace ising {
 int propose_clusters_launch(const ising_problem* const* probs, int32_t m, int8_t* spins, int32_t B,
                             const float* logits, int32_t* accepted, int accumulate, cudaStream_t st) {
   ClusterArgs a{};
-  const int rc = cluster_check(probs, m, B, &a);
+  const int rc = cluster_check<0>(probs, m, B, &a);
   if (rc != ISING_OK) return rc;
   if (B > 0 && (!spins || !logits)) return ISING_ERR_ARG;
   if (B == 0) return ISING_OK;
@@ -337,7 +330,7 @@ int propose_clusters_launch(const ising_problem* const* probs, int32_t m, int8_t
 int transcribe_launch(const ising_problem* const* probs, int32_t m, const int8_t* spins, int8_t* out, int32_t B,
                       int32_t shift, int32_t* accepted, int accumulate, cudaStream_t st) {
   ClusterArgs a{};
-  const int rc = cluster_check(probs, m, B, &a);
+  const int rc = cluster_check<2>(probs, m, B, &a);
   if (rc != ISING_OK) return rc;
   if (shift < 0 || (B > 0 && (!spins || !out || spins == out))) return ISING_ERR_ARG;
   if (B == 0) return ISING_OK;
@@ -361,7 +354,7 @@ extern "C" int ising_propose_clusters(const ising_problem* const* probs, int32_t
 extern "C" int ising_droplet_targets(const ising_problem* p, const int8_t* spins, const int8_t* ref, int32_t B,
                                      uint8_t* targets, void* cuda_stream) {
   ising::ClusterArgs a{};
-  const int rc = ising::cluster_check(&p, 1, B, &a);
+  const int rc = ising::cluster_check<1>(&p, 1, B, &a);
   if (rc != ISING_OK) return rc;
   if (B > 0 && (!spins || !ref || !targets)) return ISING_ERR_ARG;
   if (B == 0) return ISING_OK;
