@@ -38,6 +38,18 @@
  *     row-major [trials][n].  Cuts are int32 (|cut| <= |E| = 2n).
  *   - A problem handle is bound to the device that was current at creation;
  *     do not use one handle from two streams at the same time.
+ *   - CUDA graphs: ising_anneal, ising_anneal_trace, ising_anneal_batched,
+ *     ising_anneal_pt, ising_batch_create, ising_learned_create and
+ *     ising_get_status copy per-call tables from host memory or wait on the
+ *     stream, so they cannot be recorded into a graph: while `cuda_stream`
+ *     is capturing they return ISING_ERR_UNSUPPORTED before queuing
+ *     anything, and the capture stays valid.  For replayable work use
+ *     ising_batch_create / ising_learned_create (each one graph, created
+ *     outside any capture) or, after its first call, ising_anneal_noalloc.
+ *     Calls that only queue kernels on device memory may be captured:
+ *     ising_cut, ising_energy, ising_cnn_forward, ising_propose,
+ *     ising_propose_clusters, ising_droplet_targets and ising_transcribe
+ *     (the learned plan's graph records several of them).
  */
 #ifndef ISING_H
 #define ISING_H
@@ -111,8 +123,8 @@ void ising_destroy(ising_problem* p);
  * library's own per device, which keeps the memory it has held until the
  * process exits, so that a call after a synchronisation does not map its
  * scratch again.
- * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (no launch shape fits),
- * ISING_ERR_OOM, ISING_ERR_CUDA.
+ * Errors: ISING_ERR_ARG, ISING_ERR_UNSUPPORTED (no launch shape fits, or
+ * cuda_stream is capturing a graph), ISING_ERR_OOM, ISING_ERR_CUDA.
  */
 int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t S,
                  uint64_t seed, uint32_t sweep_offset, const int8_t* init_spins,

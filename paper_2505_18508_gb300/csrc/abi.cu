@@ -991,6 +991,7 @@ int ising_last_kernel(const ising_problem* p, int32_t* kind) {
 int ising_get_status(ising_problem* p, void* cuda_stream, int32_t* code) {
   if (!p || !code) return ISING_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (const int crc = ising::refuse_capture(st)) return crc;
   int32_t v = 0;
   cudaError_t e = cudaMemcpyAsync(&v, p->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1020,6 +1021,7 @@ int ising_anneal(ising_problem* p, int32_t trials, const double* betas, int32_t 
                  uint32_t sweep_offset, const int8_t* init_spins, int8_t* out_spins, int32_t* out_cuts,
                  void* cuda_stream) {
   if (!p || trials < 0 || S < 0 || (S > 0 && !betas)) return ISING_ERR_ARG;
+  if (const int crc = ising::refuse_capture(static_cast<cudaStream_t>(cuda_stream))) return crc;
   if (p->graph)
     return run_graph(p, trials, betas, S, seed, sweep_offset, init_spins, out_spins, out_cuts,
                      static_cast<cudaStream_t>(cuda_stream));
@@ -1098,6 +1100,7 @@ int ising_cut(const ising_problem* p, const int8_t* spins, int32_t k, int32_t* o
 int ising_anneal_batched(ising_problem* const* probs, int32_t m, const int32_t* trials, const int32_t* sweeps,
                          const double* const* betas, const uint64_t* seeds, int8_t* const* out_spins,
                          int32_t* const* out_cuts, void* cuda_stream) {
+  if (const int crc = ising::refuse_capture(static_cast<cudaStream_t>(cuda_stream))) return crc;
   HostBatch hb;
   try {
     const int rc = prepare_batch(probs, m, trials, sweeps, betas, seeds, out_spins, out_cuts, 0, 0, hb);
@@ -1150,6 +1153,7 @@ int ising_batch_create(ising_problem* const* probs, int32_t m, const int32_t* tr
                        int32_t* const* out_cuts, int32_t group_trials, int32_t ctas_per_sm, void* cuda_stream,
                        ising_batch** out) {
   if (!out) return ISING_ERR_ARG;
+  if (const int crc = ising::refuse_capture(static_cast<cudaStream_t>(cuda_stream))) return crc;
   HostBatch hb;
   try {
     const int rc = prepare_batch(probs, m, trials, sweeps, betas, seeds, out_spins, out_cuts, group_trials,
@@ -1228,6 +1232,7 @@ int ising_learned_create(ising_problem* const* probs, int32_t m, int32_t trials,
       k_first > S || every < 1 || partner_period < 0 || warm < 0 || warm > 1 || (warm && !net) || !spins || !cuts ||
       (net && (!logits || !ws)))
     return ISING_ERR_ARG;
+  if (const int crc = ising::refuse_capture(static_cast<cudaStream_t>(cuda_stream))) return crc;
   for (int32_t q = 0; q < m; ++q) {
     if (!probs[q]) return ISING_ERR_ARG;
     if (probs[q]->graph) return ISING_ERR_UNSUPPORTED;

@@ -100,6 +100,17 @@ size_t static_smem_of(const void* kernel) {
   return fa.sharedSizeBytes;
 }
 
+int refuse_capture(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    // the legacy stream while another stream captures in global mode
+    return e == cudaErrorStreamCaptureImplicit ? ISING_ERR_UNSUPPORTED : ISING_ERR_CUDA;
+  }
+  return cs == cudaStreamCaptureStatusNone ? ISING_OK : ISING_ERR_UNSUPPORTED;
+}
+
 int log_level() {
   static const int level = [] {
     const char* v = std::getenv("ISING_LOG");

@@ -56,6 +56,11 @@ int log_level();
 // against the per-block opt-in limit together with the dynamic size; 1 KiB
 // when the attributes cannot be read.
 size_t static_smem_of(const void* kernel);
+// Entry points that stage per-call tables from host memory (or wait on the
+// stream) cannot be recorded into a CUDA graph: ISING_ERR_UNSUPPORTED while
+// `st` is capturing, checked before anything is queued so that the caller's
+// capture stays valid; ISING_OK otherwise.
+int refuse_capture(cudaStream_t st);
 
 // Everything the strip kernel reads; passed by value as the kernel parameter.
 struct AnnealArgs {

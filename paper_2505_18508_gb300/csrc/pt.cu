@@ -77,6 +77,7 @@ extern "C" int ising_anneal_pt(ising_problem* p, int32_t temps, const double* be
       !out_spins || !out_cuts)
     return ISING_ERR_ARG;
   if (p->graph || p->draw_bits != 32) return ISING_ERR_UNSUPPORTED;
+  if (const int crc = ising::refuse_capture(static_cast<cudaStream_t>(cuda_stream))) return crc;
   for (int32_t r = 0; r < temps; ++r)
     if (!(betas[r] > 0.0) || !std::isfinite(betas[r])) return ISING_ERR_ARG;
   if (static_cast<int64_t>(temps) * chains > (int64_t(1) << 30)) return ISING_ERR_UNSUPPORTED;

@@ -53,8 +53,9 @@ extern "C" int ising_anneal_trace(ising_problem* p, int32_t trials, const double
     return ISING_ERR_ARG;
   for (int32_t k = 0; k < S; ++k)
     if (!(betas[k] > 0.0)) return ISING_ERR_ARG;
-  if (trials == 0) return ISING_OK;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (const int crc = ising::refuse_capture(st)) return crc;
+  if (trials == 0) return ISING_OK;
   const size_t spin_bytes = static_cast<size_t>(trials) * p->n;
   const int32_t points = (S + trace_every - 1) / trace_every;
 

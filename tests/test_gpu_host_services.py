@@ -89,3 +89,47 @@ def test_log_line(ia):
                        text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     assert "ising: anneal n=64 trials=32 sweeps=3 kernel=" in r.stderr
+
+
+def test_staging_calls_refuse_stream_capture(ia):
+    """The calls that copy per-call tables from host memory (or wait on the
+    stream) return ISING_ERR_UNSUPPORTED while the stream captures a graph,
+    before queuing anything: the capture stays valid, records the work around
+    them and replays it; outside the capture the same calls run exactly."""
+    import torch
+    X, Y, T, S = 16, 8, 40, 30
+    inst = synth.torus_instance(X, Y, 3)
+    prob = ia.Problem.from_instance(inst)
+    betas = synth.linear_betas(0.2, 2.0, S)
+    x = torch.zeros(4, device="cuda")
+    calls = {
+        "anneal": lambda: ia.anneal(prob, T, betas, 5),
+        "anneal_trace": lambda: ia.anneal_trace(prob, T, betas, 5, 10),
+        "anneal_batched": lambda: ia.anneal_batched([prob], [T], [S], [betas], [5]),
+        "batch_create": lambda: ia.BatchPlan([prob], [T], [S], [betas], [5]),
+        "anneal_pt": lambda: ia.anneal_pt(prob, betas[:2], 32, 2, 5, 5),
+        "learned_create": lambda: ia.LearnedPlan([prob], None, T, betas, [5], 20, every=5, partner_period=3),
+        "get_status": lambda: prob.get_status(),
+    }
+    codes = {}
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        x.add_(1.0)
+        for name, call in calls.items():
+            with pytest.raises(ia.IsingError) as e:
+                call()
+            codes[name] = e.value.code
+        x.add_(1.0)
+    assert codes == {name: -8 for name in calls}     # ISING_ERR_UNSUPPORTED
+    g.replay()
+    torch.cuda.synchronize()
+    assert x.tolist() == [2.0] * 4
+    spins, cuts = ia.anneal(prob, T, betas, 5)
+    torch.cuda.synchronize()
+    rs, rc = oracle.anneal(inst, betas, 5, t_begin=0, t_count=T)
+    np.testing.assert_array_equal(spins.cpu().numpy(), rs)
+    np.testing.assert_array_equal(cuts.cpu().numpy(), rc)
+    assert prob.get_status() == 0
+    del g
+    prob.destroy()
