@@ -2,7 +2,10 @@
 
 Every step of the annealing path runs in the CUDA kernels of libising.so;
 this module only marshals arguments.  PyTorch provides device memory and the
-current CUDA stream.
+current CUDA stream.  Output tensors (and contiguous copies of inputs) are
+allocated on the current stream; a caller that passes another `stream`
+orders the two streams itself (for example with `stream.wait_stream`) and
+keeps the tensors alive until that stream's work is done.
 
     import paper_2505_18508_gb300 as ia
     prob = ia.Problem.from_csr(n, row_ptr, col, J, X, Y)
