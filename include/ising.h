@@ -47,9 +47,9 @@
  *     ising_batch_create / ising_learned_create (each one graph, created
  *     outside any capture) or, after its first call, ising_anneal_noalloc.
  *     Calls that only queue kernels on device memory may be captured:
- *     ising_cut, ising_energy, ising_cnn_forward, ising_propose,
- *     ising_propose_clusters, ising_droplet_targets and ising_transcribe
- *     (the learned plan's graph records several of them).
+ *     ising_cut, ising_cnn_forward, ising_propose, ising_propose_clusters,
+ *     ising_droplet_targets and ising_transcribe (the learned plan's graph
+ *     records the same launches).
  */
 #ifndef ISING_H
 #define ISING_H
