@@ -21,7 +21,10 @@
 //   store.  A reader loads the 8 bytes of each word it needs and uses them
 //   once the tag is the half-sweep it waits for; no fence and no counter is
 //   needed on either side (a writer cannot get a half-sweep ahead of a
-//   reader of the same word, since its next update needs the reader's).
+//   reader of the same word, since its next update needs the reader's; the
+//   readers of a word are its neighbours, and each stored word is computed
+//   from the loads before it, so the PTX model's no-thin-air rule excludes a
+//   load that sees the writer's next value).
 //   Published rows come first in each half-sweep, so their words are usually
 //   there long before anyone reads them.
 //
