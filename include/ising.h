@@ -158,6 +158,10 @@ int ising_cut(const ising_problem* p, const int8_t* spins, int32_t k,
  * Scratch: descriptors, work list and thresholds in one stream-ordered
  * allocation from the library's pool (as ising_anneal), freed in stream
  * order.
+ * Errors: ISING_ERR_ARG (NULL arrays, negative counts, a beta <= 0 or NaN,
+ * handles on different devices), ISING_ERR_UNSUPPORTED (a general-graph
+ * handle, a torus too large for one CTA's shared memory, or cuda_stream
+ * capturing a graph), ISING_ERR_OOM, ISING_ERR_CUDA.
  */
 int ising_anneal_batched(ising_problem* const* probs, int32_t m, const int32_t* trials,
                          const int32_t* sweeps, const double* const* betas,
@@ -172,6 +176,8 @@ int ising_anneal_batched(ising_problem* const* probs, int32_t m, const int32_t* 
  * kernel) on the given stream.  The output pointers are baked into the plan.
  * group_trials (4..32, multiple of 4, or 0 = auto) and ctas_per_sm (1..4, or
  * 0 = auto) set the work-unit width and the persistent grid.
+ * ising_batch_create errors: those of ising_anneal_batched, and
+ * ISING_ERR_ARG for a NULL `out` or group_trials / ctas_per_sm out of range.
  */
 typedef struct ising_batch ising_batch;
 int ising_batch_create(ising_problem* const* probs, int32_t m, const int32_t* trials,
@@ -201,7 +207,7 @@ void ising_batch_destroy(ising_batch* b);
 int ising_set_launch(ising_problem* p, int32_t group_trials, int32_t strips, int32_t threads);
 
 /* ising_last_launch -- the shape the last ising_anneal call on this handle
- * used (any pointer may be NULL). */
+ * used (any pointer may be NULL).  Errors: ISING_ERR_ARG (NULL handle). */
 int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* strips,
                       int32_t* threads, int32_t* grid_ctas);
 
@@ -376,12 +382,13 @@ int ising_graph_create(int32_t n, const int64_t* row_ptr, const int32_t* col_idx
  * ising_greedy_colouring -- the colouring the general-graph sweep uses
  * (host only, no GPU): site i takes the smallest colour no neighbour j < i
  * holds.  colour: int32 [n] (host, caller-owned); *ncol: classes used.
+ * Errors: ISING_ERR_ARG (n < 0 or a NULL pointer), ISING_ERR_OOM.
  */
 int ising_greedy_colouring(int32_t n, const int64_t* row_ptr, const int32_t* col_idx, int32_t* colour,
                            int32_t* ncol);
 
 /* ising_graph_info -- n, colour classes and the largest sum |J| + |h| of a
- * general-graph handle (ISING_ERR_ARG for a torus handle). */
+ * general-graph handle.  Errors: ISING_ERR_ARG (NULL or torus handle). */
 int ising_graph_info(const ising_problem* p, int32_t* n, int32_t* ncol, int32_t* Dmax);
 
 /*
@@ -435,7 +442,8 @@ int ising_anneal_trace(ising_problem* p, int32_t trials, const double* betas, in
  */
 int ising_set_draw_bits(ising_problem* p, int32_t bits);
 
-/* ising_last_kernel -- the kernel (1 or 2) the last ising_anneal call used. */
+/* ising_last_kernel -- the kernel (1 or 2) the last ising_anneal call used.
+ * Errors: ISING_ERR_ARG (NULL pointer). */
 int ising_last_kernel(const ising_problem* p, int32_t* kind);
 
 /*
@@ -443,6 +451,8 @@ int ising_last_kernel(const ising_problem* p, int32_t* kind);
  * device status word.  *code is ISING_OK, or ISING_ERR_TIMEOUT when a bounded
  * device-side wait of the persistent kernel ran out (the results of that call
  * are then undefined; the CUDA context stays usable).
+ * Errors: ISING_ERR_ARG (NULL pointer), ISING_ERR_UNSUPPORTED (cuda_stream
+ * capturing a graph), ISING_ERR_CUDA.
  */
 int ising_get_status(ising_problem* p, void* cuda_stream, int32_t* code);
 
@@ -456,7 +466,8 @@ int ising_get_status(ising_problem* p, void* cuda_stream, int32_t* code);
 int ising_set_wait_limit(ising_problem* p, int64_t cycles, int32_t stall_test);
 
 /* ising_problem_info -- X, Y and W = sum of the weights over the 2n edges
- * (so that H = W - 2 cut); any pointer may be NULL. */
+ * (so that H = W - 2 cut); any pointer may be NULL.  Errors: ISING_ERR_ARG
+ * (NULL handle). */
 int ising_problem_info(const ising_problem* p, int32_t* X, int32_t* Y, int32_t* weight_sum);
 
 /*
@@ -515,9 +526,11 @@ int ising_cnn_create(const float* params, ising_cnn** out);
 /* ising_cnn_destroy -- free the network's device memory (NULL is a no-op);
  * the caller must not destroy it while work that uses it is still queued. */
 void ising_cnn_destroy(ising_cnn* net);
-/* host copy of the FP32 master parameters */
+/* host copy of the FP32 master parameters (synchronous).  Errors:
+ * ISING_ERR_ARG (NULL pointer), ISING_ERR_CUDA. */
 int ising_cnn_get_params(const ising_cnn* net, float* params);
-/* replace the parameters (host) and reset the Adam state */
+/* replace the parameters (host) and reset the Adam state (synchronous).
+ * Errors: ISING_ERR_ARG (NULL pointer), ISING_ERR_CUDA. */
 int ising_cnn_set_params(ising_cnn* net, const float* params);
 
 /* Device workspace (bytes) for B configurations of n spins; train != 0 for
@@ -567,7 +580,10 @@ int ising_cnn_grad(const ising_cnn* net, const ising_problem* p, const int8_t* s
 int ising_cnn_set_wait_limit(ising_cnn* net, int64_t cycles, int32_t stall_test);
 
 /* ising_cnn_adam_step -- one Adam update of the FP32 master parameters with
- * the device gradient `grad`, then refresh the BF16 copies. */
+ * the device gradient `grad`, then refresh the BF16 copies.  The bias
+ * corrections use the step count kept on the host, so a captured step would
+ * replay with stale ones.  Errors: ISING_ERR_ARG (NULL pointer, lr < 0,
+ * beta1 or beta2 outside [0, 1), eps <= 0), ISING_ERR_CUDA. */
 int ising_cnn_adam_step(ising_cnn* net, const float* grad, float lr, float beta1, float beta2, float eps,
                         void* cuda_stream);
 
@@ -603,7 +619,8 @@ int ising_propose(const ising_problem* p, int8_t* spins, int32_t B, const float*
  * accepted device [m * B] int32 or NULL: components flipped per configuration.
  * One CTA per configuration with all of its state in shared memory (9 bytes
  * per site): ISING_ERR_UNSUPPORTED above that (about 25,000 sites) and for
- * general-graph handles; ISING_ERR_ARG for mixed shapes or bad pointers.
+ * general-graph handles; ISING_ERR_ARG for mixed shapes or bad pointers;
+ * ISING_ERR_CUDA when the launch fails.
  */
 int ising_propose_clusters(const ising_problem* const* probs, int32_t m, int8_t* spins, int32_t B,
                            const float* logits, int32_t* accepted, void* cuda_stream);
@@ -679,9 +696,10 @@ int ising_transcribe(const ising_problem* const* probs, int32_t m, const int8_t*
  * with partner moves, a second state buffer), copies the thresholds and
  * synchronises cuda_stream.  launch enqueues the graph on cuda_stream.
  * Errors: ISING_ERR_ARG (bad pointers or sizes, mixed shapes, warm start
- * without a network), ISING_ERR_UNSUPPORTED (a general-graph handle, or an
+ * without a network), ISING_ERR_UNSUPPORTED (a general-graph handle, an
  * instance the batched launch, the network or the cluster kernel cannot
- * take), ISING_ERR_OOM, ISING_ERR_CUDA.
+ * take, or cuda_stream capturing a graph), ISING_ERR_OOM, ISING_ERR_CUDA;
+ * ising_learned_launch: ISING_ERR_ARG (NULL plan), ISING_ERR_CUDA.
  */
 typedef struct ising_learned ising_learned;
 int ising_learned_create(ising_problem* const* probs, int32_t m, int32_t trials, const double* betas, int32_t S,
@@ -697,6 +715,8 @@ void ising_learned_destroy(ising_learned* plan);
  * closer to s in Hamming distance (on a tie, the one that keeps site 0); the
  * global flip s -> -s is a symmetry of H, so only the relative orientation
  * is meaningful.  spins, ref: device [B][n] int8; targets: device [B][n] uint8.
+ * Errors: ISING_ERR_ARG (B < 0, n <= 0, a NULL pointer with B > 0),
+ * ISING_ERR_CUDA.
  */
 int ising_flip_targets(const int8_t* spins, const int8_t* ref, int32_t B, int32_t n, uint8_t* targets,
                        void* cuda_stream);
