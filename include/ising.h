@@ -618,9 +618,9 @@ int ising_propose(const ising_problem* p, int8_t* spins, int32_t B, const float*
  * logits   device [m * B][n] float.
  * accepted device [m * B] int32 or NULL: components flipped per configuration.
  * One CTA per configuration with all of its state in shared memory (9 bytes
- * per site): ISING_ERR_UNSUPPORTED above that (about 25,000 sites) and for
- * general-graph handles; ISING_ERR_ARG for mixed shapes or bad pointers;
- * ISING_ERR_CUDA when the launch fails.
+ * per site).  Errors: ISING_ERR_UNSUPPORTED above that (about 25,000 sites)
+ * and for general-graph handles; ISING_ERR_ARG for mixed shapes or bad
+ * pointers; ISING_ERR_CUDA when the launch fails.
  */
 int ising_propose_clusters(const ising_problem* const* probs, int32_t m, int8_t* spins, int32_t B,
                            const float* logits, int32_t* accepted, void* cuda_stream);

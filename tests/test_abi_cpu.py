@@ -119,3 +119,24 @@ def test_synthetic_instances_are_tori():
     assert len(cfg) == 96 and {c["X"] for c in cfg} == {50, 100, 140, 200}
     assert min(c["trials"] for c in cfg) == 32 and max(c["trials"] for c in cfg) == 512
     assert min(c["sweeps"] for c in cfg) >= 2000 and max(c["sweeps"] for c in cfg) <= 20000
+
+
+def test_every_status_returning_entry_point_documents_its_errors():
+    """Each int-returning declaration of include/ising.h is preceded by a
+    comment that states its error codes (a declaration directly after another
+    shares that one's comment)."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ising.h")
+    src = open(path).read()
+    decls = list(re.finditer(r"\n(int|void|const char\*|size_t)\s+(ising_\w+)\(", src))
+    missing, prev_end, prev_comment = [], 0, ""
+    for m in decls:
+        between = src[prev_end:m.start()]
+        start = between.rfind("/*")
+        comment = between[start:] if start >= 0 else prev_comment
+        if m.group(1) == "int" and "rrors" not in comment:
+            missing.append(m.group(2))
+        prev_end, prev_comment = m.end(), comment
+    assert len(decls) >= 40
+    assert not missing, missing
