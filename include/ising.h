@@ -169,7 +169,8 @@ int ising_anneal_batched(ising_problem* const* probs, int32_t m, const int32_t* 
                          int32_t* const* out_cuts, void* cuda_stream);
 
 /*
- * Batch plans: the same work as ising_anneal_batched, prepared once (tables
+ * Batch plans: the same work as ising_anneal_batched (Section III campaigns
+ * as one batch), prepared once (tables
  * uploaded, work list sorted longest first) and replayed as a CUDA graph.
  * ising_batch_create queues the uploads on `cuda_stream`; every
  * ising_batch_launch replays the graph (reset the work counter, persistent
@@ -380,7 +381,8 @@ int ising_graph_create(int32_t n, const int64_t* row_ptr, const int32_t* col_idx
 
 /*
  * ising_greedy_colouring -- the colouring the general-graph sweep uses
- * (host only, no GPU): site i takes the smallest colour no neighbour j < i
+ * (Eq. 2 with general J and h; a checkerboard needs a proper colouring; host
+ * only, no GPU): site i takes the smallest colour no neighbour j < i
  * holds.  colour: int32 [n] (host, caller-owned); *ncol: classes used.
  * Errors: ISING_ERR_ARG (n < 0 or a NULL pointer), ISING_ERR_OOM.
  */
@@ -457,7 +459,8 @@ int ising_last_kernel(const ising_problem* p, int32_t* kind);
 int ising_get_status(ising_problem* p, void* cuda_stream, int32_t* code);
 
 /*
- * ising_set_wait_limit -- cycles one device-side wait of the persistent kernel
+ * ising_set_wait_limit -- (this project's failure detection; the paper has no
+ * counterpart) cycles one device-side wait of the persistent kernel
  * may take before it gives up (0 restores the default of 4e9 cycles), and a
  * test switch: stall_test = 1 makes the first chunk of the first CTA wait for
  * a count that is never reached, so the limit runs out on purpose.
@@ -538,7 +541,8 @@ int ising_cnn_set_params(ising_cnn* net, const float* params);
 size_t ising_cnn_workspace_bytes(int32_t B, int32_t n, int32_t train);
 
 /*
- * ising_cnn_forward -- logits for B configurations of problem p.
+ * ising_cnn_forward -- logits for B configurations of problem p (learned
+ * stage, this project's extension; the network is the one defined above).
  * spins    device [B][n] int8 (>0 is +1).
  * logits   device [B][n] float (site order y*X + x).
  * ws       device workspace of at least ising_cnn_workspace_bytes(B, n, 0).
@@ -552,7 +556,8 @@ int ising_cnn_forward(const ising_cnn* net, const ising_problem* p, const int8_t
                       float* logits, void* ws, size_t ws_bytes, void* cuda_stream);
 
 /*
- * ising_cnn_grad -- mean binary cross-entropy of the logits against the flip
+ * ising_cnn_grad -- (learned stage, this project's extension) mean binary
+ * cross-entropy of the logits against the flip
  * targets and its gradient with respect to the parameters.
  * targets  device [B][n] uint8 (1 = the site should flip).
  * grad     device ISING_CNN_PARAMS floats (overwritten).
@@ -588,8 +593,8 @@ int ising_cnn_adam_step(ising_cnn* net, const float* grad, float lr, float beta1
                         void* cuda_stream);
 
 /*
- * ising_propose -- apply proposals built from the logits, each accepted iff
- * its exact energy change dE = -2 sum_{i in B, j ~ i, j not in B} w_ij s_i s_j
+ * ising_propose -- (learned stage, this project's extension) apply proposals
+ * built from the logits, each accepted iff its exact Eq. 2 energy change dE = -2 sum_{i in B, j ~ i, j not in B} w_ij s_i s_j
  * is <= 0.
  * tile > 0: B = sites with logit > 0 in each tile of side `tile`; tiles with
  *   even (tx + ty) first, then odd.  The number of tiles along each side must
@@ -626,7 +631,8 @@ int ising_propose_clusters(const ising_problem* const* probs, int32_t m, int8_t*
                            const float* logits, int32_t* accepted, void* cuda_stream);
 
 /*
- * ising_droplet_targets -- training targets of the cluster proposals: with
+ * ising_droplet_targets -- (learned stage, this project's extension; dE from
+ * Eq. 2) training targets of the cluster proposals: with
  * r' = ref or -ref gauge-aligned to s (as ising_flip_targets), the sites
  * where s and r' differ split into connected components on the torus;
  * targets_i = 1 iff i lies in a component whose flip alone lowers the energy
@@ -710,7 +716,9 @@ int ising_learned_launch(ising_learned* plan, void* cuda_stream);
 void ising_learned_destroy(ising_learned* plan);
 
 /*
- * ising_flip_targets -- training targets for the network: for each of B
+ * ising_flip_targets -- (learned stage, this project's extension; the global
+ * flip symmetry follows from Eq. 2 with h = 0) training targets for the
+ * network: for each of B
  * configurations, y_i = [s_i != r'_i] where r' is ref or -ref, whichever is
  * closer to s in Hamming distance (on a tie, the one that keeps site 0); the
  * global flip s -> -s is a symmetry of H, so only the relative orientation
