@@ -220,10 +220,10 @@ int ising_last_launch(const ising_problem* p, int32_t* group_trials, int32_t* st
  *   1 strip kernel: each trial group annealed by a thread-block cluster of
  *     row strips (ising_set_launch sets its shape);
  *   2 persistent kernel: the rows of all trial groups stacked and split over
- *     one CTA per SM, rows shared between CTAs exchanged through L2 with
- *     per-row completion counters; ISING_ERR_UNSUPPORTED from ising_anneal if
- *     a CTA would touch more than 4 trial groups or its rows do not fit in
- *     shared memory.
+ *     one CTA per SM, the rows another CTA reads exchanged through an L2
+ *     mirror of words tagged with their half-sweep; ISING_ERR_UNSUPPORTED
+ *     from ising_anneal if a CTA would touch more than 4 trial groups or its
+ *     rows do not fit in shared memory.
  * Results do not depend on the kernel.  Errors: ISING_ERR_ARG.
  */
 int ising_set_kernel(ising_problem* p, int32_t kind);
@@ -396,7 +396,8 @@ int ising_graph_info(const ising_problem* p, int32_t* n, int32_t* ncol, int32_t*
 /*
  * ising_energy -- Eq. 2 of k configurations (device int8 [k][n]) into
  * out_energies (device int64 [k]); asynchronous on cuda_stream.  For a torus
- * handle H = W - 2 cut.  Errors: ISING_ERR_ARG, ISING_ERR_CUDA.
+ * handle H = W - 2 cut, through a k-int32 cut buffer allocated in stream
+ * order.  Errors: ISING_ERR_ARG, ISING_ERR_OOM, ISING_ERR_CUDA.
  */
 int ising_energy(const ising_problem* p, const int8_t* spins, int32_t k, int64_t* out_energies, void* cuda_stream);
 
