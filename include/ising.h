@@ -495,11 +495,14 @@ int ising_problem_info(const ising_problem* p, int32_t* X, int32_t* Y, int32_t* 
  * last call's contents: calls whose work overlaps on the GPU (unordered
  * streams) race on it.  Nothing in the array needs to start at zero.
  *
- * Errors: those of ising_anneal, with three differences:
+ * Errors: those of ising_anneal, with four differences:
  *   ISING_ERR_UNSUPPORTED  S > 32,768, or a general-graph handle
  *                          (ising_graph_create), which ising_anneal accepts;
- *   ISING_ERR_ARG          the current device is not the problem's device.
- * Each is returned before anything is queued.  The launch this call used is
+ *   ISING_ERR_ARG          the current device is not the problem's device;
+ *   a capturing cuda_stream is not refused: after the first call on a
+ *   device, the call queues only kernels and may be recorded into a graph
+ *   (the table's words travel in the recorded kernel parameters).
+ * Each error is returned before anything is queued.  The launch this call used is
  * what ising_last_launch and ising_last_kernel then report.
  */
 int ising_anneal_noalloc(ising_problem* p, int32_t trials, const double* betas, int32_t S,
