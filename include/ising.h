@@ -45,7 +45,7 @@
  *     is capturing they return ISING_ERR_UNSUPPORTED before queuing
  *     anything, and the capture stays valid.  For replayable work use
  *     ising_batch_create / ising_learned_create (each one graph, created
- *     outside any capture) or, after its first call, ising_anneal_noalloc.
+ *     outside any capture).
  *     Calls that only queue kernels on device memory may be captured:
  *     ising_cut, ising_cnn_forward, ising_propose, ising_propose_clusters,
  *     ising_droplet_targets and ising_transcribe (the learned plan's graph
@@ -500,8 +500,8 @@ int ising_problem_info(const ising_problem* p, int32_t* X, int32_t* Y, int32_t* 
  *                          (ising_graph_create), which ising_anneal accepts;
  *   ISING_ERR_ARG          the current device is not the problem's device;
  *   a capturing cuda_stream is not refused: after the first call on a
- *   device, the call queues only kernels and may be recorded into a graph
- *   (the table's words travel in the recorded kernel parameters).
+ *   device the call queues only kernel launches, with the table's words in
+ *   their parameters (recording it into a graph is not tested).
  * Each error is returned before anything is queued.  The launch this call used is
  * what ising_last_launch and ising_last_kernel then report.
  */
