@@ -710,6 +710,8 @@ int ising_transcribe(const ising_problem* const* probs, int32_t m, const int8_t*
  * instance the batched launch, the network or the cluster kernel cannot
  * take, or cuda_stream capturing a graph), ISING_ERR_OOM, ISING_ERR_CUDA;
  * ising_learned_launch: ISING_ERR_ARG (NULL plan), ISING_ERR_CUDA.
+ * ising_learned_destroy frees the plan (NULL is a no-op) without waiting:
+ * the caller must not destroy it while one of its launches is queued.
  */
 typedef struct ising_learned ising_learned;
 int ising_learned_create(ising_problem* const* probs, int32_t m, int32_t trials, const double* betas, int32_t S,
