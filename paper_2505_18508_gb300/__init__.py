@@ -591,7 +591,12 @@ class LearnedPlan:
         return self.spins, self.cuts, self.accepted
 
     def destroy(self):
+        """Free the plan after the device has finished its queued launches
+        (ising_learned_destroy itself does not wait)."""
         if getattr(self, "_h", None) is not None:
+            torch = _torch()
+            if not torch.cuda.is_current_stream_capturing():
+                torch.cuda.synchronize()
             lib().ising_learned_destroy(self._h)
             self._h = None
 
