@@ -140,3 +140,36 @@ def test_every_status_returning_entry_point_documents_its_errors():
         prev_end, prev_comment = m.end(), comment
     assert len(decls) >= 40
     assert not missing, missing
+
+
+def test_binding_signatures_match_the_header():
+    """Every parameter of every declaration in include/ising.h has the width
+    the ctypes table passes (pointers as pointers, int32_t as a 32-bit int,
+    uint64_t as a 64-bit unsigned, size_t, float), and the return types agree."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ising.h")
+    src = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+    scalar = {"int32_t": ctypes.c_int32, "uint32_t": ctypes.c_uint32, "int64_t": ctypes.c_int64,
+              "uint64_t": ctypes.c_uint64, "size_t": ctypes.c_size_t, "float": ctypes.c_float, "int": ctypes.c_int,
+              "double": ctypes.c_double}
+    rets = {"int": ctypes.c_int, "void": None, "size_t": ctypes.c_size_t, "const char*": ctypes.c_char_p}
+    seen = 0
+    for m in re.finditer(r"\n(int|void|const char\*|size_t)\s+(ising_\w+)\(([^)]*)\);", src):
+        ret, name, params = m.group(1), m.group(2), " ".join(m.group(3).split())
+        want_ret, argtypes = _abi._SIGNATURES[name]
+        assert want_ret is rets[ret], name
+        params = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+        assert len(params) == len(argtypes), (name, params)
+        for p, t in zip(params, argtypes):
+            ctype = re.sub(r"\s*\b\w+$", "", p) if not p.endswith("*") else p
+            if "*" in ctype:
+                ok = t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer)
+                if t is ctypes.c_char_p:
+                    ok = ok and "char" in ctype
+                assert ok, (name, p, t)
+            else:
+                base = ctype.replace("const ", "").strip()
+                assert t is scalar[base], (name, p, t)
+        seen += 1
+    assert seen == len(_abi._SIGNATURES)
